@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput of the flat-layer reconstruction (Algorithm 2) on one GB300.
+
+Workload: single frequency k0 = 8 pi, X grid 128 x 128 x 64 in [-1,1]^2 x [0.2,1.0],
+32 data planes in [1.2, 1.6], xi = 3 seeded Gaussian inclusions (widths 0.05-0.2,
+peaks +-0.1), 1% noise.  Data W are made on the device by the library's own
+single-scattering forward kernel (synthetic; no dataset).
+
+A step = one full reconstruction W -> (xi, c): 2D FFT of the data planes, mode
+norms, discrepancy classification, per-mode Tikhonov solve + eq. (9), inverse FFTs
+and the pointwise xi/c recovery, replayed as one CUDA graph.  The headline is the
+mixed-precision path; the plain FP64 path is measured in the same run.  L2 is
+flushed (256 MiB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU FP64 oracle on the same workload (a band of the
+wavenumber rows per step, scaled to the metric).  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ξ voxel·frequencies/s: mixed/batched vs plain FP64 path at stated error vs oracle"
+UNIT = "voxel*freq/s"
+WORKLOAD = "c2"
+DELTA = 0.01
+FLUSH_BYTES = 256 << 20
+STAGES = ("fft_x_forward", "fft_y_forward_norms", "classify", "solve", "ifft_y_gather", "ifft_x_recover")
+KERNELS_PER_STEP = 7  # rows FFT, columns FFT, mode norms, classify, solve, gather+y-IFFT, x-IFFT+recover
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_inputs(rc, wl, geom):
+    """Noisy data W (complex128, device): library forward kernel + seeded noise."""
+    import torch
+    xi = torch.from_numpy(np.ascontiguousarray(wl.xi)).to(rc.device)
+    W = rc.forward_born(xi, list(wl.omegas), geom, precision="fp64")
+    n = torch.from_numpy(wl.noise()).to(rc.device)
+    for j in range(W.shape[0]):
+        W[j] += DELTA * torch.linalg.vector_norm(W[j]) * n[j] / torch.linalg.vector_norm(n[j])
+    torch.cuda.synchronize()
+    return W
+
+
+def algorithmic_bytes(stage, wl, rep, sc):
+    """Bytes a stage must move at minimum (one launch), sc = bytes per complex."""
+    F, N2, M, M1 = len(wl.omegas), wl.n * wl.n, wl.m, wl.m1
+    sr = sc // 2
+    act, cols = rep["n_active"], rep["n_columns"]
+    data = F * M1 * N2 * sc
+    if stage == "fft_x_forward":
+        return 2 * data
+    if stage == "fft_y_forward_norms":
+        return 2 * data + data + 8 * F * N2
+    if stage == "classify":
+        return 8 * F * N2 + 4 * F * N2 + 4 * act
+    if stage == "solve":
+        return act * (M1 + 2 * M) * sc
+    if stage == "ifft_y_gather":
+        return 4 * F * N2 + act * 2 * M * sc + 2 * M * wl.n * cols * sc
+    if stage == "ifft_x_recover":
+        return 2 * M * wl.n * cols * sc + 2 * M * N2 * sr
+    raise KeyError(stage)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1911_10487_gb300 import Geometry, Reconstructor, fs_reconstruct_host, FS_MIXED, build
+    from synth import workload
+    build.build()
+    wl = workload(WORKLOAD)
+    geom = Geometry(wl.n, wl.m, wl.z1, wl.z2, tuple(wl.zy))
+    om = [float(x) for x in wl.omegas]
+    stream = torch.cuda.Stream()
+    rc = Reconstructor(local, stream=stream)
+    with torch.cuda.stream(stream):
+        W64 = make_inputs(rc, wl, geom)
+        W32 = W64.to(torch.complex64)
+    torch.cuda.synchronize()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=rc.device)
+    outs = {}
+    graphs = {}
+    cases = (("mixed", W32, torch.float32), ("fp64", W64, torch.float64))
+    for prec, W, rdt in cases[::-1]:  # size the workspace (largest first) before any capture
+        xi = torch.empty((wl.m, wl.n, wl.n), dtype=rdt, device=rc.device)
+        outs[prec] = (xi, torch.empty_like(xi))
+        with torch.cuda.stream(stream):
+            rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, outs[prec][1], None))
+        torch.cuda.synchronize()
+    for prec, W, rdt in cases:
+        xi, c = outs[prec]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, c, None))
+        torch.cuda.synchronize()
+        graphs[prec] = g
+
+    def timed(prec, K, Wm, clocks=None):
+        g = graphs[prec]
+        with torch.cuda.stream(stream):
+            for _ in range(Wm):
+                flush.zero_()
+                g.replay()
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if clocks:
+            clocks.start()
+        with torch.cuda.stream(stream):
+            for s, e in ev:
+                flush.zero_()
+                s.record(stream)
+                g.replay()
+                e.record(stream)
+        torch.cuda.synchronize()
+        if clocks:
+            ck = clocks.stop()
+        barrier(world)
+        torch.cuda.synchronize()
+        ms = sum(s.elapsed_time(e) for s, e in ev) / K
+        return ms, (ck if clocks else None)
+
+    clocks = Clocks(local)
+    ms_mixed, ck = timed("mixed", args.steps, args.warmup, clocks)
+    ms_fp64, _ = timed("fp64", args.steps, args.warmup)
+    ms_mixed = max_over_ranks(ms_mixed, world)
+    ms_fp64 = max_over_ranks(ms_fp64, world)
+    vox = wl.voxel_freqs
+    value = world * vox / (ms_mixed * 1e-3)
+    value_fp64 = world * vox / (ms_fp64 * 1e-3)
+
+    # per-kernel durations (CUDA events recorded by the library between its kernels)
+    stage_ms = {}
+    reps = {}
+    for prec, W in (("mixed", W32), ("fp64", W64)):
+        xi, c = outs[prec]
+        acc = np.zeros(6)
+        n = max(3, min(args.steps, 20))
+        for _ in range(n):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, c, None), stage_timing=1)
+            rep = rc.report()
+            acc += np.array([rep["ms_stage"][s] for s in STAGES])
+        stage_ms[prec] = dict(zip(STAGES, (acc / n).tolist()))
+        reps[prec] = rep
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    W_h = W32.cpu().pin_memory()
+    xi_h = torch.empty((wl.m, wl.n, wl.n), dtype=torch.float32).pin_memory()
+    c_h = torch.empty_like(xi_h).pin_memory()
+    gstruct = geom.c_struct()
+
+    def e2e_once():
+        fs_reconstruct_host(rc.ctx, gstruct, FS_MIXED, W_h.data_ptr(), om, DELTA, 1.0, None, xi_h.data_ptr(),
+                            c_h.data_ptr())
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        e2e_once()
+    tot = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_once()
+        tot += time.perf_counter() - t0
+    e2e_ms = max_over_ranks(1e3 * tot / args.steps, world)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "128x128x64 X grid, 32 data planes, k0=8pi, 3 Gaussian inclusions, 1% noise",
+                   "n": wl.n, "m": wl.m, "m1": wl.m1, "n_omega": len(om), "delta": DELTA,
+                   "precision": "mixed (FP32 FFT/assembly/reduction, FP64 root-find + refinement)",
+                   "cuda_graph": True, "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "fp64_path": {"value": value_fp64, "ms_per_step": ms_fp64, "dtype": "f64"},
+        "stage_ms": stage_ms,
+        "e2e": {"value": world * vox / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(W_h.numel() * 8), "d2h_bytes_per_step": int(2 * xi_h.numel() * 4)},
+        "clocks": ck,
+    }
+    # roofline of the dominant kernel of the headline (mixed) path
+    hbm, src = peaks()
+    sm = stage_ms["mixed"]
+    dom = max(sm, key=sm.get)
+    byt = algorithmic_bytes(dom, wl, reps["mixed"], 8)
+    ach = byt / (sm[dom] * 1e-3) / 1e9
+    result["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                          "frac": ach / hbm, "traffic": None, "peak_source": src,
+                          "algorithmic_bytes": byt}
+    result["counts"] = {k: v for k, v in reps["mixed"].items() if k != "ms_stage"}
+    return result, rc, wl, geom, om, W64, outs
+
+
+def cpu_baseline(wl, W_np, om, rows=None):
+    from oracle import inverse
+    from oracle.grid import Geometry as OG
+    g = OG(wl.n, wl.m, wl.z1, wl.z2, tuple(wl.zy))
+    opts = inverse.Options(mode_rows=rows)
+    t0 = time.perf_counter()
+    res = inverse.reconstruct(W_np, om, g, DELTA, opts=opts)
+    return time.perf_counter() - t0, res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    result, rc, wl, geom, om, W64, outs = run_ours(args, rank, world, local)
+    if rank == 0:
+        import torch
+        W_np = W64.cpu().numpy()
+        if not args.no_cpu_baseline:
+            t, ref = cpu_baseline(wl, W_np, om)
+            from oracle.metrics import rel_l2
+            result["cpu_baseline"] = {"value": wl.voxel_freqs / t, "unit": UNIT, "cores": os.cpu_count(),
+                                      "kind": "oracle",
+                                      "sample": "one full reconstruction of the workload (NumPy/SciPy FP64)"}
+            result["rel_err_vs_oracle"] = {
+                "mixed": rel_l2(outs["mixed"][0].double().cpu().numpy(), ref.xi),
+                "fp64": rel_l2(outs["fp64"][0].cpu().numpy(), ref.xi)}
+        print(json.dumps(result))
+    rc.close()
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: rank 0 only, on host cores."""
+    if rank != 0:
+        return
+    import torch
+    from paper_1911_10487_gb300 import Geometry, Reconstructor
+    from synth import workload
+    wl = workload(WORKLOAD)
+    geom = Geometry(wl.n, wl.m, wl.z1, wl.z2, tuple(wl.zy))
+    om = [float(x) for x in wl.omegas]
+    rc = Reconstructor(0)
+    W_np = make_inputs(rc, wl, geom).cpu().numpy()
+    rc.close()
+    band = 8  # wavenumber rows per step: 1/16 of the per-mode work of the workload
+    frac = band / wl.n
+    for i in range(args.warmup):
+        cpu_baseline(wl, W_np, om, rows=(0, band))
+    tot = 0.0
+    for i in range(args.steps):
+        r0 = (i * band) % wl.n
+        t, _ = cpu_baseline(wl, W_np, om, rows=(r0, r0 + band))
+        tot += t
+    ms = 1e3 * tot / args.steps
+    value = frac * wl.voxel_freqs / (ms * 1e-3)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": "128x128x64 X grid, 32 data planes, k0=8pi, 3 Gaussian inclusions, 1% noise",
+                      "n": wl.n, "m": wl.m, "m1": wl.m1, "n_omega": len(om), "delta": DELTA},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"per step: full FFTs + the per-mode solve of {band} of {wl.n} "
+                                      f"wavenumber rows; metric scaled by {frac:.4f}"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

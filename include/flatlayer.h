@@ -1,0 +1,179 @@
+/*
+ * flatlayer.h -- C ABI of the GB300 (sm_103a) implementation of the flat-layer
+ * inverse multi-frequency scalar acoustics algorithm of Bakushinsky & Leonov
+ * (arXiv 1911.10487): Algorithm 2 of Sec. 4, with the discretisation of Sec. 5.
+ *
+ * Problem (Sec. 1-2).  The Helmholtz equation  Lap u + k0^2 u = f + omega^2 xi u
+ * (eq. 1), k0 = omega/c0, xi = c0^-2 - c^-2, with Green function
+ * G(rho) = -exp(i k0 rho)/(4 pi rho).  The coefficient xi is supported in the
+ * flat layer X = R^2 x [z1, z2]; the scattered field W = u - u0 is measured on
+ * M1 planes of the layer Y above it, at one or more frequencies (eq. 2-3).
+ * The incident field is the plane wave u0 = exp(-i k0 z).
+ *
+ * Discretisation.  The horizontal directions are periodic with period L on an
+ * N x N grid (nodes x0 + i L/N); the horizontal Fourier transform of Sec. 2 is
+ * the 2D DFT.  X is cut into M cells of height h_z = (z2 - z1)/M with planes at
+ * the midpoints z'_l = z1 + (l + 1/2) h_z (midpoint quadrature, Sec. 5.2).  Y
+ * planes are given explicitly and must all lie above z2.
+ *
+ * Method (Algorithm 2).  For every frequency omega and wavenumber nu = 2 pi m/L:
+ *   1. b = W~_nu (2D FFT of the data planes); A_nu[k, l] = omega^2 h_z K_nu(z_k - z'_l)
+ *      with K_nu(dz) = -i exp(i k_z |dz|)/(2 k_z), k_z = sqrt(k0^2 - |nu|^2),
+ *      Im k_z >= 0 (eq. 8);  V~_nu = (A^H A + alpha I)^-1 A^H b (Tikhonov, Sec. 5.2),
+ *      alpha chosen per mode by the discrepancy principle ||A V~ - b|| = delta_nu,
+ *      delta_nu = tau max(delta, delta_floor) ||W_omega||_2;  ||b|| <= delta_nu gives
+ *      V~ = 0; alpha is never below alpha_rel tr(A A^H).  Modes with |nu| = k0
+ *      exactly (k_z = 0) are excluded (V~ = 0).
+ *   2. U~ = U~0 + omega^2 T_nu V~, T_nu[l, l'] = h_z K_nu(z'_l - z'_l') (eq. 9);
+ *      V = F^-1[V~], u = F^-1[U~].
+ *   3. xi = Re(sum_omega conj(u) V) / sum_omega |u|^2 (least squares over the
+ *      frequencies; V/u for one frequency); c = (c0^-2 - xi)^(-1/2).
+ *
+ * Conventions of every entry point.
+ *   - Pointers documented as "device" must be device memory of the context's
+ *     device; "host" pointers are ordinary host memory.  The library never frees
+ *     caller memory.  It owns only the context's workspace.
+ *   - Complex arrays are interleaved (re, im); real arrays are contiguous.  Array
+ *     shapes are listed outermost first; x (the last index) is fastest.
+ *   - Calls are asynchronous on the context's stream unless stated otherwise and
+ *     return FS_OK once all work is enqueued.  Results are deterministic.
+ *   - Errors are returned as fs_status; fs_last_error() gives a message.  Invalid
+ *     arguments are detected on the host before any work is enqueued.
+ */
+#ifndef FLATLAYER_H
+#define FLATLAYER_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FS_OK = 0,
+  FS_EINVAL = 1,      /* invalid argument (shape, range, null pointer)           */
+  FS_ENOMEM = 2,      /* device or pinned allocation failed                      */
+  FS_ECUDA = 3,       /* a CUDA call failed; see fs_last_error                   */
+  FS_EUNSUPPORTED = 4 /* size outside the compiled limits (see below)            */
+} fs_status;
+
+typedef enum {
+  FS_FP64 = 0, /* every step in FP64: W complex128 in, xi/c float64 out               */
+  FS_MIXED = 1 /* FFTs, kernel assembly, normal matrix and its reduction in FP32;
+                  alpha root-find and an FP64-residual refinement of the solve in
+                  FP64 (FP64 factorisation when alpha/tr(A A^H) < fp64_switch);
+                  W complex64 in, xi/c float32 out                                  */
+} fs_precision;
+
+/* Limits of this build: N in {8,12,16,24,32,48,64,96,128,192,256}; 1 <= M <= 64;
+   1 <= M1 <= 32; 1 <= n_omega <= 64. */
+
+typedef struct {
+  int n;            /* N: horizontal grid points per axis                           */
+  int m;            /* M: X planes                                                  */
+  int m1;           /* M1: data (Y) planes                                          */
+  double period;    /* L > 0: horizontal period                                     */
+  double z1, z2;    /* X slab [z1, z2], z2 > z1                                     */
+  const double* zy; /* host, M1 heights of the data planes, each > z2               */
+} fs_geometry;
+
+typedef struct {
+  double tau;          /* discrepancy factor: delta_nu = tau max(delta, delta_floor) ||W|| (default 2) */
+  double delta_floor;  /* lower bound of the relative noise level (default 1e-5)          */
+  double alpha_rel;    /* alpha >= alpha_rel tr(A A^H) (default 1e-6)                     */
+  double eps_u;        /* xi := 0 where sum |u|^2 < eps_u^2 n_omega (default 1e-8)        */
+  int alpha_mode;      /* 0: per-mode discrepancy principle; 1: alpha_given per frequency,
+                          every non-grazing mode solved (default 0)                       */
+  const double* alpha_given; /* host, n_omega values, read when alpha_mode == 1           */
+  int max_iter;        /* root-find iteration cap (default 100)                           */
+  int refine_iters;    /* FS_MIXED: FP64 refinement sweeps (default 3)                    */
+  double fp64_switch;  /* FS_MIXED: FP64 factorisation below alpha/tr = this (default 1e-5) */
+  int stage_timing;    /* 1: record CUDA events between the kernels of fs_reconstruct; the
+                          durations appear in fs_report.ms_stage (default 0)              */
+} fs_options;
+
+typedef struct {
+  long long n_modes;         /* wavenumbers examined (n_omega N^2)                   */
+  long long n_active;        /* modes solved                                         */
+  long long n_zeroed;        /* modes with ||b|| <= delta_nu (V~ = 0)                */
+  long long n_grazing;       /* modes with |nu| = k0 (excluded)                      */
+  long long n_alpha_floor;   /* active modes where alpha = alpha_rel tr(A A^H)       */
+  long long n_root_capped;   /* root-finds stopped by max_iter                        */
+  long long n_u_guard;       /* voxels where sum |u|^2 < eps_u^2 n_omega (xi := 0)   */
+  long long n_nan_c;         /* voxels where xi >= c0^-2 (c := NaN)                  */
+  long long n_fp64_fallback; /* FS_MIXED: modes refactorised in FP64                  */
+  long long n_refine_iters;  /* FS_MIXED: refinement sweeps performed                 */
+  long long n_columns;       /* columns nu1 holding a nonzero mode, summed over omega:
+                                the inverse transform along y runs on these only       */
+  float ms_stage[6];         /* with stage_timing: device milliseconds of the kernels
+                                [0] forward FFT along x, [1] forward FFT along y + mode
+                                norms, [2] mode classification, [3] per-mode solve,
+                                [4] inverse FFT along y (gather), [5] inverse FFT along x
+                                + xi/c; zeros otherwise                                  */
+} fs_report;
+
+typedef struct fs_ctx fs_ctx;
+
+/* Library version string (static storage). */
+const char* fs_version(void);
+
+/* Fill *opts with the defaults listed in fs_options.  Returns FS_EINVAL on NULL. */
+fs_status fs_default_options(fs_options* opts);
+
+/* Create a context on CUDA device `device`, enqueueing on `stream` (a
+   cudaStream_t; NULL = the legacy default stream).  The context owns a workspace
+   that grows on demand and is released by fs_destroy.  *ctx receives the handle. */
+fs_status fs_create(fs_ctx** ctx, int device, void* stream);
+
+/* Release the context and its workspace (synchronises its stream).  NULL is a no-op. */
+void fs_destroy(fs_ctx* ctx);
+
+/* Message describing the last error of this context (never NULL). */
+const char* fs_last_error(const fs_ctx* ctx);
+
+/* Bytes of device workspace fs_reconstruct needs for this geometry. */
+fs_status fs_workspace_size(const fs_geometry* geom, int n_omega, fs_precision prec, size_t* bytes);
+
+/* Algorithm 2 (Sec. 4 steps 1-3) on one problem.
+     W         device, [n_omega][M1][N][N] complex (complex128 for FS_FP64,
+               complex64 for FS_MIXED): scattered field on the data planes.
+     omega     host, n_omega angular frequencies (> 0).
+     delta     relative noise level of W (>= 0).
+     c0        background sound speed (> 0).
+     opts      NULL for defaults.
+     xi        device, [M][N][N] real (float64 / float32): reconstructed xi.
+     c         device, [M][N][N] real, or NULL: sound speed (NaN where xi >= c0^-2).
+     alpha_out device, [n_omega][N][N] float64, or NULL: chosen alpha of each active
+               mode (other entries are left untouched).
+   The workspace grows (synchronously) when a larger problem arrives; otherwise the
+   call only enqueues work.  Counters of the call are read with fs_get_report. */
+fs_status fs_reconstruct(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* W,
+                         const double* omega, int n_omega, double delta, double c0,
+                         const fs_options* opts, void* xi, void* c, double* alpha_out);
+
+/* Same as fs_reconstruct with HOST buffers W, xi, c (c may be NULL): copies W to
+   the device, runs, copies xi (and c) back and synchronises the stream before
+   returning.  Page-locked host buffers give the fastest copies. */
+fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* W_host,
+                              const double* omega, int n_omega, double delta, double c0,
+                              const fs_options* opts, void* xi_host, void* c_host);
+
+/* Forward data generator in the single-scattering (Born) form: Algorithm 1 of
+   Sec. 3 with zero iterations, i.e. U~ = U~0 in eq. (7):
+     W = F^-1[ omega^2 sum_l h_z K_nu(z_k - z'_l) F[xi u0](z'_l) ]  on the data planes,
+   with u0 = exp(-i k0 z), k0 = omega/c0, and grazing modes excluded as above.
+     xi  device, [M][N][N] real (float64 for FS_FP64, float32 for FS_MIXED).
+     W   device, [n_omega][M1][N][N] complex (complex128 / complex64), written.
+   Uses the context workspace; asynchronous. */
+fs_status fs_forward_born(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* xi,
+                          const double* omega, int n_omega, double c0, void* W);
+
+/* Synchronise the context's stream and return the counters of the last
+   fs_reconstruct call. */
+fs_status fs_get_report(fs_ctx* ctx, fs_report* report);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLATLAYER_H */

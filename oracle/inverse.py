@@ -44,6 +44,8 @@ class Options:
     alpha_rel: float = 1e-6     # alpha_floor = alpha_rel * ||A_nu||_F^2
     eps_u: float = 1e-8         # |u| guard for step 3
     alpha_given: object = None  # per-frequency alpha (skips the discrepancy search)
+    mode_rows: object = None    # (r0, r1): solve only wavenumber rows r0 <= row < r1, treating the
+                                # others as zeroed -- a proportional work sample, for timing only
 
 
 @dataclass
@@ -90,7 +92,7 @@ def solve_modes(Wt, omega, k0, g: Geometry, delta_nu, opts: Options, alpha_fixed
     graz = grazing_mask(k0, g)
     alpha[graz] = np.nan
     n_floor = 0
-    for rows in _row_chunks(g, g.m1 * g.m * 4):
+    for rows in _band(_row_chunks(g, g.m1 * g.m * 4), opts.mode_rows):
         A = omega ** 2 * data_matrices(k0, g, rows)           # [y, x, M1, M]
         b = np.moveaxis(Wt[:, rows, :], 0, -1)                 # [y, x, M1]
         bnorm = np.linalg.norm(b, axis=-1)
@@ -119,10 +121,19 @@ def solve_modes(Wt, omega, k0, g: Geometry, delta_nu, opts: Options, alpha_fixed
     return Vt, alpha, active, n_floor
 
 
-def interior_field(Vt, omega, k0, g: Geometry):
+def _band(chunks, band):
+    for rows in chunks:
+        if band is not None:
+            rows = slice(max(rows.start, band[0]), min(rows.stop, band[1]))
+            if rows.start >= rows.stop:
+                continue
+        yield rows
+
+
+def interior_field(Vt, omega, k0, g: Geometry, band=None):
     """Step 2 (eq. 9): U~ = U~0 + omega^2 T_nu V~ per mode, explicit matrix product."""
     Ut = fft2(incident_plane_wave(k0, g))
-    for rows in _row_chunks(g, g.m * g.m):
+    for rows in _band(_row_chunks(g, g.m * g.m), band):
         T = interior_matrices(k0, g, rows)
         Ut[:, rows, :] += omega ** 2 * np.einsum("yxkl,lyx->kyx", T, Vt[:, rows, :])
     return Ut
@@ -154,7 +165,7 @@ def reconstruct(W, omegas, g: Geometry, delta, c0=1.0, opts: Options | None = No
         dnu = opts.tau * max(delta, opts.delta_floor) * np.linalg.norm(W[j])
         afix = None if opts.alpha_given is None else float(np.atleast_1d(opts.alpha_given)[j])
         Vt, alpha, active, nfl = solve_modes(Wt, om, k0, g, dnu, opts, afix)
-        Ut = interior_field(Vt, om, k0, g)
+        Ut = interior_field(Vt, om, k0, g, opts.mode_rows)
         Vs.append(ifft2(Vt))
         us.append(ifft2(Ut))
         Vts.append(Vt)

@@ -1,0 +1,110 @@
+"""GB300 (sm_103a) implementation of the flat-layer inverse-acoustics algorithm
+(Bakushinsky & Leonov, arXiv 1911.10487, Algorithm 2).
+
+The computation runs in the CUDA library libflatlayer.so behind the C ABI of
+include/flatlayer.h; ``_abi`` binds it with ctypes under the same names.
+``Reconstructor`` is a convenience layer that uses PyTorch only to hold device
+memory and to pick the CUDA stream.  There is no CPU fallback: if the library is
+missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+from . import _abi
+from ._abi import (FS_FP64, FS_MIXED, FlatLayerError, fs_create, fs_default_options, fs_destroy,
+                   fs_forward_born, fs_get_report, fs_last_error, fs_reconstruct, fs_reconstruct_host, fs_version,
+                   fs_workspace_size, make_geometry, make_options)
+
+__all__ = ["Geometry", "Reconstructor", "FS_FP64", "FS_MIXED", "FlatLayerError", "fs_create",
+           "fs_default_options", "fs_destroy", "fs_forward_born", "fs_get_report", "fs_last_error", "fs_reconstruct",
+           "fs_reconstruct_host", "fs_version", "fs_workspace_size", "make_geometry", "make_options"]
+
+PRECISIONS = {"fp64": FS_FP64, "mixed": FS_MIXED}
+
+
+@dataclass(frozen=True)
+class Geometry:
+    """N x N x M grid of X = [-L/2, L/2)^2 x [z1, z2] and the data planes zy (all > z2)."""
+    n: int
+    m: int
+    z1: float
+    z2: float
+    zy: tuple
+    period: float = 2.0
+
+    @property
+    def m1(self) -> int:
+        return len(self.zy)
+
+    def c_struct(self):
+        return make_geometry(self.n, self.m, self.z1, self.z2, self.zy, self.period)
+
+
+class Reconstructor:
+    """One library context bound to a CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Reconstructor needs a CUDA GPU")
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = fs_create(device, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            fs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reconstruct(self, W, omega, geom: Geometry, delta: float, c0: float = 1.0,
+                    precision: str = "fp64", want_c: bool = True, want_alpha: bool = False,
+                    out=None, **options):
+        """xi (and c, alpha) from data W[n_omega, M1, N, N] on the device.
+
+        W must be complex128 for precision='fp64' and complex64 for 'mixed'.
+        Returns (xi, c, alpha) tensors (c/alpha None unless requested)."""
+        import torch
+        prec = PRECISIONS[precision]
+        want = torch.complex128 if prec == FS_FP64 else torch.complex64
+        rdt = torch.float64 if prec == FS_FP64 else torch.float32
+        if W.dtype != want or W.device != self.device or not W.is_contiguous():
+            raise ValueError(f"W must be a contiguous {want} tensor on {self.device}")
+        n_om = len(omega)
+        if tuple(W.shape) != (n_om, geom.m1, geom.n, geom.n):
+            raise ValueError(f"W shape {tuple(W.shape)} != {(n_om, geom.m1, geom.n, geom.n)}")
+        if out is None:
+            xi = torch.empty((geom.m, geom.n, geom.n), dtype=rdt, device=self.device)
+            c = torch.empty_like(xi) if want_c else None
+            alpha = (torch.full((n_om, geom.n, geom.n), float("inf"), dtype=torch.float64,
+                                device=self.device) if want_alpha else None)
+        else:
+            xi, c, alpha = out
+        opts = make_options(**options) if options else None
+        fs_reconstruct(self.ctx, geom.c_struct(), prec, W.data_ptr(), omega, delta, c0, opts,
+                       xi.data_ptr(), c.data_ptr() if c is not None else None,
+                       alpha.data_ptr() if alpha is not None else None)
+        return xi, c, alpha
+
+    def forward_born(self, xi, omega, geom: Geometry, c0: float = 1.0, precision: str = "fp64"):
+        """Single-scattering data W[n_omega, M1, N, N] of xi[M, N, N] (device tensors)."""
+        import torch
+        prec = PRECISIONS[precision]
+        rdt = torch.float64 if prec == FS_FP64 else torch.float32
+        cdt = torch.complex128 if prec == FS_FP64 else torch.complex64
+        if xi.dtype != rdt or xi.device != self.device or not xi.is_contiguous():
+            raise ValueError(f"xi must be a contiguous {rdt} tensor on {self.device}")
+        if tuple(xi.shape) != (geom.m, geom.n, geom.n):
+            raise ValueError("xi shape does not match the geometry")
+        W = torch.empty((len(omega), geom.m1, geom.n, geom.n), dtype=cdt, device=self.device)
+        fs_forward_born(self.ctx, geom.c_struct(), prec, xi.data_ptr(), omega, c0, W.data_ptr())
+        return W
+
+    def report(self) -> dict:
+        return fs_get_report(self.ctx)

@@ -1,0 +1,186 @@
+"""ctypes binding of the C ABI in include/flatlayer.h (argument marshalling only).
+
+Every entry point of the header appears here under the same name.  The shared
+library must have been built (``paper_1911_10487_gb300.build.build()``); loading
+fails loudly otherwise -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libflatlayer.so")
+_lib = None
+
+FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED = 0, 1, 2, 3, 4
+FS_FP64, FS_MIXED = 0, 1
+STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_EUNSUPPORTED"}
+
+# every function declared in include/flatlayer.h
+EXPORTS = ("fs_version", "fs_default_options", "fs_create", "fs_destroy", "fs_last_error",
+           "fs_workspace_size", "fs_reconstruct", "fs_reconstruct_host", "fs_forward_born",
+           "fs_get_report")
+
+
+class fs_geometry(C.Structure):
+    _fields_ = [("n", C.c_int), ("m", C.c_int), ("m1", C.c_int), ("period", C.c_double),
+                ("z1", C.c_double), ("z2", C.c_double), ("zy", C.POINTER(C.c_double))]
+
+
+class fs_options(C.Structure):
+    _fields_ = [("tau", C.c_double), ("delta_floor", C.c_double), ("alpha_rel", C.c_double),
+                ("eps_u", C.c_double), ("alpha_mode", C.c_int),
+                ("alpha_given", C.POINTER(C.c_double)), ("max_iter", C.c_int),
+                ("refine_iters", C.c_int), ("fp64_switch", C.c_double), ("stage_timing", C.c_int)]
+
+
+STAGES = ("fft_x_forward", "fft_y_forward_norms", "classify", "solve", "ifft_y_gather", "ifft_x_recover")
+
+
+class fs_report(C.Structure):
+    _fields_ = [(k, C.c_longlong) for k in (
+        "n_modes", "n_active", "n_zeroed", "n_grazing", "n_alpha_floor", "n_root_capped",
+        "n_u_guard", "n_nan_c", "n_fp64_fallback", "n_refine_iters", "n_columns")] + [("ms_stage", C.c_float * 6)]
+
+    def as_dict(self):
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "ms_stage"}
+        d["ms_stage"] = dict(zip(STAGES, [float(x) for x in self.ms_stage]))
+        return d
+
+
+class FlatLayerError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libflatlayer.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is missing: build it with paper_1911_10487_gb300.build.build()")
+        L = C.CDLL(_LIB_PATH)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+        L.fs_version.restype = C.c_char_p
+        L.fs_version.argtypes = []
+        L.fs_default_options.restype = ip
+        L.fs_default_options.argtypes = [C.POINTER(fs_options)]
+        L.fs_create.restype = ip
+        L.fs_create.argtypes = [C.POINTER(vp), ip, vp]
+        L.fs_destroy.restype = None
+        L.fs_destroy.argtypes = [vp]
+        L.fs_last_error.restype = C.c_char_p
+        L.fs_last_error.argtypes = [vp]
+        L.fs_workspace_size.restype = ip
+        L.fs_workspace_size.argtypes = [C.POINTER(fs_geometry), ip, ip, C.POINTER(C.c_size_t)]
+        L.fs_reconstruct.restype = ip
+        L.fs_reconstruct.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, C.c_double,
+                                     C.POINTER(fs_options), vp, vp, dp]
+        L.fs_reconstruct_host.restype = ip
+        L.fs_reconstruct_host.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, C.c_double,
+                                          C.POINTER(fs_options), vp, vp]
+        L.fs_forward_born.restype = ip
+        L.fs_forward_born.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, vp]
+        L.fs_get_report.restype = ip
+        L.fs_get_report.argtypes = [vp, C.POINTER(fs_report)]
+        _lib = L
+    return _lib
+
+
+# ---- same-named thin wrappers ---------------------------------------------------
+
+def fs_version() -> str:
+    return lib().fs_version().decode()
+
+
+def fs_default_options() -> fs_options:
+    o = fs_options()
+    lib().fs_default_options(C.byref(o))
+    return o
+
+
+def fs_create(device: int = 0, stream: int = 0):
+    h = C.c_void_p()
+    st = lib().fs_create(C.byref(h), int(device), C.c_void_p(stream or None))
+    if st != FS_OK:
+        raise FlatLayerError(st, f"fs_create(device={device}) failed")
+    return h
+
+
+def fs_destroy(ctx) -> None:
+    lib().fs_destroy(ctx)
+
+
+def fs_last_error(ctx) -> str:
+    return lib().fs_last_error(ctx).decode()
+
+
+def fs_workspace_size(geom: fs_geometry, n_omega: int, prec: int) -> int:
+    b = C.c_size_t()
+    st = lib().fs_workspace_size(C.byref(geom), int(n_omega), int(prec), C.byref(b))
+    if st != FS_OK:
+        raise FlatLayerError(st, "fs_workspace_size")
+    return int(b.value)
+
+
+def _check(ctx, st, what):
+    if st != FS_OK:
+        raise FlatLayerError(st, f"{what}: {fs_last_error(ctx)}")
+
+
+def fs_reconstruct(ctx, geom, prec, W_ptr, omega, delta, c0, opts, xi_ptr, c_ptr=None, alpha_ptr=None):
+    om = (C.c_double * len(omega))(*[float(x) for x in omega])
+    st = lib().fs_reconstruct(ctx, C.byref(geom), int(prec), C.c_void_p(W_ptr), om, len(omega),
+                              float(delta), float(c0), C.byref(opts) if opts is not None else None,
+                              C.c_void_p(xi_ptr), C.c_void_p(c_ptr or None),
+                              C.cast(C.c_void_p(alpha_ptr or None), C.POINTER(C.c_double)))
+    _check(ctx, st, "fs_reconstruct")
+
+
+def fs_reconstruct_host(ctx, geom, prec, W_ptr, omega, delta, c0, opts, xi_ptr, c_ptr=None):
+    om = (C.c_double * len(omega))(*[float(x) for x in omega])
+    st = lib().fs_reconstruct_host(ctx, C.byref(geom), int(prec), C.c_void_p(W_ptr), om, len(omega),
+                                   float(delta), float(c0), C.byref(opts) if opts is not None else None,
+                                   C.c_void_p(xi_ptr), C.c_void_p(c_ptr or None))
+    _check(ctx, st, "fs_reconstruct_host")
+
+
+def fs_forward_born(ctx, geom, prec, xi_ptr, omega, c0, W_ptr):
+    om = (C.c_double * len(omega))(*[float(x) for x in omega])
+    st = lib().fs_forward_born(ctx, C.byref(geom), int(prec), C.c_void_p(xi_ptr), om, len(omega),
+                               float(c0), C.c_void_p(W_ptr))
+    _check(ctx, st, "fs_forward_born")
+
+
+def fs_get_report(ctx) -> dict:
+    r = fs_report()
+    st = lib().fs_get_report(ctx, C.byref(r))
+    _check(ctx, st, "fs_get_report")
+    return r.as_dict()
+
+
+def make_geometry(n, m, z1, z2, zy, period=2.0):
+    """fs_geometry for an N x N x M grid; keeps the zy array alive on the struct."""
+    zy_arr = (C.c_double * len(zy))(*[float(z) for z in zy])
+    g = fs_geometry(int(n), int(m), len(zy), float(period), float(z1), float(z2),
+                    C.cast(zy_arr, C.POINTER(C.c_double)))
+    g._keep = zy_arr
+    return g
+
+
+def make_options(**kw) -> fs_options:
+    """Defaults of fs_default_options, overridden by keyword (alpha_given: sequence)."""
+    o = fs_default_options()
+    for k, v in kw.items():
+        if k == "alpha_given":
+            arr = (C.c_double * len(v))(*[float(x) for x in v])
+            o.alpha_given = C.cast(arr, C.POINTER(C.c_double))
+            o._keep = arr
+        else:
+            setattr(o, k, v)
+    return o

@@ -1,0 +1,409 @@
+// C ABI of the flat-layer reconstruction (declared in include/flatlayer.h):
+// argument validation, context/workspace management and the launch sequence of
+// Algorithm 2 (Sec. 4):
+//   fft2_forward (W -> W~, ||W~_nu||^2) -> classify (delta_nu, active modes)
+//   -> solve (eq. 8 Tikhonov + discrepancy, eq. 9) -> recover (F^-1, step 3).
+#include <stdarg.h>
+#include <stdio.h>
+#include <new>
+#include <string.h>
+
+#include <cuda_runtime.h>
+
+#include "../../include/flatlayer.h"
+#include "pipeline.cuh"
+
+using namespace fl;
+
+namespace {
+
+constexpr int N_SIZES = 11;
+const int kSizes[N_SIZES] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256};
+
+int size_index(int n) {
+  for (int i = 0; i < N_SIZES; ++i)
+    if (kSizes[i] == n) return i;
+  return -1;
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct fs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* tw[2][N_SIZES] = {};  // [fp64?][size]
+  unsigned long long* ctr = nullptr;
+  unsigned long long* ctr_host = nullptr;
+  // staging for fs_reconstruct_host
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t ev[7] = {};
+  bool timed = false;
+  char err[512] = {0};
+};
+
+namespace {
+
+fs_status fail(fs_ctx* ctx, fs_status st, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+fs_status cuda_fail(fs_ctx* ctx, cudaError_t e, const char* where) {
+  if (ctx) snprintf(ctx->err, sizeof(ctx->err), "%s: %s", where, cudaGetErrorString(e));
+  return FS_ECUDA;
+}
+
+struct Layout {
+  size_t t12, prof, norms, slot, act, cols, ncol, count, dnu, total;
+};
+
+Layout layout(int n, int m, int m1, int n_omega, bool fp64) {
+  const size_t cxs = fp64 ? 16 : 8;
+  const size_t N2 = (size_t)n * n;
+  const size_t a = (size_t)n_omega * m1 * N2, b = (size_t)n_omega * 2 * m * N2;
+  Layout L;
+  size_t off = 0;
+  L.t12 = off; off = align_up(off + cxs * (a > b ? a : b));  // W~, later the y-inverse pass output
+  L.prof = off; off = align_up(off + cxs * (size_t)n_omega * N2 * 2 * m);
+  L.norms = off; off = align_up(off + 8 * (size_t)n_omega * N2);
+  L.slot = off; off = align_up(off + 4 * (size_t)n_omega * N2);
+  L.act = off; off = align_up(off + 4 * (size_t)n_omega * N2);
+  L.cols = off; off = align_up(off + 4 * (size_t)n_omega * n);
+  L.ncol = off; off = align_up(off + 4 * (size_t)n_omega);
+  L.count = off; off = align_up(off + 4 * (size_t)n_omega);
+  L.dnu = off; off = align_up(off + 8 * (size_t)n_omega);
+  L.total = off;
+  return L;
+}
+
+fs_status validate(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, int n_omega, const double* omega,
+                   double delta, double c0, const fs_options* o) {
+  if (!g) return fail(ctx, FS_EINVAL, "geometry is NULL");
+  if (prec != FS_FP64 && prec != FS_MIXED) return fail(ctx, FS_EINVAL, "unknown precision");
+  if (g->n <= 0 || g->m <= 0 || g->m1 <= 0) return fail(ctx, FS_EINVAL, "grid sizes must be positive");
+  if (!fft_size_supported(g->n))
+    return fail(ctx, FS_EUNSUPPORTED, "N=%d not supported (8,12,16,24,32,48,64,96,128,192,256)",
+                g->n);
+  if (g->m > MAX_M) return fail(ctx, FS_EUNSUPPORTED, "M=%d exceeds 64", g->m);
+  if (g->m1 > MAX_M1) return fail(ctx, FS_EUNSUPPORTED, "M1=%d exceeds 32", g->m1);
+  if (n_omega <= 0) return fail(ctx, FS_EINVAL, "n_omega must be positive");
+  if (n_omega > MAX_OMEGA) return fail(ctx, FS_EUNSUPPORTED, "n_omega=%d exceeds 64", n_omega);
+  if (!omega) return fail(ctx, FS_EINVAL, "omega is NULL");
+  for (int j = 0; j < n_omega; ++j)
+    if (!(omega[j] > 0.0)) return fail(ctx, FS_EINVAL, "omega[%d] must be > 0", j);
+  if (!(g->period > 0.0)) return fail(ctx, FS_EINVAL, "period must be > 0");
+  if (!(g->z2 > g->z1)) return fail(ctx, FS_EINVAL, "need z2 > z1");
+  if (!g->zy) return fail(ctx, FS_EINVAL, "zy is NULL");
+  for (int k = 0; k < g->m1; ++k)
+    if (!(g->zy[k] > g->z2)) return fail(ctx, FS_EINVAL, "data plane %d is not above X", k);
+  if (!(delta >= 0.0)) return fail(ctx, FS_EINVAL, "delta must be >= 0");
+  if (!(c0 > 0.0)) return fail(ctx, FS_EINVAL, "c0 must be > 0");
+  if (o) {
+    if (!(o->tau > 0.0) || !(o->delta_floor >= 0.0) || !(o->alpha_rel > 0.0) || !(o->eps_u >= 0.0))
+      return fail(ctx, FS_EINVAL, "options out of range (tau>0, delta_floor>=0, alpha_rel>0, eps_u>=0)");
+    if (o->alpha_mode != 0 && o->alpha_mode != 1) return fail(ctx, FS_EINVAL, "alpha_mode must be 0 or 1");
+    if (o->alpha_mode == 1) {
+      if (!o->alpha_given) return fail(ctx, FS_EINVAL, "alpha_given is NULL");
+      for (int j = 0; j < n_omega; ++j)
+        if (!(o->alpha_given[j] > 0.0)) return fail(ctx, FS_EINVAL, "alpha_given[%d] must be > 0", j);
+    }
+    if (o->max_iter < 1 || o->refine_iters < 0) return fail(ctx, FS_EINVAL, "max_iter >= 1, refine_iters >= 0");
+  }
+  return FS_OK;
+}
+
+Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, double delta, double c0,
+                     const fs_options& o) {
+  Problem P;
+  memset(&P, 0, sizeof(P));
+  P.n = g->n; P.m = g->m; P.m1 = g->m1; P.n_omega = n_omega;
+  P.alpha_mode = o.alpha_mode; P.max_iter = o.max_iter; P.refine_iters = o.refine_iters;
+  P.period = g->period; P.z1 = g->z1; P.hz = (g->z2 - g->z1) / g->m; P.c0 = c0;
+  P.delta = delta; P.tau = o.tau; P.delta_floor = o.delta_floor; P.alpha_rel = o.alpha_rel; P.eps_u = o.eps_u;
+  P.fp64_switch = o.fp64_switch;
+  for (int k = 0; k < g->m1; ++k) P.zy[k] = g->zy[k];
+  for (int j = 0; j < n_omega; ++j) {
+    P.omega[j] = omega[j];
+    P.alpha_given[j] = (o.alpha_mode == 1) ? o.alpha_given[j] : 0.0;
+  }
+  return P;
+}
+
+fs_status ensure_workspace(fs_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return FS_OK;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+  if (ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  e = cudaMalloc(&ctx->ws, bytes);
+  if (e != cudaSuccess) {
+    ctx->ws = nullptr;
+    return fail(ctx, FS_ENOMEM, "workspace allocation of %lld bytes failed", (long long)bytes);
+  }
+  ctx->ws_bytes = bytes;
+  return FS_OK;
+}
+
+template <typename R>
+fs_status ensure_twiddles(fs_ctx* ctx, int n, const cx<R>** out) {
+  const int fp = sizeof(R) == 8 ? 1 : 0;
+  const int si = size_index(n);
+  if (!ctx->tw[fp][si]) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(cx<R>) * n) != cudaSuccess) return fail(ctx, FS_ENOMEM, "twiddle table");
+    cudaError_t e = launch_twiddles<R>((cx<R>*)p, n, ctx->stream);
+    if (e != cudaSuccess) { cudaFree(p); return cuda_fail(ctx, e, "twiddles"); }
+    ctx->tw[fp][si] = p;
+  }
+  *out = (const cx<R>*)ctx->tw[fp][si];
+  return FS_OK;
+}
+
+template <typename R>
+Work<R> carve_work(void* base, const Layout& L, unsigned long long* ctr, const cx<R>* tw, double* alpha_out) {
+  char* b = (char*)base;
+  Work<R> w;
+  w.wt = (cx<R>*)(b + L.t12);
+  w.t2 = (cx<R>*)(b + L.t12);
+  w.prof = (cx<R>*)(b + L.prof);
+  w.norms = (double*)(b + L.norms);
+  w.slot = (int*)(b + L.slot);
+  w.act = (int*)(b + L.act);
+  w.cols = (int*)(b + L.cols);
+  w.ncol = (int*)(b + L.ncol);
+  w.count = (int*)(b + L.count);
+  w.dnu = (double*)(b + L.dnu);
+  w.ctr = ctr;
+  w.tw = tw;
+  w.alpha_out = alpha_out;
+  return w;
+}
+
+template <typename R>
+fs_status run(fs_ctx* ctx, const Problem& P, const Layout& L, const void* W, void* xi, void* c,
+              double* alpha_out, bool timed) {
+  const cx<R>* tw = nullptr;
+  fs_status st = ensure_twiddles<R>(ctx, P.n, &tw);
+  if (st != FS_OK) return st;
+  Work<R> w = carve_work<R>(ctx->ws, L, ctx->ctr, tw, alpha_out);
+  cudaError_t e = cudaMemsetAsync(ctx->ctr, 0, sizeof(unsigned long long) * C_COUNT, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
+  cudaEvent_t* ev = timed ? ctx->ev : nullptr;
+  ctx->timed = timed;
+  if (ev) cudaEventRecord(ev[0], ctx->stream);
+  if ((e = launch_fft2_forward<R>((const cx<R>*)W, P, w, ctx->stream, ev ? ev[1] : nullptr)) != cudaSuccess)
+    return cuda_fail(ctx, e, "fft2_forward");
+  if (ev) cudaEventRecord(ev[2], ctx->stream);
+  if ((e = launch_classify<R>(P, w, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "classify");
+  if (ev) cudaEventRecord(ev[3], ctx->stream);
+  if (sizeof(R) == 8) e = launch_solve_fp64(P, *(const Work<double>*)&w, ctx->stream);
+  else e = launch_solve_mixed(P, *(const Work<float>*)&w, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "solve");
+  if (ev) cudaEventRecord(ev[4], ctx->stream);
+  if ((e = launch_recover<R>(P, w, (R*)xi, (R*)c, ctx->stream, ev ? ev[5] : nullptr)) != cudaSuccess)
+    return cuda_fail(ctx, e, "recover");
+  if (ev) cudaEventRecord(ev[6], ctx->stream);
+  return FS_OK;
+}
+
+}  // namespace
+
+namespace fl {
+size_t workspace_bytes(int n, int m, int m1, int n_omega, bool fp64) {
+  return layout(n, m, m1, n_omega, fp64).total;
+}
+}  // namespace fl
+
+extern "C" {
+
+const char* fs_version(void) { return "flatlayer-gb300 0.1 (sm_103a)"; }
+
+fs_status fs_default_options(fs_options* o) {
+  if (!o) return FS_EINVAL;
+  o->tau = 2.0;
+  o->delta_floor = 1e-5;
+  o->alpha_rel = 1e-6;
+  o->eps_u = 1e-8;
+  o->alpha_mode = 0;
+  o->alpha_given = nullptr;
+  o->max_iter = 100;
+  o->refine_iters = 3;
+  o->fp64_switch = 1e-5;
+  o->stage_timing = 0;
+  return FS_OK;
+}
+
+fs_status fs_create(fs_ctx** out, int device, void* stream) {
+  if (!out) return FS_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FS_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return FS_ECUDA;
+  fs_ctx* ctx = new (std::nothrow) fs_ctx();
+  if (!ctx) return FS_ENOMEM;
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  if (cudaMalloc(&ctx->ctr, sizeof(unsigned long long) * C_COUNT) != cudaSuccess) {
+    delete ctx;
+    return FS_ENOMEM;
+  }
+  if (cudaMallocHost(&ctx->ctr_host, sizeof(unsigned long long) * C_COUNT) != cudaSuccess) {
+    cudaFree(ctx->ctr);
+    delete ctx;
+    return FS_ENOMEM;
+  }
+  memset(ctx->ctr_host, 0, sizeof(unsigned long long) * C_COUNT);
+  for (auto& e : ctx->ev) cudaEventCreate(&e);
+  cudaMemsetAsync(ctx->ctr, 0, sizeof(unsigned long long) * C_COUNT, ctx->stream);
+  *out = ctx;
+  return FS_OK;
+}
+
+void fs_destroy(fs_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->stage) cudaFree(ctx->stage);
+  for (auto& a : ctx->tw)
+    for (void* p : a)
+      if (p) cudaFree(p);
+  if (ctx->ctr) cudaFree(ctx->ctr);
+  if (ctx->ctr_host) cudaFreeHost(ctx->ctr_host);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char* fs_last_error(const fs_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+fs_status fs_workspace_size(const fs_geometry* g, int n_omega, fs_precision prec, size_t* bytes) {
+  if (!g || !bytes || n_omega <= 0 || g->n <= 0 || g->m <= 0 || g->m1 <= 0) return FS_EINVAL;
+  *bytes = layout(g->n, g->m, g->m1, n_omega, prec == FS_FP64).total;
+  return FS_OK;
+}
+
+fs_status fs_reconstruct(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const void* W, const double* omega,
+                         int n_omega, double delta, double c0, const fs_options* opts, void* xi, void* c,
+                         double* alpha_out) {
+  if (!ctx) return FS_EINVAL;
+  fs_status st = validate(ctx, g, prec, n_omega, omega, delta, c0, opts);
+  if (st != FS_OK) return st;
+  if (!W || !xi) return fail(ctx, FS_EINVAL, "W and xi must be device pointers");
+  fs_options o;
+  fs_default_options(&o);
+  if (opts) o = *opts;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  const bool fp64 = prec == FS_FP64;
+  const Layout L = layout(g->n, g->m, g->m1, n_omega, fp64);
+  if ((st = ensure_workspace(ctx, L.total)) != FS_OK) return st;
+  const Problem P = make_problem(g, n_omega, omega, delta, c0, o);
+  const bool timed = o.stage_timing != 0;
+  return fp64 ? run<double>(ctx, P, L, W, xi, c, alpha_out, timed)
+              : run<float>(ctx, P, L, W, xi, c, alpha_out, timed);
+}
+
+fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const void* W_host,
+                              const double* omega, int n_omega, double delta, double c0, const fs_options* opts,
+                              void* xi_host, void* c_host) {
+  if (!ctx) return FS_EINVAL;
+  fs_status st = validate(ctx, g, prec, n_omega, omega, delta, c0, opts);
+  if (st != FS_OK) return st;
+  if (!W_host || !xi_host) return fail(ctx, FS_EINVAL, "W_host and xi_host must be non-NULL");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  const size_t cxs = prec == FS_FP64 ? 16 : 8, rs = cxs / 2;
+  const size_t N2 = (size_t)g->n * g->n;
+  const size_t wbytes = cxs * (size_t)n_omega * g->m1 * N2;
+  const size_t obytes = rs * (size_t)g->m * N2;
+  const size_t need = align_up(wbytes) + 2 * align_up(obytes);
+  if (need > ctx->stage_bytes) {
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sync");
+    if (ctx->stage) cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    if (cudaMalloc(&ctx->stage, need) != cudaSuccess) return fail(ctx, FS_ENOMEM, "staging buffers");
+    ctx->stage_bytes = need;
+  }
+  char* dW = (char*)ctx->stage;
+  char* dxi = dW + align_up(wbytes);
+  char* dc = dxi + align_up(obytes);
+  if ((e = cudaMemcpyAsync(dW, W_host, wbytes, cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "H2D W");
+  st = fs_reconstruct(ctx, g, prec, dW, omega, n_omega, delta, c0, opts, dxi, c_host ? dc : nullptr, nullptr);
+  if (st != FS_OK) return st;
+  if ((e = cudaMemcpyAsync(xi_host, dxi, obytes, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "D2H xi");
+  if (c_host && (e = cudaMemcpyAsync(c_host, dc, obytes, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "D2H c");
+  if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sync");
+  return FS_OK;
+}
+
+fs_status fs_forward_born(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const void* xi,
+                          const double* omega, int n_omega, double c0, void* W) {
+  if (!ctx) return FS_EINVAL;
+  fs_status st = validate(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr);
+  if (st != FS_OK) return st;
+  if (!xi || !W) return fail(ctx, FS_EINVAL, "xi and W must be device pointers");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  const bool fp64 = prec == FS_FP64;
+  const size_t need = (fp64 ? 16 : 8) * (size_t)n_omega * g->m * g->n * g->n;
+  if ((st = ensure_workspace(ctx, need)) != FS_OK) return st;
+  fs_options o;
+  fs_default_options(&o);
+  const Problem P = make_problem(g, n_omega, omega, 0.0, c0, o);
+  if (fp64) {
+    const double2* tw = nullptr;
+    if ((st = ensure_twiddles<double>(ctx, g->n, &tw)) != FS_OK) return st;
+    e = launch_forward_born<double>(P, (const double*)xi, (double2*)ctx->ws, (double2*)W, tw, ctx->stream);
+  } else {
+    const float2* tw = nullptr;
+    if ((st = ensure_twiddles<float>(ctx, g->n, &tw)) != FS_OK) return st;
+    e = launch_forward_born<float>(P, (const float*)xi, (float2*)ctx->ws, (float2*)W, tw, ctx->stream);
+  }
+  return e == cudaSuccess ? FS_OK : cuda_fail(ctx, e, "forward_born");
+}
+
+fs_status fs_get_report(fs_ctx* ctx, fs_report* r) {
+  if (!ctx || !r) return FS_EINVAL;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->ctr_host, ctx->ctr, sizeof(unsigned long long) * C_COUNT, cudaMemcpyDeviceToHost,
+                        ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fs_get_report");
+  const unsigned long long* h = ctx->ctr_host;
+  r->n_modes = (long long)h[C_MODES];
+  r->n_active = (long long)h[C_ACTIVE];
+  r->n_zeroed = (long long)h[C_ZEROED];
+  r->n_grazing = (long long)h[C_GRAZING];
+  r->n_alpha_floor = (long long)h[C_ALPHA_FLOOR];
+  r->n_root_capped = (long long)h[C_ROOT_CAPPED];
+  r->n_u_guard = (long long)h[C_U_GUARD];
+  r->n_nan_c = (long long)h[C_NAN_C];
+  r->n_fp64_fallback = (long long)h[C_FP64_FALLBACK];
+  r->n_refine_iters = (long long)h[C_REFINE_ITERS];
+  r->n_columns = (long long)h[C_COLUMNS];
+  for (int i = 0; i < 6; ++i) {
+    float ms = 0.f;
+    if (ctx->timed && cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) ms = 0.f;
+    r->ms_stage[i] = ms;
+  }
+  return FS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Shared device helpers for the flat-layer reconstruction kernels (sm_103a).
+//
+// Complex numbers are stored interleaved (re, im) as float2 / double2 so that one
+// element is one 8- or 16-byte vector load.  `cx<R>` selects the vector type for
+// the real type R.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fl {
+
+template <typename R> struct cx_t;
+template <> struct cx_t<float> { using type = float2; };
+template <> struct cx_t<double> { using type = double2; };
+template <typename R> using cx = typename cx_t<R>::type;
+
+template <typename R> __host__ __device__ __forceinline__ cx<R> mk(R re, R im) {
+  cx<R> z; z.x = re; z.y = im; return z;
+}
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator*(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 operator*(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+
+__host__ __device__ __forceinline__ float2 conjx(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 conjx(double2 a) { return make_double2(a.x, -a.y); }
+// a * conj(b)
+__host__ __device__ __forceinline__ float2 mulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__host__ __device__ __forceinline__ double2 mulc(double2 a, double2 b) {
+  return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ double2 cmul_conj_a(double2 a, double2 b) {
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmul_conj_a(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV> __host__ __device__ __forceinline__ float2 rot90(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+template <bool INV> __host__ __device__ __forceinline__ double2 rot90(double2 a) {
+  return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
+}
+__host__ __device__ __forceinline__ double abs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ float abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+
+__host__ __device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
+__host__ __device__ __forceinline__ double2 to_d(double2 a) { return a; }
+template <typename R> __host__ __device__ __forceinline__ cx<R> from_d(double2 a);
+template <> __host__ __device__ __forceinline__ float2 from_d<float>(double2 a) {
+  return make_float2((float)a.x, (float)a.y);
+}
+template <> __host__ __device__ __forceinline__ double2 from_d<double>(double2 a) { return a; }
+
+template <typename R> __host__ __device__ __forceinline__ cx<R> czero() { return mk<R>(R(0), R(0)); }
+
+}  // namespace fl

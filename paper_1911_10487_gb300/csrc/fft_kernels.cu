@@ -1,0 +1,363 @@
+// 2D FFT passes of Algorithm 2 (steps 1 and 2) with their fused prologues and
+// epilogues, for N = 2^a 3^b <= 256, in FP64 (double2) or FP32 (float2).
+//
+//   fft2_forward  : W -> W~ on every data plane (Sec. 4, Algorithm 2 step 1 needs
+//                   W~ = F_r[W]), then ||W~_nu||^2 summed over the planes of a
+//                   frequency, which the discrepancy test needs.
+//   recover       : V~, U~ -> V = F^-1[V~], u = F^-1[U~] (Algorithm 2 step 2) and
+//                   xi = Re(sum conj(u) V)/sum |u|^2, c = (c0^-2 - xi)^-1/2
+//                   (step 3, Sec. 5.2; Sec. 1 for c).  The inverse column pass
+//                   gathers the solved profiles of the active modes only and
+//                   transforms only the columns nu1 that hold a nonzero mode; the
+//                   row pass scatters those columns and transforms full rows.
+#include <math.h>
+
+#include "fft.cuh"
+#include "pipeline.cuh"
+
+namespace fl {
+
+namespace {
+
+template <typename R> struct Cfg;
+template <> struct Cfg<double> { static constexpr int TC = 8; };
+template <> struct Cfg<float> { static constexpr int TC = 16; };
+
+constexpr int THREADS = 256;
+constexpr int TILE_ELEMS = 2048;  // elements of one shared-memory tile
+
+template <int N> __host__ __device__ constexpr int row_lines() { return TILE_ELEMS / N > 0 ? TILE_ELEMS / N : 1; }
+
+template <typename R, int N>
+__device__ __forceinline__ void load_twiddles(cx<R>* tw_s, const cx<R>* __restrict__ tw) {
+  for (int j = threadIdx.x; j < N; j += THREADS) tw_s[j] = tw[j];
+}
+
+// ---- dense pass along x (rows): forward, or inverse with 1/N^2 scaling --------
+template <typename R, int N, bool INV>
+__global__ void __launch_bounds__(THREADS)
+k_fft_rows(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, long long nrows,
+           const cx<R>* __restrict__ tw, R scale) {
+  constexpr int LINES = row_lines<N>();
+  __shared__ cx<R> buf[LINES * N];
+  __shared__ cx<R> tw_s[N];
+  load_twiddles<R, N>(tw_s, tw);
+  const long long row0 = (long long)blockIdx.x * LINES;
+  const long long base = row0 * N;
+  const long long limit = nrows * N;
+  for (int e = threadIdx.x; e < LINES * N; e += THREADS)
+    buf[e] = (base + e < limit) ? in[base + e] : czero<R>();
+  __syncthreads();
+  fft_lines<R, N, INV, LINES, THREADS, Lay::ROW>(buf, tw_s);
+  for (int e = threadIdx.x; e < LINES * N; e += THREADS)
+    if (base + e < limit) out[base + e] = INV ? scale * buf[e] : buf[e];
+}
+
+// ---- dense pass along y (columns), in place; grid (ceil(N/TC), planes) ---------
+template <typename R, int N, bool INV>
+__global__ void __launch_bounds__(THREADS)
+k_fft_cols(cx<R>* __restrict__ data, const cx<R>* __restrict__ tw) {
+  constexpr int TC = Cfg<R>::TC;
+  constexpr int E = N * TC;
+  __shared__ cx<R> buf[E];
+  __shared__ cx<R> tw_s[N];
+  load_twiddles<R, N>(tw_s, tw);
+  const int c0 = blockIdx.x * TC;
+  cx<R>* pl = data + (long long)blockIdx.y * N * N;
+  for (int e = threadIdx.x; e < E; e += THREADS) {
+    const int i = e / TC, b = e % TC;
+    buf[e] = (c0 + b < N) ? pl[(long long)i * N + c0 + b] : czero<R>();
+  }
+  __syncthreads();
+  fft_lines<R, N, INV, TC, THREADS, Lay::COL>(buf, tw_s);
+  for (int e = threadIdx.x; e < E; e += THREADS) {
+    const int i = e / TC, b = e % TC;
+    if (c0 + b < N) pl[(long long)i * N + c0 + b] = buf[e];
+  }
+}
+
+// ---- per-mode norms ||W~_nu||^2 = sum_k |W~_k(nu)|^2, summed in plane order ------
+template <typename R>
+__global__ void k_mode_norms(const cx<R>* __restrict__ wt, double* __restrict__ norms, int m1, long long N2,
+                             long long total) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long om = e / N2, nu = e - om * N2;
+    const cx<R>* p = wt + om * m1 * N2 + nu;
+    double acc = 0.0;
+    for (int k = 0; k < m1; ++k) {
+      const cx<R> v = p[k * N2];
+      acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    }
+    norms[e] = acc;
+  }
+}
+
+// ---- inverse pass 1: gather active profiles, columns (along y) ----------------
+// grid (ceil(N/TC), M, 2 n_omega).  Column chunk `blockIdx.x` of the compact column
+// list of frequency om; field f = 0 (V~) or 1 (U~).  Inactive modes are zero in
+// V~ and equal the incident field U~0 in U~; the plane wave exp(-i k0 z) has
+// U~0 = N^2 exp(-i k0 z'_l) at nu = 0 and zero elsewhere.
+template <typename R, int N>
+__global__ void __launch_bounds__(THREADS)
+k_ifft_cols_gather(Problem P, const cx<R>* __restrict__ prof, const int* __restrict__ slot,
+                   const int* __restrict__ cols, const int* __restrict__ ncol,
+                   cx<R>* __restrict__ t2, const cx<R>* __restrict__ tw) {
+  constexpr int TC = Cfg<R>::TC;
+  constexpr int E = N * TC;
+  constexpr int PER = (E + THREADS - 1) / THREADS;
+  const int om = blockIdx.z >> 1, f = blockIdx.z & 1;
+  const int l = blockIdx.y;
+  const int nc = ncol[om];
+  const int cb = blockIdx.x * TC;
+  if (cb >= nc) return;
+  __shared__ cx<R> buf[E];
+  __shared__ cx<R> tw_s[N];
+  load_twiddles<R, N>(tw_s, tw);
+  const long long N2 = (long long)N * N;
+  const int M = P.m;
+  cx<R> u0 = czero<R>();
+  if (f == 1) {
+    const double k0 = P.omega[om] / P.c0;
+    const double zl = P.z1 + (l + 0.5) * P.hz;
+    double s, c;
+    sincos(-k0 * zl, &s, &c);
+    u0 = from_d<R>(make_double2((double)N2 * c, (double)N2 * s));
+  }
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * THREADS;
+    if (e < E) {
+      const int i = e / TC, b = e % TC;
+      const int c = cb + b;
+      cx<R> v = czero<R>();
+      if (c < nc) {
+        const int nu1 = cols[om * N + c];
+        const int s = slot[om * N2 + (long long)i * N + nu1];
+        if (s >= 0) v = prof[(((long long)om * N2 + s) * 2 + f) * M + l];
+        else if (f == 1 && i == 0 && nu1 == 0) v = u0;
+      }
+      buf[e] = v;
+    }
+  }
+  __syncthreads();
+  fft_lines<R, N, true, TC, THREADS, Lay::COL>(buf, tw_s);
+  const long long ob = (((long long)om * 2 + f) * M + l) * N2;
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * THREADS;
+    if (e < E) {
+      const int i = e / TC, b = e % TC;
+      if (cb + b < nc) t2[ob + (long long)i * N + cb + b] = buf[e];
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned v, unsigned* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  unsigned long long s = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < THREADS / 32; ++w) s += red[w];
+  return s;
+}
+
+// ---- inverse pass 2: rows (along x) + step 3 ----------------------------------
+// grid ceil(M N / LINES); a block owns LINES rows (l, y) of the X grid, loops over
+// the frequencies, transforms V and u rows and accumulates the least-squares sums.
+template <typename R, int N>
+__global__ void __launch_bounds__(THREADS)
+k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restrict__ cols,
+                    const int* __restrict__ ncol, R* __restrict__ xi, R* __restrict__ cout,
+                    unsigned long long* __restrict__ ctr, const cx<R>* __restrict__ tw) {
+  constexpr int LINES = row_lines<N>() / 2 > 0 ? row_lines<N>() / 2 : 1;
+  constexpr int E = LINES * N;            // elements of one field
+  constexpr int PER = (E + THREADS - 1) / THREADS;
+  __shared__ cx<R> buf[2 * E];
+  __shared__ cx<R> tw_s[N];
+  __shared__ unsigned red[THREADS / 32];
+  load_twiddles<R, N>(tw_s, tw);
+  const int M = P.m;
+  const long long N2 = (long long)N * N;
+  const long long nrows = (long long)M * N;
+  const long long row0 = (long long)blockIdx.x * LINES;
+  const R scale = R(1.0 / (double)N2);
+  R num[PER], den[PER];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) { num[p] = R(0); den[p] = R(0); }
+  for (int om = 0; om < P.n_omega; ++om) {
+    for (int e = threadIdx.x; e < 2 * E; e += THREADS) buf[e] = czero<R>();
+    __syncthreads();
+    const int nc = ncol[om];
+    const int* cl = cols + om * N;
+    const int tot = 2 * LINES * nc;
+    for (int q = threadIdx.x; q < tot; q += THREADS) {
+      const int line = q / nc, c = q - line * nc;
+      const int f = line / LINES, b = line - f * LINES;
+      const long long r = row0 + b;
+      if (r < nrows) {
+        const long long l = r / N, i = r - l * N;
+        buf[line * N + cl[c]] = t2[(((long long)om * 2 + f) * M + l) * N2 + i * N + c];
+      }
+    }
+    __syncthreads();
+    fft_lines<R, N, true, 2 * LINES, THREADS, Lay::ROW>(buf, tw_s);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int e = threadIdx.x + p * THREADS;
+      if (e < E) {
+        const cx<R> v = scale * buf[e];
+        const cx<R> u = scale * buf[E + e];
+        num[p] += u.x * v.x + u.y * v.y;     // Re(conj(u) V)
+        den[p] += u.x * u.x + u.y * u.y;     // |u|^2
+      }
+    }
+    __syncthreads();
+  }
+  const R guard = R(P.eps_u * P.eps_u * P.n_omega);
+  const R inv_c02 = R(1.0 / (P.c0 * P.c0));
+  unsigned n_guard = 0, n_nan = 0;
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * THREADS;
+    if (e < E) {
+      const long long r = row0 + e / N;
+      if (r < nrows) {
+        const bool g = !(den[p] >= guard);
+        const R x = g ? R(0) : num[p] / den[p];
+        n_guard += g;
+        const long long o = r * N + (e % N);
+        xi[o] = x;
+        if (cout) {
+          const bool ok = x < inv_c02;
+          n_nan += !ok;
+          cout[o] = ok ? R(1) / sqrt(inv_c02 - x) : R(NAN);
+        }
+      }
+    }
+  }
+  const unsigned long long sg = block_sum_u64(n_guard, red);
+  __syncthreads();
+  const unsigned long long sn = block_sum_u64(n_nan, red);
+  if (threadIdx.x == 0) {
+    if (sg) atomicAdd(ctr + C_U_GUARD, sg);
+    if (sn) atomicAdd(ctr + C_NAN_C, sn);
+  }
+}
+
+template <typename R>
+__global__ void k_twiddles(cx<R>* tw, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) {
+    double s, c;
+    sincospi(-2.0 * (double)j / (double)n, &s, &c);
+    tw[j] = from_d<R>(make_double2(c, s));
+  }
+}
+
+template <typename R, int N>
+cudaError_t fwd_impl(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStream_t s, cudaEvent_t mid) {
+  constexpr int LINES = row_lines<N>();
+  const long long nrows = (long long)P.n_omega * P.m1 * N;
+  const long long nblk = (nrows + LINES - 1) / LINES;
+  k_fft_rows<R, N, false><<<(unsigned)nblk, THREADS, 0, s>>>(W, w.wt, nrows, w.tw, R(1));
+  if (mid) cudaEventRecord(mid, s);
+  const dim3 g2((N + Cfg<R>::TC - 1) / Cfg<R>::TC, (unsigned)(P.n_omega * P.m1));
+  k_fft_cols<R, N, false><<<g2, THREADS, 0, s>>>(w.wt, w.tw);
+  const long long modes = (long long)P.n_omega * N * N;
+  k_mode_norms<R><<<(unsigned)((modes + 255) / 256), 256, 0, s>>>(w.wt, w.norms, P.m1, (long long)N * N, modes);
+  return cudaGetLastError();
+}
+
+template <typename R, int N>
+cudaError_t rec_impl(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream_t s, cudaEvent_t mid) {
+  dim3 g1((N + Cfg<R>::TC - 1) / Cfg<R>::TC, P.m, 2 * P.n_omega);
+  k_ifft_cols_gather<R, N><<<g1, THREADS, 0, s>>>(P, w.prof, w.slot, w.cols, w.ncol, w.t2, w.tw);
+  if (mid) cudaEventRecord(mid, s);
+  constexpr int LINES = row_lines<N>() / 2 > 0 ? row_lines<N>() / 2 : 1;
+  const long long nrows = (long long)P.m * N;
+  k_ifft_rows_recover<R, N><<<(unsigned)((nrows + LINES - 1) / LINES), THREADS, 0, s>>>(
+      P, w.t2, w.cols, w.ncol, xi, c, w.ctr, w.tw);
+  return cudaGetLastError();
+}
+
+template <typename R, int N>
+cudaError_t dense_impl(cx<R>* in, cx<R>* out, long long planes, bool inverse, const cx<R>* tw, cudaStream_t s) {
+  constexpr int LINES = row_lines<N>();
+  const long long nrows = planes * N;
+  const unsigned nblk = (unsigned)((nrows + LINES - 1) / LINES);
+  const dim3 gc((N + Cfg<R>::TC - 1) / Cfg<R>::TC, (unsigned)planes);
+  if (!inverse) {
+    k_fft_rows<R, N, false><<<nblk, THREADS, 0, s>>>(in, out, nrows, tw, R(1));
+    k_fft_cols<R, N, false><<<gc, THREADS, 0, s>>>(out, tw);
+  } else {
+    k_fft_cols<R, N, true><<<gc, THREADS, 0, s>>>(in, tw);
+    k_fft_rows<R, N, true><<<nblk, THREADS, 0, s>>>(in, out, nrows, tw, R(1.0 / ((double)N * N)));
+  }
+  return cudaGetLastError();
+}
+
+#define FL_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256)
+
+}  // namespace
+
+bool fft_size_supported(int n) {
+#define FL_CASE(K) if (n == K) return true;
+  FL_SIZES(FL_CASE)
+#undef FL_CASE
+  return false;
+}
+
+template <typename R>
+cudaError_t launch_fft2_forward(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStream_t s,
+                                cudaEvent_t mid) {
+  switch (P.n) {
+#define FL_CASE(K) case K: return fwd_impl<R, K>(W, P, w, s, mid);
+    FL_SIZES(FL_CASE)
+#undef FL_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R>
+cudaError_t launch_recover(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream_t s, cudaEvent_t mid) {
+  switch (P.n) {
+#define FL_CASE(K) case K: return rec_impl<R, K>(P, w, xi, c, s, mid);
+    FL_SIZES(FL_CASE)
+#undef FL_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R>
+cudaError_t launch_fft2_dense(cx<R>* in, cx<R>* out, int n, long long planes, bool inverse, const cx<R>* tw,
+                              cudaStream_t s) {
+  switch (n) {
+#define FL_CASE(K) case K: return dense_impl<R, K>(in, out, planes, inverse, tw, s);
+    FL_SIZES(FL_CASE)
+#undef FL_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_fft2_dense<double>(double2*, double2*, int, long long, bool, const double2*, cudaStream_t);
+template cudaError_t launch_fft2_dense<float>(float2*, float2*, int, long long, bool, const float2*, cudaStream_t);
+
+template <typename R>
+cudaError_t launch_twiddles(cx<R>* tw, int n, cudaStream_t s) {
+  k_twiddles<R><<<(n + 255) / 256, 256, 0, s>>>(tw, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_fft2_forward<double>(const double2*, const Problem&, const Work<double>&, cudaStream_t,
+                                                 cudaEvent_t);
+template cudaError_t launch_fft2_forward<float>(const float2*, const Problem&, const Work<float>&, cudaStream_t,
+                                                cudaEvent_t);
+template cudaError_t launch_recover<double>(const Problem&, const Work<double>&, double*, double*, cudaStream_t,
+                                            cudaEvent_t);
+template cudaError_t launch_recover<float>(const Problem&, const Work<float>&, float*, float*, cudaStream_t,
+                                           cudaEvent_t);
+template cudaError_t launch_twiddles<double>(double2*, int, cudaStream_t);
+template cudaError_t launch_twiddles<float>(float2*, int, cudaStream_t);
+
+}  // namespace fl

@@ -1,0 +1,83 @@
+// Internal interface between the C-ABI layer (api.cu) and the kernel
+// translation units.  Not installed; the public interface is include/flatlayer.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace fl {
+
+constexpr int MAX_M1 = 32;      // data planes per problem (dual Gram is M1 x M1)
+constexpr int MAX_M = 64;       // X planes per problem
+constexpr int MAX_OMEGA = 64;   // frequencies per problem
+constexpr int MAX_N = 256;      // horizontal points per axis
+
+// Device counters (index into Work::ctr); summed over the call.
+enum Ctr {
+  C_MODES = 0, C_ACTIVE, C_ZEROED, C_GRAZING, C_ALPHA_FLOOR, C_ROOT_CAPPED,
+  C_U_GUARD, C_NAN_C, C_FP64_FALLBACK, C_NONFINITE, C_REFINE_ITERS, C_COLUMNS, C_COUNT
+};
+
+// Scalars of one problem, passed by value to every kernel.
+struct Problem {
+  int n, m, m1, n_omega;
+  int alpha_mode;     // 0: per-mode discrepancy, 1: given alpha per frequency
+  int max_iter;       // root-find iteration cap
+  int refine_iters;   // mixed precision: FP64 residual refinement sweeps
+  double period, z1, hz, c0;
+  double delta, tau, delta_floor, alpha_rel, eps_u;
+  double fp64_switch; // mixed precision: FP64 factor when alpha/tr(Gram) is below this
+  double zy[MAX_M1];
+  double omega[MAX_OMEGA];
+  double alpha_given[MAX_OMEGA];
+};
+
+// Workspace views (device pointers).  R = bulk real type (double / float).
+template <typename R> struct Work {
+  cx<R>* wt;        // [n_omega][M1][N][N] W~ (mode space)                      (aliases t2)
+  cx<R>* t2;        // [n_omega][2][M][N][N] y-inverse-transformed V~, U~ (compact columns)
+  cx<R>* prof;      // [n_omega][N*N][2][M] solved profiles V~, U~ of active modes
+  double* norms;    // [n_omega][N*N] ||b_nu||^2
+  int* slot;        // [n_omega][N*N] slot of an active mode or -1
+  int* act;         // [n_omega][N*N] active mode list (mode index, ascending)
+  int* cols;        // [n_omega][N] columns nu1 holding a nonzero mode
+  int* ncol;        // [n_omega]
+  int* count;       // [n_omega] active modes
+  double* dnu;      // [n_omega] delta_nu
+  unsigned long long* ctr;  // [C_COUNT]
+  const cx<R>* tw;  // [N] twiddles exp(-2 pi i j/N)
+  double* alpha_out;  // [n_omega][N*N] or null
+};
+
+size_t workspace_bytes(int n, int m, int m1, int n_omega, bool fp64);
+template <typename R> Work<R> carve(void* base, int n, int m, int m1, int n_omega);
+
+// Launchers (return the launch error).
+// `mid` (may be null) is recorded on `s` between the two kernels of the stage
+template <typename R>
+cudaError_t launch_fft2_forward(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStream_t s,
+                                cudaEvent_t mid = nullptr);
+template <typename R>
+cudaError_t launch_classify(const Problem& P, const Work<R>& w, cudaStream_t s);
+cudaError_t launch_solve_fp64(const Problem& P, const Work<double>& w, cudaStream_t s);
+cudaError_t launch_solve_mixed(const Problem& P, const Work<float>& w, cudaStream_t s);
+template <typename R>
+cudaError_t launch_recover(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream_t s,
+                           cudaEvent_t mid = nullptr);
+template <typename R>
+cudaError_t launch_twiddles(cx<R>* tw, int n, cudaStream_t s);
+// dense 2D FFT of `planes` N x N planes: forward (unnormalised) in -> out, or
+// inverse (with 1/N^2) transforming `in` in place along y, then in -> out along x
+template <typename R>
+cudaError_t launch_fft2_dense(cx<R>* in, cx<R>* out, int n, long long planes, bool inverse, const cx<R>* tw,
+                              cudaStream_t s);
+// forward data generator (single scattering): W = F^-1[ A_nu F[omega^2 xi u0] ]
+template <typename R>
+cudaError_t launch_forward_born(const Problem& P, const R* xi, cx<R>* src, cx<R>* W, const cx<R>* tw,
+                                cudaStream_t s);
+
+bool fft_size_supported(int n);
+
+}  // namespace fl

@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads and exports every entry point its header
+declares; host-only entry points behave as documented (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "flatlayer.h")
+
+
+@pytest.fixture(scope="module")
+def abi():
+    from paper_1911_10487_gb300 import build
+    build.build()
+    from paper_1911_10487_gb300 import _abi
+    return _abi
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fs_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_expected_entry_points(abi):
+    assert declared_functions() == sorted(abi.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(abi):
+    L = C.CDLL(abi.library_path())
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_version_and_defaults(abi):
+    assert "sm_103a" in abi.fs_version()
+    o = abi.fs_default_options()
+    assert (o.tau, o.delta_floor, o.alpha_rel, o.eps_u) == (2.0, 1e-5, 1e-6, 1e-8)
+    assert (o.alpha_mode, o.max_iter, o.refine_iters, o.fp64_switch, o.stage_timing) == (0, 100, 3, 1e-5, 0)
+    assert abi.lib().fs_default_options(None) == abi.FS_EINVAL
+
+
+def test_workspace_size_scales(abi):
+    g = abi.make_geometry(32, 16, 0.2, 1.0, [1.2 + 0.05 * k for k in range(8)])
+    b64 = abi.fs_workspace_size(g, 1, abi.FS_FP64)
+    b32 = abi.fs_workspace_size(g, 1, abi.FS_MIXED)
+    assert b64 > b32 > 0
+    assert abi.fs_workspace_size(g, 2, abi.FS_FP64) > b64
+
+
+def test_null_context_is_rejected_without_gpu(abi):
+    g = abi.make_geometry(32, 16, 0.2, 1.0, [1.3])
+    om = (C.c_double * 1)(1.0)
+    st = abi.lib().fs_reconstruct(None, C.byref(g), 0, None, om, 1, 0.0, 1.0, None, None, None, None)
+    assert st == abi.FS_EINVAL
+    assert abi.lib().fs_get_report(None, None) == abi.FS_EINVAL
+    assert abi.fs_last_error(None) == "null context"
+    abi.fs_destroy(None)
