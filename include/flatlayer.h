@@ -86,8 +86,8 @@ typedef struct {
                           every non-grazing mode solved (default 0)                       */
   const double* alpha_given; /* host, n_omega values, read when alpha_mode == 1           */
   int max_iter;        /* root-find iteration cap (default 100)                           */
-  int refine_iters;    /* FS_MIXED: FP64 refinement sweeps (default 3)                    */
-  double fp64_switch;  /* FS_MIXED: FP64 factorisation below alpha/tr = this (default 1e-5) */
+  int refine_iters;    /* FS_MIXED: cap on FP64 refinement sweeps (default 8)             */
+  double fp64_switch;  /* FS_MIXED: FP64 factorisation below alpha/tr = this (default 1e-4) */
   int stage_timing;    /* 1: record CUDA events between the kernels of fs_reconstruct; the
                           durations appear in fs_report.ms_stage (default 0)              */
 } fs_options;

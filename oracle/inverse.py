@@ -100,9 +100,11 @@ def solve_modes(Wt, omega, k0, g: Geometry, delta_nu, opts: Options, alpha_fixed
         beta = np.einsum("yxkj,yxk->yxj", U.conj(), b)
         perp2 = np.maximum(bnorm ** 2 - np.sum(np.abs(beta) ** 2, axis=-1), 0.0)
         s2 = s ** 2
-        act = (bnorm > delta_nu) & ~graz[rows]
+        # a mode whose matrix underflowed to zero carries no information: V~ = 0
+        usable = ~graz[rows] & (np.sum(s ** 2, axis=-1) > 0)
+        act = (bnorm > delta_nu) & usable
         if alpha_fixed is not None:
-            act = ~graz[rows]
+            act = usable
         a = np.full(bnorm.shape, np.inf)
         if np.any(act):
             if alpha_fixed is not None:

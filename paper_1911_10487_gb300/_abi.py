@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "F
 # every function declared in include/flatlayer.h
 EXPORTS = ("fs_version", "fs_default_options", "fs_create", "fs_destroy", "fs_last_error",
            "fs_workspace_size", "fs_reconstruct", "fs_reconstruct_host", "fs_forward_born",
-           "fs_get_report")
+           "fs_get_report", "fs_measure_alu_peaks")
 
 
 class fs_geometry(C.Structure):
@@ -46,6 +46,12 @@ class fs_report(C.Structure):
         d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "ms_stage"}
         d["ms_stage"] = dict(zip(STAGES, [float(x) for x in self.ms_stage]))
         return d
+
+
+class fs_alu_peaks(C.Structure):
+    _fields_ = [("fp64_tflops", C.c_double), ("fp32_tflops", C.c_double),
+                ("fp64_fma_cycles_1lane", C.c_double), ("fp64_fma_cycles_warp", C.c_double),
+                ("fp64_div_cycles_1lane", C.c_double), ("sms", C.c_int), ("clock_mhz", C.c_double)]
 
 
 class FlatLayerError(RuntimeError):
@@ -86,6 +92,8 @@ def lib():
                                           C.POINTER(fs_options), vp, vp]
         L.fs_forward_born.restype = ip
         L.fs_forward_born.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, vp]
+        L.fs_measure_alu_peaks.restype = ip
+        L.fs_measure_alu_peaks.argtypes = [ip, C.POINTER(fs_alu_peaks)]
         L.fs_get_report.restype = ip
         L.fs_get_report.argtypes = [vp, C.POINTER(fs_report)]
         _lib = L
@@ -184,3 +192,11 @@ def make_options(**kw) -> fs_options:
         else:
             setattr(o, k, v)
     return o
+
+
+def fs_measure_alu_peaks(device: int = 0) -> dict:
+    r = fs_alu_peaks()
+    st = lib().fs_measure_alu_peaks(int(device), C.byref(r))
+    if st != 0:
+        raise FlatLayerError(st, "fs_measure_alu_peaks")
+    return {k: getattr(r, k) for k, _ in r._fields_}

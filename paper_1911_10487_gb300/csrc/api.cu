@@ -6,6 +6,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 #include <new>
+#include <math.h>
 #include <string.h>
 
 #include <cuda_runtime.h>
@@ -64,7 +65,8 @@ fs_status cuda_fail(fs_ctx* ctx, cudaError_t e, const char* where) {
 }
 
 struct Layout {
-  size_t t12, prof, norms, slot, act, cols, ncol, count, dnu, total;
+  size_t t12, prof, norms, partial, slot, act, cols, ncol, count, dnu, total;
+  int n_partial;
 };
 
 Layout layout(int n, int m, int m1, int n_omega, bool fp64) {
@@ -76,6 +78,8 @@ Layout layout(int n, int m, int m1, int n_omega, bool fp64) {
   L.t12 = off; off = align_up(off + cxs * (a > b ? a : b));  // W~, later the y-inverse pass output
   L.prof = off; off = align_up(off + cxs * (size_t)n_omega * N2 * 2 * m);
   L.norms = off; off = align_up(off + 8 * (size_t)n_omega * N2);
+  L.n_partial = (int)((N2 + 255) / 256);
+  L.partial = off; off = align_up(off + 8 * (size_t)n_omega * L.n_partial);
   L.slot = off; off = align_up(off + 4 * (size_t)n_omega * N2);
   L.act = off; off = align_up(off + 4 * (size_t)n_omega * N2);
   L.cols = off; off = align_up(off + 4 * (size_t)n_omega * n);
@@ -117,7 +121,7 @@ fs_status validate(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, int n_o
       for (int j = 0; j < n_omega; ++j)
         if (!(o->alpha_given[j] > 0.0)) return fail(ctx, FS_EINVAL, "alpha_given[%d] must be > 0", j);
     }
-    if (o->max_iter < 1 || o->refine_iters < 0) return fail(ctx, FS_EINVAL, "max_iter >= 1, refine_iters >= 0");
+    if (o->max_iter < 1 || o->refine_iters < 1) return fail(ctx, FS_EINVAL, "max_iter >= 1, refine_iters >= 1");
   }
   return FS_OK;
 }
@@ -135,6 +139,12 @@ Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, dou
   for (int j = 0; j < n_omega; ++j) {
     P.omega[j] = omega[j];
     P.alpha_given[j] = (o.alpha_mode == 1) ? o.alpha_given[j] : 0.0;
+    // |m|^2 = (k0 L / 2 pi)^2 within a relative 1e-9 (k_z = 0: excluded modes)
+    const double sL = omega[j] / c0 * g->period / (2.0 * M_PI);
+    const double s2 = sL * sL;
+    const double lo = ceil(s2 - 1e-9 * s2), hi = floor(s2 + 1e-9 * s2);
+    P.graz_lo[j] = lo > 1e9 ? 1000000001 : (int)lo;  // |m|^2 <= 2 (N/2)^2 never reaches 1e9
+    P.graz_hi[j] = hi > 1e9 ? 1000000000 : (int)hi;
   }
   return P;
 }
@@ -178,6 +188,8 @@ Work<R> carve_work(void* base, const Layout& L, unsigned long long* ctr, const c
   w.t2 = (cx<R>*)(b + L.t12);
   w.prof = (cx<R>*)(b + L.prof);
   w.norms = (double*)(b + L.norms);
+  w.partial = (double*)(b + L.partial);
+  w.n_partial = L.n_partial;
   w.slot = (int*)(b + L.slot);
   w.act = (int*)(b + L.act);
   w.cols = (int*)(b + L.cols);
@@ -238,8 +250,8 @@ fs_status fs_default_options(fs_options* o) {
   o->alpha_mode = 0;
   o->alpha_given = nullptr;
   o->max_iter = 100;
-  o->refine_iters = 3;
-  o->fp64_switch = 1e-5;
+  o->refine_iters = 8;
+  o->fp64_switch = 1e-4;
   o->stage_timing = 0;
   return FS_OK;
 }

@@ -77,20 +77,33 @@ k_fft_cols(cx<R>* __restrict__ data, const cx<R>* __restrict__ tw) {
 }
 
 // ---- per-mode norms ||W~_nu||^2 = sum_k |W~_k(nu)|^2, summed in plane order ------
+// grid (n_partial, n_omega), one mode per thread; each block also writes the sum
+// of its modes' norms (fixed-order tree) for ||W||.
+constexpr int NORM_T = 256;
+
 template <typename R>
-__global__ void k_mode_norms(const cx<R>* __restrict__ wt, double* __restrict__ norms, int m1, long long N2,
-                             long long total) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long om = e / N2, nu = e - om * N2;
-    const cx<R>* p = wt + om * m1 * N2 + nu;
-    double acc = 0.0;
+__global__ void __launch_bounds__(NORM_T)
+k_mode_norms(const cx<R>* __restrict__ wt, double* __restrict__ norms, double* __restrict__ partial, int m1,
+             int N2) {
+  __shared__ double red[NORM_T];
+  const int om = blockIdx.y;
+  const int nu = blockIdx.x * NORM_T + threadIdx.x;
+  double acc = 0.0;
+  if (nu < N2) {
+    const cx<R>* p = wt + (long long)om * m1 * N2 + nu;
     for (int k = 0; k < m1; ++k) {
-      const cx<R> v = p[k * N2];
+      const cx<R> v = p[(long long)k * N2];
       acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
     }
-    norms[e] = acc;
+    norms[(long long)om * N2 + nu] = acc;
   }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = NORM_T / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[(long long)om * gridDim.x + blockIdx.x] = red[0];
 }
 
 // ---- inverse pass 1: gather active profiles, columns (along y) ----------------
@@ -265,8 +278,8 @@ cudaError_t fwd_impl(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStr
   if (mid) cudaEventRecord(mid, s);
   const dim3 g2((N + Cfg<R>::TC - 1) / Cfg<R>::TC, (unsigned)(P.n_omega * P.m1));
   k_fft_cols<R, N, false><<<g2, THREADS, 0, s>>>(w.wt, w.tw);
-  const long long modes = (long long)P.n_omega * N * N;
-  k_mode_norms<R><<<(unsigned)((modes + 255) / 256), 256, 0, s>>>(w.wt, w.norms, P.m1, (long long)N * N, modes);
+  const dim3 gn((unsigned)w.n_partial, (unsigned)P.n_omega);
+  k_mode_norms<R><<<gn, NORM_T, 0, s>>>(w.wt, w.norms, w.partial, P.m1, N * N);
   return cudaGetLastError();
 }
 

@@ -25,10 +25,9 @@ __global__ void k_source(Problem P, const R* __restrict__ xi, cx<R>* __restrict_
     const long long r = e - om * per;
     const int l = (int)(r / N2);
     const double k0 = P.omega[om] / P.c0;
-    const double w2 = P.omega[om] * P.omega[om];
     double s, c;
     sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s, &c);
-    const double x = w2 * (double)xi[r];
+    const double x = (double)xi[r];  // V = xi u0; omega^2 sits in the kernel factor
     src[e] = from_d<R>(make_double2(x * c, x * s));
   }
 }
@@ -52,10 +51,10 @@ __global__ void k_apply_data(Problem P, const cx<R>* __restrict__ vt, cx<R>* __r
     const int i2 = nu / N, i1 = nu - i2 * N;
     const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
     const double k0 = P.omega[om] / P.c0;
-    const double sL = k0 * P.period / (2.0 * M_PI);
-    const double msq = (double)(m1 * m1 + m2 * m2);
+    const int msq_i = m1 * m1 + m2 * m2;
+    const double msq = (double)msq_i;
     cx<R>* out = wt + (long long)om * P.m1 * N2 + nu;
-    if (fabs(msq - sL * sL) <= 1e-9 * sL * sL) {  // grazing: excluded
+    if (msq_i >= P.graz_lo[om] && msq_i <= P.graz_hi[om]) {  // grazing: excluded
       for (int k = 0; k < P.m1; ++k) out[k * N2] = czero<R>();
       continue;
     }

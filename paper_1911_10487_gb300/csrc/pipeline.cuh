@@ -32,6 +32,9 @@ struct Problem {
   double zy[MAX_M1];
   double omega[MAX_OMEGA];
   double alpha_given[MAX_OMEGA];
+  // grazing modes |nu| = k0: integer window [graz_lo, graz_hi] of m1^2 + m2^2, the
+  // integers within a relative 1e-9 of (k0 L / 2 pi)^2 (empty when lo > hi)
+  int graz_lo[MAX_OMEGA], graz_hi[MAX_OMEGA];
 };
 
 // Workspace views (device pointers).  R = bulk real type (double / float).
@@ -40,6 +43,8 @@ template <typename R> struct Work {
   cx<R>* t2;        // [n_omega][2][M][N][N] y-inverse-transformed V~, U~ (compact columns)
   cx<R>* prof;      // [n_omega][N*N][2][M] solved profiles V~, U~ of active modes
   double* norms;    // [n_omega][N*N] ||b_nu||^2
+  double* partial;  // [n_omega][n_partial] block sums of norms (fixed order)
+  int n_partial;
   int* slot;        // [n_omega][N*N] slot of an active mode or -1
   int* act;         // [n_omega][N*N] active mode list (mode index, ascending)
   int* cols;        // [n_omega][N] columns nu1 holding a nonzero mode

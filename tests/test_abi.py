@@ -7,7 +7,8 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "flatlayer.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
 
 
 @pytest.fixture(scope="module")
@@ -19,9 +20,11 @@ def abi():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(fs_[a-z_0-9]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(fs_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_expected_entry_points(abi):
@@ -38,7 +41,7 @@ def test_version_and_defaults(abi):
     assert "sm_103a" in abi.fs_version()
     o = abi.fs_default_options()
     assert (o.tau, o.delta_floor, o.alpha_rel, o.eps_u) == (2.0, 1e-5, 1e-6, 1e-8)
-    assert (o.alpha_mode, o.max_iter, o.refine_iters, o.fp64_switch, o.stage_timing) == (0, 100, 3, 1e-5, 0)
+    assert (o.alpha_mode, o.max_iter, o.refine_iters, o.fp64_switch, o.stage_timing) == (0, 100, 8, 1e-4, 0)
     assert abi.lib().fs_default_options(None) == abi.FS_EINVAL
 
 

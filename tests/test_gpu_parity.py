@@ -50,12 +50,14 @@ def run_gpu(rc, g, om, W, delta, precision="fp64", **opts):
 def check_against_oracle(res, ref, tol, alpha_tol=1e-7):
     xi, c, alpha, rep = res
     err = rel_l2(xi, ref.xi)
-    assert err <= tol, f"xi rel L2 {err:.3e} > {tol:.1e}"
     act_gpu = np.isfinite(alpha)
-    assert np.array_equal(act_gpu, ref.active), "active mode sets differ"
-    if ref.active.any():
-        ra = np.abs(alpha[ref.active] / ref.alpha[ref.active] - 1)
-        assert ra.max() <= alpha_tol, f"alpha rel err {ra.max():.3e}"
+    same = np.array_equal(act_gpu, ref.active)
+    ra = np.abs(alpha[ref.active] / ref.alpha[ref.active] - 1) if same and ref.active.any() else np.zeros(1)
+    print(f"xi rel L2 {err:.3e}; active gpu/oracle {act_gpu.sum()}/{ref.active.sum()}; "
+          f"alpha max rel err {ra.max():.3e}; nan in xi {np.isnan(xi).sum()}; report {rep}")
+    assert err <= tol, f"xi rel L2 {err:.3e} > {tol:.1e}"
+    assert same, "active mode sets differ"
+    assert ra.max() <= alpha_tol, f"alpha rel err {ra.max():.3e}"
     assert rep["n_active"] == int(ref.active.sum())
     assert rep["n_grazing"] == ref.counts["grazing"]
     assert rep["n_zeroed"] == ref.counts["zeroed"]
