@@ -178,27 +178,22 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned v, unsigned
 
 // ---- inverse pass 2: rows (along x) + step 3 ----------------------------------
 // grid ceil(M N / LINES); a block owns LINES rows (l, y) of the X grid, loops over
-// the frequencies, transforms V and u rows and accumulates the least-squares sums.
-template <typename R, int N>
-__global__ void __launch_bounds__(THREADS)
-k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restrict__ cols,
-                    const int* __restrict__ ncol, R* __restrict__ xi, R* __restrict__ cout,
-                    unsigned long long* __restrict__ ctr, const cx<R>* __restrict__ tw) {
+// the frequencies, transforms V and u rows and accumulates the least-squares sums
+// in the accumulator type A.  Returns (block-uniform) whether any sum overflowed.
+template <typename R, int N, typename A>
+__device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __restrict__ t2,
+                                             const int* __restrict__ cols, const int* __restrict__ ncol,
+                                             cx<R>* buf, const cx<R>* tw_s, A* num, A* den) {
   constexpr int LINES = row_lines<N>() / 2 > 0 ? row_lines<N>() / 2 : 1;
-  constexpr int E = LINES * N;            // elements of one field
+  constexpr int E = LINES * N;
   constexpr int PER = (E + THREADS - 1) / THREADS;
-  __shared__ cx<R> buf[2 * E];
-  __shared__ cx<R> tw_s[N];
-  __shared__ unsigned red[THREADS / 32];
-  load_twiddles<R, N>(tw_s, tw);
   const int M = P.m;
   const long long N2 = (long long)N * N;
   const long long nrows = (long long)M * N;
   const long long row0 = (long long)blockIdx.x * LINES;
   const R scale = R(1.0 / (double)N2);
-  R num[PER], den[PER];
 #pragma unroll
-  for (int p = 0; p < PER; ++p) { num[p] = R(0); den[p] = R(0); }
+  for (int p = 0; p < PER; ++p) { num[p] = A(0); den[p] = A(0); }
   for (int om = 0; om < P.n_omega; ++om) {
     for (int e = threadIdx.x; e < 2 * E; e += THREADS) buf[e] = czero<R>();
     __syncthreads();
@@ -222,11 +217,44 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
       if (e < E) {
         const cx<R> v = scale * buf[e];
         const cx<R> u = scale * buf[E + e];
-        num[p] += u.x * v.x + u.y * v.y;     // Re(conj(u) V)
-        den[p] += u.x * u.x + u.y * u.y;     // |u|^2
+        num[p] += (A)u.x * (A)v.x + (A)u.y * (A)v.y;  // Re(conj(u) V)
+        den[p] += (A)u.x * (A)u.x + (A)u.y * (A)u.y;  // |u|^2
       }
     }
     __syncthreads();
+  }
+  bool bad = false;
+#pragma unroll
+  for (int p = 0; p < PER; ++p) bad |= !(isfinite(num[p]) && isfinite(den[p]));
+  return __syncthreads_or(bad) != 0;
+}
+
+template <typename R, int N>
+__global__ void __launch_bounds__(THREADS)
+k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restrict__ cols,
+                    const int* __restrict__ ncol, R* __restrict__ xi, R* __restrict__ cout,
+                    unsigned long long* __restrict__ ctr, const cx<R>* __restrict__ tw) {
+  constexpr int LINES = row_lines<N>() / 2 > 0 ? row_lines<N>() / 2 : 1;
+  constexpr int E = LINES * N;            // elements of one field
+  constexpr int PER = (E + THREADS - 1) / THREADS;
+  __shared__ cx<R> buf[2 * E];
+  __shared__ cx<R> tw_s[N];
+  __shared__ unsigned red[THREADS / 32];
+  load_twiddles<R, N>(tw_s, tw);
+  const long long nrows = (long long)P.m * N;
+  const long long row0 = (long long)blockIdx.x * LINES;
+  R num[PER], den[PER];
+  if (recover_pass<R, N, R>(P, t2, cols, ncol, buf, tw_s, num, den)) {
+    // the sums left the range of R (|u| |V| beyond FP32 for huge evanescent
+    // profiles): redo this block with FP64 sums; xi itself is in range
+    double nd[PER], dd[PER];
+    recover_pass<R, N, double>(P, t2, cols, ncol, buf, tw_s, nd, dd);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const bool g = !(dd[p] >= P.eps_u * P.eps_u * P.n_omega);
+      num[p] = g ? R(0) : R(nd[p] / dd[p]);
+      den[p] = g ? R(0) : R(1);
+    }
   }
   const R guard = R(P.eps_u * P.eps_u * P.n_omega);
   const R inv_c02 = R(1.0 / (P.c0 * P.c0));

@@ -170,7 +170,7 @@ __device__ __forceinline__ double rcp64(double x) {
 }
 
 template <typename T> __device__ __forceinline__ T rcp(T x);
-template <> __device__ __forceinline__ float rcp<float>(float x) { return 1.0f / x; }
+template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }  // ~2 ulp
 template <> __device__ __forceinline__ double rcp<double>(double x) { return rcp64(x); }
 
 __device__ __forceinline__ double2 warp_sum(double2 v) {
@@ -226,7 +226,7 @@ struct Shared {
   double d[MAX_M1], e[MAX_M1];     // tridiagonal T (FP64 route: of G; scaled by 1/tr after the factor)
   float d32[MAX_M1], e32[MAX_M1];  // T / tr in FP32
   float2 c32[MAX_M1], cz[MAX_M1];
-  double tr, sb, dnu, lo, hi, a_s, red[8];  // a_s = alpha / tr
+  double tr, sb, inv_sb, dnu, lo, hi, a_s, red[8];  // a_s = alpha / tr
   int fp64;
 };
 
@@ -366,7 +366,7 @@ __device__ void apply_QH(Shared& S, int n, const double2* in, double s, cx<W>* o
     for (int j = 0; j + 2 < n; ++j) {
       const W beta = (W)K.beta[j];
       if (beta == W(0)) continue;
-      const bool mine = r > j;
+      const bool mine = r > j && r < n;  // lanes of the reflector's rows only
       const cx<W> v = mine ? from_d<W>(to_d(K.V[j][r - j - 1])) : czero<W>();
       const cx<W> dot = warp_sum(cmul_conj_a(v, x));  // v^H x
       if (mine) x = x - beta * (v * dot);
@@ -386,7 +386,7 @@ __device__ void apply_Q(Shared& S, int n, const cx<W>* in, double s, double2* ou
     for (int j = n - 3; j >= 0; --j) {
       const W beta = (W)K.beta[j];
       if (beta == W(0)) continue;
-      const bool mine = r > j;
+      const bool mine = r > j && r < n;  // lanes of the reflector's rows only
       const cx<W> v = mine ? from_d<W>(to_d(K.V[j][r - j - 1])) : czero<W>();
       const cx<W> dot = warp_sum(cmul_conj_a(v, x));
       if (mine) x = x - beta * (v * dot);
@@ -570,8 +570,7 @@ __device__ double block_sum(Shared& S, double v) {
 
 // mixed precision: y += (QD)(T/tr + a_s I)^-1 (QD)^H r / tr, returns ||dy||^2/||y||^2
 __device__ double refine_step(Shared& S, int n) {
-  const double is = 1.0 / S.sb;  // (precomputed scale would do; one FP64 division per sweep)
-  qd_h(S, n, S.r, is, S.c32);
+  qd_h(S, n, S.r, S.inv_sb, S.c32);
   if (threadIdx.x == 0 && !tri_solve<float>(S.d32, S.e32, n, (float)S.a_s, S.c32, S.cz)) S.fp64 = 1;
   __syncthreads();
   if (S.fp64) return 0.0;  // FP32 model not positive definite here: caller takes the FP64 route
@@ -704,6 +703,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     if (threadIdx.x == 0) {
       S.tr = tr;
       S.sb = sqrt(bb);
+      S.inv_sb = 1.0 / S.sb;
       S.dnu = dnu_arr[om];
       S.lo = P.alpha_rel * tr;
       S.hi = fmax(tr * S.dnu / (S.sb - S.dnu), S.lo);
@@ -721,7 +721,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       gram<float>(S, n, m);
       tridiagonalize<float>(S, n);
       form_QD(S, n);
-      qd_h(S, n, S.b, 1.0 / S.sb, S.c32);
+      qd_h(S, n, S.b, S.inv_sb, S.c32);
       if (threadIdx.x == 0) {
         const double target = (S.dnu / S.sb) * (S.dnu / S.sb);
         const double lo = P.alpha_rel, hi = S.hi / S.tr;

@@ -31,7 +31,7 @@ def case(name: str, delta: float = 0.01, method: str = "gmres"):
         "r96": (96, 24, 17, [5 * np.pi]),
         "r8": (8, 3, 1, [np.pi]),
         "r192": (192, 9, 4, [3 * np.pi]),
-        "r256": (256, 6, 2, [2 * np.pi, 3 * np.pi]),
+        "r256": (256, 6, 6, [2 * np.pi, 3 * np.pi]),
     }[name]
     n, m, m1, om = spec
     g = geometry(n, m, m1)
