@@ -168,6 +168,32 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* geom, fs_precision
 fs_status fs_forward_born(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* xi,
                           const double* omega, int n_omega, double c0, void* W);
 
+/* Size of the device array that holds every intermediate of fs_reconstruct_static. */
+#define FS_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* fs_reconstruct without any device allocation.  The paper has no counterpart:
+   this entry point exists for callers that cannot call cudaMalloc -- a host
+   framework that hands out all device memory from its own pool, or a real-time
+   or embedded caller that must not grow its memory or synchronise the device
+   once it is running (a cudaMalloc may do both).  It takes no context and
+   allocates nothing: the caller passes W, xi and c (same layouts, precisions and
+   results as fs_reconstruct; no alpha_out, no report), and every intermediate
+   lives in one device array of FS_STATIC_SCRATCH_BYTES (32 MiB) that every GPU
+   which loads the library holds until the process exits.  `stream` is a
+   cudaStream_t (NULL = the legacy default stream); the call is asynchronous on it.
+   A problem whose intermediates do not fit returns FS_EUNSUPPORTED before any
+   work is enqueued: for one frequency, 128 x 128 x 32 with 32 data planes fits in
+   FS_MIXED, 128 x 128 x 64 does not, and 64 x 64 x 64 with 32 planes fits in FS_FP64.
+   The first call on a device looks up the device address of that array
+   (cudaGetSymbolAddress) and keeps it; make that first call before any stream
+   capture.  Every call uses the same array: calls whose work overlaps on the GPU
+   (different streams, or different host threads without ordering) race and
+   corrupt each other's results, so serialise them.  Other errors as for
+   fs_reconstruct (FS_EINVAL, FS_EUNSUPPORTED, FS_ECUDA), without a message. */
+fs_status fs_reconstruct_static(const fs_geometry* geom, fs_precision prec, const void* W, const double* omega,
+                                int n_omega, double delta, double c0, const fs_options* opts, void* xi, void* c,
+                                void* stream);
+
 /* Synchronise the context's stream and return the counters of the last
    fs_reconstruct call. */
 fs_status fs_get_report(fs_ctx* ctx, fs_report* report);

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "F
 # every function declared in include/flatlayer.h
 EXPORTS = ("fs_version", "fs_default_options", "fs_create", "fs_destroy", "fs_last_error",
            "fs_workspace_size", "fs_reconstruct", "fs_reconstruct_host", "fs_forward_born",
-           "fs_get_report", "fs_measure_alu_peaks")
+           "fs_get_report", "fs_measure_alu_peaks", "fs_reconstruct_static")
 
 
 class fs_geometry(C.Structure):
@@ -92,6 +92,9 @@ def lib():
                                           C.POINTER(fs_options), vp, vp]
         L.fs_forward_born.restype = ip
         L.fs_forward_born.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, vp]
+        L.fs_reconstruct_static.restype = ip
+        L.fs_reconstruct_static.argtypes = [C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, C.c_double,
+                                            C.POINTER(fs_options), vp, vp, vp]
         L.fs_measure_alu_peaks.restype = ip
         L.fs_measure_alu_peaks.argtypes = [ip, C.POINTER(fs_alu_peaks)]
         L.fs_get_report.restype = ip
@@ -200,3 +203,11 @@ def fs_measure_alu_peaks(device: int = 0) -> dict:
     if st != 0:
         raise FlatLayerError(st, "fs_measure_alu_peaks")
     return {k: getattr(r, k) for k, _ in r._fields_}
+
+
+def fs_reconstruct_static(geom, prec, W_ptr, omega, delta, c0, opts, xi_ptr, c_ptr=None, stream=0) -> int:
+    """Allocation-free reconstruction (see include/flatlayer.h); returns the fs_status."""
+    om = (C.c_double * len(omega))(*[float(x) for x in omega])
+    return lib().fs_reconstruct_static(C.byref(geom), int(prec), C.c_void_p(W_ptr), om, len(omega), float(delta),
+                                       float(c0), C.byref(opts) if opts is not None else None,
+                                       C.c_void_p(xi_ptr), C.c_void_p(c_ptr or None), C.c_void_p(stream or None))
