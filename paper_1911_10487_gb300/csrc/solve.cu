@@ -41,6 +41,22 @@
 
 #include "pipeline.cuh"
 
+// FL_PHASE_TIMING (development builds only) records clock64() at phase
+// boundaries of the first mode of block 0; it is compiled out otherwise.
+#ifdef FL_PHASE_TIMING
+__device__ long long g_phase[24];
+extern "C" int fs_debug_phases(long long* out) {
+  return (int)cudaMemcpyFromSymbol(out, g_phase, sizeof(long long) * 24);
+}
+#define FL_MARK(i) \
+  if (blockIdx.x == 0 && (threadIdx.x & 31) == 0 && item == 0) g_phase[i] = clock64()
+#define FL_MARK_S(i) \
+  if (S.tflag && (threadIdx.x & 31) == 0) g_phase[i] = clock64()
+#else
+#define FL_MARK(i)
+#define FL_MARK_S(i)
+#endif
+
 namespace fl {
 
 namespace {
@@ -184,13 +200,6 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ float2 warp_sum(float2 v) {
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-  }
-  return v;
-}
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -205,6 +214,62 @@ __device__ __forceinline__ double2 exp_ikz(double2 kz, double d) {
 }
 
 // ------------------------------------------------------------------------------
+// two-float arithmetic: a value is hi + lo (|lo| <= ulp(hi)/2); sums and products
+// use the error-free transformations TwoSum (Knuth) and TwoProd (with fma), which
+// gives about 48 significant bits on the FP32 pipe.  The mixed route computes its
+// refinement residual and V~ = A^H y this way: FP64-class accuracy without the
+// FP64 pipe, which runs at 1/64 of the FP32 rate on this GPU.
+// ------------------------------------------------------------------------------
+struct ff { float hi, lo; };
+struct ffc { ff re, im; };
+
+__device__ __forceinline__ ff ff_from(double x) {
+  ff r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ double ff_to(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // requires |a| >= |b| (or a == 0)
+  ff r;
+  r.hi = a + b;
+  r.lo = b - (r.hi - a);
+  return r;
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  return fast_two_sum(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ffc ffc_from(double2 z) { return ffc{ff_from(z.x), ff_from(z.y)}; }
+__device__ __forceinline__ double2 ffc_to(ffc z) { return make_double2(ff_to(z.re), ff_to(z.im)); }
+__device__ __forceinline__ ffc ffc_zero() { return ffc{ff{0.f, 0.f}, ff{0.f, 0.f}}; }
+__device__ __forceinline__ ffc ffc_add(ffc a, ffc b) { return ffc{ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
+__device__ __forceinline__ ffc ffc_sub(ffc a, ffc b) { return ffc{ff_add(a.re, ff_neg(b.re)), ff_add(a.im, ff_neg(b.im))}; }
+__device__ __forceinline__ ffc ffc_mul(ffc a, ffc b) {
+  return ffc{ff_add(ff_mul(a.re, b.re), ff_neg(ff_mul(a.im, b.im))), ff_add(ff_mul(a.re, b.im), ff_mul(a.im, b.re))};
+}
+__device__ __forceinline__ ffc ffc_conj_mul(ffc a, ffc b) {  // conj(a) b
+  return ffc{ff_add(ff_mul(a.re, b.re), ff_mul(a.im, b.im)), ff_add(ff_mul(a.re, b.im), ff_neg(ff_mul(a.im, b.re)))};
+}
+__device__ __forceinline__ ffc ffc_shfl_xor(ffc a, int m) {
+  ffc r;
+  r.re.hi = __shfl_xor_sync(0xffffffffu, a.re.hi, m);
+  r.re.lo = __shfl_xor_sync(0xffffffffu, a.re.lo, m);
+  r.im.hi = __shfl_xor_sync(0xffffffffu, a.im.hi, m);
+  r.im.lo = __shfl_xor_sync(0xffffffffu, a.im.lo, m);
+  return r;
+}
+
+// ------------------------------------------------------------------------------
 // shared state of one block
 // ------------------------------------------------------------------------------
 template <typename B> struct Bulk {
@@ -216,23 +281,25 @@ template <typename B> struct Bulk {
 struct BulkF : Bulk<float> {
   float2 A[MAX_M1][MAX_M + 1];   // A_nu / sqrt(tr G) in FP32 (mixed precision)
   float2 Q[MAX_M1][MAX_M1 + 1];  // Q D formed explicitly (mixed precision)
+  float2 ts[MAX_M1][32];         // per-lane tridiagonal solves: scaled forward values
+  float tmu[MAX_M1][32];         //                              and multipliers
 };
 
 struct Shared {
   double2 A[MAX_M1][MAX_M + 1];  // A_nu in FP64
   union { Bulk<double> d; BulkF f; } u;
   double2 E[MAX_M1], Pz[MAX_M], b[MAX_M1], c[MAX_M1], y[MAX_M1], r[MAX_M1], z[MAX_M1];
-  double2 ph[MAX_M1], Vt[MAX_M], t[MAX_M], F[MAX_M], Bk[MAX_M];
+  double2 ph[MAX_M1], Vt[MAX_M], t[MAX_M], F[MAX_M], Bk[MAX_M], z64[MAX_M];
   double d[MAX_M1], e[MAX_M1];     // tridiagonal T (FP64 route: of G; scaled by 1/tr after the factor)
   float d32[MAX_M1], e32[MAX_M1];  // T / tr in FP32
-  float2 c32[MAX_M1], cz[MAX_M1];
+  float2 c32[MAX_M1], cz[MAX_M1], r32[MAX_M1];
+  ffc yh[MAX_M1], rh[MAX_M1], bh[MAX_M1], th[MAX_M], Ef[MAX_M1], Pf[MAX_M];  // two-float (mixed route)
   double tr, sb, inv_sb, dnu, lo, hi, a_s, red[8];  // a_s = alpha / tr
-  int fp64;
+  int fp64, tflag;
 };
 
 template <typename B> __device__ __forceinline__ Bulk<B>& bulk(Shared& s);
 template <> __device__ __forceinline__ Bulk<double>& bulk<double>(Shared& s) { return s.u.d; }
-template <> __device__ __forceinline__ Bulk<float>& bulk<float>(Shared& s) { return s.u.f; }
 
 // G = A A^H in precision B: FP64 from S.A, or FP32 from the scaled copy (G / tr)
 template <typename B>
@@ -396,70 +463,6 @@ __device__ void apply_Q(Shared& S, int n, const cx<W>* in, double s, double2* ou
   __syncwarp();
 }
 
-// Q D formed explicitly in FP32 (mixed precision): backward accumulation of the
-// reflectors on the identity, 4 threads per column, then column c times ph_c.
-__device__ void form_QD(Shared& S, int n) {
-  BulkF& K = S.u.f;
-  const int col = threadIdx.x >> 2, part = threadIdx.x & 3;
-  for (int e = threadIdx.x; e < n * n; e += ST) {
-    const int r = e / n, c = e - r * n;
-    K.Q[r][c] = make_float2(r == c ? 1.f : 0.f, 0.f);
-  }
-  __syncthreads();
-  for (int j = n - 3; j >= 0; --j) {
-    const float beta = K.beta[j];
-    if (beta == 0.f) continue;
-    const int ml = n - j - 1;
-    float2 acc = make_float2(0.f, 0.f);
-    if (col < n)
-      for (int r = part; r < ml; r += 4) acc = acc + cmul_conj_a(K.V[j][r], K.Q[j + 1 + r][col]);
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
-    if (col < n)
-      for (int r = part; r < ml; r += 4) K.Q[j + 1 + r][col] = K.Q[j + 1 + r][col] - beta * (K.V[j][r] * acc);
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < n * n; e += ST) {
-    const int r = e / n, c = e - r * n;
-    const double2 p = S.ph[c];
-    K.Q[r][c] = K.Q[r][c] * make_float2((float)p.x, (float)p.y);
-  }
-  __syncthreads();
-}
-
-// out = s * (QD)^H in  (FP32 dense matvec, 4 threads per output)
-__device__ void qd_h(Shared& S, int n, const double2* in, double s, float2* out) {
-  const int k = threadIdx.x >> 2, part = threadIdx.x & 3;
-  float2 acc = make_float2(0.f, 0.f);
-  if (k < n)
-    for (int j = part; j < n; j += 4) {
-      const double2 v = s * in[j];
-      acc = acc + cmul_conj_a(S.u.f.Q[j][k], make_float2((float)v.x, (float)v.y));
-    }
-  acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-  acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-  acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
-  acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
-  if (k < n && part == 0) out[k] = acc;
-  __syncthreads();
-}
-
-// out = s * (QD) in
-__device__ void qd(Shared& S, int n, const float2* in, double s, double2* out) {
-  const int j = threadIdx.x >> 2, part = threadIdx.x & 3;
-  float2 acc = make_float2(0.f, 0.f);
-  if (j < n)
-    for (int k = part; k < n; k += 4) acc = acc + S.u.f.Q[j][k] * in[k];
-  acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-  acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-  acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
-  acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
-  if (j < n && part == 0) out[j] = s * to_d(acc);
-  __syncthreads();
-}
-
 // (T + a I) z = rhs, T real symmetric tridiagonal (d, e); single thread.
 // Returns false if a pivot is not positive (T + a I not numerically SPD).
 template <typename T>
@@ -533,32 +536,6 @@ __device__ double phi2(const T* d, const T* e, const cx<T>* c, int n, double a, 
   return a * a * (double)zz;
 }
 
-// r = b - A (A^H y) - alpha y in FP64 (S.t = A^H y as scratch); all threads
-__device__ void residual_fp64(Shared& S, int n, int m, double alpha) {
-  {  // 2 threads per column l (2 M <= blockDim); every lane reaches the shuffles
-    const int l = threadIdx.x >> 1, h = threadIdx.x & 1;
-    double2 acc = make_double2(0, 0);
-    if (l < m)
-      for (int k = h; k < n; k += 2) acc = acc + cmul_conj_a(S.A[k][l], S.y[k]);
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-    if (l < m && h == 0) S.t[l] = acc;
-  }
-  __syncthreads();
-  {  // 4 threads per row k
-    const int k = threadIdx.x >> 2, h = threadIdx.x & 3;
-    double2 acc = make_double2(0, 0);
-    if (k < n)
-      for (int l = h; l < m; l += 4) acc = acc + S.A[k][l] * S.t[l];
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
-    if (k < n && h == 0) S.r[k] = S.b[k] - acc - alpha * S.y[k];
-  }
-  __syncthreads();
-}
-
 // block-wide sum of one double per thread (all threads get it)
 __device__ double block_sum(Shared& S, double v) {
   v = warp_sum(v);
@@ -566,28 +543,6 @@ __device__ double block_sum(Shared& S, double v) {
   if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = v;
   __syncthreads();
   return (S.red[0] + S.red[1]) + (S.red[2] + S.red[3]);
-}
-
-// mixed precision: y += (QD)(T/tr + a_s I)^-1 (QD)^H r / tr, returns ||dy||^2/||y||^2
-__device__ double refine_step(Shared& S, int n) {
-  qd_h(S, n, S.r, S.inv_sb, S.c32);
-  if (threadIdx.x == 0 && !tri_solve<float>(S.d32, S.e32, n, (float)S.a_s, S.c32, S.cz)) S.fp64 = 1;
-  __syncthreads();
-  if (S.fp64) return 0.0;  // FP32 model not positive definite here: caller takes the FP64 route
-  qd(S, n, S.cz, S.sb / S.tr, S.z);
-  double dd = 0.0, yy = 0.0;
-  if (threadIdx.x < n) {
-    S.y[threadIdx.x] = S.y[threadIdx.x] + S.z[threadIdx.x];
-    dd = abs2(S.z[threadIdx.x]);
-    yy = abs2(S.y[threadIdx.x]);
-  }
-  if (threadIdx.x < 32) {
-    dd = warp_sum(dd);
-    yy = warp_sum(yy);
-    if (threadIdx.x == 0) S.red[4] = yy > 0.0 ? dd / yy : 0.0;
-  }
-  __syncthreads();
-  return S.red[4];
 }
 
 // FP64 route: FP64 factorisation, FP32-seeded root on the scaled tridiagonal,
@@ -637,6 +592,321 @@ __device__ void solve_fp64(Shared& S, int n, int m, const Problem& P, int om, un
   __syncthreads();
 }
 
+// ------------------------------------------------------------------------------
+// mixed precision route: warp-synchronous FP32 factorisation held in registers
+// ------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ cx<T> pick(const cx<T>* v, int j) {  // v[j] for a runtime j, register-resident v
+  cx<T> r = czero<T>();
+#pragma unroll
+  for (int c = 0; c < MAX_M1; ++c)
+    if (c == j) r = v[c];
+  return r;
+}
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// G32 = A32 A32^H (full Hermitian matrix), all threads: row = lane, 8 columns per warp
+__device__ void gram32(Shared& S, int n, int m) {
+  BulkF& K = S.u.f;
+  const int r = threadIdx.x & 31, cg = threadIdx.x >> 5;
+  float2 acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+  if (r < n)
+#pragma unroll 4
+    for (int l = 0; l < m; ++l) {
+      const float2 a = K.A[r][l];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = acc[q] + mulc(a, K.A[cg * 8 + q][l]);
+    }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int c = cg * 8 + q;
+    if (r < n && c < n) K.G[r][c] = r == c ? make_float2(acc[q].x, 0.f) : acc[q];
+  }
+  __syncthreads();
+}
+
+// Householder reduction of G32 (shared) by warp 0, lane r owning row r.
+// Output: reflectors V[j], beta[j]; d32, e32 and the phases ph of T = D^H Q^H G Q D.
+__device__ void tridiag32_warp(Shared& S, int n) {
+  BulkF& K = S.u.f;
+  const int lane = threadIdx.x;
+  float2 eh = make_float2(0.f, 0.f);  // lane j keeps the complex subdiagonal entry e_j
+  for (int j = 0; j + 2 < n; ++j) {
+    const bool below = lane > j && lane < n;
+    if (j == 3) FL_MARK_S(13);
+    float2 x = below ? K.G[lane][j] : make_float2(0.f, 0.f);
+    const float nx2 = warp_sum(abs2(x));
+    const float2 x0 = shfl2(x, j + 1);
+    float beta = 0.f;
+    float2 ah = make_float2(0.f, 0.f);
+    if (nx2 > 0.f) {
+      const float nx = sqrtf(nx2), ax0 = sqrtf(abs2(x0));
+      const float2 ph = ax0 > 0.f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
+      ah = make_float2(-ph.x * nx, -ph.y * nx);
+      if (lane == j + 1) x = make_float2(ph.x * (ax0 + nx), ph.y * (ax0 + nx));
+      beta = 1.f / (nx * (nx + ax0));
+    }
+    if (lane == j) eh = ah;
+    if (below) K.V[j][lane - j - 1] = x;
+    if (lane == 0) K.beta[j] = beta;
+    if (beta == 0.f) continue;  // warp-uniform
+    K.p[lane] = x;              // v by absolute row, zero outside the block
+    __syncwarp();
+    if (j == 3) FL_MARK_S(14);
+    float2 p = make_float2(0.f, 0.f);
+    if (below)
+      for (int c0 = j + 1; c0 < n; c0 += 8) {  // explicit batches: all loads issued before use
+        float2 gv[8], pv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = c0 + q < n ? c0 + q : n - 1;
+          gv[q] = K.G[lane][c];
+          pv[q] = c0 + q < n ? K.p[c] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p = p + gv[q] * pv[q];
+      }
+    p = beta * p;
+    if (j == 3) FL_MARK_S(15);
+    const float kk = 0.5f * beta * warp_sum(x.x * p.x + x.y * p.y);  // (beta/2) Re(v^H p)
+    const float2 w = p - kk * x;
+    K.wv[lane] = w;
+    __syncwarp();
+    if (j == 3) FL_MARK_S(16);
+    if (below)
+      for (int c0 = j + 1; c0 < n; c0 += 8) {
+        float2 gv[8], wq[8], pq[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = c0 + q < n ? c0 + q : n - 1;
+          gv[q] = K.G[lane][c];
+          wq[q] = K.wv[c];
+          pq[q] = K.p[c];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (c0 + q < n) K.G[lane][c0 + q] = gv[q] - (mulc(x, wq[q]) + mulc(w, pq[q]));
+      }
+    __syncwarp();
+    if (j == 3) FL_MARK_S(17);
+  }
+  if (n >= 2 && lane == n - 2) eh = K.G[n - 1][n - 2];
+  if (lane < n) S.d32[lane] = K.G[lane][lane].x;
+  float2 u = make_float2(1.f, 0.f);
+  if (lane + 1 < n) {
+    const float ae = sqrtf(abs2(eh));
+    if (ae > 0.f) u = make_float2(eh.x / ae, eh.y / ae);
+    S.e32[lane] = ae;
+  }
+  for (int off = 1; off < 32; off <<= 1) {  // ph[i+1] = u_0 ... u_i
+    const float2 o = make_float2(__shfl_up_sync(0xffffffffu, u.x, off), __shfl_up_sync(0xffffffffu, u.y, off));
+    if (lane >= off) u = o * u;
+  }
+  if (lane + 1 < n) S.ph[lane + 1] = to_d(u);
+  if (lane == 0) S.ph[0] = make_double2(1.0, 0.0);
+  __syncwarp();
+}
+
+// Q D formed explicitly by warp 0 in K.Q: lane c accumulates column c of
+// H_0 ... H_{n-3} (reflectors applied last to first), then scales it by ph_c.
+__device__ void form_qd_warp(Shared& S, int n) {
+  BulkF& K = S.u.f;
+  const int c = threadIdx.x;
+  if (c < n)
+    for (int r = 0; r < n; ++r) K.Q[r][c] = make_float2(r == c ? 1.f : 0.f, 0.f);
+  for (int j = n - 3; j >= 0; --j) {
+    const float beta = K.beta[j];
+    if (beta == 0.f || c <= j || c >= n) continue;  // columns c <= j are still e_c here
+    float2 dot = make_float2(0.f, 0.f);
+    for (int r0 = j + 1; r0 < n; r0 += 8) {
+      float2 vq[8], qq[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = r0 + q < n ? r0 + q : n - 1;
+        vq[q] = r0 + q < n ? K.V[j][r - j - 1] : make_float2(0.f, 0.f);
+        qq[q] = K.Q[r][c];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) dot = dot + cmul_conj_a(vq[q], qq[q]);
+    }
+    dot = beta * dot;
+    for (int r0 = j + 1; r0 < n; r0 += 8) {
+      float2 vq[8], qq[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = r0 + q < n ? r0 + q : n - 1;
+        vq[q] = K.V[j][r - j - 1];
+        qq[q] = K.Q[r][c];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (r0 + q < n) K.Q[r0 + q][c] = qq[q] - vq[q] * dot;
+    }
+  }
+  if (c < n) {
+    const double2 p = S.ph[c];
+    const float2 pf = make_float2((float)p.x, (float)p.y);
+    for (int r = 0; r < n; ++r) K.Q[r][c] = K.Q[r][c] * pf;
+  }
+  __syncwarp();
+}
+
+// cz_k = ((QD)^H v)_k for an FP32 vector v in shared memory; lane k, warp 0
+__device__ __forceinline__ float2 qdh_lane(Shared& S, int n, const float2* v) {
+  const int k = threadIdx.x;
+  float2 acc = make_float2(0.f, 0.f);
+  if (k < n) {
+    float2 acc2 = make_float2(0.f, 0.f);
+    int j = 0;
+#pragma unroll 4
+    for (; j + 1 < n; j += 2) {
+      acc = acc + cmul_conj_a(S.u.f.Q[j][k], v[j]);
+      acc2 = acc2 + cmul_conj_a(S.u.f.Q[j + 1][k], v[j + 1]);
+    }
+    if (j < n) acc = acc + cmul_conj_a(S.u.f.Q[j][k], v[j]);
+    acc = acc + acc2;
+  }
+  return acc;
+}
+
+// two-float residual of the scaled dual system: th = Ah^H yh, rh = bh - Ah th - a yh
+__device__ void residual_ff(Shared& S, int n, int m, ff a) {
+  ffc (*Af)[MAX_M + 1] = reinterpret_cast<ffc (*)[MAX_M + 1]>(S.A);
+  {  // 2 threads per column l
+    const int l = threadIdx.x >> 1, h = threadIdx.x & 1;
+    ffc acc = ffc_zero();
+    if (l < m)
+#pragma unroll 4
+      for (int k = h; k < n; k += 2) acc = ffc_add(acc, ffc_conj_mul(Af[k][l], S.yh[k]));
+    acc = ffc_add(acc, ffc_shfl_xor(acc, 1));
+    if (l < m && h == 0) S.th[l] = acc;
+  }
+  __syncthreads();
+  {  // 4 threads per row k
+    const int k = threadIdx.x >> 2, h = threadIdx.x & 3;
+    ffc acc = ffc_zero();
+    if (k < n)
+#pragma unroll 4
+      for (int l = h; l < m; l += 4) acc = ffc_add(acc, ffc_mul(Af[k][l], S.th[l]));
+    acc = ffc_add(acc, ffc_shfl_xor(acc, 1));
+    acc = ffc_add(acc, ffc_shfl_xor(acc, 2));
+    if (k < n && h == 0) {
+      const ffc ay = ffc{ff_mul(a, S.yh[k].re), ff_mul(a, S.yh[k].im)};
+      const ffc r = ffc_sub(ffc_sub(S.bh[k], acc), ay);
+      S.rh[k] = r;
+      S.r32[k] = make_float2(r.re.hi, r.im.hi);
+    }
+  }
+  __syncthreads();
+}
+
+// (T + a I) z = c with per-lane scratch in shared memory; returns a^2 ||z||^2 (FP32 T)
+__device__ float lane_phi2(Shared& S, int n, float a, const float2* c, bool& ok) {
+  BulkF& K = S.u.f;
+  const int L = threadIdx.x & 31;
+  float lp = S.d32[0] + a;
+  ok = lp > 0.f;
+  float il = __fdividef(1.f, lp);
+  float2 w = c[0];
+  K.ts[0][L] = il * w;
+  for (int i = 1; i < n; ++i) {
+    const float mu = S.e32[i - 1] * il;
+    lp = S.d32[i] + a - mu * S.e32[i - 1];
+    ok = ok && lp > 0.f;
+    il = __fdividef(1.f, lp);
+    w = c[i] - mu * w;
+    K.tmu[i][L] = mu;
+    K.ts[i][L] = il * w;
+  }
+  float2 x = K.ts[n - 1][L];
+  float zz = abs2(x);
+  for (int i = n - 2; i >= 0; --i) {
+    x = K.ts[i][L] - K.tmu[i + 1][L] * x;
+    zz += abs2(x);
+  }
+  return a * a * zz;
+}
+
+// single-lane solve of (T + a I) z = c into K.tz (shared), FP32
+__device__ void lane_solve(Shared& S, int n, float a, const float2* c, float2* z) {
+  BulkF& K = S.u.f;
+  float lp = S.d32[0] + a;
+  float il = __fdividef(1.f, lp);
+  float2 w = c[0];
+  K.ts[0][0] = il * w;
+  for (int i = 1; i < n; ++i) {
+    const float mu = S.e32[i - 1] * il;
+    lp = S.d32[i] + a - mu * S.e32[i - 1];
+    il = __fdividef(1.f, lp);
+    w = c[i] - mu * w;
+    K.tmu[i][0] = mu;
+    K.ts[i][0] = il * w;
+  }
+  float2 x = K.ts[n - 1][0];
+  z[n - 1] = x;
+  for (int i = n - 2; i >= 0; --i) {
+    x = K.ts[i][0] - K.tmu[i + 1][0] * x;
+    z[i] = x;
+  }
+}
+
+// Discrepancy root on the scaled FP32 model by three rounds of a 32-point search
+// in log(a) (one point per lane) and a final secant step.  Warp 0.  Returns a;
+// floor = g(lo) >= 0; ok = false on a breakdown.
+__device__ float root32_warp(Shared& S, int n, float lo, float hi, float target, bool& floor_case, bool& ok) {
+  const int lane = threadIdx.x;
+  float tl = logf(lo), th = logf(hi);
+  const float lt = logf(target);
+  float gl = 0.f, gh = 0.f;
+  floor_case = false;
+  ok = true;
+  for (int round = 0; round < 3; ++round) {
+    const float t = tl + (th - tl) * (float)lane * (1.f / 31.f);
+    bool okl;
+    const float f = lane_phi2(S, n, expf(t), S.c32, okl);
+    const float g = logf(f) - lt;
+    if (!__all_sync(0xffffffffu, okl && isfinite(g))) { ok = false; return 0.f; }
+    const unsigned above = __ballot_sync(0xffffffffu, g >= 0.f);
+    if (round == 0 && (above & 1u)) { floor_case = true; return lo; }
+    const int k = above ? __ffs(above) - 1 : 31;  // first grid point at or above the target
+    const float gk = __shfl_sync(0xffffffffu, g, k), gk1 = __shfl_sync(0xffffffffu, g, k > 0 ? k - 1 : 0);
+    const float tk = __shfl_sync(0xffffffffu, t, k), tk1 = __shfl_sync(0xffffffffu, t, k > 0 ? k - 1 : 0);
+    if (!above) return expf(th);  // phi stays below target up to hi: cannot happen for an active mode
+    tl = tk1; th = tk; gl = gk1; gh = gk;
+  }
+  const float t = gh > gl ? tl + (th - tl) * (-gl / (gh - gl)) : 0.5f * (tl + th);
+  return expf(t);
+}
+
+// F_l = sum_{l' <= l} q^(l - l') s_l' for l < len <= 64, one warp, lanes own two
+// consecutive elements; an inclusive scan of the affine maps x -> A x + B.
+__device__ void affine_scan64(const double2* s, int len, double2 q, double2* out) {
+  const int lane = threadIdx.x & 31;
+  const int l0 = 2 * lane, l1 = l0 + 1;
+  const double2 s0 = l0 < len ? s[l0] : make_double2(0, 0);
+  const double2 s1 = l1 < len ? s[l1] : make_double2(0, 0);
+  double2 A = q * q;
+  double2 B = q * s0 + s1;
+  for (int off = 1; off < 32; off <<= 1) {
+    const double2 Ap = make_double2(__shfl_up_sync(0xffffffffu, A.x, off), __shfl_up_sync(0xffffffffu, A.y, off));
+    const double2 Bp = make_double2(__shfl_up_sync(0xffffffffu, B.x, off), __shfl_up_sync(0xffffffffu, B.y, off));
+    if (lane >= off) {
+      B = A * Bp + B;
+      A = A * Ap;
+    }
+  }
+  // B = F_{l1}; F_{l0} = q F_{l0 - 1} + s0
+  double2 prev = make_double2(__shfl_up_sync(0xffffffffu, B.x, 1), __shfl_up_sync(0xffffffffu, B.y, 1));
+  if (lane == 0) prev = make_double2(0, 0);
+  if (l0 < len) out[l0] = q * prev + s0;
+  if (l1 < len) out[l1] = B;
+}
+
 template <typename B, bool MIXED>
 __global__ void __launch_bounds__(ST)
 k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
@@ -653,6 +923,10 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     long long i = item;
     while (i >= count[om]) { i -= count[om]; ++om; }
     const int nu = act[om * N2 + i];
+    FL_MARK(0);
+#ifdef FL_PHASE_TIMING
+    if (threadIdx.x == 0) S.tflag = blockIdx.x == 0 && item == 0;
+#endif
     const int i2 = nu / N, i1 = nu - i2 * N;
     const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
     const double k0 = P.omega[om] / P.c0;
@@ -670,16 +944,12 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     }
     for (int l = threadIdx.x; l < m; l += ST) S.Pz[l] = exp_ikz(kz, ztop - (P.z1 + (l + 0.5) * P.hz));
     __syncthreads();
-    // A (FP64), ||A||_F^2 = tr(G), ||b||^2
-    double tr_part = 0.0;
-    for (int e = threadIdx.x; e < n * m; e += ST) {
-      const int k = e / m, l = e - k * m;
-      const double2 a = S.E[k] * S.Pz[l];
-      S.A[k][l] = a;
-      tr_part += abs2(a);
-    }
-    const double tr = block_sum(S, tr_part);
+    // ||A||_F^2 = tr(G) = (sum_k |E_k|^2)(sum_l |P_l|^2) since A_kl = E_k P_l; ||b||^2
+    FL_MARK(1);
+    const double sE = block_sum(S, threadIdx.x < n ? abs2(S.E[threadIdx.x]) : 0.0);
+    const double sP = block_sum(S, threadIdx.x < m ? abs2(S.Pz[threadIdx.x]) : 0.0);
     const double bb = block_sum(S, threadIdx.x < n ? abs2(S.b[threadIdx.x]) : 0.0);
+    const double tr = sE * sP;
     if (!(tr > 0.0)) {  // A_nu underflowed to zero: the mode carries no information, V~ = 0
       if (threadIdx.x == 0) {
         atomicAdd(ctr + C_ACTIVE, ~0ull);  // -1: counted as zeroed instead
@@ -711,60 +981,126 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     }
     __syncthreads();
     if (MIXED) {
-      const double sa = rsqrt(tr);  // scaled in FP64 so that tiny tr(G) cannot underflow FP32
+      // scaled problem Ah = A / sqrt(tr) (||Ah||_F = 1), bh = b / ||b||, a = alpha / tr:
+      // Ah in two-float (for the residual and V~) and its FP32 part (for the model)
+      ffc (*Af)[MAX_M + 1] = reinterpret_cast<ffc (*)[MAX_M + 1]>(S.A);
+      const double sa = rsqrt(tr);
+      if (threadIdx.x < n) {
+        S.Ef[threadIdx.x] = ffc_from(sa * S.E[threadIdx.x]);
+        S.bh[threadIdx.x] = ffc_from(S.inv_sb * S.b[threadIdx.x]);
+      }
+      if (threadIdx.x < m) S.Pf[threadIdx.x] = ffc_from(S.Pz[threadIdx.x]);
+      __syncthreads();
       for (int e = threadIdx.x; e < n * m; e += ST) {
         const int k = e / m, l = e - k * m;
-        const double2 a = sa * S.A[k][l];
-        S.u.f.A[k][l] = make_float2((float)a.x, (float)a.y);
+        const ffc a = ffc_mul(S.Ef[k], S.Pf[l]);
+        Af[k][l] = a;
+        S.u.f.A[k][l] = make_float2(a.re.hi, a.im.hi);
       }
       __syncthreads();
-      gram<float>(S, n, m);
-      tridiagonalize<float>(S, n);
-      form_QD(S, n);
-      qd_h(S, n, S.b, S.inv_sb, S.c32);
-      if (threadIdx.x == 0) {
-        const double target = (S.dnu / S.sb) * (S.dnu / S.sb);
-        const double lo = P.alpha_rel, hi = S.hi / S.tr;
-        bool ok = true;
-        int it;
-        double a = 0.0, gp = 0.0;
+      FL_MARK(2);
+      gram32(S, n, m);
+      FL_MARK(3);
+      if (threadIdx.x < 32) {
+        tridiag32_warp(S, n);
+        FL_MARK(4);
+        form_qd_warp(S, n);
+        FL_MARK(5);
+        if (threadIdx.x < n) S.r32[threadIdx.x] = make_float2(S.bh[threadIdx.x].re.hi, S.bh[threadIdx.x].im.hi);
+        __syncwarp();
+        const float2 cz = qdh_lane(S, n, S.r32);  // c = (QD)^H b / ||b||
+        if (threadIdx.x < n) S.c32[threadIdx.x] = cz;
+        __syncwarp();
+        FL_MARK(6);
+        bool ok = true, fl = false;
+        float a;
         if (P.alpha_mode == 1) {
-          a = P.alpha_given[om] / S.tr;
+          a = (float)(P.alpha_given[om] / S.tr);
         } else {
-          const double f_lo = phi2<float>(S.d32, S.e32, S.c32, n, lo, ok);
-          if (ok && f_lo < target) {
-            const double t_mid = 0.5 * (log(lo) + log(hi));
-            const double t = newton_log_alpha<float>(S.d32, S.e32, S.c32, n, lo, hi, target, t_mid, 1e-6,
-                                                     P.max_iter, gp, ok, it);
-            a = exp(t);
-          } else {
-            ok = false;  // floor case (or FP32 breakdown): decided in FP64
-          }
-        }
-        S.a_s = a;
-        S.fp64 = (!ok || a < P.fp64_switch) ? 1 : 0;
-        if (S.fp64) atomicAdd(ctr + C_FP64_FALLBACK, 1ull);
-      }
-      __syncthreads();
-      if (!S.fp64) {
-        // y by refinement against the FP64 residual, to ||dy|| <= 1e-9 ||y||
-        for (int k = threadIdx.x; k < n; k += ST) { S.y[k] = make_double2(0, 0); S.r[k] = S.b[k]; }
-        __syncthreads();
-        const double alpha = S.a_s * S.tr;
-        int sweeps = 0;
-        for (double rel = 1.0; sweeps < P.refine_iters && rel > 1e-18 && !S.fp64; ++sweeps) {
-          if (sweeps) residual_fp64(S, n, m, alpha);
-          rel = refine_step(S, n);
+          const float target = (float)((S.dnu * S.inv_sb) * (S.dnu * S.inv_sb));
+          a = root32_warp(S, n, (float)P.alpha_rel, (float)(S.hi / S.tr), target, fl, ok);
         }
         if (threadIdx.x == 0) {
-          atomicAdd(ctr + C_REFINE_ITERS, (unsigned long long)sweeps);
+          S.a_s = (double)a;
+          // floor cases, breakdowns and small alpha/tr are decided and solved in FP64
+          S.fp64 = (!ok || fl || a < (float)P.fp64_switch) ? 1 : 0;
           if (S.fp64) atomicAdd(ctr + C_FP64_FALLBACK, 1ull);
         }
       }
+      __syncthreads();
+      FL_MARK(7);
+      if (!S.fp64) {
+        // yh by refinement against the two-float residual, to ||dy|| <= 1e-9 ||y||
+        for (int k = threadIdx.x; k < n; k += ST) {
+          S.yh[k] = ffc_zero();
+          S.r32[k] = make_float2(S.bh[k].re.hi, S.bh[k].im.hi);
+        }
+        __syncthreads();
+        const ff a_ff = ff{(float)S.a_s, 0.f};  // the FP32 root is exact in two-float
+        int sweeps = 0;
+        for (float rel = 1.f; sweeps < P.refine_iters && rel > 1e-18f; ++sweeps) {
+          if (sweeps) residual_ff(S, n, m, a_ff);
+          if (threadIdx.x < 32) {
+            const float2 cz = qdh_lane(S, n, S.r32);
+            if (threadIdx.x < n) S.c32[threadIdx.x] = cz;
+            __syncwarp();
+            if (threadIdx.x == 0) lane_solve(S, n, (float)S.a_s, S.c32, S.cz);
+            __syncwarp();
+            const int j = threadIdx.x;
+            float dd = 0.f, yy = 0.f;
+            if (j < n) {
+              float2 acc = make_float2(0.f, 0.f), acc2 = make_float2(0.f, 0.f);
+              int k = 0;
+#pragma unroll 4
+              for (; k + 1 < n; k += 2) {
+                acc = acc + S.u.f.Q[j][k] * S.cz[k];
+                acc2 = acc2 + S.u.f.Q[j][k + 1] * S.cz[k + 1];
+              }
+              if (k < n) acc = acc + S.u.f.Q[j][k] * S.cz[k];
+              acc = acc + acc2;
+              const ffc yn = ffc_add(S.yh[j], ffc{ff{acc.x, 0.f}, ff{acc.y, 0.f}});
+              S.yh[j] = yn;
+              dd = abs2(acc);
+              yy = yn.re.hi * yn.re.hi + yn.im.hi * yn.im.hi;
+            }
+            dd = warp_sum(dd);
+            yy = warp_sum(yy);
+            if (j == 0) S.red[4] = yy > 0.f ? dd / yy : 0.f;
+          }
+          __syncthreads();
+          rel = (float)S.red[4];
+        }
+        if (threadIdx.x == 0) atomicAdd(ctr + C_REFINE_ITERS, (unsigned long long)sweeps);
+        FL_MARK(8);
+        // V~ = A^H y = (||b|| / sqrt(tr)) Ah^H yh, two-float, 2 threads per column
+        {
+          const int l = threadIdx.x >> 1, h = threadIdx.x & 1;
+          ffc acc = ffc_zero();
+          if (l < m)
+            for (int k = h; k < n; k += 2) acc = ffc_add(acc, ffc_conj_mul(Af[k][l], S.yh[k]));
+          acc = ffc_add(acc, ffc_shfl_xor(acc, 1));
+          if (l < m && h == 0) S.Vt[l] = (S.sb * sa) * ffc_to(acc);
+        }
+        __syncthreads();
+      } else {
+        // FP64 route for this mode: A in FP64 over the two-float storage
+        for (int e = threadIdx.x; e < n * m; e += ST) {
+          const int k = e / m, l = e - k * m;
+          S.A[k][l] = S.E[k] * S.Pz[l];
+        }
+        __syncthreads();
+      }
+    } else {
+      for (int e = threadIdx.x; e < n * m; e += ST) {
+        const int k = e / m, l = e - k * m;
+        S.A[k][l] = S.E[k] * S.Pz[l];
+      }
+      __syncthreads();
     }
-    if (S.fp64) solve_fp64(S, n, m, P, om, ctr);
-    // V~ = A^H y (FP64), 2 threads per column
-    {
+    FL_MARK(9);
+    if (S.fp64) {
+      solve_fp64(S, n, m, P, om, ctr);
+      // V~ = A^H y (FP64), 2 threads per column
       const int l = threadIdx.x >> 1, h = threadIdx.x & 1;
       double2 acc = make_double2(0, 0);
       if (l < m)
@@ -772,21 +1108,27 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
       if (l < m && h == 0) S.Vt[l] = acc;
+      __syncthreads();
     }
-    __syncthreads();
-    // U~ = U~0 + gamma (F + B): forward/backward sweeps of T_nu's geometric kernel
-    if (threadIdx.x == 0 || threadIdx.x == 32) {
+    FL_MARK(10);
+    // U~ = U~0 + gamma (F + B): T_nu's geometric kernel as a forward recurrence
+    // F_l = q F_{l-1} + V~_l and a backward one B_l = q (B_{l+1} + V~_{l+1}), each an
+    // inclusive scan over the planes (warp 0: F, warp 1: B in reversed order)
+    if (threadIdx.x < 64) {
       const double2 qz = exp_ikz(kz, P.hz);
-      if (threadIdx.x == 0) {
-        double2 f = make_double2(0, 0);
-        for (int l = 0; l < m; ++l) { f = qz * f + S.Vt[l]; S.F[l] = f; }
+      if (threadIdx.x < 32) {
+        affine_scan64(S.Vt, m, qz, S.F);
       } else {
-        double2 bk = make_double2(0, 0);
-        S.Bk[m - 1] = bk;
-        for (int l = m - 2; l >= 0; --l) { bk = qz * (bk + S.Vt[l + 1]); S.Bk[l] = bk; }
+        const int r = threadIdx.x - 32;  // reversed sequence s'_r = q V~_{m-r} (s'_0 = 0)
+        for (int rr = r; rr < m; rr += 32) S.t[rr] = rr == 0 ? make_double2(0, 0) : qz * S.Vt[m - rr];
+        __syncwarp();
+        affine_scan64(S.t, m, qz, S.z64);
+        __syncwarp();
+        for (int rr = r; rr < m; rr += 32) S.Bk[m - 1 - rr] = S.z64[rr];
       }
     }
     __syncthreads();
+    FL_MARK(11);
     cx<B>* out = prof + ((long long)om * N2 + i) * 2 * m;
     for (int l = threadIdx.x; l < m; l += ST) {
       double2 u = gamma * (S.F[l] + S.Bk[l]);
@@ -800,6 +1142,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     }
     if (threadIdx.x == 0 && alpha_out) alpha_out[om * N2 + nu] = S.a_s * S.tr;
     __syncthreads();
+    FL_MARK(12);
   }
 }
 
