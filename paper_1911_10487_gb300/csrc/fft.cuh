@@ -70,28 +70,28 @@ template <typename R, bool INV> struct Dft {
   }
 };
 
-template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int PAD, int RAD>
-__device__ __forceinline__ void fft_stage(cx<R>* buf, const cx<R>* tw, int Ns) {
+template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int PAD, int RAD, int NS>
+__device__ __forceinline__ void fft_stage(cx<R>* buf, const cx<R>* tw) {
   using C = cx<R>;
   using IX = LayIdx<L, N, LINES, PAD>;
   constexpr int NB = N / RAD;                 // butterflies per line
   constexpr int TOTAL = LINES * NB;
   constexpr int PER = (TOTAL + THREADS - 1) / THREADS;
+  constexpr int STRIDE_TW = N / (NS * RAD);
   C v[PER][RAD];
   int out_b[PER], out_i[PER];
-  const int stride_tw = N / (Ns * RAD);
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int t = threadIdx.x + p * THREADS;
     if (TOTAL % THREADS == 0 || t < TOTAL) {
       int b, j;
       IX::map(t, NB, b, j);
-      const int k = j % Ns;
+      const int k = j % NS;
 #pragma unroll
       for (int r = 0; r < RAD; ++r) {
         C x = buf[IX::at(b, j + r * NB)];
-        if (r > 0) {
-          C w = tw[r * k * stride_tw];
+        if (r > 0 && NS > 1) {
+          C w = tw[r * k * STRIDE_TW];
           if (INV) w.y = -w.y;
           x = x * w;
         }
@@ -101,7 +101,7 @@ __device__ __forceinline__ void fft_stage(cx<R>* buf, const cx<R>* tw, int Ns) {
       else if (RAD == 4) Dft<R, INV>::d4(v[p]);
       else Dft<R, INV>::d3(v[p]);
       out_b[p] = b;
-      out_i[p] = (j / Ns) * Ns * RAD + k;
+      out_i[p] = (j / NS) * NS * RAD + k;
     }
   }
   __syncthreads();
@@ -110,28 +110,30 @@ __device__ __forceinline__ void fft_stage(cx<R>* buf, const cx<R>* tw, int Ns) {
     const int t = threadIdx.x + p * THREADS;
     if (TOTAL % THREADS == 0 || t < TOTAL) {
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) buf[IX::at(out_b[p], out_i[p] + r * Ns)] = v[p][r];
+      for (int r = 0; r < RAD; ++r) buf[IX::at(out_b[p], out_i[p] + r * NS)] = v[p][r];
     }
   }
   __syncthreads();
 }
+
+// stage S of the plan, with NS = product of the earlier radices (compile-time)
+template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int PAD, int S, int NS>
+struct FftStages {
+  __device__ __forceinline__ static void run(cx<R>* buf, const cx<R>* tw) {
+    if constexpr (S < FftPlan<N>::stages) {
+      constexpr int RAD = FftPlan<N>::radix(S);
+      fft_stage<R, N, INV, LINES, THREADS, L, PAD, RAD, NS>(buf, tw);
+      FftStages<R, N, INV, LINES, THREADS, L, PAD, S + 1, NS * RAD>::run(buf, tw);
+    }
+  }
+};
 
 // Transform all LINES lines of the tile in place.  `tw` holds w^j, j < N
 // (w = exp(-2 pi i/N)), in shared or global memory.  Must be called by all
 // THREADS threads of the block; contains __syncthreads().
 template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int PAD = 0>
 __device__ __forceinline__ void fft_lines(cx<R>* buf, const cx<R>* tw) {
-  using P = FftPlan<N>;
-  int Ns = 1;
-#pragma unroll
-  for (int s = 0; s < P::stages; ++s) {
-    constexpr int dummy = 0; (void)dummy;
-    const int rad = P::radix(s);
-    if (rad == 3) fft_stage<R, N, INV, LINES, THREADS, L, PAD, 3>(buf, tw, Ns);
-    else if (rad == 4) fft_stage<R, N, INV, LINES, THREADS, L, PAD, 4>(buf, tw, Ns);
-    else fft_stage<R, N, INV, LINES, THREADS, L, PAD, 2>(buf, tw, Ns);
-    Ns *= rad;
-  }
+  FftStages<R, N, INV, LINES, THREADS, L, PAD, 0, 1>::run(buf, tw);
 }
 
 }  // namespace fl

@@ -88,16 +88,26 @@ k_mode_norms(const cx<R>* __restrict__ wt, double* __restrict__ norms, double* _
   __shared__ double red[NORM_T];
   const int om = blockIdx.y;
   const int nu = blockIdx.x * NORM_T + threadIdx.x;
-  double acc = 0.0;
+  // summed in the working precision R (FP32 in the mixed path: FP64 arithmetic
+  // here would run on the slow FP64 pipe for every mode)
+  R acc = R(0);
   if (nu < N2) {
     const cx<R>* p = wt + (long long)om * m1 * N2 + nu;
-    for (int k = 0; k < m1; ++k) {
-      const cx<R> v = p[(long long)k * N2];
-      acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    int k = 0;
+    for (; k + 8 <= m1; k += 8) {  // eight independent loads in flight, summed in plane order
+      cx<R> v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = p[(long long)(k + q) * N2];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc += v[q].x * v[q].x + v[q].y * v[q].y;
     }
-    norms[(long long)om * N2 + nu] = acc;
+    for (; k < m1; ++k) {
+      const cx<R> v = p[(long long)k * N2];
+      acc += v.x * v.x + v.y * v.y;
+    }
+    norms[(long long)om * N2 + nu] = (double)acc;
   }
-  red[threadIdx.x] = acc;
+  red[threadIdx.x] = (double)acc;
   __syncthreads();
   for (int h = NORM_T / 2; h > 0; h >>= 1) {
     if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
@@ -129,14 +139,6 @@ k_ifft_cols_gather(Problem P, const cx<R>* __restrict__ prof, const int* __restr
   load_twiddles<R, N>(tw_s, tw);
   const long long N2 = (long long)N * N;
   const int M = P.m;
-  cx<R> u0 = czero<R>();
-  if (f == 1) {
-    const double k0 = P.omega[om] / P.c0;
-    const double zl = P.z1 + (l + 0.5) * P.hz;
-    double s, c;
-    sincos(-k0 * zl, &s, &c);
-    u0 = from_d<R>(make_double2((double)N2 * c, (double)N2 * s));
-  }
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * THREADS;
@@ -147,8 +149,13 @@ k_ifft_cols_gather(Problem P, const cx<R>* __restrict__ prof, const int* __restr
       if (c < nc) {
         const int nu1 = cols[om * N + c];
         const int s = slot[om * N2 + (long long)i * N + nu1];
-        if (s >= 0) v = prof[(((long long)om * N2 + s) * 2 + f) * M + l];
-        else if (f == 1 && i == 0 && nu1 == 0) v = u0;
+        if (s >= 0) {
+          v = prof[(((long long)om * N2 + s) * 2 + f) * M + l];
+        } else if (f == 1 && i == 0 && nu1 == 0) {  // one thread: FP64 is slow on this GPU
+          double sn, cs;
+          sincos(-(P.omega[om] / P.c0) * (P.z1 + (l + 0.5) * P.hz), &sn, &cs);
+          v = from_d<R>(make_double2((double)N2 * cs, (double)N2 * sn));
+        }
       }
       buf[e] = v;
     }
@@ -251,13 +258,19 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
     recover_pass<R, N, double>(P, t2, cols, ncol, buf, tw_s, nd, dd);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
-      const bool g = !(dd[p] >= P.eps_u * P.eps_u * P.n_omega);
+      const bool g = !(dd[p] >= (double)P.n_omega * P.eps_u * P.eps_u);
       num[p] = g ? R(0) : R(nd[p] / dd[p]);
       den[p] = g ? R(0) : R(1);
     }
   }
-  const R guard = R(P.eps_u * P.eps_u * P.n_omega);
-  const R inv_c02 = R(1.0 / (P.c0 * P.c0));
+  __shared__ R consts[2];  // guard and c0^-2: one FP64 division per block, not per thread
+  if (threadIdx.x == 0) {
+    consts[0] = R(P.eps_u * P.eps_u * P.n_omega);
+    consts[1] = R(1.0 / (P.c0 * P.c0));
+  }
+  __syncthreads();
+  const R guard = consts[0];
+  const R inv_c02 = consts[1];
   unsigned n_guard = 0, n_nan = 0;
 #pragma unroll
   for (int p = 0; p < PER; ++p) {

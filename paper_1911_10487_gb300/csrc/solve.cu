@@ -77,60 +77,80 @@ k_classify(Problem P, const double* __restrict__ norms, const double* __restrict
   const int N = P.n;
   const int N2 = N * N;
   const double* nrm = norms + (long long)om * N2;
-  __shared__ int scan[CT];
+  __shared__ int scan[64];
   __shared__ int colflag[MAX_N];
   __shared__ unsigned cgraz[CT / 32];
   __shared__ long long thr_bits;
   for (int j = threadIdx.x; j < N; j += CT) colflag[j] = 0;
-  if (threadIdx.x == 0) {
-    // ||W||^2 = sum_nu ||W~_nu||^2 / N^2 (Parseval); partial sums in a fixed order
+  if (threadIdx.x < 32) {
+    // ||W||^2 = sum_nu ||W~_nu||^2 / N^2 (Parseval): the block partial sums are
+    // loaded by one warp and added in a fixed order (lane-strided, then a tree)
     double s = 0.0;
-    for (int i = 0; i < n_partial; ++i) s += partial[(long long)om * n_partial + i];
+    for (int i = threadIdx.x; i < n_partial; i += 32) s += partial[(long long)om * n_partial + i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) {
     const double wnorm = sqrt(s / (double)N2);
     const double dnu = P.tau * fmax(P.delta, P.delta_floor) * wnorm;
     dnu_out[om] = dnu;
     thr_bits = __double_as_longlong(dnu * dnu);
+    }
   }
   __syncthreads();
   // non-negative doubles order like their bit patterns: the test nrm > dnu^2 is
-  // an integer comparison (no FP64 pipe on a single SM)
+  // an integer comparison (no FP64 pipe on a single SM).  Thread t owns the modes
+  // v = t + k CT (coalesced); slots are handed out in (thread, k) order.
   const long long tb = thr_bits;
   const int glo = P.graz_lo[om], ghi = P.graz_hi[om];
-  const int C = (N2 + CT - 1) / CT;
-  const int v0 = threadIdx.x * C, v1 = min(N2, v0 + C);
   const long long* nb = reinterpret_cast<const long long*>(nrm);
+  const int kmax = (N2 + CT - 1) / CT;  // <= 64 for N <= 256
+  unsigned long long flags = 0ull;
   int cnt = 0;
   unsigned ngz = 0;
-  for (int v = v0; v < v1; ++v) {
-    const int i2 = v / N, i1 = v - i2 * N;
-    const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
-    const int msq = m1 * m1 + m2 * m2;
-    const bool graz = msq >= glo && msq <= ghi;
-    ngz += graz;
-    cnt += !graz && (P.alpha_mode == 1 || nb[v] > tb);
+  for (int k = 0; k < kmax; ++k) {
+    const int v = threadIdx.x + k * CT;
+    if (v < N2) {
+      const int i2 = v / N, i1 = v - i2 * N;
+      const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
+      const int msq = m1 * m1 + m2 * m2;
+      const bool graz = msq >= glo && msq <= ghi;
+      ngz += graz;
+      if (!graz && (P.alpha_mode == 1 || nb[v] > tb)) {
+        flags |= 1ull << k;
+        ++cnt;
+      }
+    }
   }
-  scan[threadIdx.x] = cnt;
+  // exclusive scan of cnt over the block: warp shuffles, then the warp totals
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = cnt;
+  for (int off = 1; off < 32; off <<= 1) {
+    const int o = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += o;
+  }
+  if (lane == 31) scan[wid] = incl;
   __syncthreads();
-  for (int off = 1; off < CT; off <<= 1) {  // inclusive Hillis-Steele scan
-    const int t = threadIdx.x >= off ? scan[threadIdx.x - off] : 0;
-    __syncthreads();
-    scan[threadIdx.x] += t;
-    __syncthreads();
+  if (wid == 0) {
+    int wv = lane < CT / 32 ? scan[lane] : 0;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, wv, off);
+      if (lane >= off) wv += o;
+    }
+    scan[32 + lane] = wv;  // inclusive warp-total prefix
   }
-  int pos = scan[threadIdx.x] - cnt;
-  const int total = scan[CT - 1];
-  for (int v = v0; v < v1; ++v) {
-    const int i2 = v / N, i1 = v - i2 * N;
-    const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
-    const int msq = m1 * m1 + m2 * m2;
-    const bool graz = msq >= glo && msq <= ghi;
-    if (!graz && (P.alpha_mode == 1 || nb[v] > tb)) {
-      slot[(long long)om * N2 + v] = pos;
-      act[(long long)om * N2 + pos] = v;
-      colflag[i1] = 1;
-      ++pos;
-    } else {
-      slot[(long long)om * N2 + v] = -1;
+  __syncthreads();
+  int pos = (wid > 0 ? scan[32 + wid - 1] : 0) + incl - cnt;
+  const int total = scan[32 + CT / 32 - 1];
+  for (int k = 0; k < kmax; ++k) {
+    const int v = threadIdx.x + k * CT;
+    if (v < N2) {
+      if (flags >> k & 1ull) {
+        slot[(long long)om * N2 + v] = pos;
+        act[(long long)om * N2 + pos] = v;
+        colflag[v % N] = 1;
+        ++pos;
+      } else {
+        slot[(long long)om * N2 + v] = -1;
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) ngz += __shfl_xor_sync(0xffffffffu, ngz, o);
@@ -950,7 +970,11 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     const double sP = block_sum(S, threadIdx.x < m ? abs2(S.Pz[threadIdx.x]) : 0.0);
     const double bb = block_sum(S, threadIdx.x < n ? abs2(S.b[threadIdx.x]) : 0.0);
     const double tr = sE * sP;
-    if (!(tr > 0.0)) {  // A_nu underflowed to zero: the mode carries no information, V~ = 0
+    const double dnu0 = dnu_arr[om];
+    // A_nu underflowed to zero (the mode carries no information), or, under the
+    // discrepancy rule, ||b|| recomputed here does not exceed delta_nu after all (a
+    // rounding tie at the threshold of the classification): V~ = 0
+    if (!(tr > 0.0) || (P.alpha_mode == 0 && !(bb > dnu0 * dnu0))) {
       if (threadIdx.x == 0) {
         atomicAdd(ctr + C_ACTIVE, ~0ull);  // -1: counted as zeroed instead
         atomicAdd(ctr + C_ZEROED, 1ull);
