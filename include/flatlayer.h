@@ -90,6 +90,8 @@ typedef struct {
   double fp64_switch;  /* FS_MIXED: FP64 factorisation below alpha/tr = this (default 1e-4) */
   int stage_timing;    /* 1: record CUDA events between the kernels of fs_reconstruct; the
                           durations appear in fs_report.ms_stage (default 0)              */
+  int solve_blocks_per_sm; /* 1 or 2: resident blocks per SM of the per-mode solve (grid =
+                          this x SM count); a tuning knob (default 2)                      */
 } fs_options;
 
 typedef struct {
@@ -157,6 +159,29 @@ fs_status fs_reconstruct(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec
 fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* W_host,
                               const double* omega, int n_omega, double delta, double c0,
                               const fs_options* opts, void* xi_host, void* c_host);
+
+/* One entry of a batch: a complete problem (arguments as for fs_reconstruct). */
+typedef struct {
+  fs_geometry geom;
+  const void* W;        /* device, [n_omega][M1][N][N] complex                */
+  const double* omega;  /* host, n_omega                                      */
+  int n_omega;
+  double delta, c0;
+  void* xi;             /* device, [M][N][N] real                             */
+  void* c;              /* device, [M][N][N] real, or NULL                    */
+} fs_problem;
+
+/* Many independent problems of uneven size in one call (the paper reconstructs one
+   problem at a time; batching is a throughput device).  Each problem is solved
+   exactly as by fs_reconstruct; the problems are dealt, largest first, over
+   n_streams (1..16) streams forked from the context's stream and joined back to
+   it, so independent problems run concurrently.  The workspace is the sum of the
+   problems' workspaces.  Fork and join use events only, so the call can be
+   captured into a CUDA graph once the workspace has been sized by an earlier call.
+   Counters of fs_get_report are summed over the batch; stage timing is off.
+   Errors: FS_EINVAL (names the first bad problem), FS_EUNSUPPORTED, FS_ENOMEM. */
+fs_status fs_reconstruct_batch(fs_ctx* ctx, const fs_problem* probs, int n_probs, fs_precision prec,
+                               const fs_options* opts, int n_streams);
 
 /* Forward data generator in the single-scattering (Born) form: Algorithm 1 of
    Sec. 3 with zero iterations, i.e. U~ = U~0 in eq. (7):

@@ -13,12 +13,14 @@ from dataclasses import dataclass
 
 from . import _abi
 from ._abi import (FS_FP64, FS_MIXED, FlatLayerError, fs_create, fs_default_options, fs_destroy,
-                   fs_forward_born, fs_get_report, fs_last_error, fs_reconstruct, fs_reconstruct_host, fs_version,
-                   fs_workspace_size, make_geometry, make_options)
+                   fs_forward_born, fs_get_report, fs_last_error, fs_reconstruct, fs_reconstruct_batch,
+                   fs_reconstruct_host, fs_reconstruct_static, fs_version, fs_workspace_size, make_geometry,
+                   make_options, make_problem)
 
 __all__ = ["Geometry", "Reconstructor", "FS_FP64", "FS_MIXED", "FlatLayerError", "fs_create",
            "fs_default_options", "fs_destroy", "fs_forward_born", "fs_get_report", "fs_last_error", "fs_reconstruct",
-           "fs_reconstruct_host", "fs_version", "fs_workspace_size", "make_geometry", "make_options"]
+           "fs_reconstruct_batch", "fs_reconstruct_host", "fs_reconstruct_static", "fs_version",
+           "fs_workspace_size", "make_geometry", "make_options", "make_problem"]
 
 PRECISIONS = {"fp64": FS_FP64, "mixed": FS_MIXED}
 
@@ -91,6 +93,32 @@ class Reconstructor:
                        xi.data_ptr(), c.data_ptr() if c is not None else None,
                        alpha.data_ptr() if alpha is not None else None)
         return xi, c, alpha
+
+    def reconstruct_batch(self, items, precision: str = "fp64", c0: float = 1.0, n_streams: int = 8,
+                          outs=None, **options):
+        """Independent problems in one call.  items: sequence of (W, omega, geom, delta);
+        returns [(xi, c)] (allocated unless `outs` gives them)."""
+        import torch
+        prec = PRECISIONS[precision]
+        want = torch.complex128 if prec == FS_FP64 else torch.complex64
+        rdt = torch.float64 if prec == FS_FP64 else torch.float32
+        probs, res = [], []
+        for j, (W, omega, geom, delta) in enumerate(items):
+            if W.dtype != want or W.device != self.device or not W.is_contiguous():
+                raise ValueError(f"problem {j}: W must be a contiguous {want} tensor on {self.device}")
+            if tuple(W.shape) != (len(omega), geom.m1, geom.n, geom.n):
+                raise ValueError(f"problem {j}: W shape does not match its geometry")
+            if outs is None:
+                xi = torch.empty((geom.m, geom.n, geom.n), dtype=rdt, device=self.device)
+                c = torch.empty_like(xi)
+            else:
+                xi, c = outs[j]
+            res.append((xi, c))
+            probs.append(make_problem(geom.c_struct(), W.data_ptr(), omega, delta, c0, xi.data_ptr(),
+                                      c.data_ptr() if c is not None else None))
+        opts = make_options(**options) if options else None
+        fs_reconstruct_batch(self.ctx, probs, prec, opts, n_streams)
+        return res
 
     def forward_born(self, xi, omega, geom: Geometry, c0: float = 1.0, precision: str = "fp64"):
         """Single-scattering data W[n_omega, M1, N, N] of xi[M, N, N] (device tensors)."""

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "F
 # every function declared in include/flatlayer.h
 EXPORTS = ("fs_version", "fs_default_options", "fs_create", "fs_destroy", "fs_last_error",
            "fs_workspace_size", "fs_reconstruct", "fs_reconstruct_host", "fs_forward_born",
-           "fs_get_report", "fs_measure_alu_peaks", "fs_reconstruct_static")
+           "fs_get_report", "fs_measure_alu_peaks", "fs_reconstruct_static", "fs_reconstruct_batch")
 
 
 class fs_geometry(C.Structure):
@@ -31,10 +31,17 @@ class fs_options(C.Structure):
     _fields_ = [("tau", C.c_double), ("delta_floor", C.c_double), ("alpha_rel", C.c_double),
                 ("eps_u", C.c_double), ("alpha_mode", C.c_int),
                 ("alpha_given", C.POINTER(C.c_double)), ("max_iter", C.c_int),
-                ("refine_iters", C.c_int), ("fp64_switch", C.c_double), ("stage_timing", C.c_int)]
+                ("refine_iters", C.c_int), ("fp64_switch", C.c_double), ("stage_timing", C.c_int),
+                ("solve_blocks_per_sm", C.c_int)]
 
 
 STAGES = ("fft_x_forward", "fft_y_forward_norms", "classify", "solve", "ifft_y_gather", "ifft_x_recover")
+
+
+class fs_problem(C.Structure):
+    _fields_ = [("geom", fs_geometry), ("W", C.c_void_p), ("omega", C.POINTER(C.c_double)),
+                ("n_omega", C.c_int), ("delta", C.c_double), ("c0", C.c_double), ("xi", C.c_void_p),
+                ("c", C.c_void_p)]
 
 
 class fs_report(C.Structure):
@@ -92,6 +99,8 @@ def lib():
                                           C.POINTER(fs_options), vp, vp]
         L.fs_forward_born.restype = ip
         L.fs_forward_born.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, vp]
+        L.fs_reconstruct_batch.restype = ip
+        L.fs_reconstruct_batch.argtypes = [vp, C.POINTER(fs_problem), ip, ip, C.POINTER(fs_options), ip]
         L.fs_reconstruct_static.restype = ip
         L.fs_reconstruct_static.argtypes = [C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, C.c_double,
                                             C.POINTER(fs_options), vp, vp, vp]
@@ -166,6 +175,22 @@ def fs_forward_born(ctx, geom, prec, xi_ptr, omega, c0, W_ptr):
     st = lib().fs_forward_born(ctx, C.byref(geom), int(prec), C.c_void_p(xi_ptr), om, len(omega),
                                float(c0), C.c_void_p(W_ptr))
     _check(ctx, st, "fs_forward_born")
+
+
+def fs_reconstruct_batch(ctx, problems, prec, opts=None, n_streams=8):
+    """problems: sequence of fs_problem (keep their buffers alive while the call runs)."""
+    arr = (fs_problem * len(problems))(*problems)
+    st = lib().fs_reconstruct_batch(ctx, arr, len(problems), int(prec),
+                                    C.byref(opts) if opts is not None else None, int(n_streams))
+    _check(ctx, st, "fs_reconstruct_batch")
+
+
+def make_problem(geom, W_ptr, omega, delta, c0, xi_ptr, c_ptr=None) -> fs_problem:
+    om = (C.c_double * len(omega))(*[float(x) for x in omega])
+    p = fs_problem(geom, C.c_void_p(W_ptr), C.cast(om, C.POINTER(C.c_double)), len(omega), float(delta),
+                   float(c0), C.c_void_p(xi_ptr), C.c_void_p(c_ptr or None))
+    p._keep = (om, geom)
+    return p
 
 
 def fs_get_report(ctx) -> dict:

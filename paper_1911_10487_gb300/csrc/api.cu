@@ -44,6 +44,10 @@ struct fs_ctx {
   size_t stage_bytes = 0;
   cudaEvent_t ev[7] = {};
   bool timed = false;
+  // batches: side streams forked from `stream` and joined back with events
+  static constexpr int MAX_SIDE = 16;
+  cudaStream_t side[MAX_SIDE] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[MAX_SIDE] = {};
   char err[512] = {0};
 };
 
@@ -122,6 +126,8 @@ fs_status validate(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, int n_o
         if (!(o->alpha_given[j] > 0.0)) return fail(ctx, FS_EINVAL, "alpha_given[%d] must be > 0", j);
     }
     if (o->max_iter < 1 || o->refine_iters < 1) return fail(ctx, FS_EINVAL, "max_iter >= 1, refine_iters >= 1");
+    if (o->solve_blocks_per_sm < 1 || o->solve_blocks_per_sm > 2)
+      return fail(ctx, FS_EINVAL, "solve_blocks_per_sm must be 1 or 2");
   }
   return FS_OK;
 }
@@ -135,6 +141,7 @@ Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, dou
   P.period = g->period; P.z1 = g->z1; P.hz = (g->z2 - g->z1) / g->m; P.c0 = c0;
   P.delta = delta; P.tau = o.tau; P.delta_floor = o.delta_floor; P.alpha_rel = o.alpha_rel; P.eps_u = o.eps_u;
   P.fp64_switch = o.fp64_switch;
+  P.solve_bps = o.solve_blocks_per_sm;
   for (int k = 0; k < g->m1; ++k) P.zy[k] = g->zy[k];
   for (int j = 0; j < n_omega; ++j) {
     P.omega[j] = omega[j];
@@ -202,31 +209,40 @@ Work<R> carve_work(void* base, const Layout& L, unsigned long long* ctr, const c
   return w;
 }
 
+// Enqueue the pipeline of one problem on `s` with workspace `base` (counters are
+// not reset here).  Twiddles for P.n must exist.
+template <typename R>
+fs_status run_on(fs_ctx* ctx, const Problem& P, const Layout& L, void* base, cudaStream_t s, const void* W,
+                 void* xi, void* c, double* alpha_out, cudaEvent_t* ev) {
+  const cx<R>* tw = (const cx<R>*)ctx->tw[sizeof(R) == 8 ? 1 : 0][size_index(P.n)];
+  Work<R> w = carve_work<R>(base, L, ctx->ctr, tw, alpha_out);
+  cudaError_t e;
+  if (ev) cudaEventRecord(ev[0], s);
+  if ((e = launch_fft2_forward<R>((const cx<R>*)W, P, w, s, ev ? ev[1] : nullptr)) != cudaSuccess)
+    return cuda_fail(ctx, e, "fft2_forward");
+  if (ev) cudaEventRecord(ev[2], s);
+  if ((e = launch_classify<R>(P, w, s)) != cudaSuccess) return cuda_fail(ctx, e, "classify");
+  if (ev) cudaEventRecord(ev[3], s);
+  if (sizeof(R) == 8) e = launch_solve_fp64(P, *(const Work<double>*)&w, s);
+  else e = launch_solve_mixed(P, *(const Work<float>*)&w, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "solve");
+  if (ev) cudaEventRecord(ev[4], s);
+  if ((e = launch_recover<R>(P, w, (R*)xi, (R*)c, s, ev ? ev[5] : nullptr)) != cudaSuccess)
+    return cuda_fail(ctx, e, "recover");
+  if (ev) cudaEventRecord(ev[6], s);
+  return FS_OK;
+}
+
 template <typename R>
 fs_status run(fs_ctx* ctx, const Problem& P, const Layout& L, const void* W, void* xi, void* c,
               double* alpha_out, bool timed) {
   const cx<R>* tw = nullptr;
   fs_status st = ensure_twiddles<R>(ctx, P.n, &tw);
   if (st != FS_OK) return st;
-  Work<R> w = carve_work<R>(ctx->ws, L, ctx->ctr, tw, alpha_out);
   cudaError_t e = cudaMemsetAsync(ctx->ctr, 0, sizeof(unsigned long long) * C_COUNT, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
-  cudaEvent_t* ev = timed ? ctx->ev : nullptr;
   ctx->timed = timed;
-  if (ev) cudaEventRecord(ev[0], ctx->stream);
-  if ((e = launch_fft2_forward<R>((const cx<R>*)W, P, w, ctx->stream, ev ? ev[1] : nullptr)) != cudaSuccess)
-    return cuda_fail(ctx, e, "fft2_forward");
-  if (ev) cudaEventRecord(ev[2], ctx->stream);
-  if ((e = launch_classify<R>(P, w, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "classify");
-  if (ev) cudaEventRecord(ev[3], ctx->stream);
-  if (sizeof(R) == 8) e = launch_solve_fp64(P, *(const Work<double>*)&w, ctx->stream);
-  else e = launch_solve_mixed(P, *(const Work<float>*)&w, ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "solve");
-  if (ev) cudaEventRecord(ev[4], ctx->stream);
-  if ((e = launch_recover<R>(P, w, (R*)xi, (R*)c, ctx->stream, ev ? ev[5] : nullptr)) != cudaSuccess)
-    return cuda_fail(ctx, e, "recover");
-  if (ev) cudaEventRecord(ev[6], ctx->stream);
-  return FS_OK;
+  return run_on<R>(ctx, P, L, ctx->ws, ctx->stream, W, xi, c, alpha_out, timed ? ctx->ev : nullptr);
 }
 
 }  // namespace
@@ -253,6 +269,7 @@ fs_status fs_default_options(fs_options* o) {
   o->refine_iters = 8;
   o->fp64_switch = 1e-4;
   o->stage_timing = 0;
+  o->solve_blocks_per_sm = 2;
   return FS_OK;
 }
 
@@ -295,6 +312,11 @@ void fs_destroy(fs_ctx* ctx) {
   if (ctx->ctr_host) cudaFreeHost(ctx->ctr_host);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (int k = 0; k < fs_ctx::MAX_SIDE; ++k) {
+    if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
+    if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   delete ctx;
 }
 
@@ -362,6 +384,87 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
     return cuda_fail(ctx, e, "D2H c");
   if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sync");
   return FS_OK;
+}
+
+fs_status fs_reconstruct_batch(fs_ctx* ctx, const fs_problem* probs, int n_probs, fs_precision prec,
+                               const fs_options* opts, int n_streams) {
+  if (!ctx) return FS_EINVAL;
+  if (!probs || n_probs <= 0) return fail(ctx, FS_EINVAL, "empty batch");
+  if (n_streams < 1 || n_streams > fs_ctx::MAX_SIDE)
+    return fail(ctx, FS_EINVAL, "n_streams must be in [1, %d]", fs_ctx::MAX_SIDE);
+  fs_options o;
+  fs_default_options(&o);
+  if (opts) o = *opts;
+  const bool fp64 = prec == FS_FP64;
+  size_t total = 0;
+  for (int i = 0; i < n_probs; ++i) {
+    const fs_problem& q = probs[i];
+    fs_status st = validate(ctx, &q.geom, prec, q.n_omega, q.omega, q.delta, q.c0, opts);
+    if (st != FS_OK) {
+      char m[256];
+      snprintf(m, sizeof(m), "%s", ctx->err);
+      return fail(ctx, st, "problem %d: %s", i, m);
+    }
+    if (!q.W || !q.xi) return fail(ctx, FS_EINVAL, "problem %d: W and xi must be device pointers", i);
+    total += align_up(layout(q.geom.n, q.geom.m, q.geom.m1, q.n_omega, fp64).total);
+  }
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  fs_status st = ensure_workspace(ctx, total);
+  if (st != FS_OK) return st;
+  for (int i = 0; i < n_probs; ++i) {
+    if (fp64) { const double2* t; st = ensure_twiddles<double>(ctx, probs[i].geom.n, &t); }
+    else { const float2* t; st = ensure_twiddles<float>(ctx, probs[i].geom.n, &t); }
+    if (st != FS_OK) return st;
+  }
+  if (!ctx->fork_ev) {
+    if (cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) != cudaSuccess) return FS_ECUDA;
+    for (int k = 0; k < fs_ctx::MAX_SIDE; ++k)
+      if (cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming) != cudaSuccess)
+        return fail(ctx, FS_ECUDA, "side streams");
+  }
+  if ((e = cudaMemsetAsync(ctx->ctr, 0, sizeof(unsigned long long) * C_COUNT, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "cudaMemsetAsync");
+  ctx->timed = false;
+  // largest problems first, dealt round-robin over the side streams
+  int* order = new (std::nothrow) int[n_probs];
+  size_t* off = new (std::nothrow) size_t[n_probs];
+  if (!order || !off) { delete[] order; delete[] off; return FS_ENOMEM; }
+  size_t acc = 0;
+  for (int i = 0; i < n_probs; ++i) {
+    order[i] = i;
+    off[i] = acc;
+    acc += align_up(layout(probs[i].geom.n, probs[i].geom.m, probs[i].geom.m1, probs[i].n_omega, fp64).total);
+  }
+  auto work = [&](int i) {
+    const fs_problem& q = probs[i];
+    return (double)q.n_omega * q.geom.n * q.geom.n * (q.geom.m + q.geom.m1);
+  };
+  for (int i = 1; i < n_probs; ++i)  // insertion sort, stable, by decreasing work
+    for (int j = i; j > 0 && work(order[j]) > work(order[j - 1]); --j) {
+      const int t = order[j]; order[j] = order[j - 1]; order[j - 1] = t;
+    }
+  const int S = n_streams < n_probs ? n_streams : n_probs;
+  cudaEventRecord(ctx->fork_ev, ctx->stream);
+  for (int k = 0; k < S; ++k) cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0);
+  for (int r = 0; r < n_probs && st == FS_OK; ++r) {
+    const int i = order[r];
+    const fs_problem& q = probs[i];
+    const Layout L = layout(q.geom.n, q.geom.m, q.geom.m1, q.n_omega, fp64);
+    const Problem P = make_problem(&q.geom, q.n_omega, q.omega, q.delta, q.c0, o);
+    char* base = (char*)ctx->ws + off[i];
+    cudaStream_t s = ctx->side[r % S];
+    st = fp64 ? run_on<double>(ctx, P, L, base, s, q.W, q.xi, q.c, nullptr, nullptr)
+              : run_on<float>(ctx, P, L, base, s, q.W, q.xi, q.c, nullptr, nullptr);
+  }
+  for (int k = 0; k < S; ++k) {
+    cudaEventRecord(ctx->join_ev[k], ctx->side[k]);
+    cudaStreamWaitEvent(ctx->stream, ctx->join_ev[k], 0);
+  }
+  delete[] order;
+  delete[] off;
+  return st;
 }
 
 fs_status fs_forward_born(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const void* xi,

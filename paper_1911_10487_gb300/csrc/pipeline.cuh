@@ -26,6 +26,7 @@ struct Problem {
   int alpha_mode;     // 0: per-mode discrepancy, 1: given alpha per frequency
   int max_iter;       // root-find iteration cap
   int refine_iters;   // mixed precision: FP64 residual refinement sweeps
+  int solve_bps;      // resident blocks per SM of the solve
   double period, z1, hz, c0;
   double delta, tau, delta_floor, alpha_rel, eps_u;
   double fp64_switch; // mixed precision: FP64 factor when alpha/tr(Gram) is below this

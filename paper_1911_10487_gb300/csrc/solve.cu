@@ -1170,15 +1170,15 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
   }
 }
 
-int solve_grid() {
-  static int grid = 0;
-  if (!grid) {
-    int dev = 0, sms = 0;
+int solve_grid(int bps) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    grid = 2 * (sms > 0 ? sms : 152);
+    if (sms <= 0) sms = 152;
   }
-  return grid;
+  return (bps == 1 ? 1 : 2) * sms;
 }
 
 template <typename B, bool MIXED>
@@ -1191,7 +1191,7 @@ cudaError_t solve_impl(const Problem& P, const Work<B>& w, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_solve<B, MIXED><<<solve_grid(), ST, smem, s>>>(P, w.wt, w.act, w.count, w.dnu, w.prof, w.alpha_out,
+  k_solve<B, MIXED><<<solve_grid(P.solve_bps), ST, smem, s>>>(P, w.wt, w.act, w.count, w.dnu, w.prof, w.alpha_out,
                                                    w.ctr);
   return cudaGetLastError();
 }
