@@ -316,6 +316,88 @@ def run_ours(args, rank, world, local):
     return result, rc, wl, geom, om, W64, outs
 
 
+def run_batch(args, local, flush, world):
+    """64 independent problems of uneven size (grids 64^2x16 .. 256^2x64, 1-8
+    frequencies, 4-32 data planes, 1% noise) in one fs_reconstruct_batch call,
+    launch configuration from the batch autotuner, replayed as one CUDA graph.
+    Its own Reconstructor, so that growing the workspace cannot invalidate the
+    single-problem graphs."""
+    import torch
+    from paper_1911_10487_gb300 import Geometry, Reconstructor
+    from paper_1911_10487_gb300.tuner import BatchTuner
+    from synth.workloads import batch_c4
+    stream = torch.cuda.Stream()
+    rc = Reconstructor(local, stream=stream)
+    wls = batch_c4()
+    items = {"fp64": [], "mixed": []}
+    outs = {"fp64": [], "mixed": []}
+    with torch.cuda.stream(stream):
+        for wl in wls:
+            geom = Geometry(wl.n, wl.m, wl.z1, wl.z2, tuple(wl.zy))
+            om = [float(x) for x in wl.omegas]
+            W = make_inputs(rc, wl, geom)
+            items["fp64"].append((W, om, geom, DELTA))
+            items["mixed"].append((W.to(torch.complex64), om, geom, DELTA))
+            for prec, rdt in (("fp64", torch.float64), ("mixed", torch.float32)):
+                xi = torch.empty((wl.m, wl.n, wl.n), dtype=rdt, device=rc.device)
+                outs[prec].append((xi, torch.empty_like(xi)))
+    torch.cuda.synchronize()
+    tuner = BatchTuner()
+    res = {}
+    cfgs = {}
+    for prec in ("fp64", "mixed"):  # FP64 first: it sizes the workspace for both
+        cfgs[prec] = tuner.best(rc, items[prec], prec, repeats=2, outs=outs[prec])
+    graphs = {}
+    for prec in ("fp64", "mixed"):
+        s_, b_ = cfgs[prec]
+        with torch.cuda.stream(stream):
+            rc.reconstruct_batch(items[prec], prec, n_streams=s_, outs=outs[prec], solve_blocks_per_sm=b_)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            rc.reconstruct_batch(items[prec], prec, n_streams=s_, outs=outs[prec], solve_blocks_per_sm=b_)
+        torch.cuda.synchronize()
+        graphs[prec] = g
+    vox = sum(wl.voxel_freqs for wl in wls)
+    K = max(3, min(args.steps, 10))
+    for prec in ("mixed", "fp64"):
+        g = graphs[prec]
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                flush.zero_()
+                g.replay()
+        torch.cuda.synchronize()
+        barrier(world)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        with torch.cuda.stream(stream):
+            for s, e in ev:
+                flush.zero_()
+                s.record(stream)
+                g.replay()
+                e.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in ev) / K, world)
+        res[prec] = {"value": world * vox / (ms * 1e-3), "ms_per_step": ms,
+                     "tuned": {"n_streams": cfgs[prec][0], "solve_blocks_per_sm": cfgs[prec][1]}}
+    grids = {}
+    for wl in wls:
+        k = f"{wl.n}^2x{wl.m}"
+        grids[k] = grids.get(k, 0) + 1
+    out = {"workload": "64 independent problems, grids " + ", ".join(f"{k}: {v}" for k, v in sorted(grids.items()))
+                       + ", 1-8 frequencies in [2pi,12pi], 4-32 data planes, 1% noise",
+           "voxel_freqs": vox, "steps": K, "cuda_graph": True, "unit": UNIT,
+           "l2": "flushed (256 MiB write) before every timed step",
+           "mixed": res["mixed"], "fp64": res["fp64"],
+           "gpu_launches_per_step": KERNELS_PER_STEP * len(wls)}
+    # smallest problem of the batch against the oracle (a parity spot check at full batch)
+    j = min(range(len(wls)), key=lambda i: wls[i].voxel_freqs * wls[i].m1)
+    out["spot_problem"] = wls[j].name
+    out["_spot"] = (wls[j], items["fp64"][j][0].cpu().numpy(), items["fp64"][j][1],
+                    outs["mixed"][j][0].double().cpu().numpy(), outs["fp64"][j][0].cpu().numpy())
+    rc.close()
+    return out
+
+
 def cpu_baseline(wl, W_np, om, rows=None):
     from oracle import inverse
     from oracle.grid import Geometry as OG
@@ -333,12 +415,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batch measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     result, rc, wl, geom, om, W64, outs = run_ours(args, rank, world, local)
+    batch = None
+    if not args.no_batch:
+        import torch
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=rc.device)
+        batch = run_batch(args, local, flush, world)
+        spot = batch.pop("_spot")
+        result["batch"] = batch
     if rank == 0:
         import torch
         W_np = W64.cpu().numpy()
@@ -351,6 +441,10 @@ def main():
             result["rel_err_vs_oracle"] = {
                 "mixed": rel_l2(outs["mixed"][0].double().cpu().numpy(), ref.xi),
                 "fp64": rel_l2(outs["fp64"][0].cpu().numpy(), ref.xi)}
+            if batch is not None:
+                swl, sW, som, sxm, sx64 = spot
+                _, sref = cpu_baseline(swl, sW, som)
+                batch["spot_rel_err_vs_oracle"] = {"mixed": rel_l2(sxm, sref.xi), "fp64": rel_l2(sx64, sref.xi)}
         print(json.dumps(result))
     rc.close()
 
