@@ -16,10 +16,12 @@ FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED = 0, 1, 2, 3, 4
 FS_FP64, FS_MIXED = 0, 1
 STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_EUNSUPPORTED"}
 
-# every function declared in include/flatlayer.h
+# every function declared in include/*.h
 EXPORTS = ("fs_version", "fs_default_options", "fs_create", "fs_destroy", "fs_last_error",
            "fs_workspace_size", "fs_reconstruct", "fs_reconstruct_host", "fs_forward_born",
-           "fs_get_report", "fs_measure_alu_peaks", "fs_reconstruct_static", "fs_reconstruct_batch")
+           "fs_get_report", "fs_measure_alu_peaks", "fs_reconstruct_static", "fs_reconstruct_batch",
+           "fs_diff_plan_create", "fs_diff_plan_destroy", "fs_diff_tape_bytes", "fs_diff_scratch_bytes",
+           "fs_reconstruct_diff", "fs_reconstruct_vjp", "fs_reconstruct_jvp")
 
 
 class fs_geometry(C.Structure):
@@ -108,6 +110,21 @@ def lib():
         L.fs_measure_alu_peaks.argtypes = [ip, C.POINTER(fs_alu_peaks)]
         L.fs_get_report.restype = ip
         L.fs_get_report.argtypes = [vp, C.POINTER(fs_report)]
+        L.fs_diff_plan_create.restype = ip
+        L.fs_diff_plan_create.argtypes = [vp, C.POINTER(fs_geometry), ip, dp, ip, C.c_double, C.c_double,
+                                          C.POINTER(vp)]
+        L.fs_diff_plan_destroy.restype = None
+        L.fs_diff_plan_destroy.argtypes = [vp]
+        L.fs_diff_tape_bytes.restype = C.c_size_t
+        L.fs_diff_tape_bytes.argtypes = [vp]
+        L.fs_diff_scratch_bytes.restype = C.c_size_t
+        L.fs_diff_scratch_bytes.argtypes = [vp, ip]
+        L.fs_reconstruct_diff.restype = ip
+        L.fs_reconstruct_diff.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.fs_reconstruct_vjp.restype = ip
+        L.fs_reconstruct_vjp.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.fs_reconstruct_jvp.restype = ip
+        L.fs_reconstruct_jvp.argtypes = [vp, vp, vp, ip, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -236,3 +253,42 @@ def fs_reconstruct_static(geom, prec, W_ptr, omega, delta, c0, opts, xi_ptr, c_p
     return lib().fs_reconstruct_static(C.byref(geom), int(prec), C.c_void_p(W_ptr), om, len(omega), float(delta),
                                        float(c0), C.byref(opts) if opts is not None else None,
                                        C.c_void_p(xi_ptr), C.c_void_p(c_ptr or None), C.c_void_p(stream or None))
+
+
+# ---- derivatives at fixed alpha (include/flatlayer_diff.h) -------------------------
+
+def fs_diff_plan_create(ctx, geom, prec, omega, c0=1.0, eps_u=1e-8):
+    om = (C.c_double * len(omega))(*[float(x) for x in omega])
+    plan = C.c_void_p()
+    st = lib().fs_diff_plan_create(ctx, C.byref(geom), int(prec), om, len(omega), float(c0), float(eps_u),
+                                   C.byref(plan))
+    _check(ctx, st, "fs_diff_plan_create")
+    return plan
+
+
+def fs_diff_plan_destroy(plan) -> None:
+    lib().fs_diff_plan_destroy(plan)
+
+
+def fs_diff_tape_bytes(plan) -> int:
+    return int(lib().fs_diff_tape_bytes(plan))
+
+
+def fs_diff_scratch_bytes(plan, n_dir: int = 1) -> int:
+    return int(lib().fs_diff_scratch_bytes(plan, int(n_dir)))
+
+
+def fs_reconstruct_diff(ctx, plan, tape, scratch, W, log_alpha, xi, c=None, phi=None):
+    """Pointer arguments are device addresses (ints) or None; ctx only for errors."""
+    st = lib().fs_reconstruct_diff(plan, tape, scratch, W, log_alpha, xi, c, phi)
+    _check(ctx, st, "fs_reconstruct_diff")
+
+
+def fs_reconstruct_vjp(ctx, plan, tape, scratch, grad_xi, grad_phi, grad_W, grad_log_alpha):
+    st = lib().fs_reconstruct_vjp(plan, tape, scratch, grad_xi, grad_phi, grad_W, grad_log_alpha)
+    _check(ctx, st, "fs_reconstruct_vjp")
+
+
+def fs_reconstruct_jvp(ctx, plan, tape, scratch, n_dir, dW, dlog_alpha, dxi, dphi=None):
+    st = lib().fs_reconstruct_jvp(plan, tape, scratch, int(n_dir), dW, dlog_alpha, dxi, dphi)
+    _check(ctx, st, "fs_reconstruct_jvp")

@@ -7,11 +7,14 @@
 #include <stdio.h>
 #include <new>
 #include <math.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <cuda_runtime.h>
 
 #include "../../include/flatlayer.h"
+#include "../../include/flatlayer_diff.h"
+#include "diff.cuh"
 #include "pipeline.cuh"
 
 using namespace fl;
@@ -519,6 +522,263 @@ fs_status fs_get_report(fs_ctx* ctx, fs_report* r) {
     r->ms_stage[i] = ms;
   }
   return FS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// derivatives at fixed alpha (include/flatlayer_diff.h)
+// ---------------------------------------------------------------------------
+struct fs_diff_plan {
+  fs_ctx* ctx = nullptr;
+  Problem P;
+  bool fp64 = true;
+  int gb = 1;              // blocks per frequency of the per-mode kernels
+  size_t P1 = 0;           // packed lower-triangle entries per mode
+  void* buf = nullptr;     // normal matrices, then the twiddle table
+  double2* gram = nullptr;
+  void* tw = nullptr;
+};
+
+namespace {
+
+struct TapeLayout {
+  size_t L, y, Vx, ux, xi, la, total;
+};
+struct ScratchLayout {
+  size_t min, mout, xsp, partial, total;
+  int nd;
+};
+
+TapeLayout tape_layout(const fs_diff_plan* p) {
+  const Problem& P = p->P;
+  const size_t cxs = p->fp64 ? 16 : 8, rs = cxs / 2;
+  const size_t N2 = (size_t)P.n * P.n, F = P.n_omega;
+  TapeLayout T;
+  size_t off = 0;
+  T.L = off; off = align_up(off + 16 * F * N2 * p->P1);
+  T.y = off; off = align_up(off + 16 * F * N2 * P.m1);
+  T.Vx = off; off = align_up(off + cxs * F * P.m * N2);
+  T.ux = off; off = align_up(off + cxs * F * P.m * N2);
+  T.xi = off; off = align_up(off + rs * P.m * N2);
+  T.la = off; off = align_up(off + 8 * F);
+  T.total = off;
+  return T;
+}
+
+ScratchLayout scratch_layout(const fs_diff_plan* p, int n_dir) {
+  const Problem& P = p->P;
+  const size_t cxs = p->fp64 ? 16 : 8;
+  const size_t N2 = (size_t)P.n * P.n, F = P.n_omega;
+  ScratchLayout S;
+  S.nd = n_dir < 1 ? 1 : (n_dir > JVP_CHUNK ? JVP_CHUNK : n_dir);
+  const size_t nd = S.nd;
+  size_t off = 0;
+  S.min = off; off = align_up(off + cxs * nd * F * P.m1 * N2);
+  S.mout = off; off = align_up(off + cxs * 2 * nd * F * P.m * N2);
+  S.xsp = off; off = align_up(off + cxs * 2 * nd * F * P.m * N2);
+  S.partial = off; off = align_up(off + 8 * nd * F * (size_t)p->gb);
+  S.total = off;
+  return S;
+}
+
+bool aligned256(const void* p) { return ((uintptr_t)p & 255) == 0; }
+
+template <typename R>
+fs_status diff_forward(fs_diff_plan* p, char* tape, char* scr, const void* W, const double* log_alpha, void* xi,
+                       void* c, double* phi) {
+  fs_ctx* ctx = p->ctx;
+  const Problem& P = p->P;
+  const TapeLayout T = tape_layout(p);
+  const ScratchLayout S = scratch_layout(p, 1);
+  const long long F = P.n_omega, N2 = (long long)P.n * P.n;
+  cudaStream_t s = ctx->stream;
+  const cx<R>* tw = (const cx<R>*)p->tw;
+  cx<R>* wt = (cx<R>*)(scr + S.min);
+  cx<R>* vt = (cx<R>*)(scr + S.mout);
+  cx<R>* ut = vt + F * P.m * N2;
+  double* part = (double*)(scr + S.partial);
+  double* la = (double*)(tape + T.la);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(la, log_alpha, 8 * F, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "log_alpha copy");
+  if ((e = launch_fft2_dense<R>((cx<R>*)W, wt, P.n, F * P.m1, false, tw, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "fft2 W");
+  if ((e = launch_diff_forward<R>(P, p->gb, p->gram, wt, la, (double2*)(tape + T.L), (double2*)(tape + T.y), vt, ut,
+                                  part, ctx->ctr, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "diff forward");
+  // V~ and U~ are adjacent, as are V and u in the tape: one inverse transform
+  if ((e = launch_fft2_dense<R>(vt, (cx<R>*)(tape + T.Vx), P.n, 2 * F * P.m, true, tw, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "ifft2 V, u");
+  if ((e = launch_diff_combine<R>(P, (const cx<R>*)(tape + T.Vx), (const cx<R>*)(tape + T.ux), (R*)xi, (R*)c,
+                                  (R*)(tape + T.xi), s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "combine");
+  if (phi && (e = launch_reduce_rows(part, (int)F, p->gb, phi, s)) != cudaSuccess) return cuda_fail(ctx, e, "phi");
+  return FS_OK;
+}
+
+template <typename R>
+fs_status diff_vjp(fs_diff_plan* p, const char* tape, char* scr, const void* gxi, const double* gphi, void* gW,
+                   double* gla) {
+  fs_ctx* ctx = p->ctx;
+  const Problem& P = p->P;
+  const TapeLayout T = tape_layout(p);
+  const ScratchLayout S = scratch_layout(p, 1);
+  const long long F = P.n_omega, N2 = (long long)P.n * P.n;
+  cudaStream_t s = ctx->stream;
+  const cx<R>* tw = (const cx<R>*)p->tw;
+  cx<R>* wbt = (cx<R>*)(scr + S.min);
+  cx<R>* vbt = (cx<R>*)(scr + S.mout);
+  cx<R>* ubt = vbt + F * P.m * N2;
+  cx<R>* Vb = (cx<R>*)(scr + S.xsp);
+  cx<R>* ub = Vb + F * P.m * N2;
+  double* part = (double*)(scr + S.partial);
+  const double* la = (const double*)(tape + T.la);
+  cudaError_t e;
+  if (gxi) {
+    if ((e = launch_diff_vjp_point<R>(P, (const R*)gxi, (const cx<R>*)(tape + T.Vx), (const cx<R>*)(tape + T.ux),
+                                      (const R*)(tape + T.xi), Vb, ub, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "vjp pointwise");
+    if ((e = launch_fft2_dense<R>(Vb, vbt, P.n, 2 * F * P.m, false, tw, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "fft2 V-bar, u-bar");
+  }
+  if ((e = launch_diff_vjp<R>(P, p->gb, (const double2*)(tape + T.L), (const double2*)(tape + T.y),
+                              gxi ? vbt : nullptr, gxi ? ubt : nullptr, la, gphi, gW ? wbt : nullptr, part, s)) !=
+      cudaSuccess)
+    return cuda_fail(ctx, e, "diff vjp");
+  if (gW && (e = launch_fft2_dense<R>(wbt, (cx<R>*)gW, P.n, F * P.m1, true, tw, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "ifft2 W-bar");
+  if (gla && (e = launch_reduce_rows(part, (int)F, p->gb, gla, s)) != cudaSuccess)
+    return cuda_fail(ctx, e, "log_alpha-bar");
+  return FS_OK;
+}
+
+template <typename R>
+fs_status diff_jvp(fs_diff_plan* p, const char* tape, char* scr, int n_dir, const void* dW, const double* dla,
+                   void* dxi, double* dphi) {
+  fs_ctx* ctx = p->ctx;
+  const Problem& P = p->P;
+  const TapeLayout T = tape_layout(p);
+  const ScratchLayout S = scratch_layout(p, n_dir);
+  const long long F = P.n_omega, N2 = (long long)P.n * P.n, MN2 = (long long)P.m * N2;
+  cudaStream_t s = ctx->stream;
+  const cx<R>* tw = (const cx<R>*)p->tw;
+  const double* la = (const double*)(tape + T.la);
+  double* part = (double*)(scr + S.partial);
+  cudaError_t e;
+  for (int d0 = 0; d0 < n_dir; d0 += S.nd) {
+    const int nd = n_dir - d0 < S.nd ? n_dir - d0 : S.nd;
+    const cx<R>* dWc = (const cx<R>*)dW + (long long)d0 * F * P.m1 * N2;
+    cx<R>* dwt = (cx<R>*)(scr + S.min);
+    cx<R>* dvt = (cx<R>*)(scr + S.mout);
+    cx<R>* dut = dvt + (long long)nd * F * MN2;
+    cx<R>* dVx = (cx<R>*)(scr + S.xsp);
+    cx<R>* dux = dVx + (long long)nd * F * MN2;
+    if ((e = launch_fft2_dense<R>((cx<R>*)dWc, dwt, P.n, (long long)nd * F * P.m1, false, tw, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "fft2 dW");
+    if ((e = launch_diff_jvp<R>(P, p->gb, nd, (const double2*)(tape + T.L), (const double2*)(tape + T.y), dwt, la,
+                                dla ? dla + (long long)d0 * F : nullptr, dvt, dut, part, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "diff jvp");
+    if ((e = launch_fft2_dense<R>(dvt, dVx, P.n, 2LL * nd * F * P.m, true, tw, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "ifft2 dV, du");
+    if ((e = launch_diff_jvp_point<R>(P, nd, (const cx<R>*)(tape + T.Vx), (const cx<R>*)(tape + T.ux),
+                                      (const R*)(tape + T.xi), dVx, dux, (R*)dxi + (long long)d0 * MN2, s)) !=
+        cudaSuccess)
+      return cuda_fail(ctx, e, "jvp pointwise");
+    if (dphi && (e = launch_reduce_rows(part, nd * (int)F, p->gb, dphi + (long long)d0 * F, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "phi-dot");
+  }
+  return FS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fs_status fs_diff_plan_create(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const double* omega,
+                              int n_omega, double c0, double eps_u, fs_diff_plan** out) {
+  if (!ctx || !out) return FS_EINVAL;
+  *out = nullptr;
+  fs_status st = validate(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr);
+  if (st != FS_OK) return st;
+  if (!(eps_u >= 0.0)) return fail(ctx, FS_EINVAL, "eps_u must be >= 0");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  fs_diff_plan* p = new (std::nothrow) fs_diff_plan();
+  if (!p) return fail(ctx, FS_ENOMEM, "plan");
+  fs_options o;
+  fs_default_options(&o);
+  o.eps_u = eps_u;
+  p->ctx = ctx;
+  p->P = make_problem(g, n_omega, omega, 0.0, c0, o);
+  p->fp64 = prec == FS_FP64;
+  p->gb = diff_blocks_per_omega(g->n, n_omega);
+  p->P1 = (size_t)g->m1 * (g->m1 + 1) / 2;
+  const size_t gbytes = align_up(16 * (size_t)n_omega * g->n * g->n * p->P1);
+  const size_t twb = (p->fp64 ? 16 : 8) * (size_t)g->n;
+  if (cudaMalloc(&p->buf, gbytes + twb) != cudaSuccess) {
+    delete p;
+    return fail(ctx, FS_ENOMEM, "normal matrices (%lld bytes)", (long long)(gbytes + twb));
+  }
+  p->gram = (double2*)p->buf;
+  p->tw = (char*)p->buf + gbytes;
+  e = p->fp64 ? launch_twiddles<double>((double2*)p->tw, g->n, ctx->stream)
+              : launch_twiddles<float>((float2*)p->tw, g->n, ctx->stream);
+  if (e == cudaSuccess) e = launch_diff_gram(p->P, p->gram, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaFree(p->buf);
+    delete p;
+    return cuda_fail(ctx, e, "plan kernels");
+  }
+  *out = p;
+  return FS_OK;
+}
+
+void fs_diff_plan_destroy(fs_diff_plan* p) {
+  if (!p) return;
+  cudaSetDevice(p->ctx->device);
+  cudaStreamSynchronize(p->ctx->stream);
+  cudaFree(p->buf);
+  delete p;
+}
+
+size_t fs_diff_tape_bytes(const fs_diff_plan* p) { return p ? tape_layout(p).total : 0; }
+
+size_t fs_diff_scratch_bytes(const fs_diff_plan* p, int n_dir) { return p ? scratch_layout(p, n_dir).total : 0; }
+
+fs_status fs_reconstruct_diff(fs_diff_plan* p, void* tape, void* scratch, const void* W, const double* log_alpha,
+                              void* xi, void* c, double* phi) {
+  if (!p) return FS_EINVAL;
+  if (!tape || !scratch || !W || !log_alpha || !xi)
+    return fail(p->ctx, FS_EINVAL, "tape, scratch, W, log_alpha and xi must be device pointers");
+  if (!aligned256(tape) || !aligned256(scratch)) return fail(p->ctx, FS_EINVAL, "tape and scratch must be 256-byte aligned");
+  cudaError_t e = cudaSetDevice(p->ctx->device);
+  if (e != cudaSuccess) return cuda_fail(p->ctx, e, "cudaSetDevice");
+  return p->fp64 ? diff_forward<double>(p, (char*)tape, (char*)scratch, W, log_alpha, xi, c, phi)
+                 : diff_forward<float>(p, (char*)tape, (char*)scratch, W, log_alpha, xi, c, phi);
+}
+
+fs_status fs_reconstruct_vjp(fs_diff_plan* p, const void* tape, void* scratch, const void* grad_xi,
+                             const double* grad_phi, void* grad_W, double* grad_log_alpha) {
+  if (!p) return FS_EINVAL;
+  if (!tape || !scratch) return fail(p->ctx, FS_EINVAL, "tape and scratch must be device pointers");
+  if (!aligned256(tape) || !aligned256(scratch)) return fail(p->ctx, FS_EINVAL, "tape and scratch must be 256-byte aligned");
+  cudaError_t e = cudaSetDevice(p->ctx->device);
+  if (e != cudaSuccess) return cuda_fail(p->ctx, e, "cudaSetDevice");
+  return p->fp64 ? diff_vjp<double>(p, (const char*)tape, (char*)scratch, grad_xi, grad_phi, grad_W, grad_log_alpha)
+                 : diff_vjp<float>(p, (const char*)tape, (char*)scratch, grad_xi, grad_phi, grad_W, grad_log_alpha);
+}
+
+fs_status fs_reconstruct_jvp(fs_diff_plan* p, const void* tape, void* scratch, int n_dir, const void* dW,
+                             const double* dlog_alpha, void* dxi, double* dphi) {
+  if (!p) return FS_EINVAL;
+  if (n_dir < 1) return fail(p->ctx, FS_EINVAL, "n_dir must be >= 1");
+  if (!tape || !scratch || !dW || !dxi) return fail(p->ctx, FS_EINVAL, "tape, scratch, dW and dxi must be device pointers");
+  if (!aligned256(tape) || !aligned256(scratch)) return fail(p->ctx, FS_EINVAL, "tape and scratch must be 256-byte aligned");
+  cudaError_t e = cudaSetDevice(p->ctx->device);
+  if (e != cudaSuccess) return cuda_fail(p->ctx, e, "cudaSetDevice");
+  return p->fp64 ? diff_jvp<double>(p, (const char*)tape, (char*)scratch, n_dir, dW, dlog_alpha, dxi, dphi)
+                 : diff_jvp<float>(p, (const char*)tape, (char*)scratch, n_dir, dW, dlog_alpha, dxi, dphi);
 }
 
 }  // extern "C"

@@ -339,14 +339,22 @@ cudaError_t rec_impl(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream
 template <typename R, int N>
 cudaError_t dense_impl(cx<R>* in, cx<R>* out, long long planes, bool inverse, const cx<R>* tw, cudaStream_t s) {
   constexpr int LINES = row_lines<N>();
+  constexpr long long MAX_Y = 32768;  // planes per column launch (grid y <= 65535)
   const long long nrows = planes * N;
   const unsigned nblk = (unsigned)((nrows + LINES - 1) / LINES);
-  const dim3 gc((N + Cfg<R>::TC - 1) / Cfg<R>::TC, (unsigned)planes);
+  auto cols = [&](cx<R>* buf, bool inv) {
+    for (long long p0 = 0; p0 < planes; p0 += MAX_Y) {
+      const long long np = planes - p0 < MAX_Y ? planes - p0 : MAX_Y;
+      const dim3 gc((N + Cfg<R>::TC - 1) / Cfg<R>::TC, (unsigned)np);
+      if (inv) k_fft_cols<R, N, true><<<gc, THREADS, 0, s>>>(buf + p0 * N * N, tw);
+      else k_fft_cols<R, N, false><<<gc, THREADS, 0, s>>>(buf + p0 * N * N, tw);
+    }
+  };
   if (!inverse) {
     k_fft_rows<R, N, false><<<nblk, THREADS, 0, s>>>(in, out, nrows, tw, R(1));
-    k_fft_cols<R, N, false><<<gc, THREADS, 0, s>>>(out, tw);
+    cols(out, false);
   } else {
-    k_fft_cols<R, N, true><<<gc, THREADS, 0, s>>>(in, tw);
+    cols(in, true);
     k_fft_rows<R, N, true><<<nblk, THREADS, 0, s>>>(in, out, nrows, tw, R(1.0 / ((double)N * N)));
   }
   return cudaGetLastError();

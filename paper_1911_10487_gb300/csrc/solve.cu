@@ -39,6 +39,7 @@
 //            refinement) take the FS_FP64 route.
 #include <math.h>
 
+#include "modes.cuh"
 #include "pipeline.cuh"
 
 // FL_PHASE_TIMING (development builds only) records clock64() at phase
@@ -183,55 +184,6 @@ k_classify(Problem P, const double* __restrict__ norms, const double* __restrict
 // ------------------------------------------------------------------------------
 // scalar helpers
 // ------------------------------------------------------------------------------
-
-// Reciprocal of a normal double by Newton-Raphson (y <- y (2 - x y), quadratic
-// convergence) from an FP32 seed of the mantissa; two steps take the 24-bit seed
-// past 53 bits.  Exponent handled on the bit pattern.  Four dependent FP64
-// operations instead of a full FP64 division.
-__device__ __forceinline__ double rcp64(double x) {
-  const long long bits = __double_as_longlong(x);
-  const int ex = (int)((bits >> 52) & 0x7ff);
-  if (ex == 0 || ex == 0x7ff) return 1.0 / x;  // zero, subnormal, inf, nan
-  const double m = __longlong_as_double((bits & ~(0x7ffLL << 52)) | (1023LL << 52));  // [1,2), sign kept
-  double y = (double)(1.0f / (float)m);
-  double t = fma(-m, y, 1.0);
-  y = fma(y, t, y);
-  t = fma(-m, y, 1.0);
-  y = fma(y, t, y);
-  // y ~ 1/m in (0.5, 1]; scale by 2^-(ex-1023) through the exponent field
-  const long long yb = __double_as_longlong(y);
-  const int ey = (int)((yb >> 52) & 0x7ff) - (ex - 1023);
-  if (ey <= 0 || ey >= 0x7ff) return 1.0 / x;
-  return __longlong_as_double((yb & ~(0x7ffLL << 52)) | ((long long)ey << 52));
-}
-
-template <typename T> __device__ __forceinline__ T rcp(T x);
-template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }  // ~2 ulp
-template <> __device__ __forceinline__ double rcp<double>(double x) { return rcp64(x); }
-
-__device__ __forceinline__ double2 warp_sum(double2 v) {
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-  }
-  return v;
-}
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ float warp_sum(float v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// exp(i kz d) for kz real (propagating) or purely imaginary (evanescent), d >= 0
-__device__ __forceinline__ double2 exp_ikz(double2 kz, double d) {
-  const double mag = exp(-kz.y * d);
-  double s, c;
-  sincos(kz.x * d, &s, &c);
-  return make_double2(mag * c, mag * s);
-}
 
 // ------------------------------------------------------------------------------
 // two-float arithmetic: a value is hi + lo (|lo| <= ulp(hi)/2); sums and products
@@ -901,30 +853,6 @@ __device__ float root32_warp(Shared& S, int n, float lo, float hi, float target,
   }
   const float t = gh > gl ? tl + (th - tl) * (-gl / (gh - gl)) : 0.5f * (tl + th);
   return expf(t);
-}
-
-// F_l = sum_{l' <= l} q^(l - l') s_l' for l < len <= 64, one warp, lanes own two
-// consecutive elements; an inclusive scan of the affine maps x -> A x + B.
-__device__ void affine_scan64(const double2* s, int len, double2 q, double2* out) {
-  const int lane = threadIdx.x & 31;
-  const int l0 = 2 * lane, l1 = l0 + 1;
-  const double2 s0 = l0 < len ? s[l0] : make_double2(0, 0);
-  const double2 s1 = l1 < len ? s[l1] : make_double2(0, 0);
-  double2 A = q * q;
-  double2 B = q * s0 + s1;
-  for (int off = 1; off < 32; off <<= 1) {
-    const double2 Ap = make_double2(__shfl_up_sync(0xffffffffu, A.x, off), __shfl_up_sync(0xffffffffu, A.y, off));
-    const double2 Bp = make_double2(__shfl_up_sync(0xffffffffu, B.x, off), __shfl_up_sync(0xffffffffu, B.y, off));
-    if (lane >= off) {
-      B = A * Bp + B;
-      A = A * Ap;
-    }
-  }
-  // B = F_{l1}; F_{l0} = q F_{l0 - 1} + s0
-  double2 prev = make_double2(__shfl_up_sync(0xffffffffu, B.x, 1), __shfl_up_sync(0xffffffffu, B.y, 1));
-  if (lane == 0) prev = make_double2(0, 0);
-  if (l0 < len) out[l0] = q * prev + s0;
-  if (l1 < len) out[l1] = B;
 }
 
 template <typename B, bool MIXED>
