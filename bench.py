@@ -398,6 +398,96 @@ def run_batch(args, local, flush, world):
     return out
 
 
+def run_diff(args, local, flush, world):
+    """Derivatives at fixed alpha per frequency on 128x128x64, 4 frequencies
+    (4pi..10pi), 32 data planes, 3 Gaussians, 1% noise: alpha tuned by 50
+    Gauss-Newton-scaled gradient steps on sum (Phi/target - 1)^2, 16 seeded data
+    perturbations of 1% pushed through as JVPs, one full VJP; full-size checks by
+    the dot-product test and a central difference (h = 1e-6, FP64)."""
+    import torch
+    from paper_1911_10487_gb300 import Geometry, Reconstructor
+    from paper_1911_10487_gb300.diff import DiffPlan, jvp_study, tune_log_alpha
+    from synth import noise_direction, workload
+    wl = workload("c5")
+    stream = torch.cuda.Stream()
+    rc = Reconstructor(local, stream=stream)
+    geom = Geometry(wl.n, wl.m, wl.z1, wl.z2, tuple(wl.zy))
+    om = [float(x) for x in wl.omegas]
+    F, N2 = len(om), wl.n * wl.n
+    rng = np.random.default_rng(44)
+    nd = 16
+    dirs = noise_direction(rng, (nd, F, wl.m1, wl.n, wl.n))
+    out = {"workload": "128x128x64 X grid, 32 data planes, 4 frequencies 4pi..10pi, 3 Gaussians, 1% noise",
+           "voxel_freqs": wl.voxel_freqs}
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    with torch.cuda.stream(stream):
+        W64 = make_inputs(rc, wl, geom)
+        tgt = torch.stack([N2 * (2.0 * DELTA * torch.linalg.vector_norm(W64[j])) ** 2 for j in range(F)]).double()
+        la0 = torch.zeros(F, dtype=torch.float64, device=rc.device)
+        dW_all = torch.from_numpy(dirs).to(rc.device)
+        for j in range(F):  # each direction scaled to 1% of ||W_omega|| per frequency
+            nrm = torch.linalg.vector_norm(dW_all[:, j].reshape(nd, -1), dim=1).reshape(nd, 1, 1, 1)
+            dW_all[:, j] *= DELTA * torch.linalg.vector_norm(W64[j]) / nrm
+        for prec in ("mixed", "fp64"):
+            W = W64 if prec == "fp64" else W64.to(torch.complex64)
+            dW = dW_all if prec == "fp64" else dW_all.to(torch.complex64)
+            t0, t1 = ev()
+            t0.record(stream)
+            plan = DiffPlan(rc, geom, om, prec)
+            t1.record(stream)
+            tune_log_alpha(plan, W, la0, tgt, steps=3)  # warm-up
+            a0, a1 = ev()
+            a0.record(stream)
+            la, hist = tune_log_alpha(plan, W, la0, tgt, steps=50)
+            a1.record(stream)
+            plan.jvp(plan.forward(W, la)[3], dW)  # warm-up of the JVP scratch
+            reps = max(3, min(args.steps, 10))
+            f0, f1 = ev()
+            f0.record(stream)
+            for _ in range(reps):
+                flush.zero_()
+                xi, _, phi, tape = plan.forward(W, la)
+            f1.record(stream)
+            gxi = torch.ones_like(xi)
+            b0, b1 = ev()
+            b0.record(stream)
+            for _ in range(reps):
+                flush.zero_()
+                gW, gla = plan.vjp(tape, gxi, None)
+            b1.record(stream)
+            j0, j1 = ev()
+            j0.record(stream)
+            dxi, amp = jvp_study(plan, tape, W, dW, xi)
+            j1.record(stream)
+            torch.cuda.synchronize()
+            # full-size checks: dot-product test on direction 0; FP64 central difference
+            lhs = float((dxi[0].double() * gxi.double()).sum())
+            rhs = float((torch.conj(gW[0:F]).to(torch.complex128) * dW[0].to(torch.complex128)).real.sum())
+            res = {"ms_plan_normal_matrices": t0.elapsed_time(t1),
+                   "ms_tune_alpha_50_steps": a0.elapsed_time(a1),
+                   "ms_forward": f0.elapsed_time(f1) / reps, "ms_vjp": b0.elapsed_time(b1) / reps,
+                   "ms_jvp_16_directions": j0.elapsed_time(j1),
+                   "forward_voxel_freqs_per_s": wl.voxel_freqs / (f0.elapsed_time(f1) / reps * 1e-3),
+                   "tuned_log_alpha": la.cpu().tolist(), "misfit_first_last": [float(hist[0]), float(hist[-1])],
+                   "jvp_amplification_mean_max": [float(amp.mean()), float(amp.max())],
+                   "dot_product_rel_err": abs(lhs - rhs) / abs(lhs)}
+            if prec == "fp64":
+                h = 1e-6
+                xp = plan.forward(W + h * dW[0], la)[0]
+                xm = plan.forward(W - h * dW[0], la)[0]
+                fd = (xp - xm) / (2 * h)
+                res["central_difference_rel_err"] = float(torch.linalg.vector_norm(fd - dxi[0]) /
+                                                          torch.linalg.vector_norm(fd))
+            out[prec] = res
+            plan.close()
+    torch.cuda.synchronize()
+    rc.close()
+    return out
+
+
 def cpu_baseline(wl, W_np, om, rows=None):
     from oracle import inverse
     from oracle.grid import Geometry as OG
@@ -416,6 +506,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batch measurement")
+    ap.add_argument("--no-diff", action="store_true", help="skip the derivative measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_setup(args.gpus)
@@ -429,6 +520,10 @@ def main():
         batch = run_batch(args, local, flush, world)
         spot = batch.pop("_spot")
         result["batch"] = batch
+    if not args.no_diff:
+        import torch
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=rc.device)
+        result["differentiation"] = run_diff(args, local, flush, world)
     if rank == 0:
         import torch
         W_np = W64.cpu().numpy()
