@@ -9,17 +9,17 @@
 //      exp(i k_z (z_k - z'_l)) is evaluated as exp(i k_z (z_k - z'_top)) *
 //      exp(i k_z (z'_top - z'_l)) with both factors of modulus <= 1;
 //   2. forms the dual normal matrix G = A A^H (M1 x M1, Hermitian);
-//   3. reduces G to a real symmetric tridiagonal T = D^H Q^H G Q D by Householder
-//      reflections (Q) and a diagonal phase scaling (D);
-//   4. picks alpha by the discrepancy principle: with c = D^H Q^H b and
-//      z(alpha) = (T + alpha I)^-1 c (tridiagonal LDL^T solve), the residual of the
-//      Tikhonov solution is b - A A^H y = alpha y, so
-//      phi(alpha) = ||A V~ - b|| = alpha ||z(alpha)||; the root of phi = delta_nu is
-//      found by Newton's method in log(alpha) inside a bisection bracket
-//      [alpha_floor, tr(G) delta_nu/(||b|| - delta_nu)], alpha_floor = alpha_rel tr(G);
-//      phi(alpha_floor) >= delta_nu selects alpha_floor;
-//   5. y = Q D z, V~ = A^H y (the Tikhonov solution (A^H A + alpha I)^-1 A^H b in
-//      its dual form);
+//   3. reduces G to a real symmetric tridiagonal T = Q^H G Q by the Lanczos process
+//      started from q_1 = b / ||b|| (full reorthogonalisation), stopped when the
+//      Krylov space is invariant to working precision -- after two steps for these
+//      kernels, whose matrices are rank one up to rounding;
+//   4. picks alpha by the discrepancy principle: since q_1 = b / ||b|| and the
+//      residual of the Tikhonov solution is b - A A^H y = alpha y,
+//      phi(alpha) = ||A V~ - b|| = ||b|| alpha ||(T + alpha I)^-1 e_1||; the root of
+//      phi = delta_nu lies in the bracket [alpha_floor, tr(G) delta_nu/(||b|| - delta_nu)],
+//      alpha_floor = alpha_rel tr(G); phi(alpha_floor) >= delta_nu selects alpha_floor;
+//   5. y = (G + alpha I)^-1 b, V~ = A^H y (the Tikhonov solution
+//      (A^H A + alpha I)^-1 A^H b in its dual form);
 //   6. U~ = U~0 + omega^2 T_nu V~ with T_nu[l, l'] = h_z K_nu(z'_l - z'_l'): since the
 //      X planes are uniform, T_nu is h_z(-i/2k_z) q^|l-l'| with q = exp(i k_z h_z),
 //      applied as one forward and one backward first-order recurrence (the z part
@@ -27,16 +27,18 @@
 //
 // Cost model on this GPU: a dependent FP64 operation costs ~64 cycles and an FP64
 // division ~640, while FP32 runs at 64x the FP64 rate.  So every sequential chain
-// (Householder scalars, tridiagonal solves, the root-find) runs in FP32 wherever
-// the precision allows, and FP64 is kept to parallel matrix-vector products.
-//  FS_FP64 : steps 2-3 in FP64; the root is seeded by an FP32 root-find on T and
-//            finished by FP64 Newton steps (reciprocals by Newton-Raphson from an
-//            FP32 seed instead of FP64 division).
-//  FS_MIXED: steps 2-4 in FP32; y is refined against the FP64 residual
-//            b - A (A^H y) - alpha y, and alpha gets one FP64 Newton correction
-//            from the refined residual.  Modes whose alpha/tr(G) falls below
-//            fp64_switch (where the FP32 factorisation no longer converges the
-//            refinement) take the FS_FP64 route.
+// (the Lanczos scalars, tridiagonal solves, the root-find) is kept short and runs
+// in FP32 wherever the precision allows.
+//  FS_FP64 : steps 2-3 in FP64; the root is seeded by an FP32 search on T and
+//            finished by FP64 Newton steps in log(alpha) (reciprocals by
+//            Newton-Raphson from an FP32 seed instead of FP64 division);
+//            y = (||b||/tr) Q (T/tr + a I)^-1 e_1.
+//  FS_MIXED: steps 2-4 in FP32 on the scaled problem; y is then refined against
+//            the residual b - A (A^H y) - alpha y evaluated in two-float arithmetic
+//            (about 48 bits), each correction solved with a Cholesky factor of
+//            G + alpha I (FP32).  Modes whose alpha/tr(G) falls below fp64_switch
+//            (where the FP32 factor no longer makes the refinement contract), floor
+//            cases and FP32 breakdowns take the FS_FP64 route.
 #include <math.h>
 
 #include "modes.cuh"
@@ -63,6 +65,10 @@ namespace fl {
 namespace {
 
 constexpr int ST = 128;  // threads per solve block (>= 2 MAX_M and >= 4 MAX_M1)
+// Lanczos stops when the next off-diagonal of T is at most this fraction of
+// tr(G): a few units of round-off of the normal matrix in each precision
+constexpr float LANCZOS_TOL32 = 1e-6f;
+constexpr double LANCZOS_TOL64 = 1e-14;
 static_assert(ST >= 2 * MAX_M && ST >= 4 * MAX_M1, "solve block too small");
 
 // ------------------------------------------------------------------------------
@@ -246,13 +252,13 @@ __device__ __forceinline__ ffc ffc_shfl_xor(ffc a, int m) {
 // ------------------------------------------------------------------------------
 template <typename B> struct Bulk {
   cx<B> G[MAX_M1][MAX_M1 + 1];
-  cx<B> V[MAX_M1][MAX_M1];  // reflector j: V[j][0 .. n-j-2]
+  cx<B> V[MAX_M1][MAX_M1 + 1];  // Lanczos basis, column j = q_j (FP64 route)
   B beta[MAX_M1];
   cx<B> p[MAX_M1], wv[MAX_M1];
 };
 struct BulkF : Bulk<float> {
   float2 A[MAX_M1][MAX_M + 1];   // A_nu / sqrt(tr G) in FP32 (mixed precision)
-  float2 Q[MAX_M1][MAX_M1 + 1];  // Q D formed explicitly (mixed precision)
+  float2 Q[MAX_M1][MAX_M1 + 1];  // Lanczos basis, column j = q_j (mixed precision)
   float2 ts[MAX_M1][32];         // per-lane tridiagonal solves: scaled forward values
   float tmu[MAX_M1][32];         //                              and multipliers
 };
@@ -261,13 +267,13 @@ struct Shared {
   double2 A[MAX_M1][MAX_M + 1];  // A_nu in FP64
   union { Bulk<double> d; BulkF f; } u;
   double2 E[MAX_M1], Pz[MAX_M], b[MAX_M1], c[MAX_M1], y[MAX_M1], r[MAX_M1], z[MAX_M1];
-  double2 ph[MAX_M1], Vt[MAX_M], t[MAX_M], F[MAX_M], Bk[MAX_M], z64[MAX_M];
+  double2 Vt[MAX_M], t[MAX_M], F[MAX_M], Bk[MAX_M], z64[MAX_M];
   double d[MAX_M1], e[MAX_M1];     // tridiagonal T (FP64 route: of G; scaled by 1/tr after the factor)
   float d32[MAX_M1], e32[MAX_M1];  // T / tr in FP32
-  float2 c32[MAX_M1], cz[MAX_M1], r32[MAX_M1];
+  float2 c32[MAX_M1], r32[MAX_M1];
   ffc yh[MAX_M1], rh[MAX_M1], bh[MAX_M1], th[MAX_M], Ef[MAX_M1], Pf[MAX_M];  // two-float (mixed route)
   double tr, sb, inv_sb, dnu, lo, hi, a_s, red[8];  // a_s = alpha / tr
-  int fp64, tflag;
+  int fp64, tflag, kd;  // kd: dimension of the Lanczos model
 };
 
 template <typename B> __device__ __forceinline__ Bulk<B>& bulk(Shared& s);
@@ -296,143 +302,57 @@ __device__ void gram(Shared& S, int n, int m) {
   __syncthreads();
 }
 
-// Householder reduction of the Hermitian G to tridiagonal form, then d, |e| and
-// the phases D (prefix products of e_i/|e_i|) that make the off-diagonal real.
-template <typename B>
-__device__ void tridiagonalize(Shared& S, int n) {
-  Bulk<B>& K = bulk<B>(S);
-  for (int j = 0; j + 2 < n; ++j) {
-    const int ml = n - j - 1;  // length of the column below the diagonal
-    if (threadIdx.x < 32) {
-      const int r = threadIdx.x;
-      cx<B> x = (r < ml) ? K.G[j + 1 + r][j] : czero<B>();
-      const B nx2 = warp_sum(abs2(x));
-      const cx<B> x0 = K.G[j + 1][j];
-      const B ax02 = abs2(x0);
-      B beta = B(0);
-      cx<B> ah = czero<B>();
-      if (nx2 > B(0)) {
-        const B nx = sqrt(nx2);
-        const B ax0 = sqrt(ax02);
-        const B inv = ax0 > B(0) ? rcp<B>(ax0) : B(0);
-        const cx<B> ph = ax0 > B(0) ? mk<B>(x0.x * inv, x0.y * inv) : mk<B>(B(1), B(0));
-        ah = mk<B>(-ph.x * nx, -ph.y * nx);
-        if (r == 0) x = mk<B>(ph.x * (ax0 + nx), ph.y * (ax0 + nx));
-        beta = rcp<B>(nx * (nx + ax0));
+// Lanczos tridiagonalisation of the Hermitian G (n x n, shared) from the unit
+// vector in column 0 of Q, with full reorthogonalisation (classical Gram-Schmidt,
+// twice): Q^H G Q = T, real symmetric tridiagonal with diagonal d and
+// off-diagonal e >= 0.  Stops when the next off-diagonal is not above tol (the
+// Krylov space of q_0 is then invariant to that level) or at n columns, and
+// returns the number k of columns.  Warp 0, lane r owning row r.
+// The (1,1) entries of (T + a I)^-1 and (T + a I)^-2, from which the discrepancy
+// is computed, depend on e only through the squares e_j^2, so stopping at
+// e_k <= tol changes phi^2 by O(tol^2 / a^2) relative.
+template <typename T>
+__device__ int lanczos_warp(const cx<T> (*G)[MAX_M1 + 1], int n, cx<T> (*Q)[MAX_M1 + 1], T* d, T* e,
+                            cx<T>* wbuf, cx<T>* hbuf, T tol) {
+  const int lane = threadIdx.x & 31;
+  int k = n;
+  for (int j = 0; j < n; ++j) {
+    cx<T> w = czero<T>();
+    if (lane < n) {  // w = G q_j
+      cx<T> a0 = czero<T>(), a1 = czero<T>();
+      int c = 0;
+      for (; c + 1 < n; c += 2) {
+        a0 = a0 + G[lane][c] * Q[c][j];
+        a1 = a1 + G[lane][c + 1] * Q[c + 1][j];
       }
-      if (r < ml) K.V[j][r] = x;
-      if (r == 0) {
-        K.beta[j] = beta;
-        K.G[j + 1][j] = ah;
-        K.G[j][j + 1] = conjx(ah);
-      }
+      if (c < n) a0 = a0 + G[lane][c] * Q[c][j];
+      w = a0 + a1;
     }
-    __syncthreads();
-    const B beta = K.beta[j];
-    if (beta == B(0)) continue;  // uniform across the block
-    {  // p = beta S v, S = trailing block; 4 threads per row
-      const int r = threadIdx.x >> 2, part = threadIdx.x & 3;
-      cx<B> acc = czero<B>();
-      if (r < ml)
-        for (int cc = part; cc < ml; cc += 4) acc = acc + K.G[j + 1 + r][j + 1 + cc] * K.V[j][cc];
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
-      if (r < ml && part == 0) K.p[r] = beta * acc;
+    const cx<T> qj = lane < n ? Q[lane][j] : czero<T>();
+    const T aj = warp_sum(qj.x * w.x + qj.y * w.y);  // q_j^H G q_j (real)
+    w = w - aj * qj;
+    if (j > 0 && lane < n) w = w - e[j - 1] * Q[lane][j - 1];
+    for (int pass = 0; pass < 2; ++pass) {  // w -= Q (Q^H w) over q_0 .. q_j
+      if (lane < n) wbuf[lane] = w;
+      __syncwarp();
+      cx<T> h = czero<T>();
+      if (lane <= j)
+        for (int r = 0; r < n; ++r) h = h + cmul_conj_a(Q[r][lane], wbuf[r]);
+      hbuf[lane] = h;
+      __syncwarp();
+      if (lane < n)
+        for (int i = 0; i <= j; ++i) w = w - Q[lane][i] * hbuf[i];
+      __syncwarp();
     }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const int r = threadIdx.x;
-      const cx<B> vr = r < ml ? K.V[j][r] : czero<B>();
-      const cx<B> pr = r < ml ? K.p[r] : czero<B>();
-      const B kk = B(0.5) * beta * warp_sum(vr.x * pr.x + vr.y * pr.y);  // (beta/2) Re(v^H p)
-      if (r < ml) K.wv[r] = pr - kk * vr;
-    }
-    __syncthreads();
-    // S -= v w^H + w v^H on the lower triangle, mirrored to the upper one
-    const int nl = ml * (ml + 1) / 2;
-    for (int e = threadIdx.x; e < nl; e += ST) {
-      int r = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-      while (r * (r + 1) / 2 > e) --r;
-      while ((r + 1) * (r + 2) / 2 <= e) ++r;
-      const int cc = e - r * (r + 1) / 2;
-      const cx<B> v_r = K.V[j][r], v_c = K.V[j][cc], w_r = K.wv[r], w_c = K.wv[cc];
-      cx<B> g = K.G[j + 1 + r][j + 1 + cc] - (mulc(v_r, w_c) + mulc(w_r, v_c));
-      if (r == cc) g.y = B(0);
-      K.G[j + 1 + r][j + 1 + cc] = g;
-      K.G[j + 1 + cc][j + 1 + r] = conjx(g);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x < 32) {
-    const int i = threadIdx.x;
-    cx<B> u = mk<B>(B(1), B(0));
-    B ae = B(0);
-    if (i < n) {
-      S.d[i] = (double)K.G[i][i].x;
-      if (sizeof(B) == 4) S.d32[i] = (float)K.G[i][i].x;
-    }
-    if (i + 1 < n) {
-      const cx<B> ei = K.G[i + 1][i];
-      ae = sqrt(abs2(ei));
-      if (ae > B(0)) {
-        const B inv = rcp<B>(ae);
-        u = mk<B>(ei.x * inv, ei.y * inv);
-      }
-      S.e[i] = (double)ae;
-      if (sizeof(B) == 4) S.e32[i] = (float)ae;
-    }
-    // inclusive prefix product of u over the lanes: ph[i+1] = u_0 ... u_i
-    for (int off = 1; off < 32; off <<= 1) {
-      const B ox = __shfl_up_sync(0xffffffffu, u.x, off);
-      const B oy = __shfl_up_sync(0xffffffffu, u.y, off);
-      if (i >= off) u = mk<B>(ox, oy) * u;
-    }
-    if (i + 1 < n) S.ph[i + 1] = to_d(u);
-    if (i == 0) S.ph[0] = make_double2(1.0, 0.0);
-  }
-  __syncthreads();
-}
-
-// out = s * D^H Q^H in  (reflectors, ascending), warp 0, arithmetic in W.
-template <typename B, typename W>
-__device__ void apply_QH(Shared& S, int n, const double2* in, double s, cx<W>* out) {
-  Bulk<B>& K = bulk<B>(S);
-  if (threadIdx.x < 32) {
-    const int r = threadIdx.x;
-    cx<W> x = r < n ? from_d<W>(s * in[r]) : czero<W>();
-    for (int j = 0; j + 2 < n; ++j) {
-      const W beta = (W)K.beta[j];
-      if (beta == W(0)) continue;
-      const bool mine = r > j && r < n;  // lanes of the reflector's rows only
-      const cx<W> v = mine ? from_d<W>(to_d(K.V[j][r - j - 1])) : czero<W>();
-      const cx<W> dot = warp_sum(cmul_conj_a(v, x));  // v^H x
-      if (mine) x = x - beta * (v * dot);
-    }
-    if (r < n) out[r] = cmul_conj_a(from_d<W>(S.ph[r]), x);
+    const T beta = sqrt(warp_sum(abs2(w)));
+    if (lane == 0) d[j] = aj;
+    if (j + 1 == n || !(beta > tol)) { k = j + 1; break; }
+    if (lane == 0) e[j] = beta;
+    if (lane < n) Q[lane][j + 1] = rcp<T>(beta) * w;
+    __syncwarp();
   }
   __syncwarp();
-}
-
-// out = s * Q D in  (reflectors, descending), warp 0, arithmetic in W.
-template <typename B, typename W>
-__device__ void apply_Q(Shared& S, int n, const cx<W>* in, double s, double2* out) {
-  Bulk<B>& K = bulk<B>(S);
-  if (threadIdx.x < 32) {
-    const int r = threadIdx.x;
-    cx<W> x = r < n ? from_d<W>(S.ph[r]) * in[r] : czero<W>();
-    for (int j = n - 3; j >= 0; --j) {
-      const W beta = (W)K.beta[j];
-      if (beta == W(0)) continue;
-      const bool mine = r > j && r < n;  // lanes of the reflector's rows only
-      const cx<W> v = mine ? from_d<W>(to_d(K.V[j][r - j - 1])) : czero<W>();
-      const cx<W> dot = warp_sum(cmul_conj_a(v, x));
-      if (mine) x = x - beta * (v * dot);
-    }
-    if (r < n) out[r] = s * to_d(x);
-  }
-  __syncwarp();
+  return k;
 }
 
 // (T + a I) z = rhs, T real symmetric tridiagonal (d, e); single thread.
@@ -517,23 +437,31 @@ __device__ double block_sum(Shared& S, double v) {
   return (S.red[0] + S.red[1]) + (S.red[2] + S.red[3]);
 }
 
-// FP64 route: FP64 factorisation, FP32-seeded root on the scaled tridiagonal,
-// FP64 Newton to full accuracy, y = Q D (T + alpha I)^-1 D^H Q^H b.
+// FP64 route: FP64 normal matrix and Lanczos model, FP32-seeded root on the
+// scaled tridiagonal, FP64 Newton to full accuracy, y = (||b||/tr) Q (T/tr + a I)^-1 e_1.
 __device__ void solve_fp64(Shared& S, int n, int m, const Problem& P, int om, unsigned long long* ctr) {
   gram<double>(S, n, m);
-  tridiagonalize<double>(S, n);
+  Bulk<double>& K = S.u.d;
   const double inv_sb = rcp64(S.sb), inv_tr = rcp64(S.tr);
-  apply_QH<double, double>(S, n, S.b, inv_sb, S.c);  // scaled: c = D^H Q^H b / ||b||
-  __syncthreads();
-  if (threadIdx.x < n) {  // scaled tridiagonal T / tr, and FP32 copies for the seed
-    const int i = threadIdx.x;
-    S.d[i] *= inv_tr;
-    if (i + 1 < n) S.e[i] *= inv_tr;
-    S.d32[i] = (float)S.d[i];
-    if (i + 1 < n) S.e32[i] = (float)S.e[i];
-    S.c32[i] = make_float2((float)S.c[i].x, (float)S.c[i].y);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    if (lane < n) K.V[lane][0] = inv_sb * S.b[lane];
+    __syncwarp();
+    const int kd = lanczos_warp<double>(K.G, n, K.V, S.d, S.e, K.p, K.wv, LANCZOS_TOL64 * S.tr);
+    if (lane < kd) {  // scaled model T / tr, c = e_1, and FP32 copies for the seed
+      S.d[lane] *= inv_tr;
+      S.d32[lane] = (float)S.d[lane];
+      if (lane + 1 < kd) {
+        S.e[lane] *= inv_tr;
+        S.e32[lane] = (float)S.e[lane];
+      }
+      S.c[lane] = make_double2(lane == 0 ? 1.0 : 0.0, 0.0);
+      S.c32[lane] = make_float2(lane == 0 ? 1.f : 0.f, 0.f);
+    }
+    if (lane == 0) S.kd = kd;
   }
   __syncthreads();
+  const int kd = S.kd;
   if (threadIdx.x == 0) {
     const double target = (S.dnu * inv_sb) * (S.dnu * inv_sb);
     const double lo = P.alpha_rel, hi = S.hi * inv_tr;
@@ -541,7 +469,7 @@ __device__ void solve_fp64(Shared& S, int n, int m, const Problem& P, int om, un
     double a;
     if (P.alpha_mode == 1) {
       a = P.alpha_given[om] * inv_tr;
-    } else if (phi2<double>(S.d, S.e, S.c, n, lo, ok) >= target) {
+    } else if (phi2<double>(S.d, S.e, S.c, kd, lo, ok) >= target) {
       a = lo;
       atomicAdd(ctr + C_ALPHA_FLOOR, 1ull);
     } else {
@@ -549,18 +477,22 @@ __device__ void solve_fp64(Shared& S, int n, int m, const Problem& P, int om, un
       bool ok32;
       int it32, it64;
       const double t_mid = 0.5 * (log(lo) + log(hi));
-      double t = newton_log_alpha<float>(S.d32, S.e32, S.c32, n, lo, hi, target, t_mid, 1e-5, P.max_iter, gp,
+      double t = newton_log_alpha<float>(S.d32, S.e32, S.c32, kd, lo, hi, target, t_mid, 1e-5, P.max_iter, gp,
                                          ok32, it32);
       if (!ok32 || !(t > log(lo) && t < log(hi))) t = t_mid;
-      t = newton_log_alpha<double>(S.d, S.e, S.c, n, lo, hi, target, t, 1e-14, P.max_iter, gp, ok, it64);
+      t = newton_log_alpha<double>(S.d, S.e, S.c, kd, lo, hi, target, t, 1e-14, P.max_iter, gp, ok, it64);
       if (it64 >= P.max_iter) atomicAdd(ctr + C_ROOT_CAPPED, 1ull);
       a = exp(t);
     }
     S.a_s = a;
-    tri_solve<double>(S.d, S.e, n, a, S.c, S.z);
+    tri_solve<double>(S.d, S.e, kd, a, S.c, S.z);
   }
   __syncthreads();
-  apply_Q<double, double>(S, n, S.z, S.sb * inv_tr, S.y);
+  if (threadIdx.x < n) {  // y = (||b|| / tr) Q z
+    double2 acc = make_double2(0, 0);
+    for (int j = 0; j < kd; ++j) acc = acc + K.V[threadIdx.x][j] * S.z[j];
+    S.y[threadIdx.x] = (S.sb * inv_tr) * acc;
+  }
   __syncthreads();
 }
 
@@ -602,148 +534,47 @@ __device__ void gram32(Shared& S, int n, int m) {
   __syncthreads();
 }
 
-// Householder reduction of G32 (shared) by warp 0, lane r owning row r.
-// Output: reflectors V[j], beta[j]; d32, e32 and the phases ph of T = D^H Q^H G Q D.
-__device__ void tridiag32_warp(Shared& S, int n) {
-  BulkF& K = S.u.f;
-  const int lane = threadIdx.x;
-  float2 eh = make_float2(0.f, 0.f);  // lane j keeps the complex subdiagonal entry e_j
-  for (int j = 0; j + 2 < n; ++j) {
-    const bool below = lane > j && lane < n;
-    if (j == 3) FL_MARK_S(13);
-    float2 x = below ? K.G[lane][j] : make_float2(0.f, 0.f);
-    const float nx2 = warp_sum(abs2(x));
-    const float2 x0 = shfl2(x, j + 1);
-    float beta = 0.f;
-    float2 ah = make_float2(0.f, 0.f);
-    if (nx2 > 0.f) {
-      const float nx = sqrtf(nx2), ax0 = sqrtf(abs2(x0));
-      const float2 ph = ax0 > 0.f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
-      ah = make_float2(-ph.x * nx, -ph.y * nx);
-      if (lane == j + 1) x = make_float2(ph.x * (ax0 + nx), ph.y * (ax0 + nx));
-      beta = 1.f / (nx * (nx + ax0));
-    }
-    if (lane == j) eh = ah;
-    if (below) K.V[j][lane - j - 1] = x;
-    if (lane == 0) K.beta[j] = beta;
-    if (beta == 0.f) continue;  // warp-uniform
-    K.p[lane] = x;              // v by absolute row, zero outside the block
-    __syncwarp();
-    if (j == 3) FL_MARK_S(14);
-    float2 p = make_float2(0.f, 0.f);
-    if (below)
-      for (int c0 = j + 1; c0 < n; c0 += 8) {  // explicit batches: all loads issued before use
-        float2 gv[8], pv[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int c = c0 + q < n ? c0 + q : n - 1;
-          gv[q] = K.G[lane][c];
-          pv[q] = c0 + q < n ? K.p[c] : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) p = p + gv[q] * pv[q];
-      }
-    p = beta * p;
-    if (j == 3) FL_MARK_S(15);
-    const float kk = 0.5f * beta * warp_sum(x.x * p.x + x.y * p.y);  // (beta/2) Re(v^H p)
-    const float2 w = p - kk * x;
-    K.wv[lane] = w;
-    __syncwarp();
-    if (j == 3) FL_MARK_S(16);
-    if (below)
-      for (int c0 = j + 1; c0 < n; c0 += 8) {
-        float2 gv[8], wq[8], pq[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int c = c0 + q < n ? c0 + q : n - 1;
-          gv[q] = K.G[lane][c];
-          wq[q] = K.wv[c];
-          pq[q] = K.p[c];
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (c0 + q < n) K.G[lane][c0 + q] = gv[q] - (mulc(x, wq[q]) + mulc(w, pq[q]));
-      }
-    __syncwarp();
-    if (j == 3) FL_MARK_S(17);
-  }
-  if (n >= 2 && lane == n - 2) eh = K.G[n - 1][n - 2];
-  if (lane < n) S.d32[lane] = K.G[lane][lane].x;
-  float2 u = make_float2(1.f, 0.f);
-  if (lane + 1 < n) {
-    const float ae = sqrtf(abs2(eh));
-    if (ae > 0.f) u = make_float2(eh.x / ae, eh.y / ae);
-    S.e32[lane] = ae;
-  }
-  for (int off = 1; off < 32; off <<= 1) {  // ph[i+1] = u_0 ... u_i
-    const float2 o = make_float2(__shfl_up_sync(0xffffffffu, u.x, off), __shfl_up_sync(0xffffffffu, u.y, off));
-    if (lane >= off) u = o * u;
-  }
-  if (lane + 1 < n) S.ph[lane + 1] = to_d(u);
-  if (lane == 0) S.ph[0] = make_double2(1.0, 0.0);
+// In-place Cholesky G + a I = L L^H of the lower triangle of G32 (right-looking,
+// lane k owns row k), 1/L_jj in dinv.  Returns false if a pivot is not positive.
+// Warp 0.
+__device__ bool cholesky32_warp(float2 (*G)[MAX_M1 + 1], int n, float a, float* dinv) {
+  const int lane = threadIdx.x & 31;
+  if (lane < n) G[lane][lane].x += a;
   __syncwarp();
+  bool ok = true;
+  for (int j = 0; j < n; ++j) {
+    const float djj = G[j][j].x;
+    ok = ok && djj > 0.f;
+    const float ljj = sqrtf(fmaxf(djj, 1e-30f));
+    const float inv = rcp<float>(ljj);
+    __syncwarp();
+    if (lane == j) { G[j][j] = make_float2(ljj, 0.f); dinv[j] = inv; }
+    if (lane > j && lane < n) G[lane][j] = inv * G[lane][j];
+    __syncwarp();
+    if (lane > j && lane < n) {
+      const float2 lk = G[lane][j];
+      for (int c = j + 1; c <= lane; ++c) G[lane][c] = G[lane][c] - mulc(lk, G[c][j]);
+    }
+    __syncwarp();
+  }
+  return ok;
 }
 
-// Q D formed explicitly by warp 0 in K.Q: lane c accumulates column c of
-// H_0 ... H_{n-3} (reflectors applied last to first), then scales it by ph_c.
-__device__ void form_qd_warp(Shared& S, int n) {
-  BulkF& K = S.u.f;
-  const int c = threadIdx.x;
-  if (c < n)
-    for (int r = 0; r < n; ++r) K.Q[r][c] = make_float2(r == c ? 1.f : 0.f, 0.f);
-  for (int j = n - 3; j >= 0; --j) {
-    const float beta = K.beta[j];
-    if (beta == 0.f || c <= j || c >= n) continue;  // columns c <= j are still e_c here
-    float2 dot = make_float2(0.f, 0.f);
-    for (int r0 = j + 1; r0 < n; r0 += 8) {
-      float2 vq[8], qq[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int r = r0 + q < n ? r0 + q : n - 1;
-        vq[q] = r0 + q < n ? K.V[j][r - j - 1] : make_float2(0.f, 0.f);
-        qq[q] = K.Q[r][c];
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) dot = dot + cmul_conj_a(vq[q], qq[q]);
-    }
-    dot = beta * dot;
-    for (int r0 = j + 1; r0 < n; r0 += 8) {
-      float2 vq[8], qq[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int r = r0 + q < n ? r0 + q : n - 1;
-        vq[q] = K.V[j][r - j - 1];
-        qq[q] = K.Q[r][c];
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (r0 + q < n) K.Q[r0 + q][c] = qq[q] - vq[q] * dot;
-    }
+// x = (L L^H)^-1 r for the factor of cholesky32_warp; lane k holds r_k (zero for
+// lanes >= n) and gets x_k.  Warp 0.
+__device__ float2 chol_solve32(const float2 (*L)[MAX_M1 + 1], const float* dinv, int n, float2 r) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < n; ++j) {
+    const float2 zj = dinv[j] * shfl2(r, j);
+    if (lane == j) r = zj;
+    if (lane > j && lane < n) r = r - L[lane][j] * zj;
   }
-  if (c < n) {
-    const double2 p = S.ph[c];
-    const float2 pf = make_float2((float)p.x, (float)p.y);
-    for (int r = 0; r < n; ++r) K.Q[r][c] = K.Q[r][c] * pf;
+  for (int j = n - 1; j >= 0; --j) {
+    const float2 xj = dinv[j] * shfl2(r, j);
+    if (lane == j) r = xj;
+    if (lane < j) r = r - cmul_conj_a(L[j][lane], xj);
   }
-  __syncwarp();
-}
-
-// cz_k = ((QD)^H v)_k for an FP32 vector v in shared memory; lane k, warp 0
-__device__ __forceinline__ float2 qdh_lane(Shared& S, int n, const float2* v) {
-  const int k = threadIdx.x;
-  float2 acc = make_float2(0.f, 0.f);
-  if (k < n) {
-    float2 acc2 = make_float2(0.f, 0.f);
-    int j = 0;
-#pragma unroll 4
-    for (; j + 1 < n; j += 2) {
-      acc = acc + cmul_conj_a(S.u.f.Q[j][k], v[j]);
-      acc2 = acc2 + cmul_conj_a(S.u.f.Q[j + 1][k], v[j + 1]);
-    }
-    if (j < n) acc = acc + cmul_conj_a(S.u.f.Q[j][k], v[j]);
-    acc = acc + acc2;
-  }
-  return acc;
+  return r;
 }
 
 // two-float residual of the scaled dual system: th = Ah^H yh, rh = bh - Ah th - a yh
@@ -802,29 +633,6 @@ __device__ float lane_phi2(Shared& S, int n, float a, const float2* c, bool& ok)
     zz += abs2(x);
   }
   return a * a * zz;
-}
-
-// single-lane solve of (T + a I) z = c into K.tz (shared), FP32
-__device__ void lane_solve(Shared& S, int n, float a, const float2* c, float2* z) {
-  BulkF& K = S.u.f;
-  float lp = S.d32[0] + a;
-  float il = __fdividef(1.f, lp);
-  float2 w = c[0];
-  K.ts[0][0] = il * w;
-  for (int i = 1; i < n; ++i) {
-    const float mu = S.e32[i - 1] * il;
-    lp = S.d32[i] + a - mu * S.e32[i - 1];
-    il = __fdividef(1.f, lp);
-    w = c[i] - mu * w;
-    K.tmu[i][0] = mu;
-    K.ts[i][0] = il * w;
-  }
-  float2 x = K.ts[n - 1][0];
-  z[n - 1] = x;
-  for (int i = n - 2; i >= 0; --i) {
-    x = K.ts[i][0] - K.tmu[i + 1][0] * x;
-    z[i] = x;
-  }
 }
 
 // Discrepancy root on the scaled FP32 model by three rounds of a 32-point search
@@ -954,29 +762,35 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       gram32(S, n, m);
       FL_MARK(3);
       if (threadIdx.x < 32) {
-        tridiag32_warp(S, n);
+        BulkF& K = S.u.f;
+        const int lane = threadIdx.x;
+        // Lanczos model of the scaled G from q_0 = bh (renormalised in FP32)
+        const float2 q0 = lane < n ? make_float2(S.bh[lane].re.hi, S.bh[lane].im.hi) : make_float2(0.f, 0.f);
+        const float inq = rsqrtf(warp_sum(abs2(q0)));
+        if (lane < n) K.Q[lane][0] = inq * q0;
+        __syncwarp();
+        const int kd = lanczos_warp<float>(K.G, n, K.Q, S.d32, S.e32, K.p, K.wv, LANCZOS_TOL32);
         FL_MARK(4);
-        form_qd_warp(S, n);
+        if (lane < kd) S.c32[lane] = make_float2(lane == 0 ? 1.f : 0.f, 0.f);  // c = e_1
+        __syncwarp();
         FL_MARK(5);
-        if (threadIdx.x < n) S.r32[threadIdx.x] = make_float2(S.bh[threadIdx.x].re.hi, S.bh[threadIdx.x].im.hi);
-        __syncwarp();
-        const float2 cz = qdh_lane(S, n, S.r32);  // c = (QD)^H b / ||b||
-        if (threadIdx.x < n) S.c32[threadIdx.x] = cz;
-        __syncwarp();
-        FL_MARK(6);
         bool ok = true, fl = false;
         float a;
         if (P.alpha_mode == 1) {
           a = (float)(P.alpha_given[om] / S.tr);
         } else {
           const float target = (float)((S.dnu * S.inv_sb) * (S.dnu * S.inv_sb));
-          a = root32_warp(S, n, (float)P.alpha_rel, (float)(S.hi / S.tr), target, fl, ok);
+          a = root32_warp(S, kd, (float)P.alpha_rel, (float)(S.hi / S.tr), target, fl, ok);
         }
-        if (threadIdx.x == 0) {
+        FL_MARK(6);
+        // floor cases, breakdowns and small alpha/tr are decided and solved in FP64;
+        // otherwise factor G + a I for the refinement
+        bool fp64 = !ok || fl || a < (float)P.fp64_switch;
+        if (!fp64) fp64 = !cholesky32_warp(K.G, n, a, K.beta);
+        if (lane == 0) {
           S.a_s = (double)a;
-          // floor cases, breakdowns and small alpha/tr are decided and solved in FP64
-          S.fp64 = (!ok || fl || a < (float)P.fp64_switch) ? 1 : 0;
-          if (S.fp64) atomicAdd(ctr + C_FP64_FALLBACK, 1ull);
+          S.fp64 = fp64 ? 1 : 0;
+          if (fp64) atomicAdd(ctr + C_FP64_FALLBACK, 1ull);
         }
       }
       __syncthreads();
@@ -993,26 +807,13 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         for (float rel = 1.f; sweeps < P.refine_iters && rel > 1e-18f; ++sweeps) {
           if (sweeps) residual_ff(S, n, m, a_ff);
           if (threadIdx.x < 32) {
-            const float2 cz = qdh_lane(S, n, S.r32);
-            if (threadIdx.x < n) S.c32[threadIdx.x] = cz;
-            __syncwarp();
-            if (threadIdx.x == 0) lane_solve(S, n, (float)S.a_s, S.c32, S.cz);
-            __syncwarp();
             const int j = threadIdx.x;
+            const float2 dy = chol_solve32(S.u.f.G, S.u.f.beta, n, j < n ? S.r32[j] : make_float2(0.f, 0.f));
             float dd = 0.f, yy = 0.f;
             if (j < n) {
-              float2 acc = make_float2(0.f, 0.f), acc2 = make_float2(0.f, 0.f);
-              int k = 0;
-#pragma unroll 4
-              for (; k + 1 < n; k += 2) {
-                acc = acc + S.u.f.Q[j][k] * S.cz[k];
-                acc2 = acc2 + S.u.f.Q[j][k + 1] * S.cz[k + 1];
-              }
-              if (k < n) acc = acc + S.u.f.Q[j][k] * S.cz[k];
-              acc = acc + acc2;
-              const ffc yn = ffc_add(S.yh[j], ffc{ff{acc.x, 0.f}, ff{acc.y, 0.f}});
+              const ffc yn = ffc_add(S.yh[j], ffc{ff{dy.x, 0.f}, ff{dy.y, 0.f}});
               S.yh[j] = yn;
-              dd = abs2(acc);
+              dd = abs2(dy);
               yy = yn.re.hi * yn.re.hi + yn.im.hi * yn.im.hi;
             }
             dd = warp_sum(dd);
