@@ -72,7 +72,7 @@ fs_status cuda_fail(fs_ctx* ctx, cudaError_t e, const char* where) {
 }
 
 struct Layout {
-  size_t t12, prof, norms, partial, slot, act, cols, ncol, count, dnu, total;
+  size_t t12, prof, norms, partial, slot, act, flagbits, blkcnt, blkgz, colblk, cols, ncol, count, dnu, total;
   int n_partial;
 };
 
@@ -89,6 +89,11 @@ Layout layout(int n, int m, int m1, int n_omega, bool fp64) {
   L.partial = off; off = align_up(off + 8 * (size_t)n_omega * L.n_partial);
   L.slot = off; off = align_up(off + 4 * (size_t)n_omega * N2);
   L.act = off; off = align_up(off + 4 * (size_t)n_omega * N2);
+  const size_t cb = (size_t)n_omega * classify_blocks(n);
+  L.flagbits = off; off = align_up(off + 4 * cb * 32);
+  L.blkcnt = off; off = align_up(off + 4 * cb);
+  L.blkgz = off; off = align_up(off + 4 * cb);
+  L.colblk = off; off = align_up(off + 4 * cb * 8);
   L.cols = off; off = align_up(off + 4 * (size_t)n_omega * n);
   L.ncol = off; off = align_up(off + 4 * (size_t)n_omega);
   L.count = off; off = align_up(off + 4 * (size_t)n_omega);
@@ -202,6 +207,10 @@ Work<R> carve_work(void* base, const Layout& L, unsigned long long* ctr, const c
   w.n_partial = L.n_partial;
   w.slot = (int*)(b + L.slot);
   w.act = (int*)(b + L.act);
+  w.flagbits = (unsigned*)(b + L.flagbits);
+  w.blkcnt = (int*)(b + L.blkcnt);
+  w.blkgz = (int*)(b + L.blkgz);
+  w.colblk = (unsigned*)(b + L.colblk);
   w.cols = (int*)(b + L.cols);
   w.ncol = (int*)(b + L.ncol);
   w.count = (int*)(b + L.count);

@@ -13,6 +13,7 @@
 #include <math.h>
 
 #include "fft.cuh"
+#include "modes.cuh"
 #include "pipeline.cuh"
 
 namespace fl {
@@ -187,6 +188,17 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned v, unsigned
 // grid ceil(M N / LINES); a block owns LINES rows (l, y) of the X grid, loops over
 // the frequencies, transforms V and u rows and accumulates the least-squares sums
 // in the accumulator type A.  Returns (block-uniform) whether any sum overflowed.
+// a / b and 1/sqrt(x) of the pointwise recovery: IEEE in FP32; in FP64 by
+// Newton-Raphson from FP32 seeds (rcp64, rsqrt64), a few dependent FP64 operations
+// instead of the FP64 division and square root, which dominate this kernel on a
+// GPU whose FP64 pipe runs at 1/64 of the FP32 rate.
+template <typename R> __device__ __forceinline__ R quot(R a, R b);
+template <> __device__ __forceinline__ float quot<float>(float a, float b) { return a / b; }
+template <> __device__ __forceinline__ double quot<double>(double a, double b) { return a * rcp64(b); }
+template <typename R> __device__ __forceinline__ R inv_sqrt(R x);
+template <> __device__ __forceinline__ float inv_sqrt<float>(float x) { return 1.0f / sqrtf(x); }
+template <> __device__ __forceinline__ double inv_sqrt<double>(double x) { return rsqrt64(x); }
+
 template <typename R, int N, typename A>
 __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __restrict__ t2,
                                              const int* __restrict__ cols, const int* __restrict__ ncol,
@@ -279,14 +291,14 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
       const long long r = row0 + e / N;
       if (r < nrows) {
         const bool g = !(den[p] >= guard);
-        const R x = g ? R(0) : num[p] / den[p];
+        const R x = g ? R(0) : quot<R>(num[p], den[p]);
         n_guard += g;
         const long long o = r * N + (e % N);
         xi[o] = x;
         if (cout) {
           const bool ok = x < inv_c02;
           n_nan += !ok;
-          cout[o] = ok ? R(1) / sqrt(inv_c02 - x) : R(NAN);
+          cout[o] = ok ? inv_sqrt<R>(inv_c02 - x) : R(NAN);
         }
       }
     }

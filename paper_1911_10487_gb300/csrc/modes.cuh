@@ -31,11 +31,38 @@ __device__ __forceinline__ double rcp64(double x) {
   return __longlong_as_double((yb & ~(0x7ffLL << 52)) | ((long long)ey << 52));
 }
 
+// 1/sqrt(x) for a positive normal double by Newton-Raphson on f(y) = 1/y^2 - x
+// (y <- y + y (1 - x y^2)/2, quadratic convergence) from an FP32 seed of the
+// mantissa scaled to [1, 4); two steps take the ~23-bit seed past FP64
+// precision.  Exponent handled on the bit pattern.  About six dependent FP64
+// operations instead of an FP64 square root and division.
+__device__ __forceinline__ double rsqrt64(double x) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  if (ex == 0 || ex == 0x7ff || bits < 0) return 1.0 / sqrt(x);  // zero, subnormal, inf, nan, negative
+  const int e = ex - 1023, h = e >> 1;  // x = m 2^(2h), m in [1, 4)
+  const double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | ((long long)(1023 + e - 2 * h) << 52));
+  double y = (double)rsqrtf((float)m);
+  double r = fma(-m * y, y, 1.0);
+  y = fma(0.5 * y, r, y);
+  r = fma(-m * y, y, 1.0);
+  y = fma(0.5 * y, r, y);
+  const long long yb = __double_as_longlong(y);  // y in (0.5, 1]: scale by 2^-h
+  return __longlong_as_double(yb - ((long long)h << 52));
+}
+
 template <typename T> __device__ __forceinline__ T rcp(T x);
 template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }  // ~2 ulp
 template <> __device__ __forceinline__ double rcp<double>(double x) { return rcp64(x); }
 
 __device__ __forceinline__ double2 warp_sum(double2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+__device__ __forceinline__ float2 warp_sum(float2 v) {
   for (int o = 16; o > 0; o >>= 1) {
     v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
     v.y += __shfl_xor_sync(0xffffffffu, v.y, o);

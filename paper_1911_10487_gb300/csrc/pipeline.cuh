@@ -48,6 +48,10 @@ template <typename R> struct Work {
   int n_partial;
   int* slot;        // [n_omega][N*N] slot of an active mode or -1
   int* act;         // [n_omega][N*N] active mode list (mode index, ascending)
+  unsigned* flagbits;  // [n_omega][classify_blocks][32] active-mode bitmask (classification)
+  int* blkcnt;      // [n_omega][classify_blocks] active modes per classification block
+  int* blkgz;       // [n_omega][classify_blocks] grazing modes per classification block
+  unsigned* colblk; // [n_omega][classify_blocks][8] columns holding an active mode, per block
   int* cols;        // [n_omega][N] columns nu1 holding a nonzero mode
   int* ncol;        // [n_omega]
   int* count;       // [n_omega] active modes
@@ -58,6 +62,8 @@ template <typename R> struct Work {
 };
 
 size_t workspace_bytes(int n, int m, int m1, int n_omega, bool fp64);
+// blocks of 1024 consecutive modes in the classification of an N x N grid
+inline int classify_blocks(int n) { return (n * n + 1023) / 1024; }
 template <typename R> Work<R> carve(void* base, int n, int m, int m1, int n_omega);
 
 // Launchers (return the launch error).

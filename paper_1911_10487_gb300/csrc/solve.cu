@@ -64,125 +64,179 @@ namespace fl {
 
 namespace {
 
-constexpr int ST = 128;  // threads per solve block (>= 2 MAX_M and >= 4 MAX_M1)
+// Threads per solve block: 4 warps.  The per-mode critical path is warp 0's
+// sequential part (Lanczos, root, Cholesky, triangular solves); with 4 warps on
+// the 4 schedulers of an SM that warp does not share its issue slots with another
+// warp of the same block (8 warps measured slower).
+constexpr int ST = 128;
+constexpr int SW = ST / 32;
 // Lanczos stops when the next off-diagonal of T is at most this fraction of
 // tr(G): a few units of round-off of the normal matrix in each precision
 constexpr float LANCZOS_TOL32 = 1e-6f;
 constexpr double LANCZOS_TOL64 = 1e-14;
-static_assert(ST >= 2 * MAX_M && ST >= 4 * MAX_M1, "solve block too small");
+static_assert(ST == 2 * MAX_M && ST == 4 * MAX_M1, "thread maps of the solve assume 2 threads per plane l and 4 per data plane k");
 
 // ------------------------------------------------------------------------------
-// classification: one block per frequency, integer arithmetic only
+// classification (integer arithmetic only), in two passes over blocks of CMB
+// consecutive modes of one frequency:
+//  k_classify_flags   delta_nu (every block sums the same norm partials in the
+//                     same order), the active-mode bitmask, and per block the
+//                     count of active and of grazing modes and a column mask;
+//  k_classify_scatter slot and the ascending active list from the per-block
+//                     prefix; block 0 of a frequency compacts the column list and
+//                     adds the counters.
+// Everything a later kernel reads is a fixed-order function of the inputs.
 // ------------------------------------------------------------------------------
-constexpr int CT = 1024;
+constexpr int CT = 256;            // threads per classify block
+constexpr int CMB = 4 * CT;        // modes per classify block
+constexpr int CWB = CMB / 32;      // bitmask words per block
+constexpr int NWC = (MAX_N + 31) / 32;
+static_assert((MAX_N * MAX_N + CMB - 1) / CMB <= 64, "the scatter prefix covers at most 64 blocks");
 
 __global__ void __launch_bounds__(CT)
-k_classify(Problem P, const double* __restrict__ norms, const double* __restrict__ partial, int n_partial,
-           int* __restrict__ slot, int* __restrict__ act, int* __restrict__ cols, int* __restrict__ ncol,
-           int* __restrict__ count, double* __restrict__ dnu_out, unsigned long long* __restrict__ ctr) {
-  const int om = blockIdx.x;
-  const int N = P.n;
-  const int N2 = N * N;
-  const double* nrm = norms + (long long)om * N2;
-  __shared__ int scan[64];
-  __shared__ int colflag[MAX_N];
-  __shared__ unsigned cgraz[CT / 32];
+k_classify_flags(Problem P, const double* __restrict__ norms, const double* __restrict__ partial, int n_partial,
+                 unsigned* __restrict__ flagbits, int* __restrict__ blkcnt, int* __restrict__ blkgz,
+                 unsigned* __restrict__ colblk, double* __restrict__ dnu_out) {
+  const int om = blockIdx.y, b = blockIdx.x, CB = gridDim.x;
+  const int N = P.n, N2 = N * N;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __shared__ long long thr_bits;
-  for (int j = threadIdx.x; j < N; j += CT) colflag[j] = 0;
+  __shared__ unsigned cm[NWC];
+  __shared__ int wc[CT / 32], wg[CT / 32];
+  if (threadIdx.x < NWC) cm[threadIdx.x] = 0u;
   if (threadIdx.x < 32) {
-    // ||W||^2 = sum_nu ||W~_nu||^2 / N^2 (Parseval): the block partial sums are
-    // loaded by one warp and added in a fixed order (lane-strided, then a tree)
+    // ||W||^2 = sum_nu ||W~_nu||^2 / N^2 (Parseval): the block partial sums of the
+    // norms kernel, lane-strided then a tree (the same order in every block)
     double s = 0.0;
-    for (int i = threadIdx.x; i < n_partial; i += 32) s += partial[(long long)om * n_partial + i];
+    for (int i = lane; i < n_partial; i += 32) s += partial[(long long)om * n_partial + i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) {
-    const double wnorm = sqrt(s / (double)N2);
-    const double dnu = P.tau * fmax(P.delta, P.delta_floor) * wnorm;
-    dnu_out[om] = dnu;
-    thr_bits = __double_as_longlong(dnu * dnu);
+    if (lane == 0) {
+      const double wnorm = sqrt(s / (double)N2);
+      const double dnu = P.tau * fmax(P.delta, P.delta_floor) * wnorm;
+      if (b == 0) dnu_out[om] = dnu;
+      thr_bits = __double_as_longlong(dnu * dnu);
     }
   }
   __syncthreads();
-  // non-negative doubles order like their bit patterns: the test nrm > dnu^2 is
-  // an integer comparison (no FP64 pipe on a single SM).  Thread t owns the modes
-  // v = t + k CT (coalesced); slots are handed out in (thread, k) order.
+  // non-negative doubles order like their bit patterns: nrm > dnu^2 is an
+  // integer comparison
   const long long tb = thr_bits;
   const int glo = P.graz_lo[om], ghi = P.graz_hi[om];
-  const long long* nb = reinterpret_cast<const long long*>(nrm);
-  const int kmax = (N2 + CT - 1) / CT;  // <= 64 for N <= 256
-  unsigned long long flags = 0ull;
-  int cnt = 0;
-  unsigned ngz = 0;
-  for (int k = 0; k < kmax; ++k) {
-    const int v = threadIdx.x + k * CT;
+  const long long* nb = reinterpret_cast<const long long*>(norms + (long long)om * N2);
+  int cnt = 0, ngz = 0;
+#pragma unroll
+  for (int k = 0; k < CMB / CT; ++k) {
+    const int v = b * CMB + k * CT + threadIdx.x;
+    bool on = false;
     if (v < N2) {
       const int i2 = v / N, i1 = v - i2 * N;
       const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
       const int msq = m1 * m1 + m2 * m2;
       const bool graz = msq >= glo && msq <= ghi;
       ngz += graz;
-      if (!graz && (P.alpha_mode == 1 || nb[v] > tb)) {
-        flags |= 1ull << k;
-        ++cnt;
-      }
+      on = !graz && (P.alpha_mode == 1 || nb[v] > tb);
+      if (on) atomicOr(&cm[i1 >> 5], 1u << (i1 & 31));
+    }
+    const unsigned word = __ballot_sync(0xffffffffu, on);  // modes v0 .. v0 + 31, v0 = v - lane
+    if (lane == 0) {
+      flagbits[((long long)om * CB + b) * CWB + k * (CT / 32) + wid] = word;
+      cnt += __popc(word);
     }
   }
-  // exclusive scan of cnt over the block: warp shuffles, then the warp totals
+  for (int o = 16; o > 0; o >>= 1) ngz += __shfl_xor_sync(0xffffffffu, ngz, o);
+  if (lane == 0) {
+    wc[wid] = cnt;
+    wg[wid] = ngz;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int c = 0, g = 0;
+    for (int w = 0; w < CT / 32; ++w) {
+      c += wc[w];
+      g += wg[w];
+    }
+    blkcnt[om * CB + b] = c;
+    blkgz[om * CB + b] = g;
+  }
+  if (threadIdx.x < NWC) colblk[((long long)om * CB + b) * NWC + threadIdx.x] = cm[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(CT)
+k_classify_scatter(Problem P, const unsigned* __restrict__ flagbits, const int* __restrict__ blkcnt,
+                   const int* __restrict__ blkgz, const unsigned* __restrict__ colblk, int* __restrict__ slot,
+                   int* __restrict__ act, int* __restrict__ cols, int* __restrict__ ncol, int* __restrict__ count,
+                   unsigned long long* __restrict__ ctr) {
+  const int om = blockIdx.y, b = blockIdx.x, CB = gridDim.x;
+  const int N = P.n, N2 = N * N;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int incl = cnt;
-  for (int off = 1; off < 32; off <<= 1) {
-    const int o = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += o;
-  }
-  if (lane == 31) scan[wid] = incl;
-  __syncthreads();
+  __shared__ int base_s, total_s;
+  __shared__ unsigned words[CWB];
+  __shared__ int wpre[CWB];
   if (wid == 0) {
-    int wv = lane < CT / 32 ? scan[lane] : 0;
-    for (int off = 1; off < 32; off <<= 1) {
-      const int o = __shfl_up_sync(0xffffffffu, wv, off);
-      if (lane >= off) wv += o;
+    // active modes of the blocks before this one (fixed order), and the total
+    const int c0 = lane < CB ? blkcnt[om * CB + lane] : 0;
+    const int c1 = lane + 32 < CB ? blkcnt[om * CB + lane + 32] : 0;
+    int before = (lane < b ? c0 : 0) + (lane + 32 < b ? c1 : 0), all = c0 + c1;
+    for (int o = 16; o > 0; o >>= 1) {
+      before += __shfl_xor_sync(0xffffffffu, before, o);
+      all += __shfl_xor_sync(0xffffffffu, all, o);
     }
-    scan[32 + lane] = wv;  // inclusive warp-total prefix
+    // exclusive prefix of the popcounts of this block's words (ascending modes)
+    const unsigned w = flagbits[((long long)om * CB + b) * CWB + lane];
+    const int c = __popc(w);
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    words[lane] = w;
+    wpre[lane] = incl - c;
+    if (lane == 0) {
+      base_s = before;
+      total_s = all;
+    }
   }
   __syncthreads();
-  int pos = (wid > 0 ? scan[32 + wid - 1] : 0) + incl - cnt;
-  const int total = scan[32 + CT / 32 - 1];
-  for (int k = 0; k < kmax; ++k) {
-    const int v = threadIdx.x + k * CT;
+  static_assert(CWB == 32, "one warp holds the words of a block");
+#pragma unroll
+  for (int k = 0; k < CMB / CT; ++k) {
+    const int v = b * CMB + k * CT + threadIdx.x;
     if (v < N2) {
-      if (flags >> k & 1ull) {
+      const int j = k * (CT / 32) + wid;
+      const unsigned w = words[j];
+      if (w >> lane & 1u) {
+        const int pos = base_s + wpre[j] + __popc(w & ((1u << lane) - 1u));
         slot[(long long)om * N2 + v] = pos;
         act[(long long)om * N2 + pos] = v;
-        colflag[v % N] = 1;
-        ++pos;
       } else {
         slot[(long long)om * N2 + v] = -1;
       }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) ngz += __shfl_xor_sync(0xffffffffu, ngz, o);
-  if ((threadIdx.x & 31) == 0) cgraz[threadIdx.x >> 5] = ngz;
-  __syncthreads();
-  if (threadIdx.x < 32) {  // compact the column list in order, one warp
-    colflag[0] = 1;  // the incident plane wave lives at nu = 0
+  if (b == 0 && wid == 0) {  // columns holding an active mode, in order, and the counters
+    int gz = 0;
+    for (int i = lane; i < CB; i += 32) gz += blkgz[om * CB + i];
+    for (int o = 16; o > 0; o >>= 1) gz += __shfl_xor_sync(0xffffffffu, gz, o);
     int base = 0;
     for (int j0 = 0; j0 < N; j0 += 32) {
-      const int j = j0 + threadIdx.x;
-      const bool f = j < N && colflag[j];
+      unsigned cmw = 0u;
+      for (int i = 0; i < CB; ++i) cmw |= colblk[((long long)om * CB + i) * NWC + (j0 >> 5)];
+      if (j0 == 0) cmw |= 1u;  // the incident plane wave lives at nu = 0
+      const int j = j0 + lane;
+      const bool f = j < N && (cmw >> lane & 1u);
       const unsigned bal = __ballot_sync(0xffffffffu, f);
-      if (f) cols[om * N + base + __popc(bal & ((1u << threadIdx.x) - 1u))] = j;
+      if (f) cols[om * N + base + __popc(bal & ((1u << lane) - 1u))] = j;
       base += __popc(bal);
     }
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
+      const int total = total_s;
       ncol[om] = base;
       count[om] = total;
-      unsigned long long g = 0;
-      for (int w = 0; w < CT / 32; ++w) g += cgraz[w];
       atomicAdd(ctr + C_MODES, (unsigned long long)N2);
       atomicAdd(ctr + C_COLUMNS, (unsigned long long)base);
       atomicAdd(ctr + C_ACTIVE, (unsigned long long)total);
-      atomicAdd(ctr + C_GRAZING, g);
-      atomicAdd(ctr + C_ZEROED, (unsigned long long)(N2 - total) - g);
+      atomicAdd(ctr + C_GRAZING, (unsigned long long)gz);
+      atomicAdd(ctr + C_ZEROED, (unsigned long long)(N2 - total - gz));
     }
   }
 }
@@ -273,6 +327,8 @@ struct Shared {
   float2 c32[MAX_M1], r32[MAX_M1];
   ffc yh[MAX_M1], rh[MAX_M1], bh[MAX_M1], th[MAX_M], Ef[MAX_M1], Pf[MAX_M];  // two-float (mixed route)
   double tr, sb, inv_sb, dnu, lo, hi, a_s, red[8];  // a_s = alpha / tr
+  double3 red3[8];
+  double2 qz;  // exp(i k_z h_z)
   int fp64, tflag, kd;  // kd: dimension of the Lanczos model
 };
 
@@ -312,8 +368,7 @@ __device__ void gram(Shared& S, int n, int m) {
 // is computed, depend on e only through the squares e_j^2, so stopping at
 // e_k <= tol changes phi^2 by O(tol^2 / a^2) relative.
 template <typename T>
-__device__ int lanczos_warp(const cx<T> (*G)[MAX_M1 + 1], int n, cx<T> (*Q)[MAX_M1 + 1], T* d, T* e,
-                            cx<T>* wbuf, cx<T>* hbuf, T tol) {
+__device__ int lanczos_warp(const cx<T> (*G)[MAX_M1 + 1], int n, cx<T> (*Q)[MAX_M1 + 1], T* d, T* e, T tol) {
   const int lane = threadIdx.x & 31;
   int k = n;
   for (int j = 0; j < n; ++j) {
@@ -333,16 +388,13 @@ __device__ int lanczos_warp(const cx<T> (*G)[MAX_M1 + 1], int n, cx<T> (*Q)[MAX_
     w = w - aj * qj;
     if (j > 0 && lane < n) w = w - e[j - 1] * Q[lane][j - 1];
     for (int pass = 0; pass < 2; ++pass) {  // w -= Q (Q^H w) over q_0 .. q_j
-      if (lane < n) wbuf[lane] = w;
-      __syncwarp();
-      cx<T> h = czero<T>();
-      if (lane <= j)
-        for (int r = 0; r < n; ++r) h = h + cmul_conj_a(Q[r][lane], wbuf[r]);
-      hbuf[lane] = h;
-      __syncwarp();
-      if (lane < n)
-        for (int i = 0; i <= j; ++i) w = w - Q[lane][i] * hbuf[i];
-      __syncwarp();
+      cx<T> corr = czero<T>();
+      for (int i = 0; i <= j; ++i) {
+        const cx<T> qi = lane < n ? Q[lane][i] : czero<T>();
+        const cx<T> h = warp_sum(cmul_conj_a(qi, w));  // q_i^H w
+        corr = corr + qi * h;
+      }
+      w = w - corr;
     }
     const T beta = sqrt(warp_sum(abs2(w)));
     if (lane == 0) d[j] = aj;
@@ -428,26 +480,46 @@ __device__ double phi2(const T* d, const T* e, const cx<T>* c, int n, double a, 
   return a * a * (double)zz;
 }
 
-// block-wide sum of one double per thread (all threads get it)
+// block-wide sums of one double per thread (all threads get them)
 __device__ double block_sum(Shared& S, double v) {
   v = warp_sum(v);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = v;
   __syncthreads();
-  return (S.red[0] + S.red[1]) + (S.red[2] + S.red[3]);
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < SW; ++w) t += S.red[w];
+  return t;
+}
+__device__ double3 block_sum3(Shared& S, double3 v) {
+  v.x = warp_sum(v.x);
+  v.y = warp_sum(v.y);
+  v.z = warp_sum(v.z);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) S.red3[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double3 t = make_double3(0.0, 0.0, 0.0);
+#pragma unroll
+  for (int w = 0; w < SW; ++w) {
+    t.x += S.red3[w].x;
+    t.y += S.red3[w].y;
+    t.z += S.red3[w].z;
+  }
+  return t;
 }
 
 // FP64 route: FP64 normal matrix and Lanczos model, FP32-seeded root on the
 // scaled tridiagonal, FP64 Newton to full accuracy, y = (||b||/tr) Q (T/tr + a I)^-1 e_1.
 __device__ void solve_fp64(Shared& S, int n, int m, const Problem& P, int om, unsigned long long* ctr) {
   gram<double>(S, n, m);
+  FL_MARK_S(13);
   Bulk<double>& K = S.u.d;
   const double inv_sb = rcp64(S.sb), inv_tr = rcp64(S.tr);
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     if (lane < n) K.V[lane][0] = inv_sb * S.b[lane];
     __syncwarp();
-    const int kd = lanczos_warp<double>(K.G, n, K.V, S.d, S.e, K.p, K.wv, LANCZOS_TOL64 * S.tr);
+    const int kd = lanczos_warp<double>(K.G, n, K.V, S.d, S.e, LANCZOS_TOL64 * S.tr);
     if (lane < kd) {  // scaled model T / tr, c = e_1, and FP32 copies for the seed
       S.d[lane] *= inv_tr;
       S.d32[lane] = (float)S.d[lane];
@@ -461,6 +533,7 @@ __device__ void solve_fp64(Shared& S, int n, int m, const Problem& P, int om, un
     if (lane == 0) S.kd = kd;
   }
   __syncthreads();
+  FL_MARK_S(14);
   const int kd = S.kd;
   if (threadIdx.x == 0) {
     const double target = (S.dnu * inv_sb) * (S.dnu * inv_sb);
@@ -488,6 +561,7 @@ __device__ void solve_fp64(Shared& S, int n, int m, const Problem& P, int om, un
     tri_solve<double>(S.d, S.e, kd, a, S.c, S.z);
   }
   __syncthreads();
+  FL_MARK_S(15);
   if (threadIdx.x < n) {  // y = (||b|| / tr) Q z
     double2 acc = make_double2(0, 0);
     for (int j = 0; j < kd; ++j) acc = acc + K.V[threadIdx.x][j] * S.z[j];
@@ -512,69 +586,57 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
   return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-// G32 = A32 A32^H (full Hermitian matrix), all threads: row = lane, 8 columns per warp
+// G32 = A32 A32^H (full Hermitian matrix), all threads: row = lane, 4 columns per warp
 __device__ void gram32(Shared& S, int n, int m) {
   BulkF& K = S.u.f;
+  constexpr int CW = MAX_M1 / SW;
   const int r = threadIdx.x & 31, cg = threadIdx.x >> 5;
-  float2 acc[8];
+  float2 acc[CW];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int q = 0; q < CW; ++q) acc[q] = make_float2(0.f, 0.f);
   if (r < n)
 #pragma unroll 4
     for (int l = 0; l < m; ++l) {
       const float2 a = K.A[r][l];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc[q] = acc[q] + mulc(a, K.A[cg * 8 + q][l]);
+      for (int q = 0; q < CW; ++q) acc[q] = acc[q] + mulc(a, K.A[cg * CW + q][l]);
     }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int c = cg * 8 + q;
+  for (int q = 0; q < CW; ++q) {
+    const int c = cg * CW + q;
     if (r < n && c < n) K.G[r][c] = r == c ? make_float2(acc[q].x, 0.f) : acc[q];
   }
   __syncthreads();
 }
 
-// In-place Cholesky G + a I = L L^H of the lower triangle of G32 (right-looking,
-// lane k owns row k), 1/L_jj in dinv.  Returns false if a pivot is not positive.
-// Warp 0.
-__device__ bool cholesky32_warp(float2 (*G)[MAX_M1 + 1], int n, float a, float* dinv) {
+// Approximate (G + a I)^-1 r from the Lanczos model of the FP32 normal matrix,
+// exact on the Krylov space spanned by the model and r/a on its orthogonal
+// complement:  Q (T + a I)^-1 Q^H r + (r - Q Q^H r)/a.  The complement holds the
+// eigenvalues the Lanczos process did not reach, round-off for these kernels
+// (rank one in exact arithmetic); the refinement around it checks that its
+// corrections contract and sends the mode to the FP64 route otherwise.  Warp 0,
+// lane k holding r_k (zero for lanes >= n).
+__device__ float2 lanczos_apply32(Shared& S, int n, int kd, float a, float2 r) {
+  BulkF& K = S.u.f;
   const int lane = threadIdx.x & 31;
-  if (lane < n) G[lane][lane].x += a;
+  float2 mine = make_float2(0.f, 0.f), proj = make_float2(0.f, 0.f);
+  for (int i = 0; i < kd; ++i) {
+    const float2 qi = lane < n ? K.Q[lane][i] : make_float2(0.f, 0.f);
+    const float2 ci = warp_sum(cmul_conj_a(qi, r));  // q_i^H r
+    if (lane == i) mine = ci;
+    proj = proj + qi * ci;
+  }
+  if (lane < kd) S.c32[lane] = mine;
   __syncwarp();
-  bool ok = true;
-  for (int j = 0; j < n; ++j) {
-    const float djj = G[j][j].x;
-    ok = ok && djj > 0.f;
-    const float ljj = sqrtf(fmaxf(djj, 1e-30f));
-    const float inv = rcp<float>(ljj);
-    __syncwarp();
-    if (lane == j) { G[j][j] = make_float2(ljj, 0.f); dinv[j] = inv; }
-    if (lane > j && lane < n) G[lane][j] = inv * G[lane][j];
-    __syncwarp();
-    if (lane > j && lane < n) {
-      const float2 lk = G[lane][j];
-      for (int c = j + 1; c <= lane; ++c) G[lane][c] = G[lane][c] - mulc(lk, G[c][j]);
-    }
-    __syncwarp();
+  if (lane == 0) tri_solve<float>(S.d32, S.e32, kd, a, S.c32, K.p);  // z = (T + a I)^-1 Q^H r
+  __syncwarp();
+  float2 y = make_float2(0.f, 0.f);
+  if (lane < n) {
+    for (int i = 0; i < kd; ++i) y = y + K.Q[lane][i] * K.p[i];
+    y = y + rcp<float>(a) * (r - proj);
   }
-  return ok;
-}
-
-// x = (L L^H)^-1 r for the factor of cholesky32_warp; lane k holds r_k (zero for
-// lanes >= n) and gets x_k.  Warp 0.
-__device__ float2 chol_solve32(const float2 (*L)[MAX_M1 + 1], const float* dinv, int n, float2 r) {
-  const int lane = threadIdx.x & 31;
-  for (int j = 0; j < n; ++j) {
-    const float2 zj = dinv[j] * shfl2(r, j);
-    if (lane == j) r = zj;
-    if (lane > j && lane < n) r = r - L[lane][j] * zj;
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    const float2 xj = dinv[j] * shfl2(r, j);
-    if (lane == j) r = xj;
-    if (lane < j) r = r - cmul_conj_a(L[j][lane], xj);
-  }
-  return r;
+  __syncwarp();
+  return y;
 }
 
 // two-float residual of the scaled dual system: th = Ah^H yh, rh = bh - Ah th - a yh
@@ -689,23 +751,33 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     const double om2 = P.omega[om] * P.omega[om];
     const double kn = 2.0 * M_PI / P.period;
     const double q = k0 * k0 - kn * kn * (double)(m1 * m1 + m2 * m2);
-    const double2 kz = q >= 0.0 ? make_double2(sqrt(q), 0.0) : make_double2(0.0, sqrt(-q));
+    // k_z = sqrt(|q|) (real, or i sqrt(|q|) for an evanescent mode; active modes are
+    // never grazing, q != 0) and 1/k_z from one reciprocal square root
+    const double rq = rsqrt64(fabs(q));
+    const double2 kz = q >= 0.0 ? make_double2(fabs(q) * rq, 0.0) : make_double2(0.0, fabs(q) * rq);
     // gamma = omega^2 h_z (-i / (2 k_z))
     const double g0 = 0.5 * om2 * P.hz;
-    const double2 gamma = q >= 0.0 ? make_double2(0.0, -g0 / kz.x) : make_double2(-g0 / kz.y, 0.0);
+    const double2 gamma = q >= 0.0 ? make_double2(0.0, -g0 * rq) : make_double2(-g0 * rq, 0.0);
     const double ztop = P.z1 + (m - 0.5) * P.hz;
-    for (int k = threadIdx.x; k < n; k += ST) {
+    // the exponentials are FP64 chains, one per thread: threads 0..63 take P,
+    // threads 64..95 take E, thread 96 the plane-to-plane factor q of eq. (9)
+    if (threadIdx.x < m) {
+      const int l = threadIdx.x;
+      S.Pz[l] = exp_ikz(kz, ztop - (P.z1 + (l + 0.5) * P.hz));
+    } else if (threadIdx.x >= MAX_M && threadIdx.x < MAX_M + n) {
+      const int k = threadIdx.x - MAX_M;
       S.b[k] = to_d(wt[((long long)om * n + k) * N2 + nu]);
       S.E[k] = gamma * exp_ikz(kz, P.zy[k] - ztop);
+    } else if (threadIdx.x == MAX_M + MAX_M1) {
+      S.qz = exp_ikz(kz, P.hz);
     }
-    for (int l = threadIdx.x; l < m; l += ST) S.Pz[l] = exp_ikz(kz, ztop - (P.z1 + (l + 0.5) * P.hz));
     __syncthreads();
     // ||A||_F^2 = tr(G) = (sum_k |E_k|^2)(sum_l |P_l|^2) since A_kl = E_k P_l; ||b||^2
     FL_MARK(1);
-    const double sE = block_sum(S, threadIdx.x < n ? abs2(S.E[threadIdx.x]) : 0.0);
-    const double sP = block_sum(S, threadIdx.x < m ? abs2(S.Pz[threadIdx.x]) : 0.0);
-    const double bb = block_sum(S, threadIdx.x < n ? abs2(S.b[threadIdx.x]) : 0.0);
-    const double tr = sE * sP;
+    const double3 sums = block_sum3(S, make_double3(threadIdx.x < n ? abs2(S.E[threadIdx.x]) : 0.0,
+                                                    threadIdx.x < m ? abs2(S.Pz[threadIdx.x]) : 0.0,
+                                                    threadIdx.x < n ? abs2(S.b[threadIdx.x]) : 0.0));
+    const double tr = sums.x * sums.y, bb = sums.z;
     const double dnu0 = dnu_arr[om];
     // A_nu underflowed to zero (the mode carries no information), or, under the
     // discrepancy rule, ||b|| recomputed here does not exceed delta_nu after all (a
@@ -732,11 +804,11 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     }
     if (threadIdx.x == 0) {
       S.tr = tr;
-      S.sb = sqrt(bb);
-      S.inv_sb = 1.0 / S.sb;
+      S.inv_sb = rsqrt64(bb);
+      S.sb = bb * S.inv_sb;
       S.dnu = dnu_arr[om];
       S.lo = P.alpha_rel * tr;
-      S.hi = fmax(tr * S.dnu / (S.sb - S.dnu), S.lo);
+      S.hi = fmax(tr * S.dnu * rcp64(S.sb - S.dnu), S.lo);
       S.fp64 = MIXED ? 0 : 1;
     }
     __syncthreads();
@@ -744,7 +816,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       // scaled problem Ah = A / sqrt(tr) (||Ah||_F = 1), bh = b / ||b||, a = alpha / tr:
       // Ah in two-float (for the residual and V~) and its FP32 part (for the model)
       ffc (*Af)[MAX_M + 1] = reinterpret_cast<ffc (*)[MAX_M + 1]>(S.A);
-      const double sa = rsqrt(tr);
+      const double sa = rsqrt64(tr);
       if (threadIdx.x < n) {
         S.Ef[threadIdx.x] = ffc_from(sa * S.E[threadIdx.x]);
         S.bh[threadIdx.x] = ffc_from(S.inv_sb * S.b[threadIdx.x]);
@@ -769,7 +841,8 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         const float inq = rsqrtf(warp_sum(abs2(q0)));
         if (lane < n) K.Q[lane][0] = inq * q0;
         __syncwarp();
-        const int kd = lanczos_warp<float>(K.G, n, K.Q, S.d32, S.e32, K.p, K.wv, LANCZOS_TOL32);
+        const int kd = lanczos_warp<float>(K.G, n, K.Q, S.d32, S.e32, LANCZOS_TOL32);
+        if (lane == 0) S.kd = kd;
         FL_MARK(4);
         if (lane < kd) S.c32[lane] = make_float2(lane == 0 ? 1.f : 0.f, 0.f);  // c = e_1
         __syncwarp();
@@ -783,10 +856,8 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           a = root32_warp(S, kd, (float)P.alpha_rel, (float)(S.hi / S.tr), target, fl, ok);
         }
         FL_MARK(6);
-        // floor cases, breakdowns and small alpha/tr are decided and solved in FP64;
-        // otherwise factor G + a I for the refinement
-        bool fp64 = !ok || fl || a < (float)P.fp64_switch;
-        if (!fp64) fp64 = !cholesky32_warp(K.G, n, a, K.beta);
+        // floor cases, breakdowns and small alpha/tr are decided and solved in FP64
+        const bool fp64 = !ok || fl || a < (float)P.fp64_switch;
         if (lane == 0) {
           S.a_s = (double)a;
           S.fp64 = fp64 ? 1 : 0;
@@ -802,13 +873,26 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           S.r32[k] = make_float2(S.bh[k].re.hi, S.bh[k].im.hi);
         }
         __syncthreads();
-        const ff a_ff = ff{(float)S.a_s, 0.f};  // the FP32 root is exact in two-float
+        const float a32 = (float)S.a_s;
+        const ff a_ff = ff{a32, 0.f};  // the FP32 root is exact in two-float
+        const int kd = S.kd;
+        // stop once the next correction, predicted from the contraction of the last
+        // two (||dy_k||^2 rho^2, rho = ||dy_k|| / ||dy_k-1||), is below 1e-18 ||y||^2;
+        // a correction that does not shrink ends the refinement unconverged
         int sweeps = 0;
-        for (float rel = 1.f; sweeps < P.refine_iters && rel > 1e-18f; ++sweeps) {
+        float prev = 0.f, rel = 1.f;
+        bool conv = false;
+        for (; sweeps < P.refine_iters; ++sweeps) {
+          if (sweeps == 1 && rel <= 1e-18f) { conv = true; break; }
+          if (sweeps >= 2) {
+            if (rel * rel <= 1e-18f * prev) { conv = true; break; }
+            if (!(rel < prev)) break;
+          }
+          prev = rel;
           if (sweeps) residual_ff(S, n, m, a_ff);
           if (threadIdx.x < 32) {
             const int j = threadIdx.x;
-            const float2 dy = chol_solve32(S.u.f.G, S.u.f.beta, n, j < n ? S.r32[j] : make_float2(0.f, 0.f));
+            const float2 dy = lanczos_apply32(S, n, kd, a32, j < n ? S.r32[j] : make_float2(0.f, 0.f));
             float dd = 0.f, yy = 0.f;
             if (j < n) {
               const ffc yn = ffc_add(S.yh[j], ffc{ff{dy.x, 0.f}, ff{dy.y, 0.f}});
@@ -823,10 +907,17 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           __syncthreads();
           rel = (float)S.red[4];
         }
-        if (threadIdx.x == 0) atomicAdd(ctr + C_REFINE_ITERS, (unsigned long long)sweeps);
+        if (!conv) conv = rel <= 1e-18f || (sweeps >= 2 && rel * rel <= 1e-18f * prev);
+        if (threadIdx.x == 0) {
+          atomicAdd(ctr + C_REFINE_ITERS, (unsigned long long)sweeps);
+          if (!conv) {
+            S.fp64 = 1;
+            atomicAdd(ctr + C_FP64_FALLBACK, 1ull);
+          }
+        }
         FL_MARK(8);
-        // V~ = A^H y = (||b|| / sqrt(tr)) Ah^H yh, two-float, 2 threads per column
-        {
+        if (conv) {
+          // V~ = A^H y = (||b|| / sqrt(tr)) Ah^H yh, two-float, 2 threads per column
           const int l = threadIdx.x >> 1, h = threadIdx.x & 1;
           ffc acc = ffc_zero();
           if (l < m)
@@ -835,7 +926,8 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           if (l < m && h == 0) S.Vt[l] = (S.sb * sa) * ffc_to(acc);
         }
         __syncthreads();
-      } else {
+      }
+      if (S.fp64) {
         // FP64 route for this mode: A in FP64 over the two-float storage
         for (int e = threadIdx.x; e < n * m; e += ST) {
           const int k = e / m, l = e - k * m;
@@ -868,7 +960,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     // F_l = q F_{l-1} + V~_l and a backward one B_l = q (B_{l+1} + V~_{l+1}), each an
     // inclusive scan over the planes (warp 0: F, warp 1: B in reversed order)
     if (threadIdx.x < 64) {
-      const double2 qz = exp_ikz(kz, P.hz);
+      const double2 qz = S.qz;
       if (threadIdx.x < 32) {
         affine_scan64(S.Vt, m, qz, S.F);
       } else {
@@ -929,8 +1021,11 @@ cudaError_t solve_impl(const Problem& P, const Work<B>& w, cudaStream_t s) {
 
 template <typename R>
 cudaError_t launch_classify(const Problem& P, const Work<R>& w, cudaStream_t s) {
-  k_classify<<<P.n_omega, CT, 0, s>>>(P, w.norms, w.partial, w.n_partial, w.slot, w.act, w.cols, w.ncol,
-                                      w.count, w.dnu, w.ctr);
+  const dim3 g(classify_blocks(P.n), P.n_omega);
+  k_classify_flags<<<g, CT, 0, s>>>(P, w.norms, w.partial, w.n_partial, w.flagbits, w.blkcnt, w.blkgz, w.colblk,
+                                    w.dnu);
+  k_classify_scatter<<<g, CT, 0, s>>>(P, w.flagbits, w.blkcnt, w.blkgz, w.colblk, w.slot, w.act, w.cols, w.ncol,
+                                      w.count, w.ctr);
   return cudaGetLastError();
 }
 template cudaError_t launch_classify<double>(const Problem&, const Work<double>&, cudaStream_t);

@@ -62,6 +62,11 @@ fs_status run_static(const Problem& P, unsigned char* base, const void* W, void*
   w.n_partial = n_partial;
   w.slot = (int*)(base + off); off = up(off + 4 * F * N2);
   w.act = (int*)(base + off); off = up(off + 4 * F * N2);
+  const size_t cb = F * classify_blocks(P.n);
+  w.flagbits = (unsigned*)(base + off); off = up(off + 4 * cb * 32);
+  w.blkcnt = (int*)(base + off); off = up(off + 4 * cb);
+  w.blkgz = (int*)(base + off); off = up(off + 4 * cb);
+  w.colblk = (unsigned*)(base + off); off = up(off + 4 * cb * 8);
   w.cols = (int*)(base + off); off = up(off + 4 * F * P.n);
   w.ncol = (int*)(base + off); off = up(off + 4 * F);
   w.count = (int*)(base + off); off = up(off + 4 * F);
