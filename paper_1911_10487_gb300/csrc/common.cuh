@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace fl {
 
 template <typename R> struct cx_t;
@@ -66,5 +68,29 @@ template <> __host__ __device__ __forceinline__ float2 from_d<float>(double2 a) 
 template <> __host__ __device__ __forceinline__ double2 from_d<double>(double2 a) { return a; }
 
 template <typename R> __host__ __device__ __forceinline__ cx<R> czero() { return mk<R>(R(0), R(0)); }
+
+// Programmatic dependent launch.  The kernels of one reconstruction are launched
+// with programmatic stream serialisation: a kernel may become resident while its
+// predecessor is still running, and waits at pdl_wait() -- before its first
+// global-memory access -- until the predecessor grid has completed and its writes
+// are visible.  pdl_trigger() lets the successor launch as soon as every block of
+// this grid has started.  Launched without the attribute, both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 }  // namespace fl

@@ -39,6 +39,8 @@ template <typename R, int N, bool INV>
 __global__ void __launch_bounds__(THREADS)
 k_fft_rows(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, long long nrows,
            const cx<R>* __restrict__ tw, R scale) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int LINES = row_lines<N>();
   __shared__ cx<R> buf[LINES * N];
   __shared__ cx<R> tw_s[N];
@@ -58,6 +60,8 @@ k_fft_rows(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, long long nrow
 template <typename R, int N, bool INV>
 __global__ void __launch_bounds__(THREADS)
 k_fft_cols(cx<R>* __restrict__ data, const cx<R>* __restrict__ tw) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int TC = Cfg<R>::TC;
   constexpr int E = N * TC;
   __shared__ cx<R> buf[E];
@@ -86,6 +90,8 @@ template <typename R>
 __global__ void __launch_bounds__(NORM_T)
 k_mode_norms(const cx<R>* __restrict__ wt, double* __restrict__ norms, double* __restrict__ partial, int m1,
              int N2) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[NORM_T];
   const int om = blockIdx.y;
   const int nu = blockIdx.x * NORM_T + threadIdx.x;
@@ -127,6 +133,8 @@ __global__ void __launch_bounds__(THREADS)
 k_ifft_cols_gather(Problem P, const cx<R>* __restrict__ prof, const int* __restrict__ slot,
                    const int* __restrict__ cols, const int* __restrict__ ncol,
                    cx<R>* __restrict__ t2, const cx<R>* __restrict__ tw) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int TC = Cfg<R>::TC;
   constexpr int E = N * TC;
   constexpr int PER = (E + THREADS - 1) / THREADS;
@@ -253,6 +261,8 @@ __global__ void __launch_bounds__(THREADS)
 k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restrict__ cols,
                     const int* __restrict__ ncol, R* __restrict__ xi, R* __restrict__ cout,
                     unsigned long long* __restrict__ ctr, const cx<R>* __restrict__ tw) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int LINES = row_lines<N>() / 2 > 0 ? row_lines<N>() / 2 : 1;
   constexpr int E = LINES * N;            // elements of one field
   constexpr int PER = (E + THREADS - 1) / THREADS;
@@ -327,24 +337,31 @@ cudaError_t fwd_impl(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStr
   constexpr int LINES = row_lines<N>();
   const long long nrows = (long long)P.n_omega * P.m1 * N;
   const long long nblk = (nrows + LINES - 1) / LINES;
-  k_fft_rows<R, N, false><<<(unsigned)nblk, THREADS, 0, s>>>(W, w.wt, nrows, w.tw, R(1));
+  cudaError_t e = launch_pdl(k_fft_rows<R, N, false>, dim3((unsigned)nblk), dim3(THREADS), 0, s, W, w.wt, nrows,
+                             (const cx<R>*)w.tw, R(1));
+  if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
   const dim3 g2((N + Cfg<R>::TC - 1) / Cfg<R>::TC, (unsigned)(P.n_omega * P.m1));
-  k_fft_cols<R, N, false><<<g2, THREADS, 0, s>>>(w.wt, w.tw);
+  e = launch_pdl(k_fft_cols<R, N, false>, g2, dim3(THREADS), 0, s, w.wt, (const cx<R>*)w.tw);
+  if (e != cudaSuccess) return e;
   const dim3 gn((unsigned)w.n_partial, (unsigned)P.n_omega);
-  k_mode_norms<R><<<gn, NORM_T, 0, s>>>(w.wt, w.norms, w.partial, P.m1, N * N);
+  e = launch_pdl(k_mode_norms<R>, gn, dim3(NORM_T), 0, s, (const cx<R>*)w.wt, w.norms, w.partial, P.m1, N * N);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 template <typename R, int N>
 cudaError_t rec_impl(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream_t s, cudaEvent_t mid) {
   dim3 g1((N + Cfg<R>::TC - 1) / Cfg<R>::TC, P.m, 2 * P.n_omega);
-  k_ifft_cols_gather<R, N><<<g1, THREADS, 0, s>>>(P, w.prof, w.slot, w.cols, w.ncol, w.t2, w.tw);
+  cudaError_t e = launch_pdl(k_ifft_cols_gather<R, N>, g1, dim3(THREADS), 0, s, P, (const cx<R>*)w.prof,
+                             (const int*)w.slot, (const int*)w.cols, (const int*)w.ncol, w.t2, (const cx<R>*)w.tw);
+  if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
   constexpr int LINES = row_lines<N>() / 2 > 0 ? row_lines<N>() / 2 : 1;
   const long long nrows = (long long)P.m * N;
-  k_ifft_rows_recover<R, N><<<(unsigned)((nrows + LINES - 1) / LINES), THREADS, 0, s>>>(
-      P, w.t2, w.cols, w.ncol, xi, c, w.ctr, w.tw);
+  e = launch_pdl(k_ifft_rows_recover<R, N>, dim3((unsigned)((nrows + LINES - 1) / LINES)), dim3(THREADS), 0, s, P,
+                 (const cx<R>*)w.t2, (const int*)w.cols, (const int*)w.ncol, xi, c, w.ctr, (const cx<R>*)w.tw);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

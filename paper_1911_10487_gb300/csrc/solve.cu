@@ -97,6 +97,8 @@ __global__ void __launch_bounds__(CT)
 k_classify_flags(Problem P, const double* __restrict__ norms, const double* __restrict__ partial, int n_partial,
                  unsigned* __restrict__ flagbits, int* __restrict__ blkcnt, int* __restrict__ blkgz,
                  unsigned* __restrict__ colblk, double* __restrict__ dnu_out) {
+  pdl_wait();
+  pdl_trigger();
   const int om = blockIdx.y, b = blockIdx.x, CB = gridDim.x;
   const int N = P.n, N2 = N * N;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -166,6 +168,8 @@ k_classify_scatter(Problem P, const unsigned* __restrict__ flagbits, const int* 
                    const int* __restrict__ blkgz, const unsigned* __restrict__ colblk, int* __restrict__ slot,
                    int* __restrict__ act, int* __restrict__ cols, int* __restrict__ ncol, int* __restrict__ count,
                    unsigned long long* __restrict__ ctr) {
+  pdl_wait();
+  pdl_trigger();
   const int om = blockIdx.y, b = blockIdx.x, CB = gridDim.x;
   const int N = P.n, N2 = N * N;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -730,6 +734,8 @@ __global__ void __launch_bounds__(ST)
 k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         const int* __restrict__ count, const double* __restrict__ dnu_arr,
         cx<B>* __restrict__ prof, double* __restrict__ alpha_out, unsigned long long* __restrict__ ctr) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared& S = *reinterpret_cast<Shared*>(smem_raw);
   const int N = P.n, n = P.m1, m = P.m;
@@ -1012,9 +1018,8 @@ cudaError_t solve_impl(const Problem& P, const Work<B>& w, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_solve<B, MIXED><<<solve_grid(P.solve_bps), ST, smem, s>>>(P, w.wt, w.act, w.count, w.dnu, w.prof, w.alpha_out,
-                                                   w.ctr);
-  return cudaGetLastError();
+  return launch_pdl(k_solve<B, MIXED>, dim3(solve_grid(P.solve_bps)), dim3(ST), smem, s, P, (const cx<B>*)w.wt,
+                    (const int*)w.act, (const int*)w.count, (const double*)w.dnu, w.prof, w.alpha_out, w.ctr);
 }
 
 }  // namespace
@@ -1022,11 +1027,11 @@ cudaError_t solve_impl(const Problem& P, const Work<B>& w, cudaStream_t s) {
 template <typename R>
 cudaError_t launch_classify(const Problem& P, const Work<R>& w, cudaStream_t s) {
   const dim3 g(classify_blocks(P.n), P.n_omega);
-  k_classify_flags<<<g, CT, 0, s>>>(P, w.norms, w.partial, w.n_partial, w.flagbits, w.blkcnt, w.blkgz, w.colblk,
-                                    w.dnu);
-  k_classify_scatter<<<g, CT, 0, s>>>(P, w.flagbits, w.blkcnt, w.blkgz, w.colblk, w.slot, w.act, w.cols, w.ncol,
-                                      w.count, w.ctr);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(k_classify_flags, g, dim3(CT), 0, s, P, (const double*)w.norms, (const double*)w.partial,
+                             w.n_partial, w.flagbits, w.blkcnt, w.blkgz, w.colblk, w.dnu);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_classify_scatter, g, dim3(CT), 0, s, P, (const unsigned*)w.flagbits, (const int*)w.blkcnt,
+                    (const int*)w.blkgz, (const unsigned*)w.colblk, w.slot, w.act, w.cols, w.ncol, w.count, w.ctr);
 }
 template cudaError_t launch_classify<double>(const Problem&, const Work<double>&, cudaStream_t);
 template cudaError_t launch_classify<float>(const Problem&, const Work<float>&, cudaStream_t);
