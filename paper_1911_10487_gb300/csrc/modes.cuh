@@ -78,8 +78,11 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// exp(i kz d) for kz real (propagating) or purely imaginary (evanescent), d >= 0
-__device__ __forceinline__ double2 exp_ikz(double2 kz, double d) {
+// exp(i kz d) for kz real (propagating) or purely imaginary (evanescent), d >= 0.
+// A real call, not inlined: the FP64 exp and sincos are long, and the per-mode
+// kernels call this from several places executed by different warps, so one
+// shared copy keeps the instruction footprint (and its fetch stalls) down.
+static __device__ __noinline__ double2 exp_ikz(double2 kz, double d) {
   const double mag = exp(-kz.y * d);
   double s, c;
   sincos(kz.x * d, &s, &c);
