@@ -37,7 +37,7 @@ WORKLOAD = "c2"
 DELTA = 0.01
 FLUSH_BYTES = 256 << 20
 STAGES = ("fft_x_forward", "fft_y_forward_norms", "classify", "solve", "ifft_y_gather", "ifft_x_recover")
-KERNELS_PER_STEP = 7  # rows FFT, columns FFT, mode norms, classify, solve, gather+y-IFFT, x-IFFT+recover
+KERNELS_PER_STEP = 8  # rows FFT, columns FFT, mode norms, classify (flags, scatter), solve, gather+y-IFFT, x-IFFT+recover
 
 
 def peaks():
