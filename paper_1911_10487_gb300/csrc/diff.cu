@@ -112,10 +112,28 @@ __device__ __forceinline__ void store_lower(double2* __restrict__ dst, const War
     if (lane < n - j) dst[col_off(j, n) + lane] = S.H[j + lane][j];
 }
 
-// In-place Cholesky H = L L^H of the lower triangle (right-looking, lane k owns
-// row k).  A pivot that is not positive (H not positive definite to rounding)
-// is replaced by the smallest positive double and reported through `bad`.
-__device__ void cholesky(WarpMem& S, int n, int lane, bool& bad) {
+// (row, column) of the packed lower triangle in column-major order (column j holds
+// rows j..n-1), one entry per element, for the trailing updates of the Cholesky
+// factorisation; built once per block for the problem's M1.
+constexpr int MAX_P1 = MAX_M1 * (MAX_M1 + 1) / 2;
+__device__ void build_rc(unsigned short* rc, int n) {
+  const int P1 = n * (n + 1) / 2;
+  for (int e = threadIdx.x; e < P1; e += blockDim.x) {
+    int j = 0;
+    while (col_off(j + 1, n) <= e) ++j;
+    const int r = j + (int)(e - col_off(j, n));
+    rc[e] = (unsigned short)(r << 8 | j);
+  }
+}
+
+// In-place Cholesky H = L L^H of the lower triangle (right-looking).  The pivot
+// column is scaled by lane (lane k, row k); the trailing update of step j -- the
+// entries (r, c), j < c <= r, a contiguous suffix of the packed order -- is dealt
+// evenly over the 32 lanes, so the FP64 pipe is not spent on idle lanes.  A pivot
+// that is not positive (H not positive definite to rounding) is replaced by the
+// smallest positive double and reported through `bad`.
+__device__ void cholesky(WarpMem& S, int n, int lane, const unsigned short* rc, bool& bad) {
+  const int P1 = n * (n + 1) / 2;
   for (int j = 0; j < n; ++j) {
     double d = S.H[j][j].x;
     if (!(d > 0.0)) { bad = true; d = 2.2250738585072014e-308; }
@@ -124,9 +142,9 @@ __device__ void cholesky(WarpMem& S, int n, int lane, bool& bad) {
     if (lane == j) { S.H[j][j] = make_double2(ljj, 0.0); S.dinv[j] = inv; }
     if (lane > j && lane < n) S.H[lane][j] = inv * S.H[lane][j];
     __syncwarp();
-    if (lane > j && lane < n) {
-      const double2 lk = S.H[lane][j];
-      for (int c = j + 1; c <= lane; ++c) S.H[lane][c] = S.H[lane][c] - mulc(lk, S.H[c][j]);
+    for (int e = (int)col_off(j + 1, n) + lane; e < P1; e += 32) {
+      const int r = rc[e] >> 8, c = rc[e] & 255;
+      S.H[r][c] = S.H[r][c] - mulc(S.H[r][j], S.H[c][j]);
     }
     __syncwarp();
   }
@@ -274,12 +292,15 @@ k_diff_forward(Problem P, const double2* __restrict__ gram, const cx<R>* __restr
                unsigned long long* __restrict__ ctr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[DW];
+  __shared__ unsigned short rc[MAX_P1];
   WarpMem& S = reinterpret_cast<WarpMem*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int om = blockIdx.y, n = P.m1, m = P.m;
   const int P1 = n * (n + 1) / 2;
   const long long N2 = (long long)P.n * P.n;
   const double alpha = exp(log_alpha[om]);
+  build_rc(rc, n);
+  __syncthreads();
   double phi = 0.0;
   bool bad = false;
   for (long long nu = (long long)blockIdx.x * DW + warp; nu < N2; nu += (long long)gridDim.x * DW) {
@@ -292,7 +313,7 @@ k_diff_forward(Problem P, const double2* __restrict__ gram, const cx<R>* __restr
       load_lower(S, gram + mode * P1, n, lane);
       if (lane < n) S.H[lane][lane].x += ap;
       __syncwarp();
-      cholesky(S, n, lane, bad);
+      cholesky(S, n, lane, rc, bad);
       store_lower(Ls + mode * P1, S, n, lane);
       const double2 y = chol_solve(S, n, lane, b);
       if (lane < n) ys[mode * n + lane] = y;
