@@ -37,6 +37,10 @@ WORKLOAD = "c2"
 DELTA = 0.01
 FLUSH_BYTES = 256 << 20
 STAGES = ("fft_x_forward", "fft_y_forward_norms", "classify", "solve", "ifft_y_gather", "ifft_x_recover")
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the mixed
+# per-mode solve on this workload, from one ncu capture of the current kernel; to be
+# measured again whenever that kernel changes
+SOLVE_DRAM_BYTES = 306688
 KERNELS_PER_STEP = 8  # rows FFT, columns FFT, mode norms, classify (flags, scatter), solve, gather+y-IFFT, x-IFFT+recover
 
 
@@ -303,7 +307,7 @@ def run_ours(args, rank, world, local):
         flops = solve_flops(wl, reps["mixed"])
         ach = flops / (sm[dom] * 1e-3) / 1e12
         result["roofline"] = {"kernel": "solve", "bound": "alu", "achieved": ach, "peak": alu["fp32_tflops"],
-                              "unit": "TFLOP/s", "frac": ach / alu["fp32_tflops"], "traffic": None,
+                              "unit": "TFLOP/s", "frac": ach / alu["fp32_tflops"], "traffic": SOLVE_DRAM_BYTES,
                               "peak_source": "measured (fs_measure_alu_peaks, FP32 FMA)",
                               "algorithmic_flops": flops, "fp64_peak_tflops": alu["fp64_tflops"]}
     else:
