@@ -15,6 +15,9 @@ Steps, in the paper's order (Sec. 4, Algorithm 2; Sec. 5.2):
      phi(alpha_floor) >= delta_nu -> alpha = alpha_floor = alpha_rel * ||A||_F^2,
      otherwise the root of phi(alpha) = delta_nu, found by bisection in log(alpha).
    phi^2(alpha) = sum_j (alpha/(s_j^2+alpha))^2 |(U* b)_j|^2 + ||b - U U* b||^2.
+   Option: truncated SVD instead of Tikhonov (the regularising algorithm Sec. 5
+   reports as the best), V~ = sum_{j<r} (U* b)_j / s_j v_j with the truncation
+   rank r chosen by the same discrepancy principle (`tsvd_filter`).
 2. U~ = U~0 + omega^2 T_nu V~ with T_nu[l, l'] = h_z K_nu(z'_l - z'_l') (eq. 9),
    an explicit M x M matrix-vector product per mode (Sec. 5.2: 'matrix
    multiplication'); then V = F^-1[V~], u = F^-1[U~] on X.
@@ -46,6 +49,8 @@ class Options:
     alpha_given: object = None  # per-frequency alpha (skips the discrepancy search)
     mode_rows: object = None    # (r0, r1): solve only wavenumber rows r0 <= row < r1, treating the
                                 # others as zeroed -- a proportional work sample, for timing only
+    regularizer: str = "tikhonov"  # or "tsvd": truncated SVD, rank by the discrepancy principle
+    tsvd_rcut: float = 1e-8     # TSVD: singular values below tsvd_rcut * s_1 count as zero
 
 
 @dataclass
@@ -85,6 +90,20 @@ def choose_alpha(s2, beta2, perp2, bnorm, delta_nu, alpha_rel):
     return np.where(floor_case, a_lo, alpha), floor_case
 
 
+def tsvd_filter(s, beta2, bnorm2, delta_nu, rcut):
+    """Truncated SVD (Sec. 4, the regularising algorithm the paper found best): the
+    filter 1/s_j for j < r and 0 beyond, r the smallest rank whose residual
+    ||b||^2 - sum_{j<r} |beta_j|^2 is within delta_nu^2 (the discrepancy principle),
+    counting only singular values above rcut s_1; the numerical rank if no rank is
+    enough.  Returns (filter [..., K], r [...])."""
+    num = s > rcut * s[..., :1]
+    cum = np.cumsum(np.where(num, beta2, 0.0), axis=-1)
+    ok = ((bnorm2[..., None] - cum) <= delta_nu ** 2) & num
+    r = np.where(ok.any(axis=-1), ok.argmax(axis=-1) + 1, num.sum(axis=-1))
+    j = np.arange(s.shape[-1])
+    return np.where(j < r[..., None], 1.0 / np.where(num, s, 1.0), 0.0), r
+
+
 def solve_modes(Wt, omega, k0, g: Geometry, delta_nu, opts: Options, alpha_fixed=None):
     """Step 1 for one frequency: V~[M, N, N] from W~[M1, N, N]; alpha[N, N]; active."""
     Vt = np.zeros((g.m, g.n, g.n), dtype=np.complex128)
@@ -106,6 +125,15 @@ def solve_modes(Wt, omega, k0, g: Geometry, delta_nu, opts: Options, alpha_fixed
         if alpha_fixed is not None:
             act = usable
         a = np.full(bnorm.shape, np.inf)
+        if opts.regularizer == "tsvd":
+            f, _ = tsvd_filter(s, np.abs(beta) ** 2, bnorm ** 2, delta_nu, opts.tsvd_rcut)
+            filt = np.where(act[..., None], f, 0.0)
+            vt = np.einsum("yxjl,yxj->yxl", Vh.conj(), filt * beta)
+            Vt[:, rows, :] = np.moveaxis(vt, -1, 0)
+            sub = alpha[rows]
+            sub[act] = 0.0  # no Tikhonov parameter: recorded as 0 on active modes
+            alpha[rows] = sub
+            continue
         if np.any(act):
             if alpha_fixed is not None:
                 a[act] = alpha_fixed

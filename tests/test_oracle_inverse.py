@@ -202,3 +202,39 @@ def test_zero_data_gives_zero():
     r = inverse.reconstruct(W, [np.pi], g, 0.01)
     assert np.all(r.Vt == 0) and np.all(r.xi == 0)
     assert r.counts["zeroed"] == 64 - r.counts["grazing"]
+
+
+def test_tsvd_filter_is_the_smallest_rank_meeting_the_discrepancy():
+    """Brute force over ranks on random full-rank matrices: the truncated solution of
+    the smallest rank whose explicit residual is within delta."""
+    rng = np.random.default_rng(5)
+    for trial in range(20):
+        A = rng.standard_normal((5, 7)) + 1j * rng.standard_normal((5, 7))
+        b = rng.standard_normal(5) + 1j * rng.standard_normal(5)
+        U, s, Vh = np.linalg.svd(A, full_matrices=False)
+        beta = U.conj().T @ b
+        res = [np.linalg.norm(A @ (Vh[:r].conj().T @ (beta[:r] / s[:r])) - b) for r in range(0, 6)]
+        delta = rng.uniform(0.1, 1.0) * res[0]
+        f, r = inverse.tsvd_filter(s[None], np.abs(beta[None]) ** 2, np.array([np.linalg.norm(b) ** 2]),
+                                   delta, 1e-8)
+        r_brute = next((k for k in range(1, 6) if res[k] <= delta), 5)
+        assert int(r[0]) == r_brute
+        x = Vh.conj().T @ (f[0] * beta)
+        x_brute = Vh[:r_brute].conj().T @ (beta[:r_brute] / s[:r_brute])
+        assert np.allclose(x, x_brute, rtol=1e-12, atol=0)
+
+
+def test_tsvd_on_the_rank_one_kernel_is_the_pseudo_inverse(c1_case):
+    """Every A_nu is rank one, so TSVD keeps one singular value on every active mode:
+    V~ = pinv(A_nu) b (the library pseudo-inverse at the same cutoff)."""
+    w, g, W, u, Wd = c1_case
+    res = inverse.reconstruct(Wd, w.omegas, g, 0.01, opts=inverse.Options(regularizer="tsvd"))
+    om = w.omegas[0]
+    A = om ** 2 * data_matrices(om, g)
+    Wt = fft2(Wd[0])
+    idx = np.argwhere(res.active[0])
+    assert len(idx) > 10
+    for (i2, i1) in idx[:: max(1, len(idx) // 12)]:
+        ref = np.linalg.pinv(A[i2, i1], rcond=1e-8) @ Wt[:, i2, i1]
+        assert np.allclose(res.Vt[0][:, i2, i1], ref, rtol=1e-12, atol=1e-12 * np.linalg.norm(ref))
+    assert np.all(np.isfinite(res.xi))
