@@ -92,6 +92,17 @@ typedef struct {
                           durations appear in fs_report.ms_stage (default 0)              */
   int solve_blocks_per_sm; /* 1 or 2: resident blocks per SM of the per-mode solve (grid =
                           this x SM count); a tuning knob (default 2)                      */
+  int solve_form;      /* 0: dense -- the normal matrix A A^H formed and reduced per mode
+                          (default); 1: rank-one closed form.  Every data plane lies above
+                          X, so K_nu(z_k - z'_l) factors and A_nu = E P^T has rank one
+                          exactly: the Tikhonov solution is conj(P) (E^H b)/(tr + alpha) and
+                          the discrepancy root is explicit, O(M1 + M) per mode.  The two
+                          forms agree to rounding.                                        */
+  int regularizer;     /* 0: Tikhonov (default); 1: truncated SVD (Sec. 5: the paper's best
+                          regularising algorithm), truncation rank by the discrepancy
+                          principle -- rank one on these kernels, i.e. the pseudo-inverse on
+                          every active mode.  Requires solve_form 1 and alpha_mode 0
+                          (FS_EUNSUPPORTED / FS_EINVAL otherwise); alpha output 0.        */
 } fs_options;
 
 typedef struct {

@@ -136,6 +136,12 @@ fs_status validate(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, int n_o
     if (o->max_iter < 1 || o->refine_iters < 1) return fail(ctx, FS_EINVAL, "max_iter >= 1, refine_iters >= 1");
     if (o->solve_blocks_per_sm < 1 || o->solve_blocks_per_sm > 2)
       return fail(ctx, FS_EINVAL, "solve_blocks_per_sm must be 1 or 2");
+    if (o->solve_form != 0 && o->solve_form != 1) return fail(ctx, FS_EINVAL, "solve_form must be 0 or 1");
+    if (o->regularizer != 0 && o->regularizer != 1) return fail(ctx, FS_EINVAL, "regularizer must be 0 or 1");
+    if (o->regularizer == 1 && o->solve_form != 1)
+      return fail(ctx, FS_EUNSUPPORTED, "the truncated SVD is implemented in the rank-one form (solve_form 1)");
+    if (o->regularizer == 1 && o->alpha_mode != 0)
+      return fail(ctx, FS_EINVAL, "the truncated SVD takes no alpha (alpha_mode must be 0)");
   }
   return FS_OK;
 }
@@ -150,6 +156,8 @@ Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, dou
   P.delta = delta; P.tau = o.tau; P.delta_floor = o.delta_floor; P.alpha_rel = o.alpha_rel; P.eps_u = o.eps_u;
   P.fp64_switch = o.fp64_switch;
   P.solve_bps = o.solve_blocks_per_sm;
+  P.solve_form = o.solve_form;
+  P.regularizer = o.regularizer;
   for (int k = 0; k < g->m1; ++k) P.zy[k] = g->zy[k];
   for (int j = 0; j < n_omega; ++j) {
     P.omega[j] = omega[j];
@@ -235,7 +243,8 @@ fs_status run_on(fs_ctx* ctx, const Problem& P, const Layout& L, void* base, cud
   if (ev) cudaEventRecord(ev[2], s);
   if ((e = launch_classify<R>(P, w, s)) != cudaSuccess) return cuda_fail(ctx, e, "classify");
   if (ev) cudaEventRecord(ev[3], s);
-  if (sizeof(R) == 8) e = launch_solve_fp64(P, *(const Work<double>*)&w, s);
+  if (P.solve_form == 1) e = launch_solve_rank1<R>(P, w, s);
+  else if (sizeof(R) == 8) e = launch_solve_fp64(P, *(const Work<double>*)&w, s);
   else e = launch_solve_mixed(P, *(const Work<float>*)&w, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "solve");
   if (ev) cudaEventRecord(ev[4], s);
@@ -282,6 +291,8 @@ fs_status fs_default_options(fs_options* o) {
   o->fp64_switch = 1e-4;
   o->stage_timing = 0;
   o->solve_blocks_per_sm = 2;
+  o->solve_form = 0;
+  o->regularizer = 0;
   return FS_OK;
 }
 

@@ -27,6 +27,8 @@ struct Problem {
   int max_iter;       // root-find iteration cap
   int refine_iters;   // mixed precision: FP64 residual refinement sweeps
   int solve_bps;      // resident blocks per SM of the solve
+  int solve_form;     // 0: dense per-mode solve; 1: rank-one closed form
+  int regularizer;    // 0: Tikhonov; 1: truncated SVD (rank-one form only)
   double period, z1, hz, c0;
   double delta, tau, delta_floor, alpha_rel, eps_u;
   double fp64_switch; // mixed precision: FP64 factor when alpha/tr(Gram) is below this
@@ -75,6 +77,9 @@ template <typename R>
 cudaError_t launch_classify(const Problem& P, const Work<R>& w, cudaStream_t s);
 cudaError_t launch_solve_fp64(const Problem& P, const Work<double>& w, cudaStream_t s);
 cudaError_t launch_solve_mixed(const Problem& P, const Work<float>& w, cudaStream_t s);
+// rank-one closed form of the per-mode problem (Problem::solve_form == 1), either precision
+template <typename R>
+cudaError_t launch_solve_rank1(const Problem& P, const Work<R>& w, cudaStream_t s);
 template <typename R>
 cudaError_t launch_recover(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream_t s,
                            cudaEvent_t mid = nullptr);

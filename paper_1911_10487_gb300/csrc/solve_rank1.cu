@@ -1,0 +1,171 @@
+// Rank-one closed form of the per-mode problem (fs_options.solve_form = 1).
+//
+// Every data plane lies above X, so the Weyl kernel of eq. (8) factors,
+// K_nu(z_k - z'_l) ~ e^{i k_z z_k} e^{-i k_z z'_l}, and the matrix of the SLAE is
+// exactly rank one:
+//   A_kl = E_k P_l,  E_k = omega^2 h_z (-i/(2 k_z)) e^{i k_z (z_k - z_top)},
+//                    P_l = e^{i k_z (z_top - z'_l)}
+// (both factors of modulus <= 1).  Then A A^H = ||P||^2 E E^H, tr = ||E||^2 ||P||^2 is
+// the only nonzero eigenvalue, and with beta = E^H b the normal solutions of Sec. 4
+// comment b are
+//   Tikhonov:  V~ = A^H (A A^H + alpha I)^-1 b = conj(P) beta / (tr + alpha)
+//   TSVD:      V~ = A^+ b                       = conj(P) beta / tr
+// (TSVD keeps the one nonzero singular value: the discrepancy principle never
+// truncates to rank zero on an active mode, whose ||b|| exceeds delta_nu).  The
+// discrepancy is phi^2(alpha) = (alpha/(tr + alpha))^2 c + p with c = |beta|^2/||E||^2
+// (the part of ||b||^2 in the range of A) and p = ||b||^2 - c (the rest), so the
+// root of phi = delta_nu is
+//   alpha = tr t/(1 - t),  t = sqrt((delta_nu^2 - p)/c),
+// floored at alpha_rel tr, which is also taken when phi(alpha_floor) >= delta_nu.
+// The dense form reaches the same values through the normal matrix; the two agree
+// to rounding.  Cost O(M1 + M) per mode, one warp per mode; eq. (9) and the output
+// layout are those of the dense solve.
+#include <math.h>
+
+#include "modes.cuh"
+#include "pipeline.cuh"
+
+namespace fl {
+
+namespace {
+
+constexpr int RW = 4;  // warps (modes) per block
+
+struct Rank1Mem {
+  double2 v[MAX_M], t[MAX_M], F[MAX_M], B[MAX_M];
+};
+
+template <typename R>
+__global__ void __launch_bounds__(RW * 32)
+k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const int* __restrict__ act, const int* __restrict__ count,
+              const double* __restrict__ dnu_arr, cx<R>* __restrict__ prof, double* __restrict__ alpha_out,
+              unsigned long long* __restrict__ ctr) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ Rank1Mem mem[RW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Rank1Mem& S = mem[warp];
+  const int N = P.n, n = P.m1, m = P.m;
+  const long long N2 = (long long)N * N;
+  long long total = 0;
+  for (int w = 0; w < P.n_omega; ++w) total += count[w];
+  unsigned long long n_floor = 0, n_zeroed = 0;
+  for (long long item = (long long)blockIdx.x * RW + warp; item < total; item += (long long)gridDim.x * RW) {
+    int om = 0;
+    long long i = item;
+    while (i >= count[om]) { i -= count[om]; ++om; }
+    const int nu = act[om * N2 + i];
+    const int i2 = nu / N, i1 = nu - i2 * N;
+    const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
+    const double k0 = P.omega[om] / P.c0;
+    const double kn = 2.0 * M_PI / P.period;
+    const double q = k0 * k0 - kn * kn * (double)(m1 * m1 + m2 * m2);
+    const double rq = rsqrt64(fabs(q));  // active modes are never grazing: q != 0
+    const double2 kz = q >= 0.0 ? make_double2(fabs(q) * rq, 0.0) : make_double2(0.0, fabs(q) * rq);
+    const double g0 = 0.5 * P.omega[om] * P.omega[om] * P.hz;
+    const double2 gamma = q >= 0.0 ? make_double2(0.0, -g0 * rq) : make_double2(-g0 * rq, 0.0);
+    const double ztop = P.z1 + (m - 0.5) * P.hz;
+    // E_k and b_k on lane k; P_l on lanes l and l - 32
+    double2 e = make_double2(0, 0), b = make_double2(0, 0);
+    if (lane < n) {
+      e = gamma * exp_ikz(kz, P.zy[lane] - ztop);
+      b = to_d(wt[((long long)om * n + lane) * N2 + nu]);
+    }
+    const int l0 = lane, l1 = lane + 32;
+    const double2 p0 = l0 < m ? exp_ikz(kz, ztop - (P.z1 + (l0 + 0.5) * P.hz)) : make_double2(0, 0);
+    const double2 p1 = l1 < m ? exp_ikz(kz, ztop - (P.z1 + (l1 + 0.5) * P.hz)) : make_double2(0, 0);
+    const double sE = warp_sum(abs2(e));
+    const double sP = warp_sum(abs2(p0) + abs2(p1));
+    const double bb = warp_sum(abs2(b));
+    const double2 beta = warp_sum(cmul_conj_a(e, b));  // E^H b
+    const double tr = sE * sP;
+    const double dnu = dnu_arr[om];
+    double2 coef = make_double2(0, 0);  // V~_l = conj(P_l) coef
+    const bool zeroed = !(tr > 0.0) || (P.alpha_mode == 0 && !(bb > dnu * dnu));
+    double alpha = INFINITY;
+    if (!zeroed) {
+      if (P.regularizer == 1) {
+        alpha = 0.0;
+        coef = rcp64(tr) * beta;
+      } else {
+        if (P.alpha_mode == 1) {
+          alpha = P.alpha_given[om];
+        } else {
+          const double c = abs2(beta) * rcp64(sE);  // |u^H b|^2, u = E / ||E||
+          const double p = fmax(bb - c, 0.0);
+          const double afl = P.alpha_rel * tr;
+          const double rf = afl * rcp64(tr + afl);
+          if (rf * rf * c + p >= dnu * dnu) {
+            alpha = afl;
+            ++n_floor;
+          } else {
+            const double t = sqrt((dnu * dnu - p) * rcp64(c));
+            alpha = fmax(tr * t * rcp64(1.0 - t), afl);
+          }
+        }
+        coef = rcp64(tr + alpha) * beta;
+      }
+    } else {
+      ++n_zeroed;
+    }
+    // V~ and eq. (9): U~ = U~0 + gamma (F + B) over the X planes (two affine scans)
+    const double2 v0 = cmul_conj_a(p0, coef), v1 = cmul_conj_a(p1, coef);
+    if (l0 < m) S.v[l0] = v0;
+    if (l1 < m) S.v[l1] = v1;
+    __syncwarp();
+    // P_{m-2} = e^{i k_z h_z}: the plane-to-plane factor of eq. (9)
+    const int src = m >= 2 ? (m - 2) & 31 : 0;
+    const double2 pq = (m >= 2 && m - 2 >= 32) ? p1 : p0;
+    const double2 qz = make_double2(__shfl_sync(0xffffffffu, pq.x, src), __shfl_sync(0xffffffffu, pq.y, src));
+    affine_scan64(S.v, m, qz, S.F);
+    for (int r = lane; r < m; r += 32) S.t[r] = r == 0 ? make_double2(0, 0) : qz * S.v[m - r];
+    __syncwarp();
+    affine_scan64(S.t, m, qz, S.B);
+    __syncwarp();
+    cx<R>* out = prof + ((long long)om * N2 + i) * 2 * m;
+    const double n2 = (double)N2;
+    for (int l = lane; l < m; l += 32) {
+      double2 u = gamma * (S.F[l] + S.B[m - 1 - l]);
+      if (nu == 0) {
+        double s0, c0;
+        sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s0, &c0);
+        u = u + make_double2(n2 * c0, n2 * s0);
+      }
+      out[l] = from_d<R>(l < 32 ? v0 : v1);
+      out[m + l] = from_d<R>(u);
+    }
+    if (lane == 0 && alpha_out) alpha_out[om * N2 + nu] = zeroed ? INFINITY : alpha;
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (n_floor) atomicAdd(ctr + C_ALPHA_FLOOR, n_floor);
+    if (n_zeroed) {
+      atomicAdd(ctr + C_ACTIVE, (unsigned long long)(-(long long)n_zeroed));
+      atomicAdd(ctr + C_ZEROED, n_zeroed);
+    }
+  }
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_solve_rank1(const Problem& P, const Work<R>& w, cudaStream_t s) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  const long long modes = (long long)P.n_omega * P.n * P.n;
+  const long long want = (modes + RW - 1) / RW;
+  const long long cap = 8LL * sms;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  return launch_pdl(k_solve_rank1<R>, dim3(grid), dim3(RW * 32), 0, s, P, (const cx<R>*)w.wt, (const int*)w.act,
+                    (const int*)w.count, (const double*)w.dnu, w.prof, w.alpha_out, w.ctr);
+}
+
+template cudaError_t launch_solve_rank1<double>(const Problem&, const Work<double>&, cudaStream_t);
+template cudaError_t launch_solve_rank1<float>(const Problem&, const Work<float>&, cudaStream_t);
+
+}  // namespace fl

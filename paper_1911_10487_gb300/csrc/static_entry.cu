@@ -82,8 +82,9 @@ fs_status run_static(const Problem& P, unsigned char* base, const void* W, void*
   if (launch_twiddles<R>(tw, P.n, s) != cudaSuccess) return FS_ECUDA;
   if (launch_fft2_forward<R>((const cx<R>*)W, P, w, s) != cudaSuccess) return FS_ECUDA;
   if (launch_classify<R>(P, w, s) != cudaSuccess) return FS_ECUDA;
-  cudaError_t e = sizeof(R) == 8 ? launch_solve_fp64(P, *(const Work<double>*)&w, s)
-                                 : launch_solve_mixed(P, *(const Work<float>*)&w, s);
+  cudaError_t e = P.solve_form == 1 ? launch_solve_rank1<R>(P, w, s)
+                  : sizeof(R) == 8   ? launch_solve_fp64(P, *(const Work<double>*)&w, s)
+                                     : launch_solve_mixed(P, *(const Work<float>*)&w, s);
   if (e != cudaSuccess) return FS_ECUDA;
   if (launch_recover<R>(P, w, (R*)xi, (R*)c, s) != cudaSuccess) return FS_ECUDA;
   return FS_OK;
@@ -109,6 +110,10 @@ extern "C" fs_status fs_reconstruct_static(const fs_geometry* g, fs_precision pr
   if (!(o.tau > 0.0) || !(o.delta_floor >= 0.0) || !(o.alpha_rel > 0.0) || !(o.eps_u >= 0.0) ||
       o.max_iter < 1 || o.refine_iters < 1 || (o.alpha_mode != 0 && o.alpha_mode != 1))
     return FS_EINVAL;
+  if (o.solve_form != 0 && o.solve_form != 1) return FS_EINVAL;
+  if (o.regularizer != 0 && o.regularizer != 1) return FS_EINVAL;
+  if (o.regularizer == 1 && o.solve_form != 1) return FS_EUNSUPPORTED;
+  if (o.regularizer == 1 && o.alpha_mode != 0) return FS_EINVAL;
   if (o.alpha_mode == 1) {
     if (!o.alpha_given) return FS_EINVAL;
     for (int j = 0; j < n_omega; ++j)
@@ -122,6 +127,8 @@ extern "C" fs_status fs_reconstruct_static(const fs_geometry* g, fs_precision pr
   P.delta = delta; P.tau = o.tau; P.delta_floor = o.delta_floor; P.alpha_rel = o.alpha_rel; P.eps_u = o.eps_u;
   P.fp64_switch = o.fp64_switch;
   P.solve_bps = (o.solve_blocks_per_sm == 1) ? 1 : 2;
+  P.solve_form = o.solve_form;
+  P.regularizer = o.regularizer;
   for (int k = 0; k < g->m1; ++k) P.zy[k] = g->zy[k];
   for (int j = 0; j < n_omega; ++j) {
     P.omega[j] = omega[j];

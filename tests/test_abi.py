@@ -43,6 +43,7 @@ def test_version_and_defaults(abi):
     assert (o.tau, o.delta_floor, o.alpha_rel, o.eps_u) == (2.0, 1e-5, 1e-6, 1e-8)
     assert (o.alpha_mode, o.max_iter, o.refine_iters, o.fp64_switch, o.stage_timing) == (0, 100, 8, 1e-4, 0)
     assert o.solve_blocks_per_sm == 2
+    assert (o.solve_form, o.regularizer) == (0, 0)
     assert abi.lib().fs_default_options(None) == abi.FS_EINVAL
 
 

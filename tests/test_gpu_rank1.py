@@ -1,0 +1,112 @@
+"""The rank-one closed form of the per-mode problem (fs_options.solve_form = 1) and
+the truncated-SVD regulariser, through the C ABI, against the FP64 oracle (SVD per
+mode, bisection for the discrepancy root).  Same tolerances as the dense form:
+xi rel. L2 <= 1e-10 (FS_FP64), <= 1e-5 (FS_MIXED); identical active sets; alpha per
+mode <= 1e-7 (FP64).  The closed form and the dense form on the GPU agree to
+rounding (<= 1e-12)."""
+import numpy as np
+import pytest
+
+from _cases import case, oracle_result
+from oracle.metrics import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["c1", "r8", "r12", "r24", "r48", "r96", "r192", "r256"]
+
+
+@pytest.fixture(scope="module")
+def rc():
+    import torch
+    from paper_1911_10487_gb300 import build
+    build.build()
+    from paper_1911_10487_gb300 import Reconstructor
+    r = Reconstructor(0)
+    yield r
+    torch.cuda.synchronize()
+    r.close()
+
+
+def _geom(g):
+    from paper_1911_10487_gb300 import Geometry
+    return Geometry(g.n, g.m, g.z1, g.z2, tuple(g.zy), g.period)
+
+
+def run(rc, name, delta, precision, **opts):
+    import torch
+    g, om, W, _ = case(name, delta)
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    Wd = torch.from_numpy(np.ascontiguousarray(W)).to(device=rc.device, dtype=dt)
+    xi, c, alpha = rc.reconstruct(Wd, list(om), _geom(g), delta, precision=precision, want_alpha=True, **opts)
+    torch.cuda.synchronize()
+    return xi.double().cpu().numpy(), alpha.cpu().numpy(), rc.report()
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tikhonov_rank1_matches_oracle(rc, name, precision):
+    ref = oracle_result(name, 0.01)
+    xi, alpha, rep = run(rc, name, 0.01, precision, solve_form=1)
+    err = rel_l2(xi, ref.xi)
+    act = np.isfinite(alpha)
+    assert np.array_equal(act, ref.active)
+    ra = np.max(np.abs(alpha[act] / ref.alpha[act] - 1)) if act.any() else 0.0
+    print(f"{name} {precision}: xi {err:.2e}, alpha {ra:.2e}, floors {rep['n_alpha_floor']}")
+    assert err <= (1e-10 if precision == "fp64" else 1e-5)
+    if precision == "fp64":
+        assert ra <= 1e-7
+
+
+@pytest.mark.parametrize("name", ["c1", "r48", "r256"])
+def test_rank1_equals_dense_form(rc, name):
+    x1, a1, _ = run(rc, name, 0.05, "fp64", solve_form=1)
+    x0, a0, _ = run(rc, name, 0.05, "fp64")
+    assert rel_l2(x1, x0) <= 1e-12
+    act = np.isfinite(a0)
+    assert np.array_equal(np.isfinite(a1), act)
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tsvd_matches_oracle(rc, name, precision):
+    ref = oracle_result(name, 0.01, regularizer="tsvd")
+    xi, alpha, _ = run(rc, name, 0.01, precision, solve_form=1, regularizer=1)
+    act = np.isfinite(alpha)
+    assert np.array_equal(act, ref.active)
+    assert np.all(alpha[act] == 0.0)
+    err = rel_l2(xi, ref.xi)
+    print(f"tsvd {name} {precision}: xi {err:.2e}")
+    assert err <= (1e-10 if precision == "fp64" else 1e-5)
+
+
+def test_given_alpha_rank1(rc):
+    g, om, W, _ = case("r24", 0.01)
+    given = [3e-2, 1e-1]
+    ref = oracle_result("r24", 0.01, alpha_given=tuple(given))
+    xi, alpha, _ = run(rc, "r24", 0.01, "fp64", solve_form=1, alpha_mode=1, alpha_given=given)
+    assert rel_l2(xi, ref.xi) <= 1e-10
+
+
+def test_batch_rank1_equals_single_calls(rc):
+    import torch
+    items, singles = [], []
+    for name in ("c1", "r24", "r96"):
+        g, om, W, _ = case(name, 0.01)
+        Wd = torch.from_numpy(np.ascontiguousarray(W)).to(device=rc.device, dtype=torch.complex64)
+        items.append((Wd, list(om), _geom(g), 0.01))
+        xi, _, _ = rc.reconstruct(Wd, list(om), _geom(g), 0.01, precision="mixed", solve_form=1)
+        singles.append(xi.cpu().numpy())
+    res = rc.reconstruct_batch(items, "mixed", n_streams=3, solve_form=1)
+    torch.cuda.synchronize()
+    for (xi, _), ref in zip(res, singles):
+        assert np.array_equal(xi.cpu().numpy(), ref)
+
+
+def test_invalid_combinations(rc):
+    from paper_1911_10487_gb300 import FlatLayerError
+    with pytest.raises(FlatLayerError, match="FS_EUNSUPPORTED"):
+        run(rc, "r12", 0.01, "fp64", regularizer=1)
+    with pytest.raises(FlatLayerError, match="FS_EINVAL"):
+        run(rc, "r12", 0.01, "fp64", solve_form=1, regularizer=1, alpha_mode=1, alpha_given=[1.0])
+    with pytest.raises(FlatLayerError, match="FS_EINVAL"):
+        run(rc, "r12", 0.01, "fp64", solve_form=2)
