@@ -9,7 +9,8 @@ single-scattering forward kernel (synthetic; no dataset).
 A step = one full reconstruction W -> (xi, c): 2D FFT of the data planes, mode
 norms, discrepancy classification, per-mode Tikhonov solve + eq. (9), inverse FFTs
 and the pointwise xi/c recovery, replayed as one CUDA graph.  The headline is the
-mixed-precision path; the plain FP64 path is measured in the same run.  L2 is
+mixed-precision path; the plain FP64 path is measured in the same run, and both
+again with the rank-one closed form of the per-mode problem (`rank1_form`).  L2 is
 flushed (256 MiB write) before every timed step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -205,6 +206,18 @@ def run_ours(args, rank, world, local):
             rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, c, None))
         torch.cuda.synchronize()
         graphs[prec] = g
+    # the same step with the rank-one closed form of the per-mode problem (solve_form 1)
+    for prec, W, rdt in cases:
+        xi = torch.empty((wl.m, wl.n, wl.n), dtype=rdt, device=rc.device)
+        outs[prec + "_r1"] = (xi, torch.empty_like(xi))
+        with torch.cuda.stream(stream):
+            rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, outs[prec + "_r1"][1], None), solve_form=1)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, outs[prec + "_r1"][1], None), solve_form=1)
+        torch.cuda.synchronize()
+        graphs[prec + "_r1"] = g
 
     def timed(prec, K, Wm, clocks=None):
         g = graphs[prec]
@@ -237,6 +250,7 @@ def run_ours(args, rank, world, local):
     ms_fp64, _ = timed("fp64", args.steps, args.warmup)
     ms_mixed = max_over_ranks(ms_mixed, world)
     ms_fp64 = max_over_ranks(ms_fp64, world)
+    ms_r1 = {p: max_over_ranks(timed(p + "_r1", args.steps, args.warmup)[0], world) for p in ("mixed", "fp64")}
     vox = wl.voxel_freqs
     value = world * vox / (ms_mixed * 1e-3)
     value_fp64 = world * vox / (ms_fp64 * 1e-3)
@@ -290,6 +304,8 @@ def run_ours(args, rank, world, local):
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "fp64_path": {"value": value_fp64, "ms_per_step": ms_fp64, "dtype": "f64"},
+        "rank1_form": {p: {"value": world * wl.voxel_freqs / (ms_r1[p] * 1e-3), "ms_per_step": ms_r1[p]}
+                       for p in ("mixed", "fp64")},
         "stage_ms": stage_ms,
         "e2e": {"value": world * vox / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(W_h.numel() * 8), "d2h_bytes_per_step": int(2 * xi_h.numel() * 4)},
@@ -540,6 +556,9 @@ def main():
             result["rel_err_vs_oracle"] = {
                 "mixed": rel_l2(outs["mixed"][0].double().cpu().numpy(), ref.xi),
                 "fp64": rel_l2(outs["fp64"][0].cpu().numpy(), ref.xi)}
+            for p in ("mixed", "fp64"):
+                result["rank1_form"][p]["rel_err_vs_oracle"] = rel_l2(outs[p + "_r1"][0].double().cpu().numpy(),
+                                                                     ref.xi)
             if batch is not None:
                 swl, sW, som, sxm, sx64 = spot
                 _, sref = cpu_baseline(swl, sW, som)
