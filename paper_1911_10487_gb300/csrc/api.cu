@@ -10,6 +10,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "../../include/flatlayer.h"
@@ -51,6 +53,10 @@ struct fs_ctx {
   static constexpr int MAX_SIDE = 16;
   cudaStream_t side[MAX_SIDE] = {};
   cudaEvent_t fork_ev = nullptr, join_ev[MAX_SIDE] = {};
+  // fs_reconstruct_host: the last call captured as a CUDA graph, replayed while the
+  // call repeats (same problem, options and buffers; pinned host memory)
+  std::vector<unsigned char> host_key;
+  cudaGraphExec_t host_exec = nullptr;
   char err[512] = {0};
 };
 
@@ -64,6 +70,21 @@ fs_status fail(fs_ctx* ctx, fs_status st, const char* fmt, ...) {
     va_end(ap);
   }
   return st;
+}
+
+// page-locked (or registered) host memory: copies from it can be captured in a graph
+bool pinned(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+template <typename T> void key_put(std::vector<unsigned char>& k, const T& v) {
+  const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+  k.insert(k.end(), b, b + sizeof(T));
 }
 
 fs_status cuda_fail(fs_ctx* ctx, cudaError_t e, const char* where) {
@@ -326,6 +347,7 @@ void fs_destroy(fs_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->host_exec) cudaGraphExecDestroy(ctx->host_exec);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->stage) cudaFree(ctx->stage);
   for (auto& a : ctx->tw)
@@ -397,15 +419,74 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
   char* dW = (char*)ctx->stage;
   char* dxi = dW + align_up(wbytes);
   char* dc = dxi + align_up(obytes);
-  if ((e = cudaMemcpyAsync(dW, W_host, wbytes, cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess)
-    return cuda_fail(ctx, e, "H2D W");
-  st = fs_reconstruct(ctx, g, prec, dW, omega, n_omega, delta, c0, opts, dxi, c_host ? dc : nullptr, nullptr);
-  if (st != FS_OK) return st;
-  if ((e = cudaMemcpyAsync(xi_host, dxi, obytes, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
-    return cuda_fail(ctx, e, "D2H xi");
-  if (c_host && (e = cudaMemcpyAsync(c_host, dc, obytes, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
-    return cuda_fail(ctx, e, "D2H c");
+  // A repeated call (same key: every argument that shapes the work, the host and
+  // device buffers) replays the graph captured after its first run: one launch
+  // instead of the copies and eight kernel launches.  Only with page-locked host
+  // buffers (copies from pageable memory cannot be captured) and without stage timing.
+  fs_options o;
+  fs_default_options(&o);
+  if (opts) o = *opts;
+  const bool graphable = o.stage_timing == 0 && pinned(W_host) && pinned(xi_host) && (!c_host || pinned(c_host));
+  std::vector<unsigned char> key;
+  if (graphable) {
+    // values only (no struct padding, no pointers to argument arrays)
+    const int ints[12] = {g->n, g->m, g->m1, n_omega, (int)prec, o.alpha_mode, o.max_iter, o.refine_iters,
+                          o.solve_blocks_per_sm, o.solve_form, o.regularizer, 0};
+    const double dbl[10] = {g->period, g->z1, g->z2, delta, c0, o.tau, o.delta_floor, o.alpha_rel, o.eps_u,
+                            o.fp64_switch};
+    key_put(key, ints);
+    key_put(key, dbl);
+    key.insert(key.end(), (const unsigned char*)g->zy, (const unsigned char*)(g->zy + g->m1));
+    key.insert(key.end(), (const unsigned char*)omega, (const unsigned char*)(omega + n_omega));
+    if (o.alpha_mode == 1)
+      key.insert(key.end(), (const unsigned char*)o.alpha_given, (const unsigned char*)(o.alpha_given + n_omega));
+    const void* ptrs[6] = {W_host, xi_host, c_host, ctx->stage, ctx->ws, ctx->stream};
+    key_put(key, ptrs);
+    if (ctx->host_exec && key == ctx->host_key) {
+      if ((e = cudaGraphLaunch(ctx->host_exec, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+      if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sync");
+      return FS_OK;
+    }
+  }
+  auto enqueue = [&]() -> fs_status {
+    cudaError_t e2;
+    if ((e2 = cudaMemcpyAsync(dW, W_host, wbytes, cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e2, "H2D W");
+    fs_status s2 = fs_reconstruct(ctx, g, prec, dW, omega, n_omega, delta, c0, opts, dxi, c_host ? dc : nullptr, nullptr);
+    if (s2 != FS_OK) return s2;
+    if ((e2 = cudaMemcpyAsync(xi_host, dxi, obytes, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e2, "D2H xi");
+    if (c_host && (e2 = cudaMemcpyAsync(c_host, dc, obytes, cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e2, "D2H c");
+    return FS_OK;
+  };
+  if ((st = enqueue()) != FS_OK) return st;
   if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sync");
+  if (graphable) {
+    // the run above sized the workspace and twiddles, so the capture allocates
+    // nothing; the key is taken again in case the workspace moved
+    const void* ptrs[6] = {W_host, xi_host, c_host, ctx->stage, ctx->ws, ctx->stream};
+    key.resize(key.size() - sizeof(ptrs));
+    key_put(key, ptrs);
+    if (ctx->host_exec) {
+      cudaGraphExecDestroy(ctx->host_exec);
+      ctx->host_exec = nullptr;
+      ctx->host_key.clear();
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const fs_status cap = enqueue();
+      const cudaError_t end = cudaStreamEndCapture(ctx->stream, &graph);
+      if (cap == FS_OK && end == cudaSuccess && graph &&
+          cudaGraphInstantiate(&ctx->host_exec, graph, 0) == cudaSuccess) {
+        ctx->host_key = key;
+      } else {
+        ctx->host_exec = nullptr;
+      }
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();  // a failed capture leaves the uncaptured path in use
+  }
   return FS_OK;
 }
 

@@ -136,6 +136,31 @@ def test_deterministic_and_host_entry(rc):
     assert np.array_equal(xh.numpy(), a)
 
 
+def test_host_entry_repeats_track_new_data(rc):
+    """Repeated host calls on the same page-locked buffers replay a captured graph; the
+    results must follow the buffers' new contents.  Pageable buffers take the
+    uncaptured path."""
+    import torch
+    from paper_1911_10487_gb300 import FS_MIXED, fs_reconstruct_host
+    g, om, W1, _ = case("r24", 0.01)
+    _, _, W2, _ = case("r24", 0.05)
+    ref = []
+    for W in (W1, W2):
+        ref.append(run_gpu(rc, g, om, W.astype(np.complex64), 0.01, precision="mixed")[0])
+    Wh = torch.from_numpy(np.ascontiguousarray(W1.astype(np.complex64))).pin_memory()
+    xh = torch.empty((g.m, g.n, g.n), dtype=torch.float32).pin_memory()
+    gs = _geom(g).c_struct()
+    for k, W in enumerate((W1, W1, W1, W2, W2, W1)):
+        Wh.copy_(torch.from_numpy(np.ascontiguousarray(W.astype(np.complex64))))
+        fs_reconstruct_host(rc.ctx, gs, FS_MIXED, Wh.data_ptr(), list(om), 0.01, 1.0, None, xh.data_ptr(), None)
+        assert np.array_equal(xh.numpy(), ref[0 if W is W1 else 1]), k
+    Wp = np.ascontiguousarray(W2.astype(np.complex64))
+    xp = np.empty((g.m, g.n, g.n), dtype=np.float32)
+    for _ in range(2):
+        fs_reconstruct_host(rc.ctx, gs, FS_MIXED, Wp.ctypes.data, list(om), 0.01, 1.0, None, xp.ctypes.data, None)
+        assert np.array_equal(xp, ref[1])
+
+
 def test_invalid_arguments_rejected(rc):
     import torch
     from paper_1911_10487_gb300 import FlatLayerError, Geometry
