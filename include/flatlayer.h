@@ -90,7 +90,7 @@ typedef struct {
   double fp64_switch;  /* FS_MIXED: FP64 factorisation below alpha/tr = this (default 1e-4) */
   int stage_timing;    /* 1: record CUDA events between the kernels of fs_reconstruct; the
                           durations appear in fs_report.ms_stage (default 0)              */
-  int solve_blocks_per_sm; /* 1 or 2: resident blocks per SM of the per-mode solve (grid =
+  int solve_blocks_per_sm; /* 1, 2 or 3: resident blocks per SM of the per-mode solve (grid =
                           this x SM count); a tuning knob (default 2)                      */
   int solve_form;      /* 0: dense -- the normal matrix A A^H formed and reduced per mode
                           (default); 1: rank-one closed form.  Every data plane lies above

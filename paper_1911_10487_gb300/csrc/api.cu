@@ -155,8 +155,8 @@ fs_status validate(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, int n_o
         if (!(o->alpha_given[j] > 0.0)) return fail(ctx, FS_EINVAL, "alpha_given[%d] must be > 0", j);
     }
     if (o->max_iter < 1 || o->refine_iters < 1) return fail(ctx, FS_EINVAL, "max_iter >= 1, refine_iters >= 1");
-    if (o->solve_blocks_per_sm < 1 || o->solve_blocks_per_sm > 2)
-      return fail(ctx, FS_EINVAL, "solve_blocks_per_sm must be 1 or 2");
+    if (o->solve_blocks_per_sm < 1 || o->solve_blocks_per_sm > 3)
+      return fail(ctx, FS_EINVAL, "solve_blocks_per_sm must be 1, 2 or 3");
     if (o->solve_form != 0 && o->solve_form != 1) return fail(ctx, FS_EINVAL, "solve_form must be 0 or 1");
     if (o->regularizer != 0 && o->regularizer != 1) return fail(ctx, FS_EINVAL, "regularizer must be 0 or 1");
     if (o->regularizer == 1 && o->solve_form != 1)

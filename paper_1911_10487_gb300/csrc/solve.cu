@@ -308,38 +308,50 @@ __device__ __forceinline__ ffc ffc_shfl_xor(ffc a, int m) {
 // ------------------------------------------------------------------------------
 // shared state of one block
 // ------------------------------------------------------------------------------
+// The union below holds what one phase of a mode needs and is dead in the next:
+// the FP64 route's normal matrix and Lanczos basis, the mixed route's FP32 model
+// (whose copy of A is dead after the normal matrix, so the root search reuses it),
+// and the arrays of eq. (9), written once the solve is done.  74 KB per block, so
+// three blocks fit on an SM.
 template <typename B> struct Bulk {
   cx<B> G[MAX_M1][MAX_M1 + 1];
   cx<B> V[MAX_M1][MAX_M1 + 1];  // Lanczos basis, column j = q_j (FP64 route)
-  B beta[MAX_M1];
-  cx<B> p[MAX_M1], wv[MAX_M1];
 };
-struct BulkF : Bulk<float> {
-  float2 A[MAX_M1][MAX_M + 1];   // A_nu / sqrt(tr G) in FP32 (mixed precision)
-  float2 Q[MAX_M1][MAX_M1 + 1];  // Lanczos basis, column j = q_j (mixed precision)
-  float2 ts[MAX_M1][32];         // per-lane tridiagonal solves: scaled forward values
-  float tmu[MAX_M1][32];         //                              and multipliers
+struct BulkF {
+  float2 G[MAX_M1][MAX_M1 + 1];  // FP32 normal matrix of the scaled problem
+  float2 Q[MAX_M1][MAX_M1 + 1];  // Lanczos basis, column j = q_j
+  float2 p[MAX_M1];              // model solve (T + a I)^-1 Q^H r
+  union {
+    float2 A[MAX_M1][MAX_M + 1];  // A_nu / sqrt(tr G) in FP32, for the normal matrix
+    struct {
+      float2 ts[MAX_M1][32];  // per-lane tridiagonal solves of the root search: scaled values
+      float tmu[MAX_M1][32];  //                                                 and multipliers
+    } rs;
+  } m;
+};
+struct Eq9 {
+  double2 Vt[MAX_M], t[MAX_M], F[MAX_M], Bk[MAX_M], z64[MAX_M];
 };
 
 struct Shared {
-  double2 A[MAX_M1][MAX_M + 1];  // A_nu in FP64
-  union { Bulk<double> d; BulkF f; } u;
-  double2 E[MAX_M1], Pz[MAX_M], b[MAX_M1], c[MAX_M1], y[MAX_M1], r[MAX_M1], z[MAX_M1];
-  double2 Vt[MAX_M], t[MAX_M], F[MAX_M], Bk[MAX_M], z64[MAX_M];
+  double2 A[MAX_M1][MAX_M + 1];  // A_nu in FP64 (FP64 route), Ah in two-float (mixed route)
+  union { Bulk<double> d; BulkF f; Eq9 q; } u;
+  double2 E[MAX_M1], Pz[MAX_M], b[MAX_M1], c[MAX_M1], y[MAX_M1], z[MAX_M1];
   double d[MAX_M1], e[MAX_M1];     // tridiagonal T (FP64 route: of G; scaled by 1/tr after the factor)
   float d32[MAX_M1], e32[MAX_M1];  // T / tr in FP32
   float2 c32[MAX_M1], r32[MAX_M1];
-  ffc yh[MAX_M1], rh[MAX_M1], bh[MAX_M1], th[MAX_M], Ef[MAX_M1], Pf[MAX_M];  // two-float (mixed route)
+  ffc yh[MAX_M1], bh[MAX_M1], th[MAX_M], Ef[MAX_M1], Pf[MAX_M];  // two-float (mixed route)
   double tr, sb, inv_sb, dnu, lo, hi, a_s, red[8];  // a_s = alpha / tr
   double3 red3[8];
   double2 qz;  // exp(i k_z h_z)
   int fp64, tflag, kd;  // kd: dimension of the Lanczos model
 };
+static_assert(sizeof(Shared) <= 75 * 1024, "three solve blocks per SM");
 
 template <typename B> __device__ __forceinline__ Bulk<B>& bulk(Shared& s);
 template <> __device__ __forceinline__ Bulk<double>& bulk<double>(Shared& s) { return s.u.d; }
 
-// G = A A^H in precision B: FP64 from S.A, or FP32 from the scaled copy (G / tr)
+// G = A A^H in FP64 from S.A (FP64 route)
 template <typename B>
 __device__ void gram(Shared& S, int n, int m) {
   Bulk<B>& K = bulk<B>(S);
@@ -350,11 +362,7 @@ __device__ void gram(Shared& S, int n, int m) {
     while ((i + 1) * (i + 2) / 2 <= e) ++i;
     const int j = e - i * (i + 1) / 2;
     cx<B> acc = czero<B>();
-    if constexpr (sizeof(B) == 8) {
-      for (int l = 0; l < m; ++l) acc = acc + mulc(S.A[i][l], S.A[j][l]);
-    } else {
-      for (int l = 0; l < m; ++l) acc = acc + mulc(S.u.f.A[i][l], S.u.f.A[j][l]);
-    }
+    for (int l = 0; l < m; ++l) acc = acc + mulc(S.A[i][l], S.A[j][l]);
     if (i == j) acc.y = B(0);
     K.G[i][j] = acc;
     K.G[j][i] = conjx(acc);
@@ -601,9 +609,9 @@ __device__ void gram32(Shared& S, int n, int m) {
   if (r < n)
 #pragma unroll 4
     for (int l = 0; l < m; ++l) {
-      const float2 a = K.A[r][l];
+      const float2 a = K.m.A[r][l];
 #pragma unroll
-      for (int q = 0; q < CW; ++q) acc[q] = acc[q] + mulc(a, K.A[cg * CW + q][l]);
+      for (int q = 0; q < CW; ++q) acc[q] = acc[q] + mulc(a, K.m.A[cg * CW + q][l]);
     }
 #pragma unroll
   for (int q = 0; q < CW; ++q) {
@@ -667,7 +675,6 @@ __device__ void residual_ff(Shared& S, int n, int m, ff a) {
     if (k < n && h == 0) {
       const ffc ay = ffc{ff_mul(a, S.yh[k].re), ff_mul(a, S.yh[k].im)};
       const ffc r = ffc_sub(ffc_sub(S.bh[k], acc), ay);
-      S.rh[k] = r;
       S.r32[k] = make_float2(r.re.hi, r.im.hi);
     }
   }
@@ -682,20 +689,20 @@ __device__ float lane_phi2(Shared& S, int n, float a, const float2* c, bool& ok)
   ok = lp > 0.f;
   float il = __fdividef(1.f, lp);
   float2 w = c[0];
-  K.ts[0][L] = il * w;
+  K.m.rs.ts[0][L] = il * w;
   for (int i = 1; i < n; ++i) {
     const float mu = S.e32[i - 1] * il;
     lp = S.d32[i] + a - mu * S.e32[i - 1];
     ok = ok && lp > 0.f;
     il = __fdividef(1.f, lp);
     w = c[i] - mu * w;
-    K.tmu[i][L] = mu;
-    K.ts[i][L] = il * w;
+    K.m.rs.tmu[i][L] = mu;
+    K.m.rs.ts[i][L] = il * w;
   }
-  float2 x = K.ts[n - 1][L];
+  float2 x = K.m.rs.ts[n - 1][L];
   float zz = abs2(x);
   for (int i = n - 2; i >= 0; --i) {
-    x = K.ts[i][L] - K.tmu[i + 1][L] * x;
+    x = K.m.rs.ts[i][L] - K.m.rs.tmu[i + 1][L] * x;
     zz += abs2(x);
   }
   return a * a * zz;
@@ -833,7 +840,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         const int k = e / m, l = e - k * m;
         const ffc a = ffc_mul(S.Ef[k], S.Pf[l]);
         Af[k][l] = a;
-        S.u.f.A[k][l] = make_float2(a.re.hi, a.im.hi);
+        S.u.f.m.A[k][l] = make_float2(a.re.hi, a.im.hi);
       }
       __syncthreads();
       FL_MARK(2);
@@ -929,7 +936,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           if (l < m)
             for (int k = h; k < n; k += 2) acc = ffc_add(acc, ffc_conj_mul(Af[k][l], S.yh[k]));
           acc = ffc_add(acc, ffc_shfl_xor(acc, 1));
-          if (l < m && h == 0) S.Vt[l] = (S.sb * sa) * ffc_to(acc);
+          if (l < m && h == 0) S.u.q.Vt[l] = (S.sb * sa) * ffc_to(acc);
         }
         __syncthreads();
       }
@@ -958,7 +965,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         for (int k = h; k < n; k += 2) acc = acc + cmul_conj_a(S.A[k][l], S.y[k]);
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-      if (l < m && h == 0) S.Vt[l] = acc;
+      if (l < m && h == 0) S.u.q.Vt[l] = acc;
       __syncthreads();
     }
     FL_MARK(10);
@@ -968,27 +975,27 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     if (threadIdx.x < 64) {
       const double2 qz = S.qz;
       if (threadIdx.x < 32) {
-        affine_scan64(S.Vt, m, qz, S.F);
+        affine_scan64(S.u.q.Vt, m, qz, S.u.q.F);
       } else {
         const int r = threadIdx.x - 32;  // reversed sequence s'_r = q V~_{m-r} (s'_0 = 0)
-        for (int rr = r; rr < m; rr += 32) S.t[rr] = rr == 0 ? make_double2(0, 0) : qz * S.Vt[m - rr];
+        for (int rr = r; rr < m; rr += 32) S.u.q.t[rr] = rr == 0 ? make_double2(0, 0) : qz * S.u.q.Vt[m - rr];
         __syncwarp();
-        affine_scan64(S.t, m, qz, S.z64);
+        affine_scan64(S.u.q.t, m, qz, S.u.q.z64);
         __syncwarp();
-        for (int rr = r; rr < m; rr += 32) S.Bk[m - 1 - rr] = S.z64[rr];
+        for (int rr = r; rr < m; rr += 32) S.u.q.Bk[m - 1 - rr] = S.u.q.z64[rr];
       }
     }
     __syncthreads();
     FL_MARK(11);
     cx<B>* out = prof + ((long long)om * N2 + i) * 2 * m;
     for (int l = threadIdx.x; l < m; l += ST) {
-      double2 u = gamma * (S.F[l] + S.Bk[l]);
+      double2 u = gamma * (S.u.q.F[l] + S.u.q.Bk[l]);
       if (nu == 0) {
         double s, c;
         sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s, &c);
         u = u + make_double2((double)N2 * c, (double)N2 * s);
       }
-      out[l] = from_d<B>(S.Vt[l]);
+      out[l] = from_d<B>(S.u.q.Vt[l]);
       out[m + l] = from_d<B>(u);
     }
     if (threadIdx.x == 0 && alpha_out) alpha_out[om * N2 + nu] = S.a_s * S.tr;
@@ -1005,7 +1012,7 @@ int solve_grid(int bps) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 152;
   }
-  return (bps == 1 ? 1 : 2) * sms;
+  return (bps < 1 ? 1 : (bps > 3 ? 3 : bps)) * sms;
 }
 
 template <typename B, bool MIXED>

@@ -126,7 +126,7 @@ extern "C" fs_status fs_reconstruct_static(const fs_geometry* g, fs_precision pr
   P.period = g->period; P.z1 = g->z1; P.hz = (g->z2 - g->z1) / g->m; P.c0 = c0;
   P.delta = delta; P.tau = o.tau; P.delta_floor = o.delta_floor; P.alpha_rel = o.alpha_rel; P.eps_u = o.eps_u;
   P.fp64_switch = o.fp64_switch;
-  P.solve_bps = (o.solve_blocks_per_sm == 1) ? 1 : 2;
+  P.solve_bps = (o.solve_blocks_per_sm >= 1 && o.solve_blocks_per_sm <= 3) ? o.solve_blocks_per_sm : 2;
   P.solve_form = o.solve_form;
   P.regularizer = o.regularizer;
   for (int k = 0; k < g->m1; ++k) P.zy[k] = g->zy[k];

@@ -11,7 +11,7 @@ from __future__ import annotations
 import json
 import os
 
-CANDIDATES = [(s, b) for s in (1, 2, 4, 8, 16) for b in (1, 2)]
+CANDIDATES = [(s, b) for s in (1, 2, 4, 8, 16) for b in (1, 2, 3)]
 
 
 def signature(items, precision):
