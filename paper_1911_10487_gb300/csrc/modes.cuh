@@ -51,6 +51,15 @@ __device__ __forceinline__ double rsqrt64(double x) {
   return __longlong_as_double(yb - ((long long)h << 52));
 }
 
+// exp(i kz d) inlined: for small kernels that evaluate several independent
+// exponentials per thread, so that their FP64 chains can overlap
+__device__ __forceinline__ double2 exp_ikz_inline(double2 kz, double d) {
+  const double mag = exp(-kz.y * d);
+  double s, c;
+  sincos(kz.x * d, &s, &c);
+  return make_double2(mag * c, mag * s);
+}
+
 template <typename T> __device__ __forceinline__ T rcp(T x);
 template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }  // ~2 ulp
 template <> __device__ __forceinline__ double rcp<double>(double x) { return rcp64(x); }

@@ -68,12 +68,12 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const int* __restrict__ a
     // E_k and b_k on lane k; P_l on lanes l and l - 32
     double2 e = make_double2(0, 0), b = make_double2(0, 0);
     if (lane < n) {
-      e = gamma * exp_ikz(kz, P.zy[lane] - ztop);
+      e = gamma * exp_ikz_inline(kz, P.zy[lane] - ztop);
       b = to_d(wt[((long long)om * n + lane) * N2 + nu]);
     }
     const int l0 = lane, l1 = lane + 32;
-    const double2 p0 = l0 < m ? exp_ikz(kz, ztop - (P.z1 + (l0 + 0.5) * P.hz)) : make_double2(0, 0);
-    const double2 p1 = l1 < m ? exp_ikz(kz, ztop - (P.z1 + (l1 + 0.5) * P.hz)) : make_double2(0, 0);
+    const double2 p0 = l0 < m ? exp_ikz_inline(kz, ztop - (P.z1 + (l0 + 0.5) * P.hz)) : make_double2(0, 0);
+    const double2 p1 = l1 < m ? exp_ikz_inline(kz, ztop - (P.z1 + (l1 + 0.5) * P.hz)) : make_double2(0, 0);
     const double sE = warp_sum(abs2(e));
     const double sP = warp_sum(abs2(p0) + abs2(p1));
     const double bb = warp_sum(abs2(b));
