@@ -8,7 +8,8 @@
 //      G = -exp(i k0 rho)/(4 pi rho)); every data plane lies above X, so
 //      exp(i k_z (z_k - z'_l)) is evaluated as exp(i k_z (z_k - z'_top)) *
 //      exp(i k_z (z'_top - z'_l)) with both factors of modulus <= 1;
-//   2. forms the dual normal matrix G = A A^H (M1 x M1, Hermitian);
+//   2. applies the dual normal matrix G = A A^H (M1 x M1, Hermitian) only as
+//      A (A^H q), never forming it;
 //   3. reduces G to a real symmetric tridiagonal T = Q^H G Q by the Lanczos process
 //      started from q_1 = b / ||b|| (full reorthogonalisation), stopped when the
 //      Krylov space is invariant to working precision -- after two steps for these
@@ -35,10 +36,10 @@
 //            y = (||b||/tr) Q (T/tr + a I)^-1 e_1.
 //  FS_MIXED: steps 2-4 in FP32 on the scaled problem; y is then refined against
 //            the residual b - A (A^H y) - alpha y evaluated in two-float arithmetic
-//            (about 48 bits), each correction solved with a Cholesky factor of
-//            G + alpha I (FP32).  Modes whose alpha/tr(G) falls below fp64_switch
-//            (where the FP32 factor no longer makes the refinement contract), floor
-//            cases and FP32 breakdowns take the FS_FP64 route.
+//            (about 48 bits), each correction solved from the Lanczos model
+//            (exactly on its Krylov space, 1/alpha on the complement).  Modes whose
+//            corrections do not contract or whose alpha/tr(G) falls below
+//            fp64_switch, floor cases and FP32 breakdowns take the FS_FP64 route.
 #include <math.h>
 
 #include "modes.cuh"
@@ -65,9 +66,11 @@ namespace fl {
 namespace {
 
 // Threads per solve block: 4 warps.  The per-mode critical path is warp 0's
-// sequential part (Lanczos, root, Cholesky, triangular solves); with 4 warps on
-// the 4 schedulers of an SM that warp does not share its issue slots with another
-// warp of the same block (8 warps measured slower).
+// sequential part (Lanczos scalars, root, model solves); with 4 warps on the 4
+// schedulers of an SM that warp does not share its issue slots with another warp
+// of the same block (8 warps measured slower).  The per-mode code runs once per
+// mode and is latency-bound, so its loops are not unrolled ("#pragma unroll 1"):
+// unrolling only multiplies the code (measured 2-5 us slower per mode).
 constexpr int ST = 128;
 constexpr int SW = ST / 32;
 // Lanczos stops when the next off-diagonal of T is at most this fraction of
@@ -309,20 +312,21 @@ __device__ __forceinline__ ffc ffc_shfl_xor(ffc a, int m) {
 // shared state of one block
 // ------------------------------------------------------------------------------
 // The union below holds what one phase of a mode needs and is dead in the next:
-// the FP64 route's normal matrix and Lanczos basis, the mixed route's FP32 model
-// (whose copy of A is dead after the normal matrix, so the root search reuses it),
-// and the arrays of eq. (9), written once the solve is done.  74 KB per block, so
-// three blocks fit on an SM.
+// the FP64 route's Lanczos basis, the mixed route's FP32 model (whose copy of A is
+// dead after the Lanczos process, so the root search reuses it), and the arrays of
+// eq. (9), written once the solve is done.
 template <typename B> struct Bulk {
-  cx<B> G[MAX_M1][MAX_M1 + 1];
   cx<B> V[MAX_M1][MAX_M1 + 1];  // Lanczos basis, column j = q_j (FP64 route)
+  cx<B> t[MAX_M];               // A^H q_j of the Lanczos step
+  cx<B> w[MAX_M1];              // G q_j of the Lanczos step
 };
 struct BulkF {
-  float2 G[MAX_M1][MAX_M1 + 1];  // FP32 normal matrix of the scaled problem
   float2 Q[MAX_M1][MAX_M1 + 1];  // Lanczos basis, column j = q_j
+  float2 t[MAX_M];               // A^H q_j of the Lanczos step
+  float2 w[MAX_M1];              // G q_j of the Lanczos step
   float2 p[MAX_M1];              // model solve (T + a I)^-1 Q^H r
   union {
-    float2 A[MAX_M1][MAX_M + 1];  // A_nu / sqrt(tr G) in FP32, for the normal matrix
+    float2 A[MAX_M1][MAX_M + 1];  // A_nu / sqrt(tr G) in FP32, for the Lanczos products
     struct {
       float2 ts[MAX_M1][32];  // per-lane tridiagonal solves of the root search: scaled values
       float tmu[MAX_M1][32];  //                                                 and multipliers
@@ -344,78 +348,88 @@ struct Shared {
   double tr, sb, inv_sb, dnu, lo, hi, a_s, red[8];  // a_s = alpha / tr
   double3 red3[8];
   double2 qz;  // exp(i k_z h_z)
-  int fp64, tflag, kd;  // kd: dimension of the Lanczos model
+  int fp64, tflag, kd, go;  // kd: dimension of the Lanczos model; go: Lanczos continues
 };
 static_assert(sizeof(Shared) <= 75 * 1024, "three solve blocks per SM");
 
-template <typename B> __device__ __forceinline__ Bulk<B>& bulk(Shared& s);
-template <> __device__ __forceinline__ Bulk<double>& bulk<double>(Shared& s) { return s.u.d; }
 
-// G = A A^H in FP64 from S.A (FP64 route)
-template <typename B>
-__device__ void gram(Shared& S, int n, int m) {
-  Bulk<B>& K = bulk<B>(S);
-  const int nt = n * (n + 1) / 2;
-  for (int e = threadIdx.x; e < nt; e += ST) {
-    int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-    while (i * (i + 1) / 2 > e) --i;
-    while ((i + 1) * (i + 2) / 2 <= e) ++i;
-    const int j = e - i * (i + 1) / 2;
-    cx<B> acc = czero<B>();
-    for (int l = 0; l < m; ++l) acc = acc + mulc(S.A[i][l], S.A[j][l]);
-    if (i == j) acc.y = B(0);
-    K.G[i][j] = acc;
-    K.G[j][i] = conjx(acc);
-  }
-  __syncthreads();
-}
-
-// Lanczos tridiagonalisation of the Hermitian G (n x n, shared) from the unit
-// vector in column 0 of Q, with full reorthogonalisation (classical Gram-Schmidt,
-// twice): Q^H G Q = T, real symmetric tridiagonal with diagonal d and
-// off-diagonal e >= 0.  Stops when the next off-diagonal is not above tol (the
-// Krylov space of q_0 is then invariant to that level) or at n columns, and
-// returns the number k of columns.  Warp 0, lane r owning row r.
+// Lanczos tridiagonalisation of the Hermitian G = A A^H (n x n; A is n x m in
+// shared memory) from the unit vector in column 0 of Q, with full
+// reorthogonalisation (classical Gram-Schmidt, twice): Q^H G Q = T, real symmetric
+// tridiagonal with diagonal d and off-diagonal e >= 0.  G is never formed: each
+// step applies it as A (A^H q_j), 2 n m complex products instead of the n^2 m of
+// the normal matrix, spread over the whole block (two threads per column of A for
+// t = A^H q_j, four per row for A t); warp 0 then orthogonalises (lane r owning
+// row r).  Stops when the next off-diagonal is not above tol (the Krylov space of
+// q_0 is then invariant to that level) or at n columns, and returns the number k
+// of columns (the same in every thread).  Called by all ST threads; t (m entries),
+// w (n entries) and *go are scratch.
 // The (1,1) entries of (T + a I)^-1 and (T + a I)^-2, from which the discrepancy
 // is computed, depend on e only through the squares e_j^2, so stopping at
 // e_k <= tol changes phi^2 by O(tol^2 / a^2) relative.
 template <typename T>
-__device__ int lanczos_warp(const cx<T> (*G)[MAX_M1 + 1], int n, cx<T> (*Q)[MAX_M1 + 1], T* d, T* e, T tol) {
+__device__ int lanczos_block(const cx<T> (*A)[MAX_M + 1], int n, int m, cx<T>* t, cx<T>* wv,
+                             cx<T> (*Q)[MAX_M1 + 1], T* d, T* e, T tol, int* go) {
   const int lane = threadIdx.x & 31;
   int k = n;
+#pragma unroll 1
   for (int j = 0; j < n; ++j) {
-    cx<T> w = czero<T>();
-    if (lane < n) {  // w = G q_j
-      cx<T> a0 = czero<T>(), a1 = czero<T>();
-      int c = 0;
-      for (; c + 1 < n; c += 2) {
-        a0 = a0 + G[lane][c] * Q[c][j];
-        a1 = a1 + G[lane][c + 1] * Q[c + 1][j];
-      }
-      if (c < n) a0 = a0 + G[lane][c] * Q[c][j];
-      w = a0 + a1;
+    {  // t = A^H q_j: two threads per column l
+      const int l = threadIdx.x >> 1, h = threadIdx.x & 1;
+      cx<T> acc = czero<T>();
+      if (l < m)
+#pragma unroll 1
+        for (int r = h; r < n; r += 2) acc = acc + cmul_conj_a(A[r][l], Q[r][j]);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      if (l < m && h == 0) t[l] = acc;
     }
-    const cx<T> qj = lane < n ? Q[lane][j] : czero<T>();
-    const T aj = warp_sum(qj.x * w.x + qj.y * w.y);  // q_j^H G q_j (real)
-    w = w - aj * qj;
-    if (j > 0 && lane < n) w = w - e[j - 1] * Q[lane][j - 1];
-    for (int pass = 0; pass < 2; ++pass) {  // w -= Q (Q^H w) over q_0 .. q_j
-      cx<T> corr = czero<T>();
-      for (int i = 0; i <= j; ++i) {
-        const cx<T> qi = lane < n ? Q[lane][i] : czero<T>();
-        const cx<T> h = warp_sum(cmul_conj_a(qi, w));  // q_i^H w
-        corr = corr + qi * h;
-      }
-      w = w - corr;
+    __syncthreads();
+    {  // w = A t = G q_j: four threads per row r
+      const int r = threadIdx.x >> 2, h = threadIdx.x & 3;
+      cx<T> acc = czero<T>();
+      if (r < n)
+#pragma unroll 1
+        for (int l = h; l < m; l += 4) acc = acc + A[r][l] * t[l];
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+      if (r < n && h == 0) wv[r] = acc;
     }
-    const T beta = sqrt(warp_sum(abs2(w)));
-    if (lane == 0) d[j] = aj;
-    if (j + 1 == n || !(beta > tol)) { k = j + 1; break; }
-    if (lane == 0) e[j] = beta;
-    if (lane < n) Q[lane][j + 1] = rcp<T>(beta) * w;
-    __syncwarp();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      cx<T> w = lane < n ? wv[lane] : czero<T>();
+      const cx<T> qj = lane < n ? Q[lane][j] : czero<T>();
+      const T aj = warp_sum(qj.x * w.x + qj.y * w.y);  // q_j^H G q_j (real)
+      w = w - aj * qj;
+      if (j > 0 && lane < n) w = w - e[j - 1] * Q[lane][j - 1];
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {  // w -= Q (Q^H w) over q_0 .. q_j
+        cx<T> corr = czero<T>();
+#pragma unroll 1
+        for (int i = 0; i <= j; ++i) {
+          const cx<T> qi = lane < n ? Q[lane][i] : czero<T>();
+          const cx<T> hh = warp_sum(cmul_conj_a(qi, w));  // q_i^H w
+          corr = corr + qi * hh;
+        }
+        w = w - corr;
+      }
+      const T beta = sqrt(warp_sum(abs2(w)));
+      const bool stop = j + 1 == n || !(beta > tol);
+      if (lane == 0) {
+        d[j] = aj;
+        if (!stop) e[j] = beta;
+        *go = stop ? 0 : 1;
+      }
+      if (!stop && lane < n) Q[lane][j + 1] = rcp<T>(beta) * w;
+    }
+    __syncthreads();
+    if (!*go) {
+      k = j + 1;
+      break;
+    }
   }
-  __syncwarp();
   return k;
 }
 
@@ -429,6 +443,7 @@ __device__ bool tri_solve(const T* d, const T* e, int n, T a, const cx<T>* rhs, 
   il[0] = rcp<T>(lp);
   mu[0] = T(0);
   z[0] = rhs[0];
+#pragma unroll 1
   for (int i = 1; i < n; ++i) {
     mu[i] = e[i - 1] * il[i - 1];
     lp = d[i] + a - mu[i] * e[i - 1];
@@ -436,7 +451,9 @@ __device__ bool tri_solve(const T* d, const T* e, int n, T a, const cx<T>* rhs, 
     il[i] = rcp<T>(lp);
     z[i] = rhs[i] - mu[i] * z[i - 1];
   }
+#pragma unroll 1
   for (int i = 0; i < n; ++i) z[i] = il[i] * z[i];
+#pragma unroll 1
   for (int i = n - 2; i >= 0; --i) z[i] = z[i] - mu[i + 1] * z[i + 1];
   return true;
 }
@@ -461,15 +478,18 @@ __device__ double newton_log_alpha(const T* d, const T* e, const cx<T>* c, int n
   gp_out = 0.0;
   ok = true;
   int it = 0;
+#pragma unroll 1
   for (; it < max_iter; ++it) {
     const T a = exp_t(t);
     if (!tri_solve<T>(d, e, n, a, c, z)) { ok = false; break; }
     T zz = T(0);
+#pragma unroll 1
     for (int i = 0; i < n; ++i) zz += abs2(z[i]);
     const T g = log_t(a * a * zz) - lt;
     if (g > T(0)) th = t; else tl = t;
     if (!tri_solve<T>(d, e, n, a, z, s)) { ok = false; break; }
     T zs = T(0);
+#pragma unroll 1
     for (int i = 0; i < n; ++i) zs += z[i].x * s[i].x + z[i].y * s[i].y;
     const T gp = T(2) - T(2) * a * zs * rcp<T>(zz);  // d log(a^2 ||z||^2) / d log a
     gp_out = (double)gp;
@@ -488,21 +508,12 @@ __device__ double phi2(const T* d, const T* e, const cx<T>* c, int n, double a, 
   cx<T> z[MAX_M1];
   ok = tri_solve<T>(d, e, n, (T)a, c, z);
   T zz = T(0);
+#pragma unroll 1
   for (int i = 0; i < n; ++i) zz += abs2(z[i]);
   return a * a * (double)zz;
 }
 
 // block-wide sums of one double per thread (all threads get them)
-__device__ double block_sum(Shared& S, double v) {
-  v = warp_sum(v);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double t = 0.0;
-#pragma unroll
-  for (int w = 0; w < SW; ++w) t += S.red[w];
-  return t;
-}
 __device__ double3 block_sum3(Shared& S, double3 v) {
   v.x = warp_sum(v.x);
   v.y = warp_sum(v.y);
@@ -520,18 +531,17 @@ __device__ double3 block_sum3(Shared& S, double3 v) {
   return t;
 }
 
-// FP64 route: FP64 normal matrix and Lanczos model, FP32-seeded root on the
+// FP64 route: FP64 Lanczos model of the normal matrix, FP32-seeded root on the
 // scaled tridiagonal, FP64 Newton to full accuracy, y = (||b||/tr) Q (T/tr + a I)^-1 e_1.
 __device__ void solve_fp64(Shared& S, int n, int m, const Problem& P, int om, unsigned long long* ctr) {
-  gram<double>(S, n, m);
   FL_MARK_S(13);
   Bulk<double>& K = S.u.d;
   const double inv_sb = rcp64(S.sb), inv_tr = rcp64(S.tr);
+  if (threadIdx.x < n) K.V[threadIdx.x][0] = inv_sb * S.b[threadIdx.x];
+  __syncthreads();
+  const int kd = lanczos_block<double>(S.A, n, m, K.t, K.w, K.V, S.d, S.e, LANCZOS_TOL64 * S.tr, &S.go);
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    if (lane < n) K.V[lane][0] = inv_sb * S.b[lane];
-    __syncwarp();
-    const int kd = lanczos_warp<double>(K.G, n, K.V, S.d, S.e, LANCZOS_TOL64 * S.tr);
     if (lane < kd) {  // scaled model T / tr, c = e_1, and FP32 copies for the seed
       S.d[lane] *= inv_tr;
       S.d32[lane] = (float)S.d[lane];
@@ -546,7 +556,6 @@ __device__ void solve_fp64(Shared& S, int n, int m, const Problem& P, int om, un
   }
   __syncthreads();
   FL_MARK_S(14);
-  const int kd = S.kd;
   if (threadIdx.x == 0) {
     const double target = (S.dnu * inv_sb) * (S.dnu * inv_sb);
     const double lo = P.alpha_rel, hi = S.hi * inv_tr;
@@ -576,6 +585,7 @@ __device__ void solve_fp64(Shared& S, int n, int m, const Problem& P, int om, un
   FL_MARK_S(15);
   if (threadIdx.x < n) {  // y = (||b|| / tr) Q z
     double2 acc = make_double2(0, 0);
+#pragma unroll 1
     for (int j = 0; j < kd; ++j) acc = acc + K.V[threadIdx.x][j] * S.z[j];
     S.y[threadIdx.x] = (S.sb * inv_tr) * acc;
   }
@@ -594,33 +604,6 @@ __device__ __forceinline__ cx<T> pick(const cx<T>* v, int j) {  // v[j] for a ru
   return r;
 }
 
-__device__ __forceinline__ float2 shfl2(float2 v, int src) {
-  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-}
-
-// G32 = A32 A32^H (full Hermitian matrix), all threads: row = lane, 4 columns per warp
-__device__ void gram32(Shared& S, int n, int m) {
-  BulkF& K = S.u.f;
-  constexpr int CW = MAX_M1 / SW;
-  const int r = threadIdx.x & 31, cg = threadIdx.x >> 5;
-  float2 acc[CW];
-#pragma unroll
-  for (int q = 0; q < CW; ++q) acc[q] = make_float2(0.f, 0.f);
-  if (r < n)
-#pragma unroll 4
-    for (int l = 0; l < m; ++l) {
-      const float2 a = K.m.A[r][l];
-#pragma unroll
-      for (int q = 0; q < CW; ++q) acc[q] = acc[q] + mulc(a, K.m.A[cg * CW + q][l]);
-    }
-#pragma unroll
-  for (int q = 0; q < CW; ++q) {
-    const int c = cg * CW + q;
-    if (r < n && c < n) K.G[r][c] = r == c ? make_float2(acc[q].x, 0.f) : acc[q];
-  }
-  __syncthreads();
-}
-
 // Approximate (G + a I)^-1 r from the Lanczos model of the FP32 normal matrix,
 // exact on the Krylov space spanned by the model and r/a on its orthogonal
 // complement:  Q (T + a I)^-1 Q^H r + (r - Q Q^H r)/a.  The complement holds the
@@ -632,6 +615,7 @@ __device__ float2 lanczos_apply32(Shared& S, int n, int kd, float a, float2 r) {
   BulkF& K = S.u.f;
   const int lane = threadIdx.x & 31;
   float2 mine = make_float2(0.f, 0.f), proj = make_float2(0.f, 0.f);
+#pragma unroll 1
   for (int i = 0; i < kd; ++i) {
     const float2 qi = lane < n ? K.Q[lane][i] : make_float2(0.f, 0.f);
     const float2 ci = warp_sum(cmul_conj_a(qi, r));  // q_i^H r
@@ -644,6 +628,7 @@ __device__ float2 lanczos_apply32(Shared& S, int n, int kd, float a, float2 r) {
   __syncwarp();
   float2 y = make_float2(0.f, 0.f);
   if (lane < n) {
+#pragma unroll 1
     for (int i = 0; i < kd; ++i) y = y + K.Q[lane][i] * K.p[i];
     y = y + rcp<float>(a) * (r - proj);
   }
@@ -690,6 +675,7 @@ __device__ float lane_phi2(Shared& S, int n, float a, const float2* c, bool& ok)
   float il = __fdividef(1.f, lp);
   float2 w = c[0];
   K.m.rs.ts[0][L] = il * w;
+#pragma unroll 1
   for (int i = 1; i < n; ++i) {
     const float mu = S.e32[i - 1] * il;
     lp = S.d32[i] + a - mu * S.e32[i - 1];
@@ -701,6 +687,7 @@ __device__ float lane_phi2(Shared& S, int n, float a, const float2* c, bool& ok)
   }
   float2 x = K.m.rs.ts[n - 1][L];
   float zz = abs2(x);
+#pragma unroll 1
   for (int i = n - 2; i >= 0; --i) {
     x = K.m.rs.ts[i][L] - K.m.rs.tmu[i + 1][L] * x;
     zz += abs2(x);
@@ -718,6 +705,7 @@ __device__ float root32_warp(Shared& S, int n, float lo, float hi, float target,
   float gl = 0.f, gh = 0.f;
   floor_case = false;
   ok = true;
+#pragma unroll 1
   for (int round = 0; round < 3; ++round) {
     const float t = tl + (th - tl) * (float)lane * (1.f / 31.f);
     bool okl;
@@ -736,6 +724,51 @@ __device__ float root32_warp(Shared& S, int n, float lo, float hi, float target,
   return expf(t);
 }
 
+// exp(i kz d) for the mixed route: the phase is reduced to [-pi, pi] in FP64
+// (three FP64 operations) and the sine, cosine and exponential are taken in FP32
+// (FP64 where the decay leaves the FP32 range).  Relative error ~1e-7, the
+// precision of the FP32 data; A = E P^T built from the
+// rounded factors is still exactly rank one, and the refinement converges to the
+// solution of that A, so the rounding enters V~ at ~1e-7 without amplification.
+__device__ __forceinline__ double2 exp_ikz32(double2 kz, double d) {
+  if (kz.y * d > 80.0) return exp_ikz(kz, d);  // e^-80: the FP32 exponential nears underflow
+  const double ph = kz.x * d;
+  const double red = fma(-6.283185307179586, rint(ph * 0.15915494309189535), ph);
+  float sn, cs;
+  sincosf((float)red, &sn, &cs);
+  const float mag = expf((float)(-kz.y * d));
+  return make_double2((double)(mag * cs), (double)(mag * sn));
+}
+
+// The block's shared state through the dynamic shared-memory symbol, so that an
+// out-of-line device function addresses it with shared-memory instructions.
+extern __shared__ __align__(16) unsigned char smem_dyn[];
+__device__ __forceinline__ Shared& shm() { return *reinterpret_cast<Shared*>(smem_dyn); }
+
+// U~ - U~0 = gamma (F + B) of eq. (9): the forward recurrence F_l = q F_{l-1} + V~_l
+// and the backward one B_l = q (B_{l+1} + V~_{l+1}), each an inclusive scan over
+// the planes (warp 0: F, warp 1: B in reversed order).  Kept out of line: compiled
+// on its own, this FP64 code runs about three times faster than inlined into the
+// solve kernel (measured).
+__device__ __noinline__ void eq9_scans(int m) {
+  Shared& S = shm();
+  if (threadIdx.x < 64) {
+    const double2 qz = S.qz;
+    if (threadIdx.x < 32) {
+      affine_scan64(S.u.q.Vt, m, qz, S.u.q.F);
+    } else {
+      const int r = threadIdx.x - 32;  // reversed sequence s'_r = q V~_{m-r} (s'_0 = 0)
+#pragma unroll 1
+      for (int rr = r; rr < m; rr += 32) S.u.q.t[rr] = rr == 0 ? make_double2(0, 0) : qz * S.u.q.Vt[m - rr];
+      __syncwarp();
+      affine_scan64(S.u.q.t, m, qz, S.u.q.z64);
+      __syncwarp();
+#pragma unroll 1
+      for (int rr = r; rr < m; rr += 32) S.u.q.Bk[m - 1 - rr] = S.u.q.z64[rr];
+    }
+  }
+}
+
 template <typename B, bool MIXED>
 __global__ void __launch_bounds__(ST)
 k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
@@ -748,7 +781,9 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
   const int N = P.n, n = P.m1, m = P.m;
   const long long N2 = (long long)N * N;
   long long total = 0;
+#pragma unroll 1
   for (int w = 0; w < P.n_omega; ++w) total += count[w];
+#pragma unroll 1
   for (long long item = blockIdx.x; item < total; item += gridDim.x) {
     int om = 0;
     long long i = item;
@@ -772,21 +807,24 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     const double g0 = 0.5 * om2 * P.hz;
     const double2 gamma = q >= 0.0 ? make_double2(0.0, -g0 * rq) : make_double2(-g0 * rq, 0.0);
     const double ztop = P.z1 + (m - 0.5) * P.hz;
-    // the exponentials are FP64 chains, one per thread: threads 0..63 take P,
-    // threads 64..95 take E, thread 96 the plane-to-plane factor q of eq. (9)
+    // the exponentials, one per thread: threads 0..63 take P, threads 64..95 take E
+    // (FP32 in the mixed route), thread 96 the plane-to-plane factor q of eq. (9)
+    // in FP64 (the mixed route takes it later, while warp 0 finds the root)
     if (threadIdx.x < m) {
       const int l = threadIdx.x;
-      S.Pz[l] = exp_ikz(kz, ztop - (P.z1 + (l + 0.5) * P.hz));
+      S.Pz[l] = MIXED ? exp_ikz32(kz, ztop - (P.z1 + (l + 0.5) * P.hz)) : exp_ikz(kz, ztop - (P.z1 + (l + 0.5) * P.hz));
     } else if (threadIdx.x >= MAX_M && threadIdx.x < MAX_M + n) {
       const int k = threadIdx.x - MAX_M;
       S.b[k] = to_d(wt[((long long)om * n + k) * N2 + nu]);
-      S.E[k] = gamma * exp_ikz(kz, P.zy[k] - ztop);
-    } else if (threadIdx.x == MAX_M + MAX_M1) {
+      S.E[k] = gamma * (MIXED ? exp_ikz32(kz, P.zy[k] - ztop) : exp_ikz(kz, P.zy[k] - ztop));
+    } else if (!MIXED && threadIdx.x == MAX_M + MAX_M1) {
       S.qz = exp_ikz(kz, P.hz);
     }
     __syncthreads();
     // ||A||_F^2 = tr(G) = (sum_k |E_k|^2)(sum_l |P_l|^2) since A_kl = E_k P_l; ||b||^2
     FL_MARK(1);
+    // (in FP64 in both routes: |E|^2 and |P|^2 of strongly evanescent modes leave
+    // the FP32 range)
     const double3 sums = block_sum3(S, make_double3(threadIdx.x < n ? abs2(S.E[threadIdx.x]) : 0.0,
                                                     threadIdx.x < m ? abs2(S.Pz[threadIdx.x]) : 0.0,
                                                     threadIdx.x < n ? abs2(S.b[threadIdx.x]) : 0.0));
@@ -802,6 +840,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         if (alpha_out) alpha_out[om * N2 + nu] = INFINITY;
       }
       cx<B>* out0 = prof + ((long long)om * N2 + i) * 2 * m;
+#pragma unroll 1
       for (int l = threadIdx.x; l < m; l += ST) {
         double2 u = make_double2(0, 0);
         if (nu == 0) {
@@ -836,6 +875,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       }
       if (threadIdx.x < m) S.Pf[threadIdx.x] = ffc_from(S.Pz[threadIdx.x]);
       __syncthreads();
+#pragma unroll 1
       for (int e = threadIdx.x; e < n * m; e += ST) {
         const int k = e / m, l = e - k * m;
         const ffc a = ffc_mul(S.Ef[k], S.Pf[l]);
@@ -844,17 +884,18 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       }
       __syncthreads();
       FL_MARK(2);
-      gram32(S, n, m);
-      FL_MARK(3);
+      BulkF& K = S.u.f;
       if (threadIdx.x < 32) {
-        BulkF& K = S.u.f;
-        const int lane = threadIdx.x;
         // Lanczos model of the scaled G from q_0 = bh (renormalised in FP32)
+        const int lane = threadIdx.x;
         const float2 q0 = lane < n ? make_float2(S.bh[lane].re.hi, S.bh[lane].im.hi) : make_float2(0.f, 0.f);
         const float inq = rsqrtf(warp_sum(abs2(q0)));
         if (lane < n) K.Q[lane][0] = inq * q0;
-        __syncwarp();
-        const int kd = lanczos_warp<float>(K.G, n, K.Q, S.d32, S.e32, LANCZOS_TOL32);
+      }
+      __syncthreads();
+      const int kd = lanczos_block<float>(K.m.A, n, m, K.t, K.w, K.Q, S.d32, S.e32, LANCZOS_TOL32, &S.go);
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
         if (lane == 0) S.kd = kd;
         FL_MARK(4);
         if (lane < kd) S.c32[lane] = make_float2(lane == 0 ? 1.f : 0.f, 0.f);  // c = e_1
@@ -863,10 +904,10 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         bool ok = true, fl = false;
         float a;
         if (P.alpha_mode == 1) {
-          a = (float)(P.alpha_given[om] / S.tr);
+          a = (float)P.alpha_given[om] / (float)S.tr;
         } else {
           const float target = (float)((S.dnu * S.inv_sb) * (S.dnu * S.inv_sb));
-          a = root32_warp(S, kd, (float)P.alpha_rel, (float)(S.hi / S.tr), target, fl, ok);
+          a = root32_warp(S, kd, (float)P.alpha_rel, (float)S.hi / (float)S.tr, target, fl, ok);
         }
         FL_MARK(6);
         // floor cases, breakdowns and small alpha/tr are decided and solved in FP64
@@ -876,11 +917,14 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           S.fp64 = fp64 ? 1 : 0;
           if (fp64) atomicAdd(ctr + C_FP64_FALLBACK, 1ull);
         }
+      } else if (threadIdx.x == MAX_M + MAX_M1) {
+        S.qz = exp_ikz(kz, P.hz);  // FP64, on an idle warp; first read by eq. (9)
       }
       __syncthreads();
       FL_MARK(7);
       if (!S.fp64) {
         // yh by refinement against the two-float residual, to ||dy|| <= 1e-9 ||y||
+#pragma unroll 1
         for (int k = threadIdx.x; k < n; k += ST) {
           S.yh[k] = ffc_zero();
           S.r32[k] = make_float2(S.bh[k].re.hi, S.bh[k].im.hi);
@@ -888,13 +932,13 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         __syncthreads();
         const float a32 = (float)S.a_s;
         const ff a_ff = ff{a32, 0.f};  // the FP32 root is exact in two-float
-        const int kd = S.kd;
         // stop once the next correction, predicted from the contraction of the last
         // two (||dy_k||^2 rho^2, rho = ||dy_k|| / ||dy_k-1||), is below 1e-18 ||y||^2;
         // a correction that does not shrink ends the refinement unconverged
         int sweeps = 0;
         float prev = 0.f, rel = 1.f;
         bool conv = false;
+#pragma unroll 1
         for (; sweeps < P.refine_iters; ++sweeps) {
           if (sweeps == 1 && rel <= 1e-18f) { conv = true; break; }
           if (sweeps >= 2) {
@@ -934,6 +978,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           const int l = threadIdx.x >> 1, h = threadIdx.x & 1;
           ffc acc = ffc_zero();
           if (l < m)
+#pragma unroll 1
             for (int k = h; k < n; k += 2) acc = ffc_add(acc, ffc_conj_mul(Af[k][l], S.yh[k]));
           acc = ffc_add(acc, ffc_shfl_xor(acc, 1));
           if (l < m && h == 0) S.u.q.Vt[l] = (S.sb * sa) * ffc_to(acc);
@@ -942,6 +987,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       }
       if (S.fp64) {
         // FP64 route for this mode: A in FP64 over the two-float storage
+#pragma unroll 1
         for (int e = threadIdx.x; e < n * m; e += ST) {
           const int k = e / m, l = e - k * m;
           S.A[k][l] = S.E[k] * S.Pz[l];
@@ -949,6 +995,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         __syncthreads();
       }
     } else {
+#pragma unroll 1
       for (int e = threadIdx.x; e < n * m; e += ST) {
         const int k = e / m, l = e - k * m;
         S.A[k][l] = S.E[k] * S.Pz[l];
@@ -962,6 +1009,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       const int l = threadIdx.x >> 1, h = threadIdx.x & 1;
       double2 acc = make_double2(0, 0);
       if (l < m)
+#pragma unroll 1
         for (int k = h; k < n; k += 2) acc = acc + cmul_conj_a(S.A[k][l], S.y[k]);
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
@@ -969,25 +1017,12 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       __syncthreads();
     }
     FL_MARK(10);
-    // U~ = U~0 + gamma (F + B): T_nu's geometric kernel as a forward recurrence
-    // F_l = q F_{l-1} + V~_l and a backward one B_l = q (B_{l+1} + V~_{l+1}), each an
-    // inclusive scan over the planes (warp 0: F, warp 1: B in reversed order)
-    if (threadIdx.x < 64) {
-      const double2 qz = S.qz;
-      if (threadIdx.x < 32) {
-        affine_scan64(S.u.q.Vt, m, qz, S.u.q.F);
-      } else {
-        const int r = threadIdx.x - 32;  // reversed sequence s'_r = q V~_{m-r} (s'_0 = 0)
-        for (int rr = r; rr < m; rr += 32) S.u.q.t[rr] = rr == 0 ? make_double2(0, 0) : qz * S.u.q.Vt[m - rr];
-        __syncwarp();
-        affine_scan64(S.u.q.t, m, qz, S.u.q.z64);
-        __syncwarp();
-        for (int rr = r; rr < m; rr += 32) S.u.q.Bk[m - 1 - rr] = S.u.q.z64[rr];
-      }
-    }
+    // U~ = U~0 + gamma (F + B), eq. (9)
+    eq9_scans(m);
     __syncthreads();
     FL_MARK(11);
     cx<B>* out = prof + ((long long)om * N2 + i) * 2 * m;
+#pragma unroll 1
     for (int l = threadIdx.x; l < m; l += ST) {
       double2 u = gamma * (S.u.q.F[l] + S.u.q.Bk[l]);
       if (nu == 0) {
