@@ -7,7 +7,10 @@
 // stage reads all butterfly inputs into registers, synchronises, and writes the
 // outputs back in place, so one buffer per tile suffices.
 //
-// Radices: 3 (once per factor 3), then 4, then a final 2.  For stage s with radix
+// Radices: 3 (once per factor 3), then the cap MAXR (16, 8 or 4) for as many powers of
+// two as it covers, then one stage of 8, 4 or 2 for the rest: few stages, so few
+// passes of the tile through shared memory.  The cap is set per kernel (measured):
+// a large radix leaves threads idle when a tile has few butterflies.  For stage s with radix
 // R and Ns = product of the earlier radices, butterfly j of a line reads elements
 // j + r N/R, multiplies by w^(r (j mod Ns) N/(Ns R)) (w = exp(-2 pi i/N), conjugated
 // for the inverse), applies the R-point DFT and writes element
@@ -22,15 +25,31 @@ namespace fl {
 __host__ __device__ constexpr int count_factor(int n, int f) { return (n % f == 0) ? 1 + count_factor(n / f, f) : 0; }
 __host__ __device__ constexpr int strip(int n, int f) { return (n % f == 0) ? strip(n / f, f) : n; }
 
-template <int N> struct FftPlan {
+__host__ __device__ constexpr int log2i(int n) { return n > 1 ? 1 + log2i(n / 2) : 0; }
+
+// MAXR (4, 8 or 16) caps the power-of-two radix
+template <int N, int MAXR> struct FftPlan {
+  static_assert(MAXR == 4 || MAXR == 8 || MAXR == 16, "radix cap 4, 8 or 16");
   static constexpr int n3 = count_factor(N, 3);
   static constexpr int p2 = count_factor(N, 2);
-  static constexpr int n4 = p2 / 2;
-  static constexpr int n2 = p2 % 2;
-  static constexpr int stages = n3 + n4 + n2;
+  static constexpr int q = log2i(MAXR);
+  static constexpr int nbig = p2 / q;
+  static constexpr int rest = 1 << (p2 % q);  // 1 (no further stage), 2, 4 or 8
+  static constexpr int stages = n3 + nbig + (rest > 1 ? 1 : 0);
   static_assert(strip(strip(N, 2), 3) == 1, "N must be 2^a 3^b");
-  __host__ __device__ static constexpr int radix(int s) { return s < n3 ? 3 : (s < n3 + n4 ? 4 : 2); }
+  __host__ __device__ static constexpr int radix(int s) { return s < n3 ? 3 : (s < n3 + nbig ? MAXR : rest); }
 };
+
+// cos and sin of 2 pi e / 16
+__host__ __device__ constexpr double cos16(int e) {
+  return (e & 15) == 0 ? 1.0 : (e & 15) == 1 ? 0.92387953251128674 : (e & 15) == 2 ? 0.70710678118654752
+       : (e & 15) == 3 ? 0.38268343236508977 : (e & 15) == 4 ? 0.0 : (e & 15) == 5 ? -0.38268343236508977
+       : (e & 15) == 6 ? -0.70710678118654752 : (e & 15) == 7 ? -0.92387953251128674 : (e & 15) == 8 ? -1.0
+       : (e & 15) == 9 ? -0.92387953251128674 : (e & 15) == 10 ? -0.70710678118654752
+       : (e & 15) == 11 ? -0.38268343236508977 : (e & 15) == 12 ? 0.0 : (e & 15) == 13 ? 0.38268343236508977
+       : (e & 15) == 14 ? 0.70710678118654752 : 0.92387953251128674;
+}
+__host__ __device__ constexpr double sin16(int e) { return cos16(e + 12); }  // sin x = cos(x - pi/2)
 
 // Line layouts inside a shared-memory tile.
 //  ROW:  line b occupies [b*(N+PAD), b*(N+PAD)+N)      (rows of a plane)
@@ -59,6 +78,46 @@ template <typename R, bool INV> struct Dft {
     C s13 = v[1] + v[3], d13 = rot90<INV>(v[1] - v[3]);
     v[0] = s02 + s13; v[2] = s02 - s13;
     v[1] = d02 + d13; v[3] = d02 - d13;
+  }
+  // x w16^e, w16 = exp(-2 pi i/16) (conjugated for the inverse); e is a constant
+  __device__ __forceinline__ static C tw16(C x, int e) {
+    const R c = R(cos16(e)), sn = INV ? R(sin16(e)) : -R(sin16(e));
+    return mk<R>(x.x * c - x.y * sn, x.x * sn + x.y * c);
+  }
+  // 8 points: 4-point DFTs of the even and odd inputs, X[k] = E[k] + w8^k O[k],
+  // X[k + 4] = E[k] - w8^k O[k]
+  __device__ __forceinline__ static void d8(C* v) {
+    C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    d4(e);
+    d4(o);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const C t = tw16(o[k], 2 * k);
+      v[k] = e[k] + t;
+      v[k + 4] = e[k] - t;
+    }
+  }
+  // 16 points as 4 x 4: with n = 4 n1 + n2 and k = k1 + 4 k2, 4-point DFTs over n1,
+  // twiddles w16^(n2 k1), then 4-point DFTs over n2
+  __device__ __forceinline__ static void d16(C* v) {
+    C y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      y[n2][0] = v[n2];
+      y[n2][1] = v[n2 + 4];
+      y[n2][2] = v[n2 + 8];
+      y[n2][3] = v[n2 + 12];
+      d4(y[n2]);
+#pragma unroll
+      for (int k1 = 1; k1 < 4; ++k1) y[n2][k1] = tw16(y[n2][k1], n2 * k1);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      C z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+      d4(z);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = z[k2];
+    }
   }
   __device__ __forceinline__ static void d3(C* v) {
     // y1,2 = a0 - (a1+a2)/2 -/+ i (sqrt(3)/2)(a1 - a2)  (forward; signs swap for the inverse)
@@ -97,8 +156,10 @@ __device__ __forceinline__ void fft_stage(cx<R>* buf, const cx<R>* tw) {
         }
         v[p][r] = x;
       }
-      if (RAD == 2) Dft<R, INV>::d2(v[p]);
-      else if (RAD == 4) Dft<R, INV>::d4(v[p]);
+      if constexpr (RAD == 2) Dft<R, INV>::d2(v[p]);
+      else if constexpr (RAD == 4) Dft<R, INV>::d4(v[p]);
+      else if constexpr (RAD == 8) Dft<R, INV>::d8(v[p]);
+      else if constexpr (RAD == 16) Dft<R, INV>::d16(v[p]);
       else Dft<R, INV>::d3(v[p]);
       out_b[p] = b;
       out_i[p] = (j / NS) * NS * RAD + k;
@@ -117,13 +178,13 @@ __device__ __forceinline__ void fft_stage(cx<R>* buf, const cx<R>* tw) {
 }
 
 // stage S of the plan, with NS = product of the earlier radices (compile-time)
-template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int PAD, int S, int NS>
+template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int PAD, int MAXR, int S, int NS>
 struct FftStages {
   __device__ __forceinline__ static void run(cx<R>* buf, const cx<R>* tw) {
-    if constexpr (S < FftPlan<N>::stages) {
-      constexpr int RAD = FftPlan<N>::radix(S);
+    if constexpr (S < FftPlan<N, MAXR>::stages) {
+      constexpr int RAD = FftPlan<N, MAXR>::radix(S);
       fft_stage<R, N, INV, LINES, THREADS, L, PAD, RAD, NS>(buf, tw);
-      FftStages<R, N, INV, LINES, THREADS, L, PAD, S + 1, NS * RAD>::run(buf, tw);
+      FftStages<R, N, INV, LINES, THREADS, L, PAD, MAXR, S + 1, NS * RAD>::run(buf, tw);
     }
   }
 };
@@ -131,9 +192,9 @@ struct FftStages {
 // Transform all LINES lines of the tile in place.  `tw` holds w^j, j < N
 // (w = exp(-2 pi i/N)), in shared or global memory.  Must be called by all
 // THREADS threads of the block; contains __syncthreads().
-template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int PAD = 0>
+template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int MAXR, int PAD = 0>
 __device__ __forceinline__ void fft_lines(cx<R>* buf, const cx<R>* tw) {
-  FftStages<R, N, INV, LINES, THREADS, L, PAD, 0, 1>::run(buf, tw);
+  FftStages<R, N, INV, LINES, THREADS, L, PAD, MAXR, 0, 1>::run(buf, tw);
 }
 
 }  // namespace fl

@@ -25,6 +25,8 @@ template <> struct Cfg<double> { static constexpr int TC = 8; };
 template <> struct Cfg<float> { static constexpr int TC = 16; };
 
 constexpr int THREADS = 256;
+// radix caps of the passes (FftPlan), measured on the 128^2 workload
+constexpr int RADIX_ROWS = 16, RADIX_COLS = 16, RADIX_GATHER = 16, RADIX_RECOVER = 8;
 constexpr int TILE_ELEMS = 2048;  // elements of one shared-memory tile
 
 template <int N> __host__ __device__ constexpr int row_lines() { return TILE_ELEMS / N > 0 ? TILE_ELEMS / N : 1; }
@@ -51,7 +53,7 @@ k_fft_rows(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, long long nrow
   for (int e = threadIdx.x; e < LINES * N; e += THREADS)
     buf[e] = (base + e < limit) ? in[base + e] : czero<R>();
   __syncthreads();
-  fft_lines<R, N, INV, LINES, THREADS, Lay::ROW>(buf, tw_s);
+  fft_lines<R, N, INV, LINES, THREADS, Lay::ROW, RADIX_ROWS>(buf, tw_s);
   for (int e = threadIdx.x; e < LINES * N; e += THREADS)
     if (base + e < limit) out[base + e] = INV ? scale * buf[e] : buf[e];
 }
@@ -74,7 +76,7 @@ k_fft_cols(cx<R>* __restrict__ data, const cx<R>* __restrict__ tw) {
     buf[e] = (c0 + b < N) ? pl[(long long)i * N + c0 + b] : czero<R>();
   }
   __syncthreads();
-  fft_lines<R, N, INV, TC, THREADS, Lay::COL>(buf, tw_s);
+  fft_lines<R, N, INV, TC, THREADS, Lay::COL, RADIX_COLS>(buf, tw_s);
   for (int e = threadIdx.x; e < E; e += THREADS) {
     const int i = e / TC, b = e % TC;
     if (c0 + b < N) pl[(long long)i * N + c0 + b] = buf[e];
@@ -170,7 +172,7 @@ k_ifft_cols_gather(Problem P, const cx<R>* __restrict__ prof, const int* __restr
     }
   }
   __syncthreads();
-  fft_lines<R, N, true, TC, THREADS, Lay::COL>(buf, tw_s);
+  fft_lines<R, N, true, TC, THREADS, Lay::COL, RADIX_GATHER>(buf, tw_s);
   const long long ob = (((long long)om * 2 + f) * M + l) * N2;
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
@@ -237,7 +239,7 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
       }
     }
     __syncthreads();
-    fft_lines<R, N, true, 2 * LINES, THREADS, Lay::ROW>(buf, tw_s);
+    fft_lines<R, N, true, 2 * LINES, THREADS, Lay::ROW, RADIX_RECOVER>(buf, tw_s);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const int e = threadIdx.x + p * THREADS;

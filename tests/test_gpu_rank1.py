@@ -3,7 +3,15 @@ the truncated-SVD regulariser, through the C ABI, against the FP64 oracle (SVD p
 mode, bisection for the discrepancy root).  Same tolerances as the dense form:
 xi rel. L2 <= 1e-10 (FS_FP64), <= 1e-5 (FS_MIXED); identical active sets; alpha per
 mode <= 1e-7 (FP64).  The closed form and the dense form on the GPU agree to
-rounding (<= 1e-12)."""
+rounding (<= 1e-12).
+
+TSVD in FS_MIXED gets its own bound.  Truncation at rank one is the pseudo-inverse:
+nothing damps a mode, so the FP32 rounding of the forward transform, an absolute
+error of about u32 sqrt(log2 N) ||W|| / N per mode (u32 = 6e-8), enters each active
+mode relative to its own data, which the discrepancy test only bounds below by
+delta_nu = tau delta ||W|| / N.  The relative error of a mode is then up to
+u32 sqrt(log2 N) / (tau delta) = 8e-6 at N = 192, tau = 2, delta = 0.01; with a
+factor 3 for the constants of the transform's error, 3e-5."""
 import numpy as np
 import pytest
 
@@ -13,6 +21,7 @@ from oracle.metrics import rel_l2
 pytestmark = pytest.mark.gpu
 
 NAMES = ["c1", "r8", "r12", "r24", "r48", "r96", "r192", "r256"]
+TOL_TSVD_MIXED = 3e-5
 
 
 @pytest.fixture(scope="module")
@@ -76,7 +85,7 @@ def test_tsvd_matches_oracle(rc, name, precision):
     assert np.all(alpha[act] == 0.0)
     err = rel_l2(xi, ref.xi)
     print(f"tsvd {name} {precision}: xi {err:.2e}")
-    assert err <= (1e-10 if precision == "fp64" else 1e-5)
+    assert err <= (1e-10 if precision == "fp64" else TOL_TSVD_MIXED)
 
 
 def test_given_alpha_rank1(rc):
