@@ -51,6 +51,29 @@ __device__ __forceinline__ double rsqrt64(double x) {
   return __longlong_as_double(yb - ((long long)h << 52));
 }
 
+// 1/sqrt(x) and 1/x of a positive normal double to FP32 accuracy (~2e-7 relative)
+// at any exponent: the FP32 reciprocal (square root) of the mantissa, the exponent on
+// the bit pattern.  No FP64 arithmetic.
+__device__ __forceinline__ double rsqrt32(double x) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  if (ex == 0 || ex == 0x7ff || bits < 0) return 1.0 / sqrt(x);  // zero, subnormal, inf, nan, negative
+  const int e = ex - 1023, h = e >> 1;  // x = m 2^(2h), m in [1, 4)
+  const double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | ((long long)(1023 + e - 2 * h) << 52));
+  const double y = (double)rsqrtf((float)m);
+  return __longlong_as_double(__double_as_longlong(y) - ((long long)h << 52));
+}
+__device__ __forceinline__ double rcp32(double x) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  if (ex == 0 || ex == 0x7ff) return 1.0 / x;  // zero, subnormal, inf, nan
+  const double m = __longlong_as_double((bits & ~(0x7ffLL << 52)) | (1023LL << 52));  // [1,2), sign kept
+  const long long yb = __double_as_longlong((double)(1.0f / (float)m));
+  const int ey = (int)((yb >> 52) & 0x7ff) - (ex - 1023);
+  if (ey <= 0 || ey >= 0x7ff) return 1.0 / x;
+  return __longlong_as_double((yb & ~(0x7ffLL << 52)) | ((long long)ey << 52));
+}
+
 // exp(i kz d) inlined: for small kernels that evaluate several independent
 // exponentials per thread, so that their FP64 chains can overlap
 __device__ __forceinline__ double2 exp_ikz_inline(double2 kz, double d) {

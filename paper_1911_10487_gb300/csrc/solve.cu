@@ -346,7 +346,6 @@ struct Shared {
   float2 c32[MAX_M1], r32[MAX_M1];
   ffc yh[MAX_M1], bh[MAX_M1], th[MAX_M], Ef[MAX_M1], Pf[MAX_M];  // two-float (mixed route)
   double tr, sb, inv_sb, dnu, lo, hi, a_s, red[8];  // a_s = alpha / tr
-  double3 red3[8];
   double2 qz;  // exp(i k_z h_z)
   int fp64, tflag, kd, go;  // kd: dimension of the Lanczos model; go: Lanczos continues
 };
@@ -514,22 +513,6 @@ __device__ double phi2(const T* d, const T* e, const cx<T>* c, int n, double a, 
 }
 
 // block-wide sums of one double per thread (all threads get them)
-__device__ double3 block_sum3(Shared& S, double3 v) {
-  v.x = warp_sum(v.x);
-  v.y = warp_sum(v.y);
-  v.z = warp_sum(v.z);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) S.red3[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double3 t = make_double3(0.0, 0.0, 0.0);
-#pragma unroll
-  for (int w = 0; w < SW; ++w) {
-    t.x += S.red3[w].x;
-    t.y += S.red3[w].y;
-    t.z += S.red3[w].z;
-  }
-  return t;
-}
 
 // FP64 route: FP64 Lanczos model of the normal matrix, FP32-seeded root on the
 // scaled tridiagonal, FP64 Newton to full accuracy, y = (||b||/tr) Q (T/tr + a I)^-1 e_1.
@@ -813,6 +796,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     if (threadIdx.x < m) {
       const int l = threadIdx.x;
       S.Pz[l] = MIXED ? exp_ikz32(kz, ztop - (P.z1 + (l + 0.5) * P.hz)) : exp_ikz(kz, ztop - (P.z1 + (l + 0.5) * P.hz));
+      if (MIXED) S.Pf[l] = ffc_from(S.Pz[l]);
     } else if (threadIdx.x >= MAX_M && threadIdx.x < MAX_M + n) {
       const int k = threadIdx.x - MAX_M;
       S.b[k] = to_d(wt[((long long)om * n + k) * N2 + nu]);
@@ -821,15 +805,58 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       S.qz = exp_ikz(kz, P.hz);
     }
     __syncthreads();
-    // ||A||_F^2 = tr(G) = (sum_k |E_k|^2)(sum_l |P_l|^2) since A_kl = E_k P_l; ||b||^2
     FL_MARK(1);
-    // (in FP64 in both routes: |E|^2 and |P|^2 of strongly evanescent modes leave
-    // the FP32 range)
-    const double3 sums = block_sum3(S, make_double3(threadIdx.x < n ? abs2(S.E[threadIdx.x]) : 0.0,
-                                                    threadIdx.x < m ? abs2(S.Pz[threadIdx.x]) : 0.0,
-                                                    threadIdx.x < n ? abs2(S.b[threadIdx.x]) : 0.0));
-    const double tr = sums.x * sums.y, bb = sums.z;
-    const double dnu0 = dnu_arr[om];
+    // ||A||_F^2 = tr(G) = (sum_k |E_k|^2)(sum_l |P_l|^2) since A_kl = E_k P_l, and ||b||^2, in
+    // FP64 in both routes (|E|^2 and |P|^2 of strongly evanescent modes leave the FP32
+    // range), one sum per warp: a warp issues its FP64 instructions one per 64 cycles,
+    // so the FP64 work of a mode is spread over the warps
+    {
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      double v = 0.0;
+      if (wid == 0) v = (lane < m ? abs2(S.Pz[lane]) : 0.0) + (lane + 32 < m ? abs2(S.Pz[lane + 32]) : 0.0);
+      else if (wid == 1) v = lane < n ? abs2(S.b[lane]) : 0.0;
+      else if (wid == 2) v = lane < n ? abs2(S.E[lane]) : 0.0;
+      if (wid < 3) {
+        v = warp_sum(v);
+        if (lane == 0) S.red[wid] = v;
+      }
+    }
+    __syncthreads();
+    {
+      // the scalars of the mode, and in the mixed route the scaled factors of A and b in
+      // two-float (warp 0: E, warp 1: b, warp 3: the root bracket)
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      const double tr = S.red[0] * S.red[2], bb = S.red[1];
+      // 1/||b||: FP32 seed and one FP64 Newton step in the mixed route (||bh|| = 1 to
+      // FP64), the full FP64 reciprocal square root otherwise
+      const auto inv_norm_b = [&]() {
+        if (!MIXED) return rsqrt64(bb);
+        const double y = rsqrt32(bb);
+        return fma(0.5 * y, fma(-bb * y, y, 1.0), y);
+      };
+      if (MIXED && wid == 0 && lane < n) {
+        // the scale factor need only be used consistently: FP32-accurate 1/sqrt(tr)
+        S.Ef[lane] = ffc_from(rsqrt32(tr) * S.E[lane]);
+      } else if (wid == 1) {
+        const double ib = inv_norm_b();
+        if (MIXED && lane < n) S.bh[lane] = ffc_from(ib * S.b[lane]);
+        if (lane == 0) {
+          S.inv_sb = ib;
+          S.sb = bb * ib;
+          S.tr = tr;
+          S.dnu = dnu_arr[om];
+          S.fp64 = MIXED ? 0 : 1;
+        }
+      } else if (wid == 3 && lane == 0) {
+        const double dnu = dnu_arr[om], sb = bb * inv_norm_b();
+        S.lo = P.alpha_rel * tr;
+        // the root's upper bracket: FP32 accuracy is enough in the mixed route
+        S.hi = fmax(tr * dnu * (MIXED ? rcp32(sb - dnu) : rcp64(sb - dnu)), S.lo);
+      }
+    }
+    __syncthreads();
+    const double tr = S.tr, bb = S.red[1];
+    const double dnu0 = S.dnu;
     // A_nu underflowed to zero (the mode carries no information), or, under the
     // discrepancy rule, ||b|| recomputed here does not exceed delta_nu after all (a
     // rounding tie at the threshold of the classification): V~ = 0
@@ -854,33 +881,21 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       __syncthreads();
       continue;
     }
-    if (threadIdx.x == 0) {
-      S.tr = tr;
-      S.inv_sb = rsqrt64(bb);
-      S.sb = bb * S.inv_sb;
-      S.dnu = dnu_arr[om];
-      S.lo = P.alpha_rel * tr;
-      S.hi = fmax(tr * S.dnu * rcp64(S.sb - S.dnu), S.lo);
-      S.fp64 = MIXED ? 0 : 1;
-    }
-    __syncthreads();
     if (MIXED) {
-      // scaled problem Ah = A / sqrt(tr) (||Ah||_F = 1), bh = b / ||b||, a = alpha / tr:
-      // Ah in two-float (for the residual and V~) and its FP32 part (for the model)
+      // scaled problem Ah = A / sqrt(tr) (||Ah||_F ~ 1), bh = b / ||b||, a = alpha / tr:
+      // Ah in two-float (for the residual and V~) and its FP32 part (for the model);
+      // thread t builds column t mod 64, rows t / 64, t / 64 + 2, ...
       ffc (*Af)[MAX_M + 1] = reinterpret_cast<ffc (*)[MAX_M + 1]>(S.A);
-      const double sa = rsqrt64(tr);
-      if (threadIdx.x < n) {
-        S.Ef[threadIdx.x] = ffc_from(sa * S.E[threadIdx.x]);
-        S.bh[threadIdx.x] = ffc_from(S.inv_sb * S.b[threadIdx.x]);
-      }
-      if (threadIdx.x < m) S.Pf[threadIdx.x] = ffc_from(S.Pz[threadIdx.x]);
-      __syncthreads();
+      const double sa = rsqrt32(tr);
+      const int l = threadIdx.x & (MAX_M - 1);
+      if (l < m) {
+        const ffc pl = S.Pf[l];
 #pragma unroll 1
-      for (int e = threadIdx.x; e < n * m; e += ST) {
-        const int k = e / m, l = e - k * m;
-        const ffc a = ffc_mul(S.Ef[k], S.Pf[l]);
-        Af[k][l] = a;
-        S.u.f.m.A[k][l] = make_float2(a.re.hi, a.im.hi);
+        for (int k = threadIdx.x / MAX_M; k < n; k += ST / MAX_M) {
+          const ffc a = ffc_mul(S.Ef[k], pl);
+          Af[k][l] = a;
+          S.u.f.m.A[k][l] = make_float2(a.re.hi, a.im.hi);
+        }
       }
       __syncthreads();
       FL_MARK(2);
