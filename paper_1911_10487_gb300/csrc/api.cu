@@ -190,6 +190,7 @@ Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, dou
     P.graz_lo[j] = lo > 1e9 ? 1000000001 : (int)lo;  // |m|^2 <= 2 (N/2)^2 never reaches 1e9
     P.graz_hi[j] = hi > 1e9 ? 1000000000 : (int)hi;
   }
+  derive_constants(P);
   return P;
 }
 

@@ -38,7 +38,20 @@ struct Problem {
   // grazing modes |nu| = k0: integer window [graz_lo, graz_hi] of m1^2 + m2^2, the
   // integers within a relative 1e-9 of (k0 L / 2 pi)^2 (empty when lo > hi)
   int graz_lo[MAX_OMEGA], graz_hi[MAX_OMEGA];
+  // derived on the host (derive_constants), so that the per-mode kernels spend no
+  // FP64 division on them: k0 = omega/c0, g0 = omega^2 h_z / 2, kn = 2 pi / L
+  double k0[MAX_OMEGA], g0[MAX_OMEGA];
+  double kn;
 };
+
+inline void derive_constants(Problem& P) {
+  P.kn = 2.0 * M_PI / P.period;
+  for (int j = 0; j < P.n_omega; ++j) {
+    const double om2 = P.omega[j] * P.omega[j];
+    P.k0[j] = P.omega[j] / P.c0;
+    P.g0[j] = 0.5 * om2 * P.hz;
+  }
+}
 
 // Workspace views (device pointers).  R = bulk real type (double / float).
 template <typename R> struct Work {

@@ -778,16 +778,14 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
 #endif
     const int i2 = nu / N, i1 = nu - i2 * N;
     const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
-    const double k0 = P.omega[om] / P.c0;
-    const double om2 = P.omega[om] * P.omega[om];
-    const double kn = 2.0 * M_PI / P.period;
+    const double k0 = P.k0[om], kn = P.kn;
     const double q = k0 * k0 - kn * kn * (double)(m1 * m1 + m2 * m2);
     // k_z = sqrt(|q|) (real, or i sqrt(|q|) for an evanescent mode; active modes are
     // never grazing, q != 0) and 1/k_z from one reciprocal square root
     const double rq = rsqrt64(fabs(q));
     const double2 kz = q >= 0.0 ? make_double2(fabs(q) * rq, 0.0) : make_double2(0.0, fabs(q) * rq);
     // gamma = omega^2 h_z (-i / (2 k_z))
-    const double g0 = 0.5 * om2 * P.hz;
+    const double g0 = P.g0[om];
     const double2 gamma = q >= 0.0 ? make_double2(0.0, -g0 * rq) : make_double2(-g0 * rq, 0.0);
     const double ztop = P.z1 + (m - 0.5) * P.hz;
     // the exponentials, one per thread: threads 0..63 take P, threads 64..95 take E
@@ -1037,16 +1035,23 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     __syncthreads();
     FL_MARK(11);
     cx<B>* out = prof + ((long long)om * N2 + i) * 2 * m;
-#pragma unroll 1
-    for (int l = threadIdx.x; l < m; l += ST) {
-      double2 u = gamma * (S.u.q.F[l] + S.u.q.Bk[l]);
-      if (nu == 0) {
-        double s, c;
-        sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s, &c);
-        u = u + make_double2((double)N2 * c, (double)N2 * s);
+    {  // V~ by threads l < 64, U~ by threads 64 + l (its FP64 arithmetic on warps 2 and 3)
+      const int l = threadIdx.x & (MAX_M - 1);
+      if (l < m) {
+        if (threadIdx.x < MAX_M) {
+          out[l] = from_d<B>(S.u.q.Vt[l]);
+        } else {
+          const double2 f = S.u.q.F[l] + S.u.q.Bk[l];
+          // gamma is imaginary (propagating mode) or real (evanescent)
+          double2 u = q >= 0.0 ? make_double2(-gamma.y * f.y, gamma.y * f.x) : make_double2(gamma.x * f.x, gamma.x * f.y);
+          if (nu == 0) {
+            double s, c;
+            sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s, &c);
+            u = u + make_double2((double)N2 * c, (double)N2 * s);
+          }
+          out[m + l] = from_d<B>(u);
+        }
       }
-      out[l] = from_d<B>(S.u.q.Vt[l]);
-      out[m + l] = from_d<B>(u);
     }
     if (threadIdx.x == 0 && alpha_out) alpha_out[om * N2 + nu] = S.a_s * S.tr;
     __syncthreads();

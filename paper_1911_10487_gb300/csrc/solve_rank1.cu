@@ -57,12 +57,11 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const int* __restrict__ a
     const int nu = act[om * N2 + i];
     const int i2 = nu / N, i1 = nu - i2 * N;
     const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
-    const double k0 = P.omega[om] / P.c0;
-    const double kn = 2.0 * M_PI / P.period;
+    const double k0 = P.k0[om], kn = P.kn;
     const double q = k0 * k0 - kn * kn * (double)(m1 * m1 + m2 * m2);
     const double rq = rsqrt64(fabs(q));  // active modes are never grazing: q != 0
     const double2 kz = q >= 0.0 ? make_double2(fabs(q) * rq, 0.0) : make_double2(0.0, fabs(q) * rq);
-    const double g0 = 0.5 * P.omega[om] * P.omega[om] * P.hz;
+    const double g0 = P.g0[om];
     const double2 gamma = q >= 0.0 ? make_double2(0.0, -g0 * rq) : make_double2(-g0 * rq, 0.0);
     const double ztop = P.z1 + (m - 0.5) * P.hz;
     // E_k and b_k on lane k; P_l on lanes l and l - 32

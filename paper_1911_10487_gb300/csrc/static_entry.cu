@@ -139,6 +139,7 @@ extern "C" fs_status fs_reconstruct_static(const fs_geometry* g, fs_precision pr
     P.graz_lo[j] = lo > 1e9 ? 1000000001 : (int)lo;
     P.graz_hi[j] = hi > 1e9 ? 1000000000 : (int)hi;
   }
+  derive_constants(P);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FS_ECUDA;
   unsigned char* base = nullptr;
