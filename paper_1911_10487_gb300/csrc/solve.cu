@@ -226,8 +226,11 @@ k_classify_scatter(Problem P, const unsigned* __restrict__ flagbits, const int* 
     for (int o = 16; o > 0; o >>= 1) gz += __shfl_xor_sync(0xffffffffu, gz, o);
     int base = 0;
     for (int j0 = 0; j0 < N; j0 += 32) {
+      // OR of the blocks' column masks: lane i loads block i's (the loads in flight
+      // together), then a warp reduction
       unsigned cmw = 0u;
-      for (int i = 0; i < CB; ++i) cmw |= colblk[((long long)om * CB + i) * NWC + (j0 >> 5)];
+      for (int i = lane; i < CB; i += 32) cmw |= colblk[((long long)om * CB + i) * NWC + (j0 >> 5)];
+      cmw = __reduce_or_sync(0xffffffffu, cmw);
       if (j0 == 0) cmw |= 1u;  // the incident plane wave lives at nu = 0
       const int j = j0 + lane;
       const bool f = j < N && (cmw >> lane & 1u);
