@@ -54,7 +54,8 @@ typedef enum {
   FS_EINVAL = 1,      /* invalid argument (shape, range, null pointer)           */
   FS_ENOMEM = 2,      /* device or pinned allocation failed                      */
   FS_ECUDA = 3,       /* a CUDA call failed; see fs_last_error                   */
-  FS_EUNSUPPORTED = 4 /* size outside the compiled limits (see below)            */
+  FS_EUNSUPPORTED = 4, /* size outside the compiled limits (see below)           */
+  FS_ENOCONV = 5       /* fs_forward: the fixed point did not converge            */
 } fs_status;
 
 typedef enum {
@@ -203,6 +204,29 @@ fs_status fs_reconstruct_batch(fs_ctx* ctx, const fs_problem* probs, int n_probs
    Uses the context workspace; asynchronous. */
 fs_status fs_forward_born(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* xi,
                           const double* omega, int n_omega, double c0, void* W);
+
+/* Forward data generator with full scattering: Algorithm 1 of Sec. 3, the fixed
+   point of eq. (6) on the mode coefficients of the field in X,
+     U~_{n+1} = U~0 + omega^2 T_nu F_r[xi F^-1 U~_n],  T_nu[l, l'] = h_z K_nu(z'_l - z'_l'),
+   from U~_1 = U~0 (the plane wave u0 = exp(-i k0 z)), stopped at the first n with
+   ||U~_{n+1} - U~_n|| <= rtol ||U~0|| (Frobenius norms over the M planes of one
+   frequency; the paper's stopping rule of Sec. 5.1 with rtol = 1e-13), then the data
+   of eq. (7) from the converged field.  Each frequency iterates on its own.
+     xi        device, [M][N][N] real (float64 for FS_FP64, float32 for FS_MIXED).
+     omega     host, n_omega values > 0.
+     max_iter  >= 0; 0 gives the single-scattering data of fs_forward_born.
+     rtol      > 0; FP32 rounding bounds it below near 1e-6 in FS_MIXED.
+     W         device, [n_omega][M1][N][N] complex, written.
+     u         device, [n_omega][M][N][N] complex (the total field on X), written; or NULL.
+     iterations host, n_omega ints (the iterations each frequency took), or NULL.
+   Returns FS_ENOCONV, with W and u of the remaining frequencies unwritten, when a
+   frequency has not converged after max_iter iterations or its iteration grows past
+   1e30 ||U~0|| (a scatterer too strong for the fixed point: omega^2 ||T xi|| >= 1).
+   Uses the context workspace; synchronises the context's stream once per iteration
+   (the stopping test is taken on the host), so it cannot be captured in a graph. */
+fs_status fs_forward(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* xi,
+                     const double* omega, int n_omega, double c0, int max_iter, double rtol, void* W, void* u,
+                     int* iterations);
 
 /* Size of the device array that holds every intermediate of fs_reconstruct_static. */
 #define FS_STATIC_SCRATCH_BYTES (32u << 20)

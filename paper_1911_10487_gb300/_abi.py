@@ -12,13 +12,13 @@ import os
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libflatlayer.so")
 _lib = None
 
-FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED = 0, 1, 2, 3, 4
+FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED, FS_ENOCONV = 0, 1, 2, 3, 4, 5
 FS_FP64, FS_MIXED = 0, 1
-STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_EUNSUPPORTED"}
+STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_EUNSUPPORTED", 5: "FS_ENOCONV"}
 
 # every function declared in include/*.h
 EXPORTS = ("fs_version", "fs_default_options", "fs_create", "fs_destroy", "fs_last_error",
-           "fs_workspace_size", "fs_reconstruct", "fs_reconstruct_host", "fs_forward_born",
+           "fs_workspace_size", "fs_reconstruct", "fs_reconstruct_host", "fs_forward_born", "fs_forward",
            "fs_get_report", "fs_measure_alu_peaks", "fs_reconstruct_static", "fs_reconstruct_batch",
            "fs_diff_plan_create", "fs_diff_plan_destroy", "fs_diff_tape_bytes", "fs_diff_scratch_bytes",
            "fs_reconstruct_diff", "fs_reconstruct_vjp", "fs_reconstruct_jvp")
@@ -101,6 +101,9 @@ def lib():
                                           C.POINTER(fs_options), vp, vp]
         L.fs_forward_born.restype = ip
         L.fs_forward_born.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, vp]
+        L.fs_forward.restype = ip
+        L.fs_forward.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, ip, C.c_double, vp, vp,
+                                 C.POINTER(C.c_int)]
         L.fs_reconstruct_batch.restype = ip
         L.fs_reconstruct_batch.argtypes = [vp, C.POINTER(fs_problem), ip, ip, C.POINTER(fs_options), ip]
         L.fs_reconstruct_static.restype = ip
@@ -192,6 +195,16 @@ def fs_forward_born(ctx, geom, prec, xi_ptr, omega, c0, W_ptr):
     st = lib().fs_forward_born(ctx, C.byref(geom), int(prec), C.c_void_p(xi_ptr), om, len(omega),
                                float(c0), C.c_void_p(W_ptr))
     _check(ctx, st, "fs_forward_born")
+
+
+def fs_forward(ctx, geom, prec, xi_ptr, omega, c0, max_iter, rtol, W_ptr, u_ptr=None):
+    """Returns the iterations each frequency took."""
+    om = (C.c_double * len(omega))(*[float(x) for x in omega])
+    its = (C.c_int * len(omega))()
+    st = lib().fs_forward(ctx, C.byref(geom), int(prec), C.c_void_p(xi_ptr), om, len(omega), float(c0),
+                          int(max_iter), float(rtol), C.c_void_p(W_ptr), C.c_void_p(u_ptr or None), its)
+    _check(ctx, st, "fs_forward")
+    return [int(x) for x in its]
 
 
 def fs_reconstruct_batch(ctx, problems, prec, opts=None, n_streams=8):

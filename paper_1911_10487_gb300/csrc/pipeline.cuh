@@ -107,6 +107,14 @@ cudaError_t launch_fft2_dense(cx<R>* in, cx<R>* out, int n, long long planes, bo
 template <typename R>
 cudaError_t launch_forward_born(const Problem& P, const R* xi, cx<R>* src, cx<R>* W, const cx<R>* tw,
                                 cudaStream_t s);
+// Algorithm 1 (fixed point of eq. 6) per frequency, then the data of eq. (7); iters and
+// converged (host arrays of n_omega, may be null) report each frequency.  ws holds
+// forward_fixed_point_bytes(P) bytes.  Synchronises the stream once per iteration.
+template <typename R>
+size_t forward_fixed_point_bytes(const Problem& P);
+template <typename R>
+cudaError_t forward_fixed_point(const Problem& P, const R* xi, cx<R>* W, cx<R>* u_out, void* ws, double rtol,
+                                int max_iter, const cx<R>* tw, cudaStream_t s, int* iters, int* converged);
 
 bool fft_size_supported(int n);
 
