@@ -165,6 +165,22 @@ def algorithmic_bytes(stage, wl, rep, sc):
     raise KeyError(stage)
 
 
+def stage_flops(stage, wl, rep):
+    """Real flops of a stage's transforms for one launch (5 L log2 L per complex line of
+    length L); the solve's count is solve_flops; classification does no flops."""
+    F, N, M, M1 = len(wl.omegas), wl.n, wl.m, wl.m1
+    line = 5.0 * N * np.log2(N)
+    if stage in ("fft_x_forward", "fft_y_forward_norms"):
+        return F * M1 * N * line
+    if stage == "ifft_y_gather":
+        return F * 2 * M * rep["n_columns"] * line
+    if stage == "ifft_x_recover":
+        return F * 2 * M * N * line
+    if stage == "solve":
+        return solve_flops(wl, rep)
+    return 0.0
+
+
 def solve_flops(wl, rep, iters=8):
     """Algorithmic real flops of the per-mode solve for one launch: per active mode,
     kernel assembly 6 M1 M, normal matrix 4 M1^2 M, I_alpha evaluations of the
@@ -310,15 +326,34 @@ def run_ours(args, rank, world, local):
                 "h2d_bytes_per_step": int(W_h.numel() * 8), "d2h_bytes_per_step": int(xi_h.numel() * 4)},
         "clocks": ck,
     }
-    # roofline of the dominant kernel of the headline (mixed) path
+    # per-stage rooflines, both precisions: algorithmic bytes against the measured copy
+    # bandwidth and algorithmic flops against the measured FMA peak of the stage's
+    # arithmetic (FP32 in the mixed path, FP64 in the plain one).  Stage times are the
+    # library's event timers of an uncaptured run (launch gaps included)
     hbm, src = peaks()
+    from paper_1911_10487_gb300._abi import fs_measure_alu_peaks
+    alu = fs_measure_alu_peaks(local)
+    stage_roof = {}
+    for prec, sc, pk in (("mixed", 8, alu["fp32_tflops"]), ("fp64", 16, alu["fp64_tflops"])):
+        stage_roof[prec] = {}
+        for stg, ms in stage_ms[prec].items():
+            byt = algorithmic_bytes(stg, wl, reps[prec], sc)
+            fl = stage_flops(stg, wl, reps[prec])
+            gbs = byt / (ms * 1e-3) / 1e9
+            tfl = fl / (ms * 1e-3) / 1e12
+            stage_roof[prec][stg] = {"ms": ms, "bytes": byt, "gbs": gbs, "hbm_frac": gbs / hbm, "flops": fl,
+                                     "tflops": tfl, "alu_frac": tfl / pk}
+    result["stage_roofline"] = {"peaks": {"hbm_gbs": hbm, "hbm_source": src, "fp32_tflops": alu["fp32_tflops"],
+                                          "fp64_tflops": alu["fp64_tflops"],
+                                          "alu_source": "measured (fs_measure_alu_peaks)"},
+                                "note": "stage times from the library's event timers, launch gaps included",
+                                **stage_roof}
+    # roofline of the dominant kernel of the headline (mixed) path
     sm = stage_ms["mixed"]
     dom = max(sm, key=sm.get)
     if dom == "solve":
         # per-mode dense solve: bound by the plain ALUs (FP32 pipe in the mixed path);
         # peak = the library's own FP32 FMA microbenchmark on this GPU
-        from paper_1911_10487_gb300._abi import fs_measure_alu_peaks
-        alu = fs_measure_alu_peaks(local)
         flops = solve_flops(wl, reps["mixed"])
         ach = flops / (sm[dom] * 1e-3) / 1e12
         result["roofline"] = {"kernel": "solve", "bound": "alu", "achieved": ach, "peak": alu["fp32_tflops"],
@@ -333,6 +368,41 @@ def run_ours(args, rank, world, local):
                               "algorithmic_bytes": byt}
     result["counts"] = {k: v for k, v in reps["mixed"].items() if k != "ms_stage"}
     return result, rc, wl, geom, om, W64, outs
+
+
+def run_forward(rc, wl, geom, om, reps=3):
+    """Algorithm 1 (fs_forward) on the headline geometry and inclusions: the full-
+    scattering data of the same xi, both precisions.  Each call synchronises once per
+    iteration (the stopping test is on the host), so the time is host wall clock around
+    whole calls; the FP64 and mixed data are compared with each other."""
+    import torch
+    xi64 = torch.from_numpy(np.ascontiguousarray(wl.xi)).to(rc.device)
+    out = {"workload": "128x128x64 X grid, 32 data planes, k0=8pi, 3 Gaussian inclusions (the headline xi)",
+           "stopping": "||U~_{n+1} - U~_n|| <= rtol ||U~0|| (rtol 1e-13 FP64, 1e-6 mixed)"}
+    Ws = {}
+    for prec, x in (("fp64", xi64), ("mixed", xi64.float())):
+        from paper_1911_10487_gb300 import FlatLayerError
+        try:
+            rc.forward(x, om, geom, precision=prec)  # warm-up (workspace, twiddles)
+        except FlatLayerError as e:
+            out[prec] = {"not_converged": str(e)}
+            continue
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            W, _, its = rc.forward(x, om, geom, precision=prec)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        ms = 1e3 * float(np.median(ts))
+        it = int(sum(its))
+        Ws[prec] = W
+        out[prec] = {"ms": ms, "iterations": its, "ms_per_iteration": ms / max(it, 1),
+                     "voxel_freq_iterations_per_s": wl.voxel_freqs * max(it, 1) / (ms * 1e-3)}
+    if len(Ws) == 2:
+        a, b = Ws["mixed"].to(torch.complex128), Ws["fp64"]
+        out["mixed_vs_fp64_rel_l2"] = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    return out
 
 
 def run_batch(args, local, flush, world):
@@ -526,6 +596,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batch measurement")
     ap.add_argument("--no-diff", action="store_true", help="skip the derivative measurement")
+    ap.add_argument("--no-forward", action="store_true", help="skip the full-scattering forward measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_setup(args.gpus)
@@ -543,6 +614,8 @@ def main():
         import torch
         flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=rc.device)
         result["differentiation"] = run_diff(args, local, flush, world)
+    if not args.no_forward:
+        result["forward_fixed_point"] = run_forward(rc, wl, geom, om)
     if rank == 0:
         import torch
         W_np = W64.cpu().numpy()
