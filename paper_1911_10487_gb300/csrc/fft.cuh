@@ -52,13 +52,17 @@ __host__ __device__ constexpr double cos16(int e) {
 __host__ __device__ constexpr double sin16(int e) { return cos16(e + 12); }  // sin x = cos(x - pi/2)
 
 // Line layouts inside a shared-memory tile.
-//  ROW:  line b occupies [b*(N+PAD), b*(N+PAD)+N)      (rows of a plane)
+//  ROW:  element i of line b at b*(N + N/S) + i + i/S    (rows of a plane), S = SKEW:
+//        one padding element after every S keeps the stride-S writes of a radix-S
+//        stage on distinct shared-memory banks (S = 0: b*N + i, no padding)
 //  COL:  element i of line b sits at i*LINES + b         (columns of a plane tile)
 enum class Lay { ROW, COL };
 
-template <Lay L, int N, int LINES, int PAD> struct LayIdx {
-  __device__ __forceinline__ static int at(int b, int i) {
-    return (L == Lay::ROW) ? b * (N + PAD) + i : i * LINES + b;
+template <Lay L, int N, int LINES, int SKEW> struct LayIdx {
+  static constexpr int STRIDE = (L == Lay::ROW && SKEW > 0) ? N + N / SKEW : N;
+  static constexpr int ELEMS = LINES * STRIDE;  // elements of the tile, padding included
+  __host__ __device__ __forceinline__ static int at(int b, int i) {
+    return (L == Lay::ROW) ? b * STRIDE + i + (SKEW > 0 ? i / SKEW : 0) : i * LINES + b;
   }
   // thread-item -> (line, butterfly) so that neighbouring threads touch
   // neighbouring shared-memory words
@@ -129,10 +133,10 @@ template <typename R, bool INV> struct Dft {
   }
 };
 
-template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int PAD, int RAD, int NS>
+template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int SKEW, int RAD, int NS>
 __device__ __forceinline__ void fft_stage(cx<R>* buf, const cx<R>* tw) {
   using C = cx<R>;
-  using IX = LayIdx<L, N, LINES, PAD>;
+  using IX = LayIdx<L, N, LINES, SKEW>;
   constexpr int NB = N / RAD;                 // butterflies per line
   constexpr int TOTAL = LINES * NB;
   constexpr int PER = (TOTAL + THREADS - 1) / THREADS;
@@ -178,13 +182,13 @@ __device__ __forceinline__ void fft_stage(cx<R>* buf, const cx<R>* tw) {
 }
 
 // stage S of the plan, with NS = product of the earlier radices (compile-time)
-template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int PAD, int MAXR, int S, int NS>
+template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int SKEW, int MAXR, int S, int NS>
 struct FftStages {
   __device__ __forceinline__ static void run(cx<R>* buf, const cx<R>* tw) {
     if constexpr (S < FftPlan<N, MAXR>::stages) {
       constexpr int RAD = FftPlan<N, MAXR>::radix(S);
-      fft_stage<R, N, INV, LINES, THREADS, L, PAD, RAD, NS>(buf, tw);
-      FftStages<R, N, INV, LINES, THREADS, L, PAD, MAXR, S + 1, NS * RAD>::run(buf, tw);
+      fft_stage<R, N, INV, LINES, THREADS, L, SKEW, RAD, NS>(buf, tw);
+      FftStages<R, N, INV, LINES, THREADS, L, SKEW, MAXR, S + 1, NS * RAD>::run(buf, tw);
     }
   }
 };
@@ -192,9 +196,9 @@ struct FftStages {
 // Transform all LINES lines of the tile in place.  `tw` holds w^j, j < N
 // (w = exp(-2 pi i/N)), in shared or global memory.  Must be called by all
 // THREADS threads of the block; contains __syncthreads().
-template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int MAXR, int PAD = 0>
+template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int MAXR, int SKEW = 0>
 __device__ __forceinline__ void fft_lines(cx<R>* buf, const cx<R>* tw) {
-  FftStages<R, N, INV, LINES, THREADS, L, PAD, MAXR, 0, 1>::run(buf, tw);
+  FftStages<R, N, INV, LINES, THREADS, L, SKEW, MAXR, 0, 1>::run(buf, tw);
 }
 
 }  // namespace fl

@@ -27,6 +27,9 @@ template <> struct Cfg<float> { static constexpr int TC = 16; };
 constexpr int THREADS = 256;
 // radix caps of the passes (FftPlan), measured on the 128^2 workload
 constexpr int RADIX_ROWS = 16, RADIX_COLS = 16, RADIX_GATHER = 16, RADIX_RECOVER = 8;
+// row tiles padded after every SKEW elements (LayIdx): the first, radix-16 or radix-8,
+// stage of a row pass writes with that stride
+constexpr int SKEW_ROWS = 16, SKEW_RECOVER = 8;
 constexpr int TILE_ELEMS = 2048;  // elements of one shared-memory tile
 
 template <int N> __host__ __device__ constexpr int row_lines() { return TILE_ELEMS / N > 0 ? TILE_ELEMS / N : 1; }
@@ -44,18 +47,22 @@ k_fft_rows(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, long long nrow
   pdl_wait();
   pdl_trigger();
   constexpr int LINES = row_lines<N>();
-  __shared__ cx<R> buf[LINES * N];
+  using IX = LayIdx<Lay::ROW, N, LINES, SKEW_ROWS>;
+  __shared__ cx<R> buf[IX::ELEMS];
   __shared__ cx<R> tw_s[N];
   load_twiddles<R, N>(tw_s, tw);
   const long long row0 = (long long)blockIdx.x * LINES;
   const long long base = row0 * N;
   const long long limit = nrows * N;
   for (int e = threadIdx.x; e < LINES * N; e += THREADS)
-    buf[e] = (base + e < limit) ? in[base + e] : czero<R>();
+    buf[IX::at(e / N, e % N)] = (base + e < limit) ? in[base + e] : czero<R>();
   __syncthreads();
-  fft_lines<R, N, INV, LINES, THREADS, Lay::ROW, RADIX_ROWS>(buf, tw_s);
+  fft_lines<R, N, INV, LINES, THREADS, Lay::ROW, RADIX_ROWS, SKEW_ROWS>(buf, tw_s);
   for (int e = threadIdx.x; e < LINES * N; e += THREADS)
-    if (base + e < limit) out[base + e] = INV ? scale * buf[e] : buf[e];
+    if (base + e < limit) {
+      const cx<R> v = buf[IX::at(e / N, e % N)];
+      out[base + e] = INV ? scale * v : v;
+    }
 }
 
 // ---- dense pass along y (columns), in place; grid (ceil(N/TC), planes) ---------
@@ -215,6 +222,7 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
                                              cx<R>* buf, const cx<R>* tw_s, A* num, A* den) {
   constexpr int LINES = row_lines<N>() / 2 > 0 ? row_lines<N>() / 2 : 1;
   constexpr int E = LINES * N;
+  using IX = LayIdx<Lay::ROW, N, 2 * LINES, SKEW_RECOVER>;  // V~ lines, then U~ lines
   constexpr int PER = (E + THREADS - 1) / THREADS;
   const int M = P.m;
   const long long N2 = (long long)N * N;
@@ -224,7 +232,7 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
 #pragma unroll
   for (int p = 0; p < PER; ++p) { num[p] = A(0); den[p] = A(0); }
   for (int om = 0; om < P.n_omega; ++om) {
-    for (int e = threadIdx.x; e < 2 * E; e += THREADS) buf[e] = czero<R>();
+    for (int e = threadIdx.x; e < IX::ELEMS; e += THREADS) buf[e] = czero<R>();
     __syncthreads();
     const int nc = ncol[om];
     const int* cl = cols + om * N;
@@ -235,17 +243,17 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
       const long long r = row0 + b;
       if (r < nrows) {
         const long long l = r / N, i = r - l * N;
-        buf[line * N + cl[c]] = t2[(((long long)om * 2 + f) * M + l) * N2 + i * N + c];
+        buf[IX::at(line, cl[c])] = t2[(((long long)om * 2 + f) * M + l) * N2 + i * N + c];
       }
     }
     __syncthreads();
-    fft_lines<R, N, true, 2 * LINES, THREADS, Lay::ROW, RADIX_RECOVER>(buf, tw_s);
+    fft_lines<R, N, true, 2 * LINES, THREADS, Lay::ROW, RADIX_RECOVER, SKEW_RECOVER>(buf, tw_s);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const int e = threadIdx.x + p * THREADS;
       if (e < E) {
-        const cx<R> v = scale * buf[e];
-        const cx<R> u = scale * buf[E + e];
+        const cx<R> v = scale * buf[IX::at(e / N, e % N)];
+        const cx<R> u = scale * buf[IX::at(LINES + e / N, e % N)];
         num[p] += (A)u.x * (A)v.x + (A)u.y * (A)v.y;  // Re(conj(u) V)
         den[p] += (A)u.x * (A)u.x + (A)u.y * (A)u.y;  // |u|^2
       }
@@ -268,7 +276,7 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
   constexpr int LINES = row_lines<N>() / 2 > 0 ? row_lines<N>() / 2 : 1;
   constexpr int E = LINES * N;            // elements of one field
   constexpr int PER = (E + THREADS - 1) / THREADS;
-  __shared__ cx<R> buf[2 * E];
+  __shared__ cx<R> buf[LayIdx<Lay::ROW, N, 2 * LINES, SKEW_RECOVER>::ELEMS];
   __shared__ cx<R> tw_s[N];
   __shared__ unsigned red[THREADS / 32];
   load_twiddles<R, N>(tw_s, tw);
