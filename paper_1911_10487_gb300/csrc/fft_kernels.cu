@@ -295,14 +295,8 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
       den[p] = g ? R(0) : R(1);
     }
   }
-  __shared__ R consts[2];  // guard and c0^-2: one FP64 division per block, not per thread
-  if (threadIdx.x == 0) {
-    consts[0] = R(P.eps_u * P.eps_u * P.n_omega);
-    consts[1] = R(1.0 / (P.c0 * P.c0));
-  }
-  __syncthreads();
-  const R guard = consts[0];
-  const R inv_c02 = consts[1];
+  const R guard = R(P.u_guard);  // host-derived: no FP64 division on the device
+  const R inv_c02 = R(P.inv_c02);
   unsigned n_guard = 0, n_nan = 0;
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
@@ -323,12 +317,15 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
       }
     }
   }
-  const unsigned long long sg = block_sum_u64(n_guard, red);
-  __syncthreads();
-  const unsigned long long sn = block_sum_u64(n_nan, red);
-  if (threadIdx.x == 0) {
-    if (sg) atomicAdd(ctr + C_U_GUARD, sg);
-    if (sn) atomicAdd(ctr + C_NAN_C, sn);
+  // the counters of guarded and NaN voxels: almost always zero, so one barrier decides
+  if (__syncthreads_or((n_guard | n_nan) != 0u)) {
+    const unsigned long long sg = block_sum_u64(n_guard, red);
+    __syncthreads();
+    const unsigned long long sn = block_sum_u64(n_nan, red);
+    if (threadIdx.x == 0) {
+      if (sg) atomicAdd(ctr + C_U_GUARD, sg);
+      if (sn) atomicAdd(ctr + C_NAN_C, sn);
+    }
   }
 }
 

@@ -38,14 +38,17 @@ struct Problem {
   // grazing modes |nu| = k0: integer window [graz_lo, graz_hi] of m1^2 + m2^2, the
   // integers within a relative 1e-9 of (k0 L / 2 pi)^2 (empty when lo > hi)
   int graz_lo[MAX_OMEGA], graz_hi[MAX_OMEGA];
-  // derived on the host (derive_constants), so that the per-mode kernels spend no
-  // FP64 division on them: k0 = omega/c0, g0 = omega^2 h_z / 2, kn = 2 pi / L
+  // derived on the host (derive_constants), so that the kernels spend no FP64
+  // division on them: k0 = omega/c0, g0 = omega^2 h_z / 2, kn = 2 pi / L
   double k0[MAX_OMEGA], g0[MAX_OMEGA];
   double kn;
+  double inv_c02, u_guard;  // c0^-2 and the |u|^2 guard eps_u^2 n_omega of the recovery
 };
 
 inline void derive_constants(Problem& P) {
   P.kn = 2.0 * M_PI / P.period;
+  P.inv_c02 = 1.0 / (P.c0 * P.c0);
+  P.u_guard = P.eps_u * P.eps_u * P.n_omega;
   for (int j = 0; j < P.n_omega; ++j) {
     const double om2 = P.omega[j] * P.omega[j];
     P.k0[j] = P.omega[j] / P.c0;

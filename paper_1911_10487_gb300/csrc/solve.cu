@@ -72,7 +72,6 @@ namespace {
 // mode and is latency-bound, so its loops are not unrolled ("#pragma unroll 1"):
 // unrolling only multiplies the code (measured 2-5 us slower per mode).
 constexpr int ST = 128;
-constexpr int SW = ST / 32;
 // Lanczos stops when the next off-diagonal of T is at most this fraction of
 // tr(G): a few units of round-off of the normal matrix in each precision
 constexpr float LANCZOS_TOL32 = 1e-6f;
