@@ -136,7 +136,10 @@ fs_status fs_default_options(fs_options* opts);
 
 /* Create a context on CUDA device `device`, enqueueing on `stream` (a
    cudaStream_t; NULL = the legacy default stream).  The context owns a workspace
-   that grows on demand and is released by fs_destroy.  *ctx receives the handle. */
+   that grows on demand and is released by fs_destroy.  *ctx receives the handle.
+   A growth reallocates the workspace: CUDA graphs captured earlier around calls on
+   this context refer to the old one and must be captured again after any call that
+   needed more (a larger problem, fs_forward_born, fs_forward). */
 fs_status fs_create(fs_ctx** ctx, int device, void* stream);
 
 /* Release the context and its workspace (synchronises its stream).  NULL is a no-op. */
