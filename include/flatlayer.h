@@ -208,28 +208,41 @@ fs_status fs_reconstruct_batch(fs_ctx* ctx, const fs_problem* probs, int n_probs
 fs_status fs_forward_born(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* xi,
                           const double* omega, int n_omega, double c0, void* W);
 
-/* Forward data generator with full scattering: Algorithm 1 of Sec. 3, the fixed
-   point of eq. (6) on the mode coefficients of the field in X,
+/* Solver of the full-scattering forward problem u = u0 + omega^2 T(xi u) on X (first
+   line of eq. 2) for fs_forward. */
+typedef enum {
+  FS_FIXED_POINT = 0,       /* Algorithm 1 of Sec. 3 (the fixed point of eq. 6)          */
+  FS_GMRES = 1,             /* restarted GMRES on u - omega^2 T(xi u) = u0                */
+  FS_FIXED_POINT_GMRES = 2  /* Algorithm 1, and GMRES for a frequency where it fails      */
+} fs_forward_method;
+
+/* Forward data generator with full scattering.  FS_FIXED_POINT iterates Algorithm 1,
      U~_{n+1} = U~0 + omega^2 T_nu F_r[xi F^-1 U~_n],  T_nu[l, l'] = h_z K_nu(z'_l - z'_l'),
-   from U~_1 = U~0 (the plane wave u0 = exp(-i k0 z)), stopped at the first n with
+   from U~_1 = U~0 (the plane wave u0 = exp(-i k0 z)), to the first n with
    ||U~_{n+1} - U~_n|| <= rtol ||U~0|| (Frobenius norms over the M planes of one
-   frequency; the paper's stopping rule of Sec. 5.1 with rtol = 1e-13), then the data
-   of eq. (7) from the converged field.  Each frequency iterates on its own.
+   frequency; the stopping rule of Sec. 5.1 with rtol = 1e-13).  FS_GMRES solves the
+   same equation in X by restarted GMRES (30 vectors per cycle, from u = 0) to
+   ||u0 - u + omega^2 T(xi u)|| <= rtol ||u0||, the residual computed afresh at each
+   restart.  Either way the data of eq. (7) follow from the converged field.  Each
+   frequency is solved on its own.
      xi        device, [M][N][N] real (float64 for FS_FP64, float32 for FS_MIXED).
      omega     host, n_omega values > 0.
-     max_iter  >= 0; 0 gives the single-scattering data of fs_forward_born.
+     max_iter  >= 0: iterations of Algorithm 1, or operator applications of GMRES (each
+               method of FS_FIXED_POINT_GMRES gets max_iter); FS_FIXED_POINT with 0
+               gives the single-scattering data of fs_forward_born.
      rtol      > 0; FP32 rounding bounds it below near 1e-6 in FS_MIXED.
      W         device, [n_omega][M1][N][N] complex, written.
      u         device, [n_omega][M][N][N] complex (the total field on X), written; or NULL.
-     iterations host, n_omega ints (the iterations each frequency took), or NULL.
+     iterations host, n_omega ints (iterations plus operator applications), or NULL.
    Returns FS_ENOCONV, with W and u of the remaining frequencies unwritten, when a
-   frequency has not converged after max_iter iterations or its iteration grows past
-   1e30 ||U~0|| (a scatterer too strong for the fixed point: omega^2 ||T xi|| >= 1).
-   Uses the context workspace; synchronises the context's stream once per iteration
-   (the stopping test is taken on the host), so it cannot be captured in a graph. */
+   frequency has not converged within max_iter or its iterate grows past 1e30 times the
+   incident field (Algorithm 1 with a scatterer too strong for the fixed point:
+   omega^2 ||T xi|| >= 1).  Uses the context workspace; synchronises the context's
+   stream at each stopping test and GMRES inner product, so it cannot be captured in a
+   graph. */
 fs_status fs_forward(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* xi,
-                     const double* omega, int n_omega, double c0, int max_iter, double rtol, void* W, void* u,
-                     int* iterations);
+                     const double* omega, int n_omega, double c0, fs_forward_method method, int max_iter,
+                     double rtol, void* W, void* u, int* iterations);
 
 /* Size of the device array that holds every intermediate of fs_reconstruct_static. */
 #define FS_STATIC_SCRATCH_BYTES (32u << 20)

@@ -12,7 +12,7 @@ from __future__ import annotations
 from dataclasses import dataclass
 
 from . import _abi
-from ._abi import (FS_FP64, FS_MIXED, FlatLayerError, fs_create, fs_default_options, fs_destroy,
+from ._abi import (FORWARD_METHODS, FS_FP64, FS_MIXED, FlatLayerError, fs_create, fs_default_options, fs_destroy,
                    fs_forward, fs_forward_born, fs_get_report, fs_last_error, fs_reconstruct, fs_reconstruct_batch,
                    fs_reconstruct_host, fs_reconstruct_static, fs_version, fs_workspace_size, make_geometry,
                    make_options, make_problem)
@@ -135,12 +135,13 @@ class Reconstructor:
         return W
 
     def forward(self, xi, omega, geom: Geometry, c0: float = 1.0, precision: str = "fp64", max_iter: int = 500,
-                rtol: float = None, want_u: bool = False):
-        """Data W[n_omega, M1, N, N] of xi[M, N, N] with full scattering (Algorithm 1,
-        the fixed point of eq. 6, to ||U~_{n+1} - U~_n|| <= rtol ||U~0||; rtol defaults to
-        1e-13 in FP64 and 1e-6 in the mixed precision).  Returns (W, u or None,
-        iterations per frequency); raises FlatLayerError (FS_ENOCONV) when a frequency
-        does not converge."""
+                rtol: float = None, want_u: bool = False, method: str = "fixed_point"):
+        """Data W[n_omega, M1, N, N] of xi[M, N, N] with full scattering: method
+        "fixed_point" (Algorithm 1, the fixed point of eq. 6, to ||U~_{n+1} - U~_n|| <=
+        rtol ||U~0||), "gmres" (restarted GMRES to a relative residual rtol) or
+        "fixed_point_gmres" (GMRES where Algorithm 1 fails); rtol defaults to 1e-13 in
+        FP64 and 1e-6 in the mixed precision.  Returns (W, u or None, iterations per
+        frequency); raises FlatLayerError (FS_ENOCONV) when a frequency does not converge."""
         import torch
         prec = PRECISIONS[precision]
         rdt = torch.float64 if prec == FS_FP64 else torch.float32
@@ -153,8 +154,8 @@ class Reconstructor:
             rtol = 1e-13 if prec == FS_FP64 else 1e-6
         W = torch.empty((len(omega), geom.m1, geom.n, geom.n), dtype=cdt, device=self.device)
         u = torch.empty((len(omega), geom.m, geom.n, geom.n), dtype=cdt, device=self.device) if want_u else None
-        its = fs_forward(self.ctx, geom.c_struct(), prec, xi.data_ptr(), omega, c0, max_iter, rtol, W.data_ptr(),
-                         u.data_ptr() if u is not None else None)
+        its = fs_forward(self.ctx, geom.c_struct(), prec, xi.data_ptr(), omega, c0, FORWARD_METHODS[method], max_iter,
+                         rtol, W.data_ptr(), u.data_ptr() if u is not None else None)
         return W, u, its
 
     def report(self) -> dict:

@@ -102,8 +102,8 @@ def lib():
         L.fs_forward_born.restype = ip
         L.fs_forward_born.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, vp]
         L.fs_forward.restype = ip
-        L.fs_forward.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, ip, C.c_double, vp, vp,
-                                 C.POINTER(C.c_int)]
+        L.fs_forward.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, ip, ip, C.c_double, vp,
+                                 vp, C.POINTER(C.c_int)]
         L.fs_reconstruct_batch.restype = ip
         L.fs_reconstruct_batch.argtypes = [vp, C.POINTER(fs_problem), ip, ip, C.POINTER(fs_options), ip]
         L.fs_reconstruct_static.restype = ip
@@ -197,12 +197,17 @@ def fs_forward_born(ctx, geom, prec, xi_ptr, omega, c0, W_ptr):
     _check(ctx, st, "fs_forward_born")
 
 
-def fs_forward(ctx, geom, prec, xi_ptr, omega, c0, max_iter, rtol, W_ptr, u_ptr=None):
+FS_FIXED_POINT, FS_GMRES, FS_FIXED_POINT_GMRES = 0, 1, 2
+FORWARD_METHODS = {"fixed_point": FS_FIXED_POINT, "gmres": FS_GMRES, "fixed_point_gmres": FS_FIXED_POINT_GMRES}
+
+
+def fs_forward(ctx, geom, prec, xi_ptr, omega, c0, method, max_iter, rtol, W_ptr, u_ptr=None):
     """Returns the iterations each frequency took."""
     om = (C.c_double * len(omega))(*[float(x) for x in omega])
     its = (C.c_int * len(omega))()
     st = lib().fs_forward(ctx, C.byref(geom), int(prec), C.c_void_p(xi_ptr), om, len(omega), float(c0),
-                          int(max_iter), float(rtol), C.c_void_p(W_ptr), C.c_void_p(u_ptr or None), its)
+                          int(method), int(max_iter), float(rtol), C.c_void_p(W_ptr), C.c_void_p(u_ptr or None),
+                          its)
     _check(ctx, st, "fs_forward")
     return [int(x) for x in its]
 

@@ -599,12 +599,14 @@ fs_status fs_forward_born(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, 
 }
 
 fs_status fs_forward(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const void* xi, const double* omega,
-                     int n_omega, double c0, int max_iter, double rtol, void* W, void* u, int* iterations) {
+                     int n_omega, double c0, fs_forward_method method, int max_iter, double rtol, void* W, void* u,
+                     int* iterations) {
   if (!ctx) return FS_EINVAL;
   fs_status st = validate(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr);
   if (st != FS_OK) return st;
   if (!xi || !W) return fail(ctx, FS_EINVAL, "xi and W must be device pointers");
   if (max_iter < 0) return fail(ctx, FS_EINVAL, "max_iter must be >= 0");
+  if (method < FS_FIXED_POINT || method > FS_FIXED_POINT_GMRES) return fail(ctx, FS_EINVAL, "unknown forward method");
   if (!(rtol > 0.0)) return fail(ctx, FS_EINVAL, "rtol must be > 0");
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
@@ -612,26 +614,26 @@ fs_status fs_forward(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const
   fs_default_options(&o);
   const Problem P = make_problem(g, n_omega, omega, 0.0, c0, o);
   const bool fp64 = prec == FS_FP64;
-  const size_t need = fp64 ? forward_fixed_point_bytes<double>(P) : forward_fixed_point_bytes<float>(P);
+  const size_t need = fp64 ? forward_bytes<double>(P) : forward_bytes<float>(P);
   if ((st = ensure_workspace(ctx, need)) != FS_OK) return st;
   std::vector<int> it(n_omega, 0), conv(n_omega, 0);
   if (fp64) {
     const double2* tw = nullptr;
     if ((st = ensure_twiddles<double>(ctx, g->n, &tw)) != FS_OK) return st;
-    e = forward_fixed_point<double>(P, (const double*)xi, (double2*)W, (double2*)u, ctx->ws, rtol, max_iter, tw,
-                                    ctx->stream, it.data(), conv.data());
+    e = forward_solve<double>(P, (const double*)xi, (double2*)W, (double2*)u, ctx->ws, (int)method, rtol, max_iter,
+                              tw, ctx->stream, it.data(), conv.data());
   } else {
     const float2* tw = nullptr;
     if ((st = ensure_twiddles<float>(ctx, g->n, &tw)) != FS_OK) return st;
-    e = forward_fixed_point<float>(P, (const float*)xi, (float2*)W, (float2*)u, ctx->ws, rtol, max_iter, tw,
-                                   ctx->stream, it.data(), conv.data());
+    e = forward_solve<float>(P, (const float*)xi, (float2*)W, (float2*)u, ctx->ws, (int)method, rtol, max_iter, tw,
+                             ctx->stream, it.data(), conv.data());
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "forward");
   if (iterations)
     for (int j = 0; j < n_omega; ++j) iterations[j] = it[j];
   for (int j = 0; j < n_omega; ++j)
     if (!conv[j])
-      return fail(ctx, FS_ENOCONV, "Algorithm 1 did not converge for omega[%d] after %d iterations", j, it[j]);
+      return fail(ctx, FS_ENOCONV, "the forward solve did not converge for omega[%d] after %d iterations", j, it[j]);
   return FS_OK;
 }
 

@@ -16,6 +16,7 @@
 // (|nu| = k0) carry K = 0.
 #include <math.h>
 
+#include <complex>
 #include <vector>
 
 #include "pipeline.cuh"
@@ -132,10 +133,11 @@ __global__ void k_times_xi(long long count, const R* __restrict__ xi, cx<R>* __r
   }
 }
 
-// One step of Algorithm 1 for every mode of one frequency: ut <- U~0 + gamma (F + B),
-// F_l = q F_{l-1} + V~_l, B_l = q (B_{l+1} + V~_{l+1}) (fbuf holds F), and the block
-// partial of ||U~_{n+1} - U~_n||^2 in a fixed order.  One thread per mode.
-template <typename R>
+// omega^2 T_nu V~ for every mode of one frequency: gamma (F + B) with
+// F_l = q F_{l-1} + V~_l, B_l = q (B_{l+1} + V~_{l+1}) (fbuf holds F).  One thread per mode.
+// STEP (a step of Algorithm 1): ut <- U~0 + gamma (F + B) and the block partial of
+// ||U~_{n+1} - U~_n||^2 in a fixed order; otherwise ut <- gamma (F + B).
+template <typename R, bool STEP>
 __global__ void __launch_bounds__(FP_T)
 k_interior(Problem P, const cx<R>* __restrict__ vt, cx<R>* __restrict__ ut, cx<R>* __restrict__ fbuf,
            double* __restrict__ partial) {
@@ -166,17 +168,20 @@ k_interior(Problem P, const cx<R>* __restrict__ vt, cx<R>* __restrict__ ut, cx<R
     cx<R> b = czero<R>();
     for (int l = M - 1; l >= 0; --l) {
       cx<R> un = gr * (fbuf[l * N2 + nu] + b);
-      if (nu == 0) {
+      if (STEP && nu == 0) {
         double s, c;
         sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s, &c);
         un = un + from_d<R>(make_double2(n2 * c, n2 * s));
       }
-      const cx<R> d = un - ut[l * N2 + nu];
-      d2 += (double)d.x * (double)d.x + (double)d.y * (double)d.y;
+      if (STEP) {
+        const cx<R> d = un - ut[l * N2 + nu];
+        d2 += (double)d.x * (double)d.x + (double)d.y * (double)d.y;
+      }
       ut[l * N2 + nu] = un;
       b = qr * (b + vt[l * N2 + nu]);
     }
   }
+  if (!STEP) return;
   red[threadIdx.x] = d2;
   __syncthreads();
   for (int h = FP_T / 2; h > 0; h >>= 1) {
@@ -186,74 +191,365 @@ k_interior(Problem P, const cx<R>* __restrict__ vt, cx<R>* __restrict__ ut, cx<R
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
+// ---- GMRES on u - omega^2 T(xi u) = u0 (the Krylov fallback) -----------------
+constexpr int GM_BLOCKS = 512;  // blocks of the reduction kernels (grid-stride)
+
+// the plane wave u0 = exp(-i k0 z'_l) on X
+template <typename R>
+__global__ void k_plane_wave(Problem P, cx<R>* __restrict__ u) {
+  const long long N2 = (long long)P.n * P.n, count = (long long)P.m * N2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(e / N2);
+    double s, c;
+    sincos(-P.k0[0] * (P.z1 + (l + 0.5) * P.hz), &s, &c);
+    u[e] = from_d<R>(make_double2(c, s));
+  }
+}
+
+// y <- xi a
+template <typename R>
+__global__ void k_xi_times(long long count, const R* __restrict__ xi, const cx<R>* __restrict__ a,
+                           cx<R>* __restrict__ y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const R x = xi[e];
+    const cx<R> v = a[e];
+    y[e] = mk<R>(x * v.x, x * v.y);
+  }
+}
+
+// y <- a - b
+template <typename R>
+__global__ void k_sub(long long count, const cx<R>* __restrict__ a, const cx<R>* __restrict__ b,
+                      cx<R>* __restrict__ y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    y[e] = a[e] - b[e];
+}
+
+// block partials of <v_i, w> = sum conj(v_i) w (FP64 sums), grid (GM_BLOCKS, nv):
+// partial[i * GM_BLOCKS + block]; summed on the host in a fixed order
+template <typename R>
+__global__ void __launch_bounds__(FP_T)
+k_dots(long long count, const cx<R>* __restrict__ V, long long ld, const cx<R>* __restrict__ w,
+       double2* __restrict__ partial) {
+  __shared__ double2 red[FP_T];
+  const cx<R>* v = V + blockIdx.y * ld;
+  double2 acc = make_double2(0.0, 0.0);
+  for (long long e = blockIdx.x * (long long)FP_T + threadIdx.x; e < count; e += (long long)gridDim.x * FP_T) {
+    const double2 a = to_d(v[e]), b = to_d(w[e]);
+    acc.x += a.x * b.x + a.y * b.y;
+    acc.y += a.x * b.y - a.y * b.x;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = FP_T / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+// w <- w + sign sum_{i < nv} c_i v_i  (c on the device)
+template <typename R>
+__global__ void k_comb(long long count, const cx<R>* __restrict__ V, long long ld, int nv,
+                       const double2* __restrict__ c, double sign, cx<R>* __restrict__ w) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    double2 acc = to_d(w[e]);
+    for (int i = 0; i < nv; ++i) {
+      const double2 t = c[i] * to_d(V[i * ld + e]);
+      acc.x += sign * t.x;
+      acc.y += sign * t.y;
+    }
+    w[e] = from_d<R>(acc);
+  }
+}
+
+// y <- s x (s real)
+template <typename R>
+__global__ void k_scale(long long count, const cx<R>* __restrict__ x, double s, cx<R>* __restrict__ y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double2 v = to_d(x[e]);
+    y[e] = from_d<R>(make_double2(s * v.x, s * v.y));
+  }
+}
+
+}  // namespace
+
+namespace {
+
+constexpr int GM_RESTART = 30;  // Krylov vectors per GMRES cycle
+
+template <typename R> struct FwdLayout {
+  long long N2, MN2;
+  long long vec_elems;
+  cx<R>* base;
+  explicit FwdLayout(const Problem& P, void* ws) {
+    N2 = (long long)P.n * P.n;
+    MN2 = (long long)P.m * N2;
+    // fixed point: ut, fb, sc; GMRES: sc, tv, fb, x, u0, GM_RESTART + 1 Krylov vectors
+    const long long fp = 3 * MN2;
+    const long long gm = (6 + GM_RESTART) * MN2;
+    vec_elems = fp > gm ? fp : gm;
+    base = reinterpret_cast<cx<R>*>(ws);
+  }
+  double2* reals() const { return reinterpret_cast<double2*>(base + vec_elems); }
+  static size_t real_elems() { return (size_t)(GM_RESTART + 1) * GM_BLOCKS + (GM_RESTART + 1) + 1024; }
+};
+
+template <typename R>
+Problem one_frequency(const Problem& P, int om) {
+  Problem Q = P;
+  Q.n_omega = 1;
+  Q.omega[0] = P.omega[om];
+  Q.graz_lo[0] = P.graz_lo[om];
+  Q.graz_hi[0] = P.graz_hi[om];
+  Q.k0[0] = P.k0[om];
+  Q.g0[0] = P.g0[om];
+  return Q;
+}
+
+// Algorithm 1 for one frequency; on convergence u (physical, M planes) is written to uo
+// (which may be the scratch sc).  The stopping test is taken on the host each iteration.
+template <typename R>
+cudaError_t fixed_point_one(const Problem& Q, const R* xi, const FwdLayout<R>& L, const cx<R>* tw, double rtol,
+                            int max_iter, cudaStream_t s, cx<R>* uo_user, cx<R>** uo, int* iters, bool* conv) {
+  const long long N2 = L.N2, MN2 = L.MN2;
+  cx<R>* ut = L.base;
+  cx<R>* fb = ut + MN2;
+  cx<R>* sc = fb + MN2;
+  double* partial = reinterpret_cast<double*>(L.reals());
+  const int nblk = (int)((N2 + FP_T - 1) / FP_T);
+  std::vector<double> host(nblk);
+  const double nrm0 = (double)N2 * sqrt((double)Q.m);  // ||U~0||: N^2 |e^{-i k0 z}| on M planes
+  const unsigned gx = (unsigned)((MN2 + FP_T - 1) / FP_T < 4096 ? (MN2 + FP_T - 1) / FP_T : 4096);
+  cudaError_t e = cudaMemsetAsync(ut, 0, sizeof(cx<R>) * MN2, s);
+  if (e != cudaSuccess) return e;
+  k_incident<R><<<(Q.m + 63) / 64, 64, 0, s>>>(Q, ut);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int it = 0;
+  bool ok = max_iter == 0;
+  while (it < max_iter) {
+    ++it;
+    // (the inverse transform works in place on its input: ut is copied first)
+    if ((e = cudaMemcpyAsync(sc, ut, sizeof(cx<R>) * MN2, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    if ((e = launch_fft2_dense<R>(sc, sc, Q.n, Q.m, true, tw, s)) != cudaSuccess) return e;
+    k_times_xi<R><<<gx, FP_T, 0, s>>>(MN2, xi, sc);
+    if ((e = launch_fft2_dense<R>(sc, sc, Q.n, Q.m, false, tw, s)) != cudaSuccess) return e;
+    k_interior<R, true><<<nblk, FP_T, 0, s>>>(Q, sc, ut, fb, partial);
+    if ((e = cudaMemcpyAsync(host.data(), partial, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    double d2 = 0.0;
+    for (int b = 0; b < nblk; ++b) d2 += host[b];
+    const double diff = sqrt(d2);
+    if (diff <= rtol * nrm0) {
+      ok = true;
+      break;
+    }
+    if (!(diff <= 1e30 * nrm0)) break;  // diverged (or not finite)
+  }
+  *iters = it;
+  *conv = ok;
+  if (!ok) return cudaSuccess;
+  *uo = uo_user ? uo_user : sc;  // u = F^-1 U~ (ut is not needed after this)
+  return launch_fft2_dense<R>(ut, *uo, Q.n, Q.m, true, tw, s);
+}
+
+template <typename R> struct Krylov {
+  const Problem& Q;
+  const R* xi;
+  const cx<R>* tw;
+  cudaStream_t s;
+  long long N2, MN2;
+  unsigned gx;
+  cx<R> *sc, *tv, *fb;
+  double2* partial;  // (GM_RESTART + 1) * GM_BLOCKS
+  double2* coef;     // GM_RESTART + 1
+  std::vector<double2> host;
+
+  // y <- x - omega^2 F^-1 T_nu F_r[xi x]
+  cudaError_t apply(const cx<R>* x, cx<R>* y) {
+    k_xi_times<R><<<gx, FP_T, 0, s>>>(MN2, xi, x, sc);
+    cudaError_t e = launch_fft2_dense<R>(sc, sc, Q.n, Q.m, false, tw, s);
+    if (e != cudaSuccess) return e;
+    k_interior<R, false><<<(unsigned)((N2 + FP_T - 1) / FP_T), FP_T, 0, s>>>(Q, sc, tv, fb, nullptr);
+    if ((e = launch_fft2_dense<R>(tv, tv, Q.n, Q.m, true, tw, s)) != cudaSuccess) return e;
+    k_sub<R><<<gx, FP_T, 0, s>>>(MN2, x, tv, y);
+    return cudaGetLastError();
+  }
+  // <v_i, w> for the nv vectors v_i = V + i MN2, summed on the host in a fixed order
+  cudaError_t dots(const cx<R>* V, int nv, const cx<R>* w, std::vector<std::complex<double>>& out) {
+    k_dots<R><<<dim3(GM_BLOCKS, nv), FP_T, 0, s>>>(MN2, V, MN2, w, partial);
+    host.resize((size_t)nv * GM_BLOCKS);
+    cudaError_t e = cudaMemcpyAsync(host.data(), partial, sizeof(double2) * host.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    out.assign(nv, 0.0);
+    for (int i = 0; i < nv; ++i) {
+      double re = 0.0, im = 0.0;
+      for (int b = 0; b < GM_BLOCKS; ++b) {
+        re += host[(size_t)i * GM_BLOCKS + b].x;
+        im += host[(size_t)i * GM_BLOCKS + b].y;
+      }
+      out[i] = std::complex<double>(re, im);
+    }
+    return cudaSuccess;
+  }
+  // w <- w + sign sum_i c_i v_i
+  cudaError_t comb(const cx<R>* V, const std::vector<std::complex<double>>& c, double sign, cx<R>* w) {
+    std::vector<double2> ch(c.size());
+    for (size_t i = 0; i < c.size(); ++i) ch[i] = make_double2(c[i].real(), c[i].imag());
+    cudaError_t e = cudaMemcpyAsync(coef, ch.data(), sizeof(double2) * ch.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_comb<R><<<gx, FP_T, 0, s>>>(MN2, V, MN2, (int)c.size(), coef, sign, w);
+    // the host vector must outlive the copy
+    return cudaStreamSynchronize(s);
+  }
+};
+
+// Restarted GMRES(GM_RESTART) with classical Gram-Schmidt applied twice and Givens
+// rotations, from x = 0, to ||u0 - A x|| <= rtol ||u0|| (the residual of each cycle's
+// start is computed, not estimated); iters counts the operator applications.
+template <typename R>
+cudaError_t gmres_one(const Problem& Q, const R* xi, const FwdLayout<R>& L, const cx<R>* tw, double rtol, int max_iter,
+                      cudaStream_t s, cx<R>** uo, int* iters, bool* conv) {
+  using cd = std::complex<double>;
+  const long long N2 = L.N2, MN2 = L.MN2;
+  Krylov<R> K{Q, xi, tw, s};
+  K.N2 = N2;
+  K.MN2 = MN2;
+  K.gx = (unsigned)((MN2 + FP_T - 1) / FP_T < 4096 ? (MN2 + FP_T - 1) / FP_T : 4096);
+  K.sc = L.base;
+  K.tv = K.sc + MN2;
+  K.fb = K.tv + MN2;
+  cx<R>* x = K.fb + MN2;
+  cx<R>* bv = x + MN2;
+  cx<R>* V = bv + MN2;
+  K.partial = L.reals();
+  K.coef = K.partial + (size_t)(GM_RESTART + 1) * GM_BLOCKS;
+  cudaError_t e;
+  k_plane_wave<R><<<K.gx, FP_T, 0, s>>>(Q, bv);
+  if ((e = cudaMemsetAsync(x, 0, sizeof(cx<R>) * MN2, s)) != cudaSuccess) return e;
+  std::vector<cd> d;
+  if ((e = K.dots(bv, 1, bv, d)) != cudaSuccess) return e;
+  const double beta0 = sqrt(d[0].real());
+  int total = 0;
+  bool ok = false;
+  const int R1 = GM_RESTART + 1;
+  for (;;) {
+    // residual r = u0 - A x in V_0
+    if (total == 0) {
+      e = cudaMemcpyAsync(V, bv, sizeof(cx<R>) * MN2, cudaMemcpyDeviceToDevice, s);
+    } else {
+      if ((e = K.apply(x, V)) != cudaSuccess) return e;
+      k_sub<R><<<K.gx, FP_T, 0, s>>>(MN2, bv, V, V);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+    if ((e = K.dots(V, 1, V, d)) != cudaSuccess) return e;
+    const double beta = sqrt(d[0].real());
+    if (beta <= rtol * beta0) {
+      ok = true;
+      break;
+    }
+    if (total >= max_iter || !(beta <= 1e30 * beta0)) break;
+    k_scale<R><<<K.gx, FP_T, 0, s>>>(MN2, V, 1.0 / beta, V);
+    std::vector<cd> H((size_t)R1 * GM_RESTART, 0.0), g(R1, 0.0), sn(GM_RESTART, 0.0);
+    std::vector<double> cs(GM_RESTART, 0.0);
+    auto h = [&](int i, int j) -> cd& { return H[(size_t)i * GM_RESTART + j]; };
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < GM_RESTART && total < max_iter; ++j) {
+      cx<R>* w = V + (long long)(j + 1) * MN2;
+      if ((e = K.apply(V + (long long)j * MN2, w)) != cudaSuccess) return e;
+      ++total;
+      for (int pass = 0; pass < 2; ++pass) {  // w -= V (V^H w), twice
+        if ((e = K.dots(V, j + 1, w, d)) != cudaSuccess) return e;
+        if ((e = K.comb(V, d, -1.0, w)) != cudaSuccess) return e;
+        for (int i = 0; i <= j; ++i) h(i, j) += d[i];
+      }
+      if ((e = K.dots(w, 1, w, d)) != cudaSuccess) return e;
+      const double hn = sqrt(d[0].real());
+      h(j + 1, j) = hn;
+      for (int i = 0; i < j; ++i) {  // earlier rotations on column j
+        const cd t = cs[i] * h(i, j) + sn[i] * h(i + 1, j);
+        h(i + 1, j) = -std::conj(sn[i]) * h(i, j) + cs[i] * h(i + 1, j);
+        h(i, j) = t;
+      }
+      const cd a = h(j, j);
+      const double r = std::sqrt(std::norm(a) + hn * hn);
+      if (std::abs(a) == 0.0) {
+        cs[j] = 0.0;
+        sn[j] = 1.0;
+      } else {
+        cs[j] = std::abs(a) / r;
+        sn[j] = (a / std::abs(a)) * hn / r;
+      }
+      h(j, j) = cs[j] * a + sn[j] * hn;
+      h(j + 1, j) = 0.0;
+      g[j + 1] = -std::conj(sn[j]) * g[j];
+      g[j] = cs[j] * g[j];
+      k = j + 1;
+      if (!(hn > 0.0) || std::abs(g[j + 1]) <= rtol * beta0) break;
+      k_scale<R><<<K.gx, FP_T, 0, s>>>(MN2, w, 1.0 / hn, w);
+    }
+    std::vector<cd> y(k);
+    for (int i = k - 1; i >= 0; --i) {  // H y = g, upper triangular
+      cd t = g[i];
+      for (int c = i + 1; c < k; ++c) t -= h(i, c) * y[c];
+      y[i] = h(i, i) != 0.0 ? t / h(i, i) : cd(0.0);  // (an exactly singular H: a lucky breakdown)
+    }
+    if (k > 0 && (e = K.comb(V, y, 1.0, x)) != cudaSuccess) return e;
+  }
+  *iters = total;
+  *conv = ok;
+  *uo = x;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 template <typename R>
-size_t forward_fixed_point_bytes(const Problem& P) {
-  const size_t plane = sizeof(cx<R>) * (size_t)P.n * P.n;
-  const int mm = P.m > P.m1 ? P.m : P.m1;
-  const size_t nblk = ((size_t)P.n * P.n + FP_T - 1) / FP_T;
-  return plane * ((size_t)P.m * 2 + mm) + sizeof(double) * nblk + 256;
+size_t forward_bytes(const Problem& P) {
+  FwdLayout<R> L(P, nullptr);
+  return sizeof(cx<R>) * (size_t)L.vec_elems + sizeof(double2) * FwdLayout<R>::real_elems() + 256;
 }
 
 template <typename R>
-cudaError_t forward_fixed_point(const Problem& P, const R* xi, cx<R>* W, cx<R>* u_out, void* ws, double rtol,
-                                int max_iter, const cx<R>* tw, cudaStream_t s, int* iters, int* converged) {
-  const long long N2 = (long long)P.n * P.n, MN2 = (long long)P.m * N2;
-  const int mm = P.m > P.m1 ? P.m : P.m1;
-  cx<R>* ut = reinterpret_cast<cx<R>*>(ws);
-  cx<R>* fb = ut + MN2;
-  cx<R>* sc = fb + MN2;  // mm planes
-  double* partial = reinterpret_cast<double*>(sc + (long long)mm * N2);
-  const int nblk = (int)((N2 + FP_T - 1) / FP_T);
-  std::vector<double> host(nblk);
-  const double nrm0 = (double)N2 * sqrt((double)P.m);  // ||U~0||: N^2 |e^{-i k0 z}| on M planes
+cudaError_t forward_solve(const Problem& P, const R* xi, cx<R>* W, cx<R>* u_out, void* ws, int method, double rtol,
+                          int max_iter, const cx<R>* tw, cudaStream_t s, int* iters, int* converged) {
+  const FwdLayout<R> L(P, ws);
+  const long long N2 = L.N2, MN2 = L.MN2;
   const unsigned gx = (unsigned)((MN2 + FP_T - 1) / FP_T < 4096 ? (MN2 + FP_T - 1) / FP_T : 4096);
   cudaError_t e = cudaSuccess;
   for (int om = 0; om < P.n_omega; ++om) {
-    Problem Q = P;  // one frequency
-    Q.n_omega = 1;
-    Q.omega[0] = P.omega[om];
-    Q.graz_lo[0] = P.graz_lo[om];
-    Q.graz_hi[0] = P.graz_hi[om];
-    Q.k0[0] = P.k0[om];
-    Q.g0[0] = P.g0[om];
-    if ((e = cudaMemsetAsync(ut, 0, sizeof(cx<R>) * MN2, s)) != cudaSuccess) return e;
-    k_incident<R><<<(P.m + 63) / 64, 64, 0, s>>>(Q, ut);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const Problem Q = one_frequency<R>(P, om);
+    cx<R>* uo_user = u_out ? u_out + (long long)om * MN2 : nullptr;
+    cx<R>* u = nullptr;
     int it = 0;
-    bool conv = max_iter == 0;
-    while (it < max_iter) {
-      ++it;
-      // (the inverse transform works in place on its input: ut is copied first)
-      if ((e = cudaMemcpyAsync(sc, ut, sizeof(cx<R>) * MN2, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-      if ((e = launch_fft2_dense<R>(sc, sc, P.n, P.m, true, tw, s)) != cudaSuccess) return e;
-      k_times_xi<R><<<gx, FP_T, 0, s>>>(MN2, xi, sc);
-      if ((e = launch_fft2_dense<R>(sc, sc, P.n, P.m, false, tw, s)) != cudaSuccess) return e;
-      k_interior<R><<<nblk, FP_T, 0, s>>>(Q, sc, ut, fb, partial);
-      if ((e = cudaMemcpyAsync(host.data(), partial, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s)) !=
-          cudaSuccess)
+    bool conv = false;
+    if (method != 1) {  // Algorithm 1 (method 0, or the first try of method 2)
+      if ((e = fixed_point_one<R>(Q, xi, L, tw, rtol, max_iter, s, uo_user, &u, &it, &conv)) != cudaSuccess) return e;
+    }
+    if (!conv && method != 0) {  // GMRES (method 1, or the fallback of method 2)
+      int it2 = 0;
+      if ((e = gmres_one<R>(Q, xi, L, tw, rtol, max_iter, s, &u, &it2, &conv)) != cudaSuccess) return e;
+      it += it2;
+      if (conv && uo_user &&
+          (e = cudaMemcpyAsync(uo_user, u, sizeof(cx<R>) * MN2, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return e;
-      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-      double d2 = 0.0;
-      for (int b = 0; b < nblk; ++b) d2 += host[b];
-      const double diff = sqrt(d2);
-      if (diff <= rtol * nrm0) {
-        conv = true;
-        break;
-      }
-      if (!(diff <= 1e30 * nrm0)) break;  // diverged (or not finite)
     }
     if (iters) iters[om] = it;
     if (converged) converged[om] = conv ? 1 : 0;
     if (!conv) return cudaSuccess;
-    // eq. (7) with the converged field: u = F^-1 U~ (ut is not needed after this), V~ =
-    // F_r[xi u], data planes
-    cx<R>* uo = u_out ? u_out + (long long)om * MN2 : sc;
-    if ((e = launch_fft2_dense<R>(ut, uo, P.n, P.m, true, tw, s)) != cudaSuccess) return e;
-    if (uo != sc && (e = cudaMemcpyAsync(sc, uo, sizeof(cx<R>) * MN2, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-      return e;
-    k_times_xi<R><<<gx, FP_T, 0, s>>>(MN2, xi, sc);
+    // eq. (7) with the converged field: V~ = F_r[xi u], data planes.  u is never at the
+    // start of the workspace (the fixed point's U~, spent; the Krylov scratch)
+    cx<R>* sc = L.base;
+    k_xi_times<R><<<gx, FP_T, 0, s>>>(MN2, xi, u, sc);
     if ((e = launch_fft2_dense<R>(sc, sc, P.n, P.m, false, tw, s)) != cudaSuccess) return e;
     cx<R>* wo = W + (long long)om * P.m1 * N2;
     k_apply_data<R><<<(unsigned)((N2 + 255) / 256), 256, 0, s>>>(Q, sc, wo);
@@ -263,11 +559,11 @@ cudaError_t forward_fixed_point(const Problem& P, const R* xi, cx<R>* W, cx<R>* 
   return cudaSuccess;
 }
 
-template size_t forward_fixed_point_bytes<double>(const Problem&);
-template size_t forward_fixed_point_bytes<float>(const Problem&);
-template cudaError_t forward_fixed_point<double>(const Problem&, const double*, double2*, double2*, void*, double,
-                                                 int, const double2*, cudaStream_t, int*, int*);
-template cudaError_t forward_fixed_point<float>(const Problem&, const float*, float2*, float2*, void*, double, int,
-                                                const float2*, cudaStream_t, int*, int*);
+template size_t forward_bytes<double>(const Problem&);
+template size_t forward_bytes<float>(const Problem&);
+template cudaError_t forward_solve<double>(const Problem&, const double*, double2*, double2*, void*, int, double, int,
+                                           const double2*, cudaStream_t, int*, int*);
+template cudaError_t forward_solve<float>(const Problem&, const float*, float2*, float2*, void*, int, double, int,
+                                          const float2*, cudaStream_t, int*, int*);
 
 }  // namespace fl

@@ -110,14 +110,16 @@ cudaError_t launch_fft2_dense(cx<R>* in, cx<R>* out, int n, long long planes, bo
 template <typename R>
 cudaError_t launch_forward_born(const Problem& P, const R* xi, cx<R>* src, cx<R>* W, const cx<R>* tw,
                                 cudaStream_t s);
-// Algorithm 1 (fixed point of eq. 6) per frequency, then the data of eq. (7); iters and
-// converged (host arrays of n_omega, may be null) report each frequency.  ws holds
-// forward_fixed_point_bytes(P) bytes.  Synchronises the stream once per iteration.
+// Full-scattering field per frequency -- method 0: Algorithm 1 (fixed point of eq. 6);
+// 1: restarted GMRES on u - omega^2 T(xi u) = u0; 2: Algorithm 1, GMRES where it does
+// not converge -- then the data of eq. (7).  iters and converged (host arrays of
+// n_omega, may be null) report each frequency.  ws holds forward_bytes(P) bytes.
+// Synchronises the stream at each stopping test and inner product.
 template <typename R>
-size_t forward_fixed_point_bytes(const Problem& P);
+size_t forward_bytes(const Problem& P);
 template <typename R>
-cudaError_t forward_fixed_point(const Problem& P, const R* xi, cx<R>* W, cx<R>* u_out, void* ws, double rtol,
-                                int max_iter, const cx<R>* tw, cudaStream_t s, int* iters, int* converged);
+cudaError_t forward_solve(const Problem& P, const R* xi, cx<R>* W, cx<R>* u_out, void* ws, int method, double rtol,
+                          int max_iter, const cx<R>* tw, cudaStream_t s, int* iters, int* converged);
 
 bool fft_size_supported(int n);
 

@@ -1,9 +1,13 @@
-"""Algorithm 1 on the device (fs_forward: the fixed point of eq. 6, then the data of
-eq. 7) against the oracle's own fixed point (oracle/forward.py), through the C ABI.
+"""The full-scattering forward solve on the device (fs_forward: Algorithm 1, the fixed
+point of eq. 6; restarted GMRES; Algorithm 1 with a GMRES fallback -- then the data of
+eq. 7) against the oracle's own fixed point and GMRES (oracle/forward.py), through the
+C ABI.
 
-FP64: W and the total field u agree to 1e-10 (relative L2) and each frequency takes
-the oracle's number of iterations (the same stopping rule, rtol = 1e-13, on iterates
-that agree to ~1e-15).  Mixed: 1e-5 at rtol = 1e-6 (the FP32 transforms' rounding).
+FP64: W and the total field u agree to 1e-10 (relative L2) and Algorithm 1 takes the
+oracle's number of iterations per frequency (the same stopping rule, rtol = 1e-13, on
+iterates that agree to ~1e-15); GMRES solutions agree to 1e-10 (1e-9 for a strong
+scatterer, condition number ~10).  Mixed: 1e-5 at rtol = 1e-6 (the FP32 transforms'
+rounding).
 """
 import numpy as np
 import pytest
@@ -34,7 +38,7 @@ def _geom(g):
     return Geometry(g.n, g.m, g.z1, g.z2, tuple(g.zy), g.period)
 
 
-def _run(rc, name, precision, **kw):
+def _run(rc, name, precision, **kw):  # kw: forward options (method, max_iter, rtol)
     import torch
     g, om, _, xi = case(name, 0.01)
     dt = torch.float64 if precision == "fp64" else torch.float32
@@ -88,3 +92,37 @@ def test_not_converged_is_reported(rc):
         rc.forward(x, list(om), _geom(g), max_iter=2)
     with pytest.raises(FlatLayerError, match="FS_ENOCONV"):
         rc.forward(60.0 * x, list(om), _geom(g), max_iter=200)
+
+
+@pytest.mark.parametrize("name", ["c1", "r24"])
+def test_gmres_matches_oracle_fp64(rc, name):
+    """FS_GMRES against the oracle's GMRES (both to a relative residual 1e-13)."""
+    g, om, xi, W, u, its = _run(rc, name, "fp64", method="gmres")
+    Wr, ur = forward.make_data(xi, om, g, method="gmres")
+    ew, eu = rel_l2(W, Wr), rel_l2(u, ur)
+    print(f"{name} gmres: W {ew:.2e}, u {eu:.2e}, operator applications {its}")
+    assert ew <= 1e-10 and eu <= 1e-10
+
+
+def test_gmres_mixed(rc):
+    g, om, xi, W, u, its = _run(rc, "c1", "mixed", method="gmres")
+    Wr, ur = forward.make_data(xi, om, g, method="gmres")
+    assert rel_l2(W, Wr) <= 1e-5 and rel_l2(u, ur) <= 1e-5
+
+
+def test_fixed_point_falls_back_to_gmres(rc):
+    """20 xi on the 24^2 case: Algorithm 1 converges at the lower frequency and
+    diverges at the upper one, where GMRES takes over; both match the oracle's GMRES."""
+    import torch
+    g, om, _, xi = case("r24", 0.01)
+    xs = 20.0 * xi
+    x = torch.from_numpy(np.ascontiguousarray(xs)).to(rc.device, torch.float64)
+    with pytest.raises(Exception, match="FS_ENOCONV"):
+        rc.forward(x, list(om), _geom(g), max_iter=200)
+    W, u, its = rc.forward(x, list(om), _geom(g), max_iter=200, want_u=True, method="fixed_point_gmres")
+    torch.cuda.synchronize()
+    Wr, ur = forward.make_data(xs, om, g, method="gmres")
+    ew, eu = rel_l2(W.cpu().numpy(), Wr), rel_l2(u.cpu().numpy(), ur)
+    print(f"fallback: W {ew:.2e}, u {eu:.2e}, iterations {its}")
+    assert its[0] == forward.fixed_point_iterations(xs, om[0], g)[1]
+    assert ew <= 1e-9 and eu <= 1e-9
