@@ -372,7 +372,7 @@ def run_ours(args, rank, world, local):
 
 def run_forward(rc, wl, geom, om, reps=3):
     """Algorithm 1 (fs_forward) on the headline geometry and inclusions: the full-
-    scattering data of the same xi, both precisions.  Each call synchronises once per
+    scattering data of the same xi, both precisions, and GMRES in FP64.  Each call synchronises once per
     iteration (the stopping test is on the host), so the time is host wall clock around
     whole calls; the FP64 and mixed data are compared with each other."""
     import torch
@@ -402,6 +402,21 @@ def run_forward(rc, wl, geom, om, reps=3):
     if len(Ws) == 2:
         a, b = Ws["mixed"].to(torch.complex128), Ws["fp64"]
         out["mixed_vs_fp64_rel_l2"] = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    # the Krylov solver on the same problem (FP64, relative residual 1e-13)
+    from paper_1911_10487_gb300 import FlatLayerError
+    try:
+        rc.forward(xi64, om, geom, method="gmres")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Wg, _, its = rc.forward(xi64, om, geom, method="gmres")
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        out["gmres_fp64"] = {"ms": ms, "operator_applications": its}
+        if "fp64" in Ws:
+            out["gmres_vs_fixed_point_rel_l2"] = float(torch.linalg.vector_norm(Wg - Ws["fp64"]) /
+                                                       torch.linalg.vector_norm(Ws["fp64"]))
+    except FlatLayerError as e:
+        out["gmres_fp64"] = {"not_converged": str(e)}
     return out
 
 
