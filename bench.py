@@ -127,9 +127,17 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(units_per_rank, ms_local, world):
+    """Whole-job throughput of `world` replicas that each process units_per_rank in
+    ms_local: all units over the slowest rank's time (weak scaling, max over ranks)."""
+    ms = max_over_ranks(ms_local, world)
+    return world * units_per_rank / (ms * 1e-3), ms
 
 
 def make_inputs(rc, wl, geom):
@@ -264,12 +272,10 @@ def run_ours(args, rank, world, local):
     clocks = Clocks(local)
     ms_mixed, ck = timed("mixed", args.steps, args.warmup, clocks)
     ms_fp64, _ = timed("fp64", args.steps, args.warmup)
-    ms_mixed = max_over_ranks(ms_mixed, world)
-    ms_fp64 = max_over_ranks(ms_fp64, world)
-    ms_r1 = {p: max_over_ranks(timed(p + "_r1", args.steps, args.warmup)[0], world) for p in ("mixed", "fp64")}
     vox = wl.voxel_freqs
-    value = world * vox / (ms_mixed * 1e-3)
-    value_fp64 = world * vox / (ms_fp64 * 1e-3)
+    value, ms_mixed = job_value(vox, ms_mixed, world)
+    value_fp64, ms_fp64 = job_value(vox, ms_fp64, world)
+    ms_r1 = {p: max_over_ranks(timed(p + "_r1", args.steps, args.warmup)[0], world) for p in ("mixed", "fp64")}
 
     # per-kernel durations (CUDA events recorded by the library between its kernels)
     stage_ms = {}
