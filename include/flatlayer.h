@@ -233,7 +233,9 @@ typedef enum {
      rtol      > 0; FP32 rounding bounds it below near 1e-6 in FS_MIXED.
      W         device, [n_omega][M1][N][N] complex, written.
      u         device, [n_omega][M][N][N] complex (the total field on X), written; or NULL.
-     iterations host, n_omega ints (iterations plus operator applications), or NULL.
+     iterations host, n_omega ints, or NULL: iterations of Algorithm 1 plus Arnoldi
+               steps of GMRES (each one operator application; the residual computed at
+               each restart is one more, not counted).
    Returns FS_ENOCONV, with W and u of the remaining frequencies unwritten, when a
    frequency has not converged within max_iter or its iterate grows past 1e30 times the
    incident field (Algorithm 1 with a scatterer too strong for the fixed point:
