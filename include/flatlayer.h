@@ -55,7 +55,9 @@ typedef enum {
   FS_ENOMEM = 2,      /* device or pinned allocation failed                      */
   FS_ECUDA = 3,       /* a CUDA call failed; see fs_last_error                   */
   FS_EUNSUPPORTED = 4, /* size outside the compiled limits (see below)           */
-  FS_ENOCONV = 5       /* fs_forward: the fixed point did not converge            */
+  FS_ENOCONV = 5,      /* fs_forward: the fixed point did not converge            */
+  FS_ENONFINITE = 6    /* fs_sync_status: the last reconstruction met a non-finite
+                          value (NaN or Inf in W, or in a recovered xi)            */
 } fs_status;
 
 typedef enum {
@@ -119,6 +121,9 @@ typedef struct {
   long long n_refine_iters;  /* FS_MIXED: refinement sweeps performed                 */
   long long n_columns;       /* columns nu1 holding a nonzero mode, summed over omega:
                                 the inverse transform along y runs on these only       */
+  long long n_nonfinite;     /* modes whose ||W~_nu||^2 is not finite (W holds a NaN or
+                                Inf) plus voxels whose recovered xi is not finite; when
+                                nonzero the outputs of the call are unspecified         */
   float ms_stage[6];         /* with stage_timing: device milliseconds of the kernels
                                 [0] forward FFT along x, [1] forward FFT along y + mode
                                 norms, [2] mode classification, [3] per-mode solve,
@@ -263,8 +268,11 @@ fs_status fs_forward(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, co
    work is enqueued: for one frequency, 128 x 128 x 32 with 32 data planes fits in
    FS_MIXED, 128 x 128 x 64 does not, and 64 x 64 x 64 with 32 planes fits in FS_FP64.
    The first call on a device looks up the device address of that array
-   (cudaGetSymbolAddress) and keeps it; make that first call before any stream
-   capture.  Every call uses the same array: calls whose work overlaps on the GPU
+   (cudaGetSymbolAddress) and keeps it.  Under CUDA's lazy module loading that
+   lookup may itself load the library's device code onto the device, which
+   allocates device memory and can synchronise: make the first call on each
+   device during start-up, before any stream capture and before the phase in
+   which the caller may not allocate.  Every call uses the same array: calls whose work overlaps on the GPU
    (different streams, or different host threads without ordering) race and
    corrupt each other's results, so serialise them.  Other errors as for
    fs_reconstruct (FS_EINVAL, FS_EUNSUPPORTED, FS_ECUDA), without a message. */
@@ -275,6 +283,15 @@ fs_status fs_reconstruct_static(const fs_geometry* geom, fs_precision prec, cons
 /* Synchronise the context's stream and return the counters of the last
    fs_reconstruct call. */
 fs_status fs_get_report(fs_ctx* ctx, fs_report* report);
+
+/* Device-side status of the last fs_reconstruct (or fs_reconstruct_batch) call on
+   this context.  The calls return once their work is enqueued, so what the
+   kernels find is reported here: synchronises the context's stream, then returns
+   FS_ECUDA if the stream reports an error, FS_ENONFINITE if the call met a
+   non-finite value (fs_report.n_nonfinite > 0: a NaN or Inf in W makes delta_nu
+   undefined, so no mode is solved and xi, c are unspecified), and FS_OK
+   otherwise.  The message of fs_last_error says what was found. */
+fs_status fs_sync_status(fs_ctx* ctx);
 
 #ifdef __cplusplus
 }

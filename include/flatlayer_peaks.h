@@ -25,6 +25,18 @@ typedef struct {
    3 on a CUDA error. */
 int fs_measure_alu_peaks(int device, fs_alu_peaks* out);
 
+/* The scalar reciprocals the per-mode kernels use in place of FP64 division and
+   square root (Newton-Raphson iterations from FP32 seeds: rcp64 and rsqrt64 to FP64
+   accuracy, rcp32 and rsqrt32 to FP32 accuracy at any exponent), evaluated beside
+   CUDA's own 1.0/x and rsqrt(x), so that a test can compare them over the whole
+   exponent range.  The paper has no counterpart.
+     x    device, n doubles.
+     out  device, [6][n] doubles: rcp64(x), 1.0/x, rsqrt64(x), rsqrt(x), rcp32(x),
+          rsqrt32(x).
+   Asynchronous on `stream` (a cudaStream_t; NULL = the legacy default stream).
+   Returns 0 on success, 1 for a bad argument, 3 on a launch error. */
+int fs_eval_reciprocals(const double* x, int n, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,12 +14,12 @@ from dataclasses import dataclass
 from . import _abi
 from ._abi import (FORWARD_METHODS, FS_FP64, FS_MIXED, FlatLayerError, fs_create, fs_default_options, fs_destroy,
                    fs_forward, fs_forward_born, fs_get_report, fs_last_error, fs_reconstruct, fs_reconstruct_batch,
-                   fs_reconstruct_host, fs_reconstruct_static, fs_version, fs_workspace_size, make_geometry,
-                   make_options, make_problem)
+                   fs_reconstruct_host, fs_reconstruct_static, fs_sync_status, fs_version, fs_workspace_size,
+                   make_geometry, make_options, make_problem)
 
 __all__ = ["Geometry", "Reconstructor", "FS_FP64", "FS_MIXED", "FlatLayerError", "fs_create",
            "fs_default_options", "fs_destroy", "fs_forward", "fs_forward_born", "fs_get_report", "fs_last_error", "fs_reconstruct",
-           "fs_reconstruct_batch", "fs_reconstruct_host", "fs_reconstruct_static", "fs_version",
+           "fs_reconstruct_batch", "fs_reconstruct_host", "fs_reconstruct_static", "fs_sync_status", "fs_version",
            "fs_workspace_size", "make_geometry", "make_options", "make_problem"]
 
 PRECISIONS = {"fp64": FS_FP64, "mixed": FS_MIXED}
@@ -160,3 +160,7 @@ class Reconstructor:
 
     def report(self) -> dict:
         return fs_get_report(self.ctx)
+
+    def sync_status(self) -> int:
+        """fs_status of what the kernels of the last reconstruction found (synchronises)."""
+        return fs_sync_status(self.ctx)

@@ -12,14 +12,15 @@ import os
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libflatlayer.so")
 _lib = None
 
-FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED, FS_ENOCONV = 0, 1, 2, 3, 4, 5
+FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED, FS_ENOCONV, FS_ENONFINITE = 0, 1, 2, 3, 4, 5, 6
 FS_FP64, FS_MIXED = 0, 1
-STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_EUNSUPPORTED", 5: "FS_ENOCONV"}
+STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_EUNSUPPORTED", 5: "FS_ENOCONV",
+                6: "FS_ENONFINITE"}
 
 # every function declared in include/*.h
 EXPORTS = ("fs_version", "fs_default_options", "fs_create", "fs_destroy", "fs_last_error",
            "fs_workspace_size", "fs_reconstruct", "fs_reconstruct_host", "fs_forward_born", "fs_forward",
-           "fs_get_report", "fs_measure_alu_peaks", "fs_reconstruct_static", "fs_reconstruct_batch",
+           "fs_get_report", "fs_sync_status", "fs_measure_alu_peaks", "fs_eval_reciprocals", "fs_reconstruct_static", "fs_reconstruct_batch",
            "fs_diff_plan_create", "fs_diff_plan_destroy", "fs_diff_tape_bytes", "fs_diff_scratch_bytes",
            "fs_reconstruct_diff", "fs_reconstruct_vjp", "fs_reconstruct_jvp")
 
@@ -49,7 +50,8 @@ class fs_problem(C.Structure):
 class fs_report(C.Structure):
     _fields_ = [(k, C.c_longlong) for k in (
         "n_modes", "n_active", "n_zeroed", "n_grazing", "n_alpha_floor", "n_root_capped",
-        "n_u_guard", "n_nan_c", "n_fp64_fallback", "n_refine_iters", "n_columns")] + [("ms_stage", C.c_float * 6)]
+        "n_u_guard", "n_nan_c", "n_fp64_fallback", "n_refine_iters", "n_columns", "n_nonfinite")] + \
+        [("ms_stage", C.c_float * 6)]
 
     def as_dict(self):
         d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "ms_stage"}
@@ -113,6 +115,10 @@ def lib():
         L.fs_measure_alu_peaks.argtypes = [ip, C.POINTER(fs_alu_peaks)]
         L.fs_get_report.restype = ip
         L.fs_get_report.argtypes = [vp, C.POINTER(fs_report)]
+        L.fs_sync_status.restype = ip
+        L.fs_sync_status.argtypes = [vp]
+        L.fs_eval_reciprocals.restype = ip
+        L.fs_eval_reciprocals.argtypes = [vp, ip, vp, vp]
         L.fs_diff_plan_create.restype = ip
         L.fs_diff_plan_create.argtypes = [vp, C.POINTER(fs_geometry), ip, dp, ip, C.c_double, C.c_double,
                                           C.POINTER(vp)]
@@ -233,6 +239,16 @@ def fs_get_report(ctx) -> dict:
     st = lib().fs_get_report(ctx, C.byref(r))
     _check(ctx, st, "fs_get_report")
     return r.as_dict()
+
+
+def fs_sync_status(ctx) -> int:
+    """Device-side status of the last reconstruction (synchronises); returns the fs_status."""
+    return int(lib().fs_sync_status(ctx))
+
+
+def fs_eval_reciprocals(x_ptr, n, out_ptr, stream=0) -> int:
+    """The library's reciprocal helpers beside CUDA's 1/x and rsqrt (device pointers)."""
+    return int(lib().fs_eval_reciprocals(C.c_void_p(x_ptr), int(n), C.c_void_p(out_ptr), C.c_void_p(stream or None)))
 
 
 def make_geometry(n, m, z1, z2, zy, period=2.0):

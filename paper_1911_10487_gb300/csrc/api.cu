@@ -10,6 +10,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -92,18 +93,19 @@ fs_status cuda_fail(fs_ctx* ctx, cudaError_t e, const char* where) {
   return FS_ECUDA;
 }
 
-struct Layout {
-  size_t t12, prof, norms, partial, slot, act, flagbits, blkcnt, blkgz, colblk, cols, ncol, count, dnu, total;
-  int n_partial;
-};
+}  // namespace
+
+namespace fl {
 
 Layout layout(int n, int m, int m1, int n_omega, bool fp64) {
   const size_t cxs = fp64 ? 16 : 8;
   const size_t N2 = (size_t)n * n;
-  const size_t a = (size_t)n_omega * m1 * N2, b = (size_t)n_omega * 2 * m * N2;
+  // W~ in complex128 in both precisions (the mixed truncated-SVD route), then the
+  // y-inverse output in the working precision over it
+  const size_t a = 16 * (size_t)n_omega * m1 * N2, b = cxs * (size_t)n_omega * 2 * m * N2;
   Layout L;
   size_t off = 0;
-  L.t12 = off; off = align_up(off + cxs * (a > b ? a : b));  // W~, later the y-inverse pass output
+  L.t12 = off; off = align_up(off + (a > b ? a : b));  // W~, later the y-inverse pass output
   L.prof = off; off = align_up(off + cxs * (size_t)n_omega * N2 * 2 * m);
   L.norms = off; off = align_up(off + 8 * (size_t)n_omega * N2);
   L.n_partial = (int)((N2 + 255) / 256);
@@ -123,7 +125,7 @@ Layout layout(int n, int m, int m1, int n_omega, bool fp64) {
   return L;
 }
 
-fs_status validate(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, int n_omega, const double* omega,
+fs_status validate_args(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, int n_omega, const double* omega,
                    double delta, double c0, const fs_options* o) {
   if (!g) return fail(ctx, FS_EINVAL, "geometry is NULL");
   if (prec != FS_FP64 && prec != FS_MIXED) return fail(ctx, FS_EINVAL, "unknown precision");
@@ -194,6 +196,94 @@ Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, dou
   return P;
 }
 
+template <typename R>
+Work<R> carve_work(void* base, const Layout& L, unsigned long long* ctr, const cx<R>* tw, double* alpha_out) {
+  char* b = (char*)base;
+  Work<R> w;
+  w.wt = (cx<R>*)(b + L.t12);
+  w.t2 = (cx<R>*)(b + L.t12);
+  w.prof = (cx<R>*)(b + L.prof);
+  w.norms = (double*)(b + L.norms);
+  w.partial = (double*)(b + L.partial);
+  w.n_partial = L.n_partial;
+  w.slot = (int*)(b + L.slot);
+  w.act = (int*)(b + L.act);
+  w.flagbits = (unsigned*)(b + L.flagbits);
+  w.blkcnt = (int*)(b + L.blkcnt);
+  w.blkgz = (int*)(b + L.blkgz);
+  w.colblk = (unsigned*)(b + L.colblk);
+  w.cols = (int*)(b + L.cols);
+  w.ncol = (int*)(b + L.ncol);
+  w.count = (int*)(b + L.count);
+  w.dnu = (double*)(b + L.dnu);
+  w.ctr = ctr;
+  w.tw = tw;
+  w.alpha_out = alpha_out;
+  w.wt64 = nullptr;
+  w.tw64 = nullptr;
+  return w;
+}
+
+template Work<double> carve_work<double>(void*, const Layout&, unsigned long long*, const double2*, double*);
+template Work<float> carve_work<float>(void*, const Layout&, unsigned long long*, const float2*, double*);
+
+template <typename R>
+cudaError_t launch_pipeline(const Problem& P, const Work<R>& w, const void* W, void* xi, void* c, cudaStream_t s,
+                            cudaEvent_t* ev, const char** stage) {
+  cudaError_t e;
+  if (ev) cudaEventRecord(ev[0], s);
+  *stage = "fft2_forward";
+  if ((e = launch_fft2_forward<R>((const cx<R>*)W, P, w, s, ev ? ev[1] : nullptr)) != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[2], s);
+  *stage = "classify";
+  if ((e = launch_classify<R>(P, w, s)) != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[3], s);
+  *stage = "solve";
+  if (P.solve_form == 1) e = launch_solve_rank1<R>(P, w, s);
+  else if (sizeof(R) == 8) e = launch_solve_fp64(P, *(const Work<double>*)&w, s);
+  else e = launch_solve_mixed(P, *(const Work<float>*)&w, s);
+  if (e != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[4], s);
+  *stage = "recover";
+  if ((e = launch_recover<R>(P, w, (R*)xi, (R*)c, s, ev ? ev[5] : nullptr)) != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[6], s);
+  return cudaSuccess;
+}
+template cudaError_t launch_pipeline<double>(const Problem&, const Work<double>&, const void*, void*, void*,
+                                             cudaStream_t, cudaEvent_t*, const char**);
+template cudaError_t launch_pipeline<float>(const Problem&, const Work<float>&, const void*, void*, void*,
+                                            cudaStream_t, cudaEvent_t*, const char**);
+
+int sm_count() {
+  static std::atomic<int> cache[MAX_DEVICES];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int v = (dev >= 0 && dev < MAX_DEVICES) ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (v <= 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 152;
+    }
+    if (dev >= 0 && dev < MAX_DEVICES) cache[dev].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
+
+cudaError_t opt_in_smem(SmemOptIn& flag, const void* kernel, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = (dev >= 0 && dev < MAX_DEVICES) ? 1ull << dev : 0ull;
+  if (bit && (flag.done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && bit) flag.done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
+}  // namespace fl
+
+namespace {
+
 fs_status ensure_workspace(fs_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_bytes) return FS_OK;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -225,32 +315,6 @@ fs_status ensure_twiddles(fs_ctx* ctx, int n, const cx<R>** out) {
   return FS_OK;
 }
 
-template <typename R>
-Work<R> carve_work(void* base, const Layout& L, unsigned long long* ctr, const cx<R>* tw, double* alpha_out) {
-  char* b = (char*)base;
-  Work<R> w;
-  w.wt = (cx<R>*)(b + L.t12);
-  w.t2 = (cx<R>*)(b + L.t12);
-  w.prof = (cx<R>*)(b + L.prof);
-  w.norms = (double*)(b + L.norms);
-  w.partial = (double*)(b + L.partial);
-  w.n_partial = L.n_partial;
-  w.slot = (int*)(b + L.slot);
-  w.act = (int*)(b + L.act);
-  w.flagbits = (unsigned*)(b + L.flagbits);
-  w.blkcnt = (int*)(b + L.blkcnt);
-  w.blkgz = (int*)(b + L.blkgz);
-  w.colblk = (unsigned*)(b + L.colblk);
-  w.cols = (int*)(b + L.cols);
-  w.ncol = (int*)(b + L.ncol);
-  w.count = (int*)(b + L.count);
-  w.dnu = (double*)(b + L.dnu);
-  w.ctr = ctr;
-  w.tw = tw;
-  w.alpha_out = alpha_out;
-  return w;
-}
-
 // Enqueue the pipeline of one problem on `s` with workspace `base` (counters are
 // not reset here).  Twiddles for P.n must exist.
 template <typename R>
@@ -258,22 +322,13 @@ fs_status run_on(fs_ctx* ctx, const Problem& P, const Layout& L, void* base, cud
                  void* xi, void* c, double* alpha_out, cudaEvent_t* ev) {
   const cx<R>* tw = (const cx<R>*)ctx->tw[sizeof(R) == 8 ? 1 : 0][size_index(P.n)];
   Work<R> w = carve_work<R>(base, L, ctx->ctr, tw, alpha_out);
-  cudaError_t e;
-  if (ev) cudaEventRecord(ev[0], s);
-  if ((e = launch_fft2_forward<R>((const cx<R>*)W, P, w, s, ev ? ev[1] : nullptr)) != cudaSuccess)
-    return cuda_fail(ctx, e, "fft2_forward");
-  if (ev) cudaEventRecord(ev[2], s);
-  if ((e = launch_classify<R>(P, w, s)) != cudaSuccess) return cuda_fail(ctx, e, "classify");
-  if (ev) cudaEventRecord(ev[3], s);
-  if (P.solve_form == 1) e = launch_solve_rank1<R>(P, w, s);
-  else if (sizeof(R) == 8) e = launch_solve_fp64(P, *(const Work<double>*)&w, s);
-  else e = launch_solve_mixed(P, *(const Work<float>*)&w, s);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "solve");
-  if (ev) cudaEventRecord(ev[4], s);
-  if ((e = launch_recover<R>(P, w, (R*)xi, (R*)c, s, ev ? ev[5] : nullptr)) != cudaSuccess)
-    return cuda_fail(ctx, e, "recover");
-  if (ev) cudaEventRecord(ev[6], s);
-  return FS_OK;
+  if (wide_route(P, sizeof(R) == 8)) {
+    w.wt64 = (double2*)((char*)base + L.t12);
+    w.tw64 = (const double2*)ctx->tw[1][size_index(P.n)];
+  }
+  const char* stage = "";
+  const cudaError_t e = launch_pipeline<R>(P, w, W, xi, c, s, ev, &stage);
+  return e == cudaSuccess ? FS_OK : cuda_fail(ctx, e, stage);
 }
 
 template <typename R>
@@ -282,6 +337,10 @@ fs_status run(fs_ctx* ctx, const Problem& P, const Layout& L, const void* W, voi
   const cx<R>* tw = nullptr;
   fs_status st = ensure_twiddles<R>(ctx, P.n, &tw);
   if (st != FS_OK) return st;
+  if (wide_route(P, sizeof(R) == 8)) {
+    const double2* tw64 = nullptr;
+    if ((st = ensure_twiddles<double>(ctx, P.n, &tw64)) != FS_OK) return st;
+  }
   cudaError_t e = cudaMemsetAsync(ctx->ctr, 0, sizeof(unsigned long long) * C_COUNT, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
   ctx->timed = timed;
@@ -289,12 +348,6 @@ fs_status run(fs_ctx* ctx, const Problem& P, const Layout& L, const void* W, voi
 }
 
 }  // namespace
-
-namespace fl {
-size_t workspace_bytes(int n, int m, int m1, int n_omega, bool fp64) {
-  return layout(n, m, m1, n_omega, fp64).total;
-}
-}  // namespace fl
 
 extern "C" {
 
@@ -378,7 +431,7 @@ fs_status fs_reconstruct(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, c
                          int n_omega, double delta, double c0, const fs_options* opts, void* xi, void* c,
                          double* alpha_out) {
   if (!ctx) return FS_EINVAL;
-  fs_status st = validate(ctx, g, prec, n_omega, omega, delta, c0, opts);
+  fs_status st = validate_args(ctx, g, prec, n_omega, omega, delta, c0, opts);
   if (st != FS_OK) return st;
   if (!W || !xi) return fail(ctx, FS_EINVAL, "W and xi must be device pointers");
   fs_options o;
@@ -399,7 +452,7 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
                               const double* omega, int n_omega, double delta, double c0, const fs_options* opts,
                               void* xi_host, void* c_host) {
   if (!ctx) return FS_EINVAL;
-  fs_status st = validate(ctx, g, prec, n_omega, omega, delta, c0, opts);
+  fs_status st = validate_args(ctx, g, prec, n_omega, omega, delta, c0, opts);
   if (st != FS_OK) return st;
   if (!W_host || !xi_host) return fail(ctx, FS_EINVAL, "W_host and xi_host must be non-NULL");
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -504,7 +557,7 @@ fs_status fs_reconstruct_batch(fs_ctx* ctx, const fs_problem* probs, int n_probs
   size_t total = 0;
   for (int i = 0; i < n_probs; ++i) {
     const fs_problem& q = probs[i];
-    fs_status st = validate(ctx, &q.geom, prec, q.n_omega, q.omega, q.delta, q.c0, opts);
+    fs_status st = validate_args(ctx, &q.geom, prec, q.n_omega, q.omega, q.delta, q.c0, opts);
     if (st != FS_OK) {
       char m[256];
       snprintf(m, sizeof(m), "%s", ctx->err);
@@ -518,8 +571,10 @@ fs_status fs_reconstruct_batch(fs_ctx* ctx, const fs_problem* probs, int n_probs
   fs_status st = ensure_workspace(ctx, total);
   if (st != FS_OK) return st;
   for (int i = 0; i < n_probs; ++i) {
-    if (fp64) { const double2* t; st = ensure_twiddles<double>(ctx, probs[i].geom.n, &t); }
-    else { const float2* t; st = ensure_twiddles<float>(ctx, probs[i].geom.n, &t); }
+    const double2* t64;
+    const float2* t32;
+    if (fp64 || o.regularizer == 1) st = ensure_twiddles<double>(ctx, probs[i].geom.n, &t64);
+    if (st == FS_OK && !fp64) st = ensure_twiddles<float>(ctx, probs[i].geom.n, &t32);
     if (st != FS_OK) return st;
   }
   if (!ctx->fork_ev) {
@@ -575,7 +630,7 @@ fs_status fs_reconstruct_batch(fs_ctx* ctx, const fs_problem* probs, int n_probs
 fs_status fs_forward_born(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const void* xi,
                           const double* omega, int n_omega, double c0, void* W) {
   if (!ctx) return FS_EINVAL;
-  fs_status st = validate(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr);
+  fs_status st = validate_args(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr);
   if (st != FS_OK) return st;
   if (!xi || !W) return fail(ctx, FS_EINVAL, "xi and W must be device pointers");
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -602,7 +657,7 @@ fs_status fs_forward(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const
                      int n_omega, double c0, fs_forward_method method, int max_iter, double rtol, void* W, void* u,
                      int* iterations) {
   if (!ctx) return FS_EINVAL;
-  fs_status st = validate(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr);
+  fs_status st = validate_args(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr);
   if (st != FS_OK) return st;
   if (!xi || !W) return fail(ctx, FS_EINVAL, "xi and W must be device pointers");
   if (max_iter < 0) return fail(ctx, FS_EINVAL, "max_iter must be >= 0");
@@ -657,11 +712,25 @@ fs_status fs_get_report(fs_ctx* ctx, fs_report* r) {
   r->n_fp64_fallback = (long long)h[C_FP64_FALLBACK];
   r->n_refine_iters = (long long)h[C_REFINE_ITERS];
   r->n_columns = (long long)h[C_COLUMNS];
+  r->n_nonfinite = (long long)h[C_NONFINITE];
   for (int i = 0; i < 6; ++i) {
     float ms = 0.f;
     if (ctx->timed && cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) ms = 0.f;
     r->ms_stage[i] = ms;
   }
+  return FS_OK;
+}
+
+fs_status fs_sync_status(fs_ctx* ctx) {
+  if (!ctx) return FS_EINVAL;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->ctr_host, ctx->ctr, sizeof(unsigned long long) * C_COUNT, cudaMemcpyDeviceToHost,
+                        ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fs_sync_status");
+  const unsigned long long nf = ctx->ctr_host[C_NONFINITE];
+  if (nf) return fail(ctx, FS_ENONFINITE, "%llu non-finite values (modes of W~ or voxels of xi)", nf);
   return FS_OK;
 }
 
@@ -840,7 +909,7 @@ fs_status fs_diff_plan_create(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
                               int n_omega, double c0, double eps_u, fs_diff_plan** out) {
   if (!ctx || !out) return FS_EINVAL;
   *out = nullptr;
-  fs_status st = validate(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr);
+  fs_status st = validate_args(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr);
   if (st != FS_OK) return st;
   if (!(eps_u >= 0.0)) return fail(ctx, FS_EINVAL, "eps_u must be >= 0");
   cudaError_t e = cudaSetDevice(ctx->device);

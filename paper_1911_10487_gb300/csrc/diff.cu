@@ -544,24 +544,10 @@ __global__ void k_reduce_rows(const double* __restrict__ partial, int rows, int 
   out[r] = s;
 }
 
-int sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
-  return sms;
-}
-
-// opt in to more than 48 KB of dynamic shared memory (once per kernel; the flag
-// is per instantiation because each caller below is a distinct template/kernel)
-template <typename K> cudaError_t allow_smem(K kernel, size_t bytes, bool& done) {
-  if (done) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  done = e == cudaSuccess;
-  return e;
+// opt in to more than 48 KB of dynamic shared memory, once per kernel and device
+// (the flag is per call site: each caller below launches a distinct kernel)
+template <typename K> cudaError_t allow_smem(K kernel, size_t bytes, SmemOptIn& flag) {
+  return opt_in_smem(flag, (const void*)kernel, bytes);
 }
 
 unsigned point_grid(long long n) {
@@ -582,7 +568,7 @@ int diff_blocks_per_omega(int n, int n_omega) {
 
 cudaError_t launch_diff_gram(const Problem& P, double2* gram, cudaStream_t s) {
   const size_t smem = sizeof(GramMem);
-  static bool done = false;
+  static SmemOptIn done;
   cudaError_t e = allow_smem(k_diff_gram, smem, done);
   if (e != cudaSuccess) return e;
   const long long total = (long long)P.n * P.n * P.n_omega;
@@ -596,7 +582,7 @@ cudaError_t launch_diff_forward(const Problem& P, int gb, const double2* gram, c
                                 const double* log_alpha, double2* Ls, double2* ys, cx<R>* vt, cx<R>* ut,
                                 double* partial, unsigned long long* ctr, cudaStream_t s) {
   const size_t smem = sizeof(WarpMem) * DW;
-  static bool done = false;
+  static SmemOptIn done;
   cudaError_t e = allow_smem(k_diff_forward<R>, smem, done);
   if (e != cudaSuccess) return e;
   k_diff_forward<R><<<dim3(gb, P.n_omega), DW * 32, smem, s>>>(P, gram, wt, log_alpha, Ls, ys, vt, ut, partial, ctr);
@@ -608,7 +594,7 @@ cudaError_t launch_diff_vjp(const Problem& P, int gb, const double2* Ls, const d
                             const cx<R>* ubt, const double* log_alpha, const double* grad_phi, cx<R>* wbt,
                             double* partial, cudaStream_t s) {
   const size_t smem = sizeof(WarpMem) * DW;
-  static bool done = false;
+  static SmemOptIn done;
   cudaError_t e = allow_smem(k_diff_vjp<R>, smem, done);
   if (e != cudaSuccess) return e;
   k_diff_vjp<R><<<dim3(gb, P.n_omega), DW * 32, smem, s>>>(P, Ls, ys, vbt, ubt, log_alpha, grad_phi, wbt, partial);
@@ -621,7 +607,7 @@ cudaError_t launch_diff_jvp(const Problem& P, int gb, int nd, const double2* Ls,
                             cx<R>* dut, double* partial, cudaStream_t s) {
   if (nd < 1 || nd > JVP_CHUNK) return cudaErrorInvalidValue;
   const size_t smem = sizeof(WarpMem) * DW;
-  static bool done = false;
+  static SmemOptIn done;
   cudaError_t e = allow_smem(k_diff_jvp<R>, smem, done);
   if (e != cudaSuccess) return e;
   k_diff_jvp<R><<<dim3(gb, P.n_omega), DW * 32, smem, s>>>(P, nd, Ls, ys, dwt, log_alpha, dlog_alpha, dvt, dut,

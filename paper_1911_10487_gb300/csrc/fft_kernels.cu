@@ -12,6 +12,8 @@
 //                   row pass scatters those columns and transforms full rows.
 #include <math.h>
 
+#include <type_traits>
+
 #include "fft.cuh"
 #include "modes.cuh"
 #include "pipeline.cuh"
@@ -40,9 +42,10 @@ __device__ __forceinline__ void load_twiddles(cx<R>* tw_s, const cx<R>* __restri
 }
 
 // ---- dense pass along x (rows): forward, or inverse with 1/N^2 scaling --------
-template <typename R, int N, bool INV>
+// TI: element type of `in` (cx<R>, or float2 read into an FP64 transform)
+template <typename R, int N, bool INV, typename TI = cx<R>>
 __global__ void __launch_bounds__(THREADS)
-k_fft_rows(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, long long nrows,
+k_fft_rows(const TI* __restrict__ in, cx<R>* __restrict__ out, long long nrows,
            const cx<R>* __restrict__ tw, R scale) {
   pdl_wait();
   pdl_trigger();
@@ -54,8 +57,14 @@ k_fft_rows(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, long long nrow
   const long long row0 = (long long)blockIdx.x * LINES;
   const long long base = row0 * N;
   const long long limit = nrows * N;
-  for (int e = threadIdx.x; e < LINES * N; e += THREADS)
-    buf[IX::at(e / N, e % N)] = (base + e < limit) ? in[base + e] : czero<R>();
+  for (int e = threadIdx.x; e < LINES * N; e += THREADS) {
+    cx<R> v = czero<R>();
+    if (base + e < limit) {
+      if constexpr (std::is_same<TI, cx<R>>::value) v = in[base + e];
+      else v = from_d<R>(to_d(in[base + e]));
+    }
+    buf[IX::at(e / N, e % N)] = v;
+  }
   __syncthreads();
   fft_lines<R, N, INV, LINES, THREADS, Lay::ROW, RADIX_ROWS, SKEW_ROWS>(buf, tw_s);
   for (int e = threadIdx.x; e < LINES * N; e += THREADS)
@@ -98,7 +107,7 @@ constexpr int NORM_T = 256;
 template <typename R>
 __global__ void __launch_bounds__(NORM_T)
 k_mode_norms(const cx<R>* __restrict__ wt, double* __restrict__ norms, double* __restrict__ partial, int m1,
-             int N2) {
+             int N2, unsigned long long* __restrict__ ctr) {
   pdl_wait();
   pdl_trigger();
   __shared__ double red[NORM_T];
@@ -124,7 +133,10 @@ k_mode_norms(const cx<R>* __restrict__ wt, double* __restrict__ norms, double* _
     norms[(long long)om * N2 + nu] = (double)acc;
   }
   red[threadIdx.x] = (double)acc;
-  __syncthreads();
+  // modes whose norm is not finite (a NaN or Inf in W), counted at the barrier
+  // the reduction needs anyway
+  const int n_bad = __syncthreads_count(nu < N2 && !isfinite(acc));
+  if (n_bad && threadIdx.x == 0) atomicAdd(ctr + C_NONFINITE, (unsigned long long)n_bad);
   for (int h = NORM_T / 2; h > 0; h >>= 1) {
     if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
     __syncthreads();
@@ -297,7 +309,7 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
   }
   const R guard = R(P.u_guard);  // host-derived: no FP64 division on the device
   const R inv_c02 = R(P.inv_c02);
-  unsigned n_guard = 0, n_nan = 0;
+  unsigned n_guard = 0, n_nan = 0, n_bad = 0;
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * THREADS;
@@ -307,6 +319,7 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
         const bool g = !(den[p] >= guard);
         const R x = g ? R(0) : quot<R>(num[p], den[p]);
         n_guard += g;
+        n_bad += !isfinite(x);
         const long long o = r * N + (e % N);
         xi[o] = x;
         if (cout) {
@@ -317,14 +330,18 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
       }
     }
   }
-  // the counters of guarded and NaN voxels: almost always zero, so one barrier decides
-  if (__syncthreads_or((n_guard | n_nan) != 0u)) {
+  // the counters of guarded, NaN-c and non-finite voxels: almost always zero, so one
+  // barrier decides
+  if (__syncthreads_or((n_guard | n_nan | n_bad) != 0u)) {
     const unsigned long long sg = block_sum_u64(n_guard, red);
     __syncthreads();
     const unsigned long long sn = block_sum_u64(n_nan, red);
+    __syncthreads();
+    const unsigned long long sb = block_sum_u64(n_bad, red);
     if (threadIdx.x == 0) {
       if (sg) atomicAdd(ctr + C_U_GUARD, sg);
       if (sn) atomicAdd(ctr + C_NAN_C, sn);
+      if (sb) atomicAdd(ctr + C_NONFINITE, sb);
     }
   }
 }
@@ -339,8 +356,32 @@ __global__ void k_twiddles(cx<R>* tw, int n) {
   }
 }
 
+// W (complex64) -> W~ (complex128 in w.wt64) and the norms: the forward transform
+// of the mixed truncated-SVD route, in FP64
+template <int N>
+cudaError_t fwd_wide_impl(const float2* W, const Problem& P, const Work<float>& w, cudaStream_t s, cudaEvent_t mid) {
+  constexpr int LINES = row_lines<N>();
+  const long long nrows = (long long)P.n_omega * P.m1 * N;
+  const long long nblk = (nrows + LINES - 1) / LINES;
+  cudaError_t e = launch_pdl(k_fft_rows<double, N, false, float2>, dim3((unsigned)nblk), dim3(THREADS), 0, s, W,
+                             w.wt64, nrows, w.tw64, 1.0);
+  if (e != cudaSuccess) return e;
+  if (mid) cudaEventRecord(mid, s);
+  const dim3 g2((N + Cfg<double>::TC - 1) / Cfg<double>::TC, (unsigned)(P.n_omega * P.m1));
+  e = launch_pdl(k_fft_cols<double, N, false>, g2, dim3(THREADS), 0, s, w.wt64, w.tw64);
+  if (e != cudaSuccess) return e;
+  const dim3 gn((unsigned)w.n_partial, (unsigned)P.n_omega);
+  e = launch_pdl(k_mode_norms<double>, gn, dim3(NORM_T), 0, s, (const double2*)w.wt64, w.norms, w.partial, P.m1,
+                 N * N, w.ctr);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 template <typename R, int N>
 cudaError_t fwd_impl(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStream_t s, cudaEvent_t mid) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (w.wt64) return fwd_wide_impl<N>(W, P, w, s, mid);
+  }
   constexpr int LINES = row_lines<N>();
   const long long nrows = (long long)P.n_omega * P.m1 * N;
   const long long nblk = (nrows + LINES - 1) / LINES;
@@ -352,7 +393,8 @@ cudaError_t fwd_impl(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStr
   e = launch_pdl(k_fft_cols<R, N, false>, g2, dim3(THREADS), 0, s, w.wt, (const cx<R>*)w.tw);
   if (e != cudaSuccess) return e;
   const dim3 gn((unsigned)w.n_partial, (unsigned)P.n_omega);
-  e = launch_pdl(k_mode_norms<R>, gn, dim3(NORM_T), 0, s, (const cx<R>*)w.wt, w.norms, w.partial, P.m1, N * N);
+  e = launch_pdl(k_mode_norms<R>, gn, dim3(NORM_T), 0, s, (const cx<R>*)w.wt, w.norms, w.partial, P.m1, N * N,
+                 w.ctr);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

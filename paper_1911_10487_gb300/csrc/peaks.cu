@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/flatlayer_peaks.h"
+#include "modes.cuh"
 
 namespace {
 
@@ -42,7 +43,27 @@ __global__ void k_lat(long long* cycles, double* out, int iters, int lanes, doub
   if (x == 12345.678) out[0] = x;
 }
 
+// the library's reciprocal helpers beside CUDA's own operations, one input per thread
+__global__ void k_eval_reciprocals(const double* __restrict__ x, int n, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  out[0 * (long long)n + i] = fl::rcp64(v);
+  out[1 * (long long)n + i] = 1.0 / v;
+  out[2 * (long long)n + i] = fl::rsqrt64(v);
+  out[3 * (long long)n + i] = rsqrt(v);
+  out[4 * (long long)n + i] = fl::rcp32(v);
+  out[5 * (long long)n + i] = fl::rsqrt32(v);
+}
+
 }  // namespace
+
+extern "C" int fs_eval_reciprocals(const double* x, int n, double* out, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return 1;
+  if (n == 0) return 0;
+  k_eval_reciprocals<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, n, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
 
 extern "C" int fs_measure_alu_peaks(int device, fs_alu_peaks* r) {
   if (!r) return 1;

@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
+#include "../../include/flatlayer.h"
 #include "common.cuh"
 
 namespace fl {
@@ -77,12 +80,64 @@ template <typename R> struct Work {
   unsigned long long* ctr;  // [C_COUNT]
   const cx<R>* tw;  // [N] twiddles exp(-2 pi i j/N)
   double* alpha_out;  // [n_omega][N*N] or null
+  // FP32 data transformed in FP64 (the truncated-SVD route of the mixed precision,
+  // whose pseudo-inverse passes the rounding of W~ through undamped): when set, the
+  // forward transform reads the complex64 W, writes W~ here in complex128 (over the
+  // start of the t12 region, sized for it by layout) with the FP64
+  // twiddles tw64, and the solve reads b from here.  Null otherwise.
+  double2* wt64;
+  const double2* tw64;
 };
 
-size_t workspace_bytes(int n, int m, int m1, int n_omega, bool fp64);
 // blocks of 1024 consecutive modes in the classification of an N x N grid
 inline int classify_blocks(int n) { return (n * n + 1023) / 1024; }
-template <typename R> Work<R> carve(void* base, int n, int m, int m1, int n_omega);
+
+// Workspace of one problem: byte offsets (multiples of 256) of every Work array
+// from the base of the workspace, and its total size.  The context entry points
+// and the allocation-free entry point carve their workspace from this one layout.
+struct Layout {
+  size_t t12, prof, norms, partial, slot, act, flagbits, blkcnt, blkgz, colblk, cols, ncol, count, dnu, total;
+  int n_partial;
+};
+// (the W~ part of the t12 region is sized for complex128 in both precisions, so
+// that the mixed truncated-SVD route can hold W~ in FP64: Work::wt64)
+Layout layout(int n, int m, int m1, int n_omega, bool fp64);
+// the Work views of a workspace laid out by `L` at `base`; counters, twiddles and the
+// alpha output live elsewhere and are passed in
+template <typename R>
+Work<R> carve_work(void* base, const Layout& L, unsigned long long* ctr, const cx<R>* tw, double* alpha_out);
+
+// The kernels of Algorithm 2 for one problem, enqueued on `s`: forward transform,
+// classification, per-mode solve, inverse transform and recovery.  With `ev` (7
+// events) the boundaries of the stages are recorded.  On failure *stage names the
+// stage whose launch failed.
+template <typename R>
+cudaError_t launch_pipeline(const Problem& P, const Work<R>& w, const void* W, void* xi, void* c, cudaStream_t s,
+                            cudaEvent_t* ev, const char** stage);
+
+// The mixed-precision truncated SVD transforms its (complex64) data in FP64: the
+// pseudo-inverse damps nothing, so FP32 rounding of W~ would reach V~ amplified by
+// the inverse of each mode's singular value.
+inline bool wide_route(const Problem& P, bool fp64) { return !fp64 && P.regularizer == 1; }
+
+// Argument checks shared by the entry points (the rules of include/flatlayer.h).
+// ctx may be null: the status is returned without a message.
+fs_status validate_args(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, int n_omega, const double* omega,
+                        double delta, double c0, const fs_options* o);
+// The by-value problem description of validated arguments.
+Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, double delta, double c0,
+                     const fs_options& o);
+
+// Launch facts kept per device, since one process may drive several GPUs:
+//   sm_count()    SM count of the current device (looked up once per device)
+//   opt_in_smem() cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for `kernel`,
+//                 done once per device; `flag` is the call site's own record
+constexpr int MAX_DEVICES = 64;
+int sm_count();
+struct SmemOptIn {
+  std::atomic<unsigned long long> done{0};  // bit d: set on device d
+};
+cudaError_t opt_in_smem(SmemOptIn& flag, const void* kernel, size_t bytes);
 
 // Launchers (return the launch error).
 // `mid` (may be null) is recorded on `s` between the two kernels of the stage

@@ -118,7 +118,9 @@ k_classify_flags(Problem P, const double* __restrict__ norms, const double* __re
       const double wnorm = sqrt(s / (double)N2);
       const double dnu = P.tau * fmax(P.delta, P.delta_floor) * wnorm;
       if (b == 0) dnu_out[om] = dnu;
-      thr_bits = __double_as_longlong(dnu * dnu);
+      // a non-finite ||W|| (W holds a NaN or Inf, counted by the norms kernel) leaves
+      // delta_nu undefined: no mode passes the test
+      thr_bits = isfinite(dnu) ? __double_as_longlong(dnu * dnu) : 0x7fffffffffffffffLL;
     }
   }
   __syncthreads();
@@ -1061,27 +1063,14 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
   }
 }
 
-int solve_grid(int bps) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
-  return (bps < 1 ? 1 : (bps > 3 ? 3 : bps)) * sms;
-}
+int solve_grid(int bps) { return (bps < 1 ? 1 : (bps > 3 ? 3 : bps)) * sm_count(); }
 
 template <typename B, bool MIXED>
 cudaError_t solve_impl(const Problem& P, const Work<B>& w, cudaStream_t s) {
   const size_t smem = sizeof(Shared);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve<B, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static SmemOptIn attr;
+  cudaError_t e = opt_in_smem(attr, (const void*)k_solve<B, MIXED>, smem);
+  if (e != cudaSuccess) return e;
   return launch_pdl(k_solve<B, MIXED>, dim3(solve_grid(P.solve_bps)), dim3(ST), smem, s, P, (const cx<B>*)w.wt,
                     (const int*)w.act, (const int*)w.count, (const double*)w.dnu, w.prof, w.alpha_out, w.ctr);
 }

@@ -37,7 +37,8 @@ struct Rank1Mem {
 
 template <typename R>
 __global__ void __launch_bounds__(RW * 32)
-k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const int* __restrict__ act, const int* __restrict__ count,
+k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict__ wt64,
+              const int* __restrict__ act, const int* __restrict__ count,
               const double* __restrict__ dnu_arr, cx<R>* __restrict__ prof, double* __restrict__ alpha_out,
               unsigned long long* __restrict__ ctr) {
   pdl_wait();
@@ -68,7 +69,8 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const int* __restrict__ a
     double2 e = make_double2(0, 0), b = make_double2(0, 0);
     if (lane < n) {
       e = gamma * exp_ikz_inline(kz, P.zy[lane] - ztop);
-      b = to_d(wt[((long long)om * n + lane) * N2 + nu]);
+      const long long at = ((long long)om * n + lane) * N2 + nu;
+      b = wt64 ? wt64[at] : to_d(wt[at]);  // W~ in FP64 on the mixed truncated-SVD route
     }
     const int l0 = lane, l1 = lane + 32;
     const double2 p0 = l0 < m ? exp_ikz_inline(kz, ztop - (P.z1 + (l0 + 0.5) * P.hz)) : make_double2(0, 0);
@@ -149,18 +151,13 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const int* __restrict__ a
 
 template <typename R>
 cudaError_t launch_solve_rank1(const Problem& P, const Work<R>& w, cudaStream_t s) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
+  const int sms = sm_count();
   const long long modes = (long long)P.n_omega * P.n * P.n;
   const long long want = (modes + RW - 1) / RW;
   const long long cap = 8LL * sms;
   const unsigned grid = (unsigned)(want < cap ? want : cap);
-  return launch_pdl(k_solve_rank1<R>, dim3(grid), dim3(RW * 32), 0, s, P, (const cx<R>*)w.wt, (const int*)w.act,
+  return launch_pdl(k_solve_rank1<R>, dim3(grid), dim3(RW * 32), 0, s, P, (const cx<R>*)w.wt,
+                    (const double2*)w.wt64, (const int*)w.act,
                     (const int*)w.count, (const double*)w.dnu, w.prof, w.alpha_out, w.ctr);
 }
 

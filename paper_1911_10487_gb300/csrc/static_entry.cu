@@ -5,9 +5,9 @@
 // caller that may not synchronise the device, which a first cudaMalloc can do).
 // The caller passes inputs and outputs; every intermediate array lives in one
 // file-scope device array of fixed size, so this entry point allocates nothing.
-#include <math.h>
+// Argument checks, the problem set-up, the workspace layout and the launch
+// sequence are those of fs_reconstruct (api.cu); only the memory differs.
 #include <mutex>
-#include <string.h>
 
 #include <cuda_runtime.h>
 
@@ -19,7 +19,7 @@ using namespace fl;
 namespace {
 
 constexpr size_t STATIC_SCRATCH_BYTES = size_t(32) << 20;  // FS_STATIC_SCRATCH_BYTES in the header
-constexpr int MAX_DEVICES = 64;
+static_assert(STATIC_SCRATCH_BYTES == (size_t)FS_STATIC_SCRATCH_BYTES, "scratch size of the header");
 
 // Scratch shared by every call on a device: intermediates, counters, twiddles.
 // Host code must not pass this symbol to a kernel (on the host it names a
@@ -37,57 +37,45 @@ fs_status scratch_address(int dev, unsigned char** out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return FS_ECUDA;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return FS_ECUDA;
+    }
     g_scratch_addr[dev] = p;
   }
   *out = (unsigned char*)g_scratch_addr[dev];
   return FS_OK;
 }
 
+// bytes of scratch a problem needs: the fs_reconstruct workspace, then the counters,
+// the twiddle table and the FP64 twiddles of the mixed truncated-SVD route
+size_t static_bytes(const Layout& L, int n, bool fp64, size_t* ctr_off, size_t* tw_off, size_t* tw64_off) {
+  *ctr_off = L.total;
+  *tw_off = up(*ctr_off + sizeof(unsigned long long) * C_COUNT);
+  *tw64_off = up(*tw_off + (fp64 ? 16 : 8) * (size_t)n);
+  return up(*tw64_off + 16 * (size_t)n);
+}
+
 template <typename R>
-fs_status run_static(const Problem& P, unsigned char* base, const void* W, void* xi, void* c, cudaStream_t s) {
-  const size_t cxs = sizeof(cx<R>);
-  const size_t N2 = (size_t)P.n * P.n;
-  const size_t F = (size_t)P.n_omega;
-  const size_t a = F * P.m1 * N2, b = F * 2 * P.m * N2;
-  const int n_partial = (int)((N2 + 255) / 256);
-  Work<R> w;
-  size_t off = 0;
-  w.wt = (cx<R>*)(base + off);
-  w.t2 = w.wt;
-  off = up(off + cxs * (a > b ? a : b));
-  w.prof = (cx<R>*)(base + off); off = up(off + cxs * F * N2 * 2 * P.m);
-  w.norms = (double*)(base + off); off = up(off + 8 * F * N2);
-  w.partial = (double*)(base + off); off = up(off + 8 * F * n_partial);
-  w.n_partial = n_partial;
-  w.slot = (int*)(base + off); off = up(off + 4 * F * N2);
-  w.act = (int*)(base + off); off = up(off + 4 * F * N2);
-  const size_t cb = F * classify_blocks(P.n);
-  w.flagbits = (unsigned*)(base + off); off = up(off + 4 * cb * 32);
-  w.blkcnt = (int*)(base + off); off = up(off + 4 * cb);
-  w.blkgz = (int*)(base + off); off = up(off + 4 * cb);
-  w.colblk = (unsigned*)(base + off); off = up(off + 4 * cb * 8);
-  w.cols = (int*)(base + off); off = up(off + 4 * F * P.n);
-  w.ncol = (int*)(base + off); off = up(off + 4 * F);
-  w.count = (int*)(base + off); off = up(off + 4 * F);
-  w.dnu = (double*)(base + off); off = up(off + 8 * F);
-  w.ctr = (unsigned long long*)(base + off); off = up(off + sizeof(unsigned long long) * C_COUNT);
-  cx<R>* tw = (cx<R>*)(base + off); off = up(off + cxs * P.n);
-  if (off > STATIC_SCRATCH_BYTES) return FS_EUNSUPPORTED;
-  w.tw = tw;
-  w.alpha_out = nullptr;
+fs_status run_static(const Problem& P, const Layout& L, unsigned char* base, const void* W, void* xi, void* c,
+                     cudaStream_t s) {
+  size_t ctr_off, tw_off, tw64_off;
+  static_bytes(L, P.n, sizeof(R) == 8, &ctr_off, &tw_off, &tw64_off);
+  unsigned long long* ctr = (unsigned long long*)(base + ctr_off);
+  cx<R>* tw = (cx<R>*)(base + tw_off);
+  Work<R> w = carve_work<R>(base, L, ctr, tw, nullptr);
   // the scratch keeps the previous call's contents: the counters start at zero,
   // the twiddles are rewritten for this N and precision
-  if (cudaMemsetAsync(w.ctr, 0, sizeof(unsigned long long) * C_COUNT, s) != cudaSuccess) return FS_ECUDA;
+  if (cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * C_COUNT, s) != cudaSuccess) return FS_ECUDA;
   if (launch_twiddles<R>(tw, P.n, s) != cudaSuccess) return FS_ECUDA;
-  if (launch_fft2_forward<R>((const cx<R>*)W, P, w, s) != cudaSuccess) return FS_ECUDA;
-  if (launch_classify<R>(P, w, s) != cudaSuccess) return FS_ECUDA;
-  cudaError_t e = P.solve_form == 1 ? launch_solve_rank1<R>(P, w, s)
-                  : sizeof(R) == 8   ? launch_solve_fp64(P, *(const Work<double>*)&w, s)
-                                     : launch_solve_mixed(P, *(const Work<float>*)&w, s);
-  if (e != cudaSuccess) return FS_ECUDA;
-  if (launch_recover<R>(P, w, (R*)xi, (R*)c, s) != cudaSuccess) return FS_ECUDA;
-  return FS_OK;
+  if (wide_route(P, sizeof(R) == 8)) {
+    double2* tw64 = (double2*)(base + tw64_off);
+    if (launch_twiddles<double>(tw64, P.n, s) != cudaSuccess) return FS_ECUDA;
+    w.wt64 = (double2*)(base + L.t12);
+    w.tw64 = tw64;
+  }
+  const char* stage = "";
+  return launch_pipeline<R>(P, w, W, xi, c, s, nullptr, &stage) == cudaSuccess ? FS_OK : FS_ECUDA;
 }
 
 }  // namespace
@@ -95,56 +83,21 @@ fs_status run_static(const Problem& P, unsigned char* base, const void* W, void*
 extern "C" fs_status fs_reconstruct_static(const fs_geometry* g, fs_precision prec, const void* W,
                                            const double* omega, int n_omega, double delta, double c0,
                                            const fs_options* opts, void* xi, void* c, void* stream) {
-  if (!g || !W || !xi || !omega || !g->zy) return FS_EINVAL;
-  if (prec != FS_FP64 && prec != FS_MIXED) return FS_EINVAL;
-  if (g->n <= 0 || g->m <= 0 || g->m1 <= 0 || n_omega <= 0) return FS_EINVAL;
-  if (!fft_size_supported(g->n) || g->m > MAX_M || g->m1 > MAX_M1 || n_omega > MAX_OMEGA) return FS_EUNSUPPORTED;
-  if (!(g->period > 0.0) || !(g->z2 > g->z1) || !(delta >= 0.0) || !(c0 > 0.0)) return FS_EINVAL;
-  for (int k = 0; k < g->m1; ++k)
-    if (!(g->zy[k] > g->z2)) return FS_EINVAL;
-  for (int j = 0; j < n_omega; ++j)
-    if (!(omega[j] > 0.0)) return FS_EINVAL;
+  fs_status st = validate_args(nullptr, g, prec, n_omega, omega, delta, c0, opts);
+  if (st != FS_OK) return st;
+  if (!W || !xi) return FS_EINVAL;
+  const bool fp64 = prec == FS_FP64;
+  const Layout L = layout(g->n, g->m, g->m1, n_omega, fp64);
+  size_t ctr_off, tw_off, tw64_off;
+  if (static_bytes(L, g->n, fp64, &ctr_off, &tw_off, &tw64_off) > STATIC_SCRATCH_BYTES) return FS_EUNSUPPORTED;
   fs_options o;
   fs_default_options(&o);
   if (opts) o = *opts;
-  if (!(o.tau > 0.0) || !(o.delta_floor >= 0.0) || !(o.alpha_rel > 0.0) || !(o.eps_u >= 0.0) ||
-      o.max_iter < 1 || o.refine_iters < 1 || (o.alpha_mode != 0 && o.alpha_mode != 1))
-    return FS_EINVAL;
-  if (o.solve_form != 0 && o.solve_form != 1) return FS_EINVAL;
-  if (o.regularizer != 0 && o.regularizer != 1) return FS_EINVAL;
-  if (o.regularizer == 1 && o.solve_form != 1) return FS_EUNSUPPORTED;
-  if (o.regularizer == 1 && o.alpha_mode != 0) return FS_EINVAL;
-  if (o.alpha_mode == 1) {
-    if (!o.alpha_given) return FS_EINVAL;
-    for (int j = 0; j < n_omega; ++j)
-      if (!(o.alpha_given[j] > 0.0)) return FS_EINVAL;
-  }
-  Problem P;
-  memset(&P, 0, sizeof(P));
-  P.n = g->n; P.m = g->m; P.m1 = g->m1; P.n_omega = n_omega;
-  P.alpha_mode = o.alpha_mode; P.max_iter = o.max_iter; P.refine_iters = o.refine_iters;
-  P.period = g->period; P.z1 = g->z1; P.hz = (g->z2 - g->z1) / g->m; P.c0 = c0;
-  P.delta = delta; P.tau = o.tau; P.delta_floor = o.delta_floor; P.alpha_rel = o.alpha_rel; P.eps_u = o.eps_u;
-  P.fp64_switch = o.fp64_switch;
-  P.solve_bps = (o.solve_blocks_per_sm >= 1 && o.solve_blocks_per_sm <= 3) ? o.solve_blocks_per_sm : 2;
-  P.solve_form = o.solve_form;
-  P.regularizer = o.regularizer;
-  for (int k = 0; k < g->m1; ++k) P.zy[k] = g->zy[k];
-  for (int j = 0; j < n_omega; ++j) {
-    P.omega[j] = omega[j];
-    P.alpha_given[j] = o.alpha_mode == 1 ? o.alpha_given[j] : 0.0;
-    const double sL = omega[j] / c0 * g->period / (2.0 * M_PI);
-    const double s2 = sL * sL;
-    const double lo = ceil(s2 - 1e-9 * s2), hi = floor(s2 + 1e-9 * s2);
-    P.graz_lo[j] = lo > 1e9 ? 1000000001 : (int)lo;
-    P.graz_hi[j] = hi > 1e9 ? 1000000000 : (int)hi;
-  }
-  derive_constants(P);
+  const Problem P = make_problem(g, n_omega, omega, delta, c0, o);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FS_ECUDA;
   unsigned char* base = nullptr;
-  fs_status st = scratch_address(dev, &base);
-  if (st != FS_OK) return st;
+  if ((st = scratch_address(dev, &base)) != FS_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  return prec == FS_FP64 ? run_static<double>(P, base, W, xi, c, s) : run_static<float>(P, base, W, xi, c, s);
+  return fp64 ? run_static<double>(P, L, base, W, xi, c, s) : run_static<float>(P, L, base, W, xi, c, s);
 }

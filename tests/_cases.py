@@ -21,8 +21,20 @@ def case(name: str, delta: float = 0.01, method: str = "gmres"):
     if name in ("c1", "c2", "c5"):
         w = workload(name)
         g = Geometry(w.n, w.m, w.z1, w.z2, tuple(w.zy))
-        W, _ = forward.make_data(w.xi, w.omegas, g, method=method)
+        # the 128^2 x 64 workloads take single-scattering data (as the bench does): a
+        # CPU full-scattering solve at that size takes many minutes
+        W, _ = forward.make_data(w.xi, w.omegas, g, method="born" if w.n >= 128 else method)
         return g, np.array(w.omegas), forward.add_noise(W, delta, w.noise()), w.xi
+    if name == "thin256":
+        # the thin data layer of Sec. 5.4: two planes 0.01 apart (the paper's
+        # [6.01, 6.02] above X), here 0.2 above the X box of the workloads
+        g = geometry(256, 6, 2, z3=1.2, z4=1.21)
+        om = [2 * np.pi, 3 * np.pi]
+        rng = np.random.default_rng(256 * 1000 + 6)
+        xi = random_gaussians(rng, 256, 6, g.z1, g.z2, 2, (0.1, 0.25), 0.05)
+        W, _ = forward.make_data(xi, om, g, method="born")
+        noise = np.random.default_rng(9).standard_normal(W.shape) + 1j * np.random.default_rng(10).standard_normal(W.shape)
+        return g, np.array(om), forward.add_noise(W, delta, noise), xi
     # small ragged cases: (n, m, m1, omegas)
     spec = {
         "r12": (12, 5, 3, [3 * np.pi]),

@@ -238,3 +238,44 @@ def test_tsvd_on_the_rank_one_kernel_is_the_pseudo_inverse(c1_case):
         ref = np.linalg.pinv(A[i2, i1], rcond=1e-8) @ Wt[:, i2, i1]
         assert np.allclose(res.Vt[0][:, i2, i1], ref, rtol=1e-12, atol=1e-12 * np.linalg.norm(ref))
     assert np.all(np.isfinite(res.xi))
+
+
+def test_alpha_floor_branch_on_a_hand_built_rank_one_mode():
+    """choose_alpha's floor branch: a mode A = gamma a e^T (the Weyl factorisation,
+    written out by hand) whose data has a component outside the range of A larger
+    than delta_nu, so phi(alpha) >= ||P_perp b|| > delta_nu for every alpha and the
+    rule (Sec. 4 comment b with the alpha floor) must return
+    alpha = alpha_rel ||A||_F^2 = alpha_rel |gamma|^2 ||a||^2 ||e||^2, flagged as floor."""
+    rng = np.random.default_rng(3)
+    m1, m, hz, kzv = 5, 9, 0.05, 3.0 + 0.0j
+    zk = 1.2 + 0.1 * np.arange(m1)
+    zl = 0.2 + (np.arange(m) + 0.5) * hz
+    gamma = -1j * hz / (2 * kzv)
+    a = np.exp(1j * kzv * zk)
+    e = np.exp(-1j * kzv * zl)
+    A = gamma * np.outer(a, e)
+    # b = A x + r with r orthogonal to a (the range of A), ||r|| = 3 delta_nu
+    x = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+    r = rng.standard_normal(m1) + 1j * rng.standard_normal(m1)
+    r -= a * (a.conj() @ r) / (a.conj() @ a)
+    dnu = 0.1 * np.linalg.norm(A @ x)
+    r *= 3 * dnu / np.linalg.norm(r)
+    b = A @ x + r
+    U, s, Vh = np.linalg.svd(A)
+    beta = U.conj().T @ b
+    bn = np.linalg.norm(b)
+    perp2 = max(bn ** 2 - np.sum(np.abs(beta[:len(s)]) ** 2), 0.0)
+    alpha, floor = inverse.choose_alpha(s[None] ** 2, np.abs(beta[None, :len(s)]) ** 2, np.array([perp2]),
+                                        np.array([bn]), dnu, 1e-6)
+    expect = 1e-6 * abs(gamma) ** 2 * np.linalg.norm(a) ** 2 * np.linalg.norm(e) ** 2
+    assert bool(floor[0])
+    assert abs(alpha[0] / expect - 1) <= 1e-12
+    # the same mode with the out-of-range part below delta_nu has an interior root
+    r2 = r * (0.5 * dnu / np.linalg.norm(r))
+    b2 = A @ x + r2
+    beta2 = U.conj().T @ b2
+    bn2 = np.linalg.norm(b2)
+    perp22 = max(bn2 ** 2 - np.sum(np.abs(beta2[:len(s)]) ** 2), 0.0)
+    alpha2, floor2 = inverse.choose_alpha(s[None] ** 2, np.abs(beta2[None, :len(s)]) ** 2, np.array([perp22]),
+                                          np.array([bn2]), dnu, 1e-6)
+    assert not bool(floor2[0]) and alpha2[0] > expect

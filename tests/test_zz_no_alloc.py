@@ -18,35 +18,63 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-10, "mixed": 1e-5}
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_static_entry_matches_context_entry(precision):
+def _context_result(name, precision, **opts):
     import torch
-    from paper_1911_10487_gb300 import build
-    build.build()
-    from paper_1911_10487_gb300 import FS_FP64, FS_MIXED, Geometry, Reconstructor
-    from paper_1911_10487_gb300._abi import FS_OK, fs_reconstruct_static, make_geometry
-    g, om, W, _ = case("c1", 0.01)
+    from paper_1911_10487_gb300 import Geometry, Reconstructor
+    g, om, W, _ = case(name, 0.01)
     geom = Geometry(g.n, g.m, g.z1, g.z2, tuple(g.zy), g.period)
-    cdt, rdt = (torch.complex128, torch.float64) if precision == "fp64" else (torch.complex64, torch.float32)
-    prec = FS_FP64 if precision == "fp64" else FS_MIXED
+    cdt = torch.complex128 if precision == "fp64" else torch.complex64
     Wd = torch.from_numpy(np.ascontiguousarray(W)).to("cuda", cdt)
     rc = Reconstructor(0)
-    ref, ref_c, _ = rc.reconstruct(Wd, list(om), geom, 0.01, precision=precision)
+    ref, ref_c, _ = rc.reconstruct(Wd, list(om), geom, 0.01, precision=precision, **opts)
     torch.cuda.synchronize()
-    ref, ref_c = ref.cpu().numpy(), ref_c.cpu().numpy()
+    out = ref.cpu().numpy(), ref_c.cpu().numpy()
     rc.close()
+    return g, om, Wd, out
+
+
+def _static_call(g, om, Wd, precision, **opts):
+    import torch
+    from paper_1911_10487_gb300 import FS_FP64, FS_MIXED
+    from paper_1911_10487_gb300._abi import FS_OK, fs_reconstruct_static, make_geometry, make_options
+    rdt = torch.float64 if precision == "fp64" else torch.float32
+    prec = FS_FP64 if precision == "fp64" else FS_MIXED
     gs = make_geometry(g.n, g.m, g.z1, g.z2, g.zy, g.period)
-    stream = torch.cuda.current_stream().cuda_stream
+    xi = torch.full((g.m, g.n, g.n), float("nan"), dtype=rdt, device="cuda")
+    c = torch.full_like(xi, float("nan"))
+    st = fs_reconstruct_static(gs, prec, Wd.data_ptr(), list(om), 0.01, 1.0, make_options(**opts) if opts else None,
+                               xi.data_ptr(), c.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert st == FS_OK
+    torch.cuda.synchronize()
+    return xi.cpu().numpy(), c.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_static_entry_matches_context_entry(precision):
+    from paper_1911_10487_gb300 import build
+    build.build()
+    g, om, Wd, (ref, ref_c) = _context_result("c1", precision)
     for call in range(2):
-        xi = torch.full((g.m, g.n, g.n), float("nan"), dtype=rdt, device="cuda")
-        c = torch.full_like(xi, float("nan"))
-        st = fs_reconstruct_static(gs, prec, Wd.data_ptr(), list(om), 0.01, 1.0, None, xi.data_ptr(),
-                                   c.data_ptr(), stream)
-        assert st == FS_OK
-        torch.cuda.synchronize()
-        err = rel_l2(xi.cpu().numpy(), ref)
+        xi, c = _static_call(g, om, Wd, precision)
+        err = rel_l2(xi, ref)
         assert err <= TOL[precision], (call, err)
-        assert rel_l2(c.cpu().numpy(), ref_c) <= TOL[precision]
+        assert rel_l2(c, ref_c) <= TOL[precision]
+
+
+def test_static_entry_sequence_of_problems():
+    """Calls of different size, precision and solve form one after the other on the
+    shared scratch: the twiddles and counters are rewritten per call and no stale
+    contents of a larger earlier call are read."""
+    from paper_1911_10487_gb300 import build
+    build.build()
+    seq = [("r24", "mixed", {}), ("c1", "fp64", {}), ("c1", "fp64", {"solve_form": 1}),
+           ("r48", "mixed", {"solve_form": 1, "regularizer": 1}), ("r24", "fp64", {}), ("c1", "mixed", {})]
+    for name, precision, opts in seq:
+        g, om, Wd, (ref, ref_c) = _context_result(name, precision, **opts)
+        xi, c = _static_call(g, om, Wd, precision, **opts)
+        err = rel_l2(xi, ref)
+        print(f"{name} {precision} {opts}: {err:.2e}")
+        assert err <= TOL[precision], (name, precision, opts, err)
 
 
 def test_static_entry_rejects_oversize_problem():
