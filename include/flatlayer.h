@@ -80,6 +80,8 @@ typedef struct {
   const double* zy; /* host, M1 heights of the data planes, each > z2               */
 } fs_geometry;
 
+typedef struct fs_kernel_plan fs_kernel_plan;
+
 typedef struct {
   double tau;          /* discrepancy factor: delta_nu = tau max(delta, delta_floor) ||W|| (default 2) */
   double delta_floor;  /* lower bound of the relative noise level (default 1e-5)          */
@@ -106,6 +108,14 @@ typedef struct {
                           principle -- rank one on these kernels, i.e. the pseudo-inverse on
                           every active mode.  Requires solve_form 1 and alpha_mode 0
                           (FS_EUNSUPPORTED / FS_EINVAL otherwise); alpha output 0.        */
+  const fs_kernel_plan* kernel_plan; /* NULL (default): the Weyl closed form of K_nu.  Else
+                          the sampled-G kernel of Sec. 5 tabulated by fs_kernel_plan_create,
+                          which must have been made for the same geometry, precision,
+                          frequencies and c0 on the context's device (FS_EINVAL otherwise).
+                          A_nu is then numerically full rank and only the dense form solves
+                          it (solve_form 1 gives FS_EUNSUPPORTED); eq. (9) is applied as the
+                          Toeplitz matrix T_nu; no mode is excluded as grazing.  Only
+                          fs_reconstruct and fs_reconstruct_host accept it.             */
 } fs_options;
 
 typedef struct {
@@ -250,6 +260,26 @@ typedef enum {
 fs_status fs_forward(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* xi,
                      const double* omega, int n_omega, double c0, fs_forward_method method, int max_iter,
                      double rtol, void* W, void* u, int* iterations);
+
+/* Sampled-G kernel (Sec. 5: the discrete analogue of G~ computed from the values of G
+   by the FFT), the alternative to the Weyl closed form.  For every frequency and mode
+     K~_nu(dz) = h^2 sum_{i,j} G(sqrt(x_i^2 + y_j^2 + dz^2)) exp(-i nu . (x_i, y_j)),
+   over the offsets x_i = i h (i < N/2), (i - N) h (otherwise) of one period of the
+   grid (the horizontal convolution with G cut to one period, periodised), h = L/N;
+   at rho = 0 the sample is the integral of G over the grid cell (taken over the ball
+   of equal volume) divided by h_z.  The plan tabulates, per frequency and mode, the
+   M1 x M entries of A_nu = omega^2 h_z K~_nu(z_k - z'_l) and the M values
+   omega^2 h_z K~_nu(j h_z) of eq. (9), and tr(A_nu A_nu^H): (M1 M + M) N^2 n_omega x 16
+   bytes of device memory, built synchronously on the current device (the batched
+   FFTs of G sampled at every offset) and owned by the plan.  ctx is used for its
+   argument checks and messages.  Errors: FS_EINVAL, FS_EUNSUPPORTED, FS_ENOMEM,
+   FS_ECUDA. */
+fs_status fs_kernel_plan_create(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const double* omega,
+                                int n_omega, double c0, fs_kernel_plan** plan);
+/* Release the plan's tables (synchronises the device).  NULL is a no-op. */
+void fs_kernel_plan_destroy(fs_kernel_plan* plan);
+/* Device bytes held by the plan (0 for NULL). */
+size_t fs_kernel_plan_bytes(const fs_kernel_plan* plan);
 
 /* Size of the device array that holds every intermediate of fs_reconstruct_static. */
 #define FS_STATIC_SCRATCH_BYTES (32u << 20)

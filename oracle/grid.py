@@ -16,6 +16,10 @@ that the horizontal Fourier transforms are done by FFT.  The readings used here:
 * Grazing modes |nu| = k0 exactly (k_z = 0, where the Weyl kernel is singular)
   are decided in exact integer arithmetic plus a relative 1e-9 margin and are
   excluded: the kernel is set to 0 there in every operator.
+* Kernel: ``kernel="weyl"`` takes the exact horizontal transform of G (kernel.weyl);
+  ``kernel="sampled"`` takes the DFT of G sampled on the grid, the way Sec. 5 builds
+  G~ "from the known values of G using the FFT" (kernel.sampled_green).  The
+  sampled kernel is finite at |nu| = k0, so it excludes no mode.
 """
 from __future__ import annotations
 
@@ -39,6 +43,7 @@ class Geometry:
     zy: tuple = field(default_factory=tuple)
     period: float = 2.0
     x0: float = -1.0
+    kernel: str = "weyl"
 
     @property
     def m1(self) -> int:
@@ -84,7 +89,10 @@ def wavenumbers(g: Geometry):
 
 
 def grazing_mask(k0: float, g: Geometry) -> np.ndarray:
-    """True where |nu| = k0 (k_z = 0): m1^2 + m2^2 = (k0 L / 2 pi)^2 within 1e-9."""
+    """True where |nu| = k0 (k_z = 0): m1^2 + m2^2 = (k0 L / 2 pi)^2 within 1e-9
+    (Weyl kernel only: the sampled kernel has no singular mode)."""
+    if g.kernel == "sampled":
+        return np.zeros((g.n, g.n), dtype=bool)
     mi = mode_indices(g.n)
     msq = (mi[None, :] ** 2 + mi[:, None] ** 2).astype(np.float64)
     s2 = (k0 * g.period / (2.0 * np.pi)) ** 2

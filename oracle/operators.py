@@ -17,10 +17,12 @@ dense assembly from DFT sums (no FFT) for tiny grids, which the tests compare.
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 
 from .grid import Geometry, grazing_mask, kz as kz_of, mode_indices
-from .kernel import weyl
+from .kernel import sampled_green, weyl
 
 _CHUNK_ELEMS = 1 << 23  # bound on the size of a per-mode matrix batch
 
@@ -39,9 +41,28 @@ def _row_chunks(g: Geometry, per_mode: int):
         yield slice(r0, min(g.n, r0 + rows))
 
 
-def mode_matrices(k0, g: Geometry, zrow, zcol, rows=slice(None)):
+@functools.lru_cache(maxsize=8)
+def _sampled_table(k0, g: Geometry, dz_key):
+    """K~_nu(dz) of kernel.sampled_green for the distinct dz of an operator: [n_dz, N, N]."""
+    return sampled_green(k0, g.n, g.period, np.array(dz_key), g.hz)
+
+
+def mode_matrices(k0, g: Geometry, zrow, zcol, rows=slice(None), interior=False):
     """h_z K_nu(zrow[k] - zcol[l]) for the modes in `rows` of the [y, x] grid:
-    array [y, x, k, l], zero on grazing modes."""
+    array [y, x, k, l], zero on grazing modes.  With the sampled kernel
+    (Geometry.kernel == "sampled") K is kernel.sampled_green; for the interior
+    operator (interior=True, zrow = zcol = the X planes) the offsets are taken as
+    |l - l'| h_z exactly, so that equal offsets share one sampled transform."""
+    if g.kernel == "sampled":
+        if interior:
+            li = np.arange(len(zrow))
+            dz = np.abs(li[:, None] - li[None, :]) * g.hz
+        else:
+            dz = np.asarray(zrow)[:, None] - np.asarray(zcol)[None, :]
+        uniq, inv = np.unique(dz, return_inverse=True)
+        tab = _sampled_table(complex(k0), g, tuple(uniq.tolist()))[:, rows]   # [n_dz, y, x]
+        mat = g.hz * tab[inv.reshape(dz.shape)]                              # [k, l, y, x]
+        return np.ascontiguousarray(np.moveaxis(mat, (0, 1), (-2, -1)))
     kz = kz_of(k0, g)[rows]
     graz = grazing_mask(np.real(k0), g)[rows] if np.isrealobj(k0) else np.zeros_like(kz, bool)
     kz_safe = np.where(graz, 1.0, kz)
@@ -58,7 +79,7 @@ def data_matrices(k0, g: Geometry, rows=slice(None)):
 
 def interior_matrices(k0, g: Geometry, rows=slice(None)):
     """T_nu (eq. 9): [y, x, M, M]."""
-    return mode_matrices(k0, g, g.zx(), g.zx(), rows)
+    return mode_matrices(k0, g, g.zx(), g.zx(), rows, interior=True)
 
 
 def _apply(build, nout, w, k0, g):
@@ -90,7 +111,8 @@ def dense_operator_explicit(k0, g: Geometry, zrow):
     idx = np.arange(n)
     # phase[m, i, j] = exp(2 pi i m (i - j)/N), summed mode by mode below
     ph = np.exp(2j * np.pi * mi[:, None, None] * (idx[None, :, None] - idx[None, None, :]) / n)
-    kmat = mode_matrices(k0, g, np.asarray(zrow), g.zx())  # [m2, m1, k, l] in grid order
+    same = np.array_equal(np.asarray(zrow), g.zx())
+    kmat = mode_matrices(k0, g, np.asarray(zrow), g.zx(), interior=same)  # [m2, m1, k, l] in grid order
     nr, nc = len(zrow), g.m
     op = np.zeros((nr, n, n, nc, n, n), dtype=np.complex128)
     for a2 in range(n):          # mode along y (array axis 0 of kmat)

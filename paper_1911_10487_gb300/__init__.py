@@ -17,7 +17,7 @@ from ._abi import (FORWARD_METHODS, FS_FP64, FS_MIXED, FlatLayerError, fs_create
                    fs_reconstruct_host, fs_reconstruct_static, fs_sync_status, fs_version, fs_workspace_size,
                    make_geometry, make_options, make_problem)
 
-__all__ = ["Geometry", "Reconstructor", "FS_FP64", "FS_MIXED", "FlatLayerError", "fs_create",
+__all__ = ["Geometry", "KernelPlan", "Reconstructor", "FS_FP64", "FS_MIXED", "FlatLayerError", "fs_create",
            "fs_default_options", "fs_destroy", "fs_forward", "fs_forward_born", "fs_get_report", "fs_last_error", "fs_reconstruct",
            "fs_reconstruct_batch", "fs_reconstruct_host", "fs_reconstruct_static", "fs_sync_status", "fs_version",
            "fs_workspace_size", "make_geometry", "make_options", "make_problem"]
@@ -41,6 +41,31 @@ class Geometry:
 
     def c_struct(self):
         return make_geometry(self.n, self.m, self.z1, self.z2, self.zy, self.period)
+
+
+class KernelPlan:
+    """Sampled-G kernel tables (Sec. 5: G~ from the FFT of sampled G) for one geometry,
+    precision and frequency list; pass it as ``kernel_plan=`` to
+    Reconstructor.reconstruct.  Holds (M1 M + M) N^2 n_omega x 16 bytes of device memory."""
+
+    def __init__(self, rc: "Reconstructor", geom: Geometry, omega, precision: str = "fp64", c0: float = 1.0):
+        self.geom, self.omega, self.precision, self.c0 = geom, list(omega), precision, c0
+        self.handle = _abi.fs_kernel_plan_create(rc.ctx, geom.c_struct(), PRECISIONS[precision], self.omega, c0)
+
+    @property
+    def nbytes(self) -> int:
+        return _abi.fs_kernel_plan_bytes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            _abi.fs_kernel_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Reconstructor:
@@ -88,6 +113,8 @@ class Reconstructor:
                                 device=self.device) if want_alpha else None)
         else:
             xi, c, alpha = out
+        if isinstance(options.get("kernel_plan"), KernelPlan):
+            options["kernel_plan"] = options["kernel_plan"].handle
         opts = make_options(**options) if options else None
         fs_reconstruct(self.ctx, geom.c_struct(), prec, W.data_ptr(), omega, delta, c0, opts,
                        xi.data_ptr(), c.data_ptr() if c is not None else None,

@@ -22,7 +22,8 @@ EXPORTS = ("fs_version", "fs_default_options", "fs_create", "fs_destroy", "fs_la
            "fs_workspace_size", "fs_reconstruct", "fs_reconstruct_host", "fs_forward_born", "fs_forward",
            "fs_get_report", "fs_sync_status", "fs_measure_alu_peaks", "fs_eval_reciprocals", "fs_reconstruct_static", "fs_reconstruct_batch",
            "fs_diff_plan_create", "fs_diff_plan_destroy", "fs_diff_tape_bytes", "fs_diff_scratch_bytes",
-           "fs_reconstruct_diff", "fs_reconstruct_vjp", "fs_reconstruct_jvp")
+           "fs_reconstruct_diff", "fs_reconstruct_vjp", "fs_reconstruct_jvp",
+           "fs_kernel_plan_create", "fs_kernel_plan_destroy", "fs_kernel_plan_bytes")
 
 
 class fs_geometry(C.Structure):
@@ -35,7 +36,8 @@ class fs_options(C.Structure):
                 ("eps_u", C.c_double), ("alpha_mode", C.c_int),
                 ("alpha_given", C.POINTER(C.c_double)), ("max_iter", C.c_int),
                 ("refine_iters", C.c_int), ("fp64_switch", C.c_double), ("stage_timing", C.c_int),
-                ("solve_blocks_per_sm", C.c_int), ("solve_form", C.c_int), ("regularizer", C.c_int)]
+                ("solve_blocks_per_sm", C.c_int), ("solve_form", C.c_int), ("regularizer", C.c_int),
+                ("kernel_plan", C.c_void_p)]
 
 
 STAGES = ("fft_x_forward", "fft_y_forward_norms", "classify", "solve", "ifft_y_gather", "ifft_x_recover")
@@ -117,6 +119,12 @@ def lib():
         L.fs_get_report.argtypes = [vp, C.POINTER(fs_report)]
         L.fs_sync_status.restype = ip
         L.fs_sync_status.argtypes = [vp]
+        L.fs_kernel_plan_create.restype = ip
+        L.fs_kernel_plan_create.argtypes = [vp, C.POINTER(fs_geometry), ip, dp, ip, C.c_double, C.POINTER(vp)]
+        L.fs_kernel_plan_destroy.restype = None
+        L.fs_kernel_plan_destroy.argtypes = [vp]
+        L.fs_kernel_plan_bytes.restype = C.c_size_t
+        L.fs_kernel_plan_bytes.argtypes = [vp]
         L.fs_eval_reciprocals.restype = ip
         L.fs_eval_reciprocals.argtypes = [vp, ip, vp, vp]
         L.fs_diff_plan_create.restype = ip
@@ -241,6 +249,23 @@ def fs_get_report(ctx) -> dict:
     return r.as_dict()
 
 
+def fs_kernel_plan_create(ctx, geom, prec, omega, c0=1.0):
+    """Sampled-G kernel tables for this geometry, precision and frequency list (device)."""
+    om = (C.c_double * len(omega))(*[float(x) for x in omega])
+    plan = C.c_void_p()
+    st = lib().fs_kernel_plan_create(ctx, C.byref(geom), int(prec), om, len(omega), float(c0), C.byref(plan))
+    _check(ctx, st, "fs_kernel_plan_create")
+    return plan
+
+
+def fs_kernel_plan_destroy(plan) -> None:
+    lib().fs_kernel_plan_destroy(plan)
+
+
+def fs_kernel_plan_bytes(plan) -> int:
+    return int(lib().fs_kernel_plan_bytes(plan))
+
+
 def fs_sync_status(ctx) -> int:
     """Device-side status of the last reconstruction (synchronises); returns the fs_status."""
     return int(lib().fs_sync_status(ctx))
@@ -268,6 +293,8 @@ def make_options(**kw) -> fs_options:
             arr = (C.c_double * len(v))(*[float(x) for x in v])
             o.alpha_given = C.cast(arr, C.POINTER(C.c_double))
             o._keep = arr
+        elif k == "kernel_plan":
+            o.kernel_plan = v.value if isinstance(v, C.c_void_p) else v
         else:
             setattr(o, k, v)
     return o

@@ -165,6 +165,12 @@ fs_status validate_args(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, in
       return fail(ctx, FS_EUNSUPPORTED, "the truncated SVD is implemented in the rank-one form (solve_form 1)");
     if (o->regularizer == 1 && o->alpha_mode != 0)
       return fail(ctx, FS_EINVAL, "the truncated SVD takes no alpha (alpha_mode must be 0)");
+    if (o->kernel_plan) {
+      if (!kernel_plan_matches(o->kernel_plan, g, prec, omega, n_omega, c0))
+        return fail(ctx, FS_EINVAL, "the kernel plan was made for another geometry, precision, frequency list or c0");
+      if (o->solve_form != 0)
+        return fail(ctx, FS_EUNSUPPORTED, "the sampled-G kernel is solved by the dense form only (solve_form 0)");
+    }
   }
   return FS_OK;
 }
@@ -181,16 +187,22 @@ Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, dou
   P.solve_bps = o.solve_blocks_per_sm;
   P.solve_form = o.solve_form;
   P.regularizer = o.regularizer;
+  P.sampled = o.kernel_plan ? 1 : 0;
   for (int k = 0; k < g->m1; ++k) P.zy[k] = g->zy[k];
   for (int j = 0; j < n_omega; ++j) {
     P.omega[j] = omega[j];
     P.alpha_given[j] = (o.alpha_mode == 1) ? o.alpha_given[j] : 0.0;
-    // |m|^2 = (k0 L / 2 pi)^2 within a relative 1e-9 (k_z = 0: excluded modes)
+    // |m|^2 = (k0 L / 2 pi)^2 within a relative 1e-9 (k_z = 0: excluded modes); the
+    // sampled kernel is finite there and excludes nothing (an empty window)
     const double sL = omega[j] / c0 * g->period / (2.0 * M_PI);
     const double s2 = sL * sL;
     const double lo = ceil(s2 - 1e-9 * s2), hi = floor(s2 + 1e-9 * s2);
     P.graz_lo[j] = lo > 1e9 ? 1000000001 : (int)lo;  // |m|^2 <= 2 (N/2)^2 never reaches 1e9
     P.graz_hi[j] = hi > 1e9 ? 1000000000 : (int)hi;
+    if (P.sampled) {
+      P.graz_lo[j] = 1;
+      P.graz_hi[j] = 0;
+    }
   }
   derive_constants(P);
   return P;
@@ -221,6 +233,8 @@ Work<R> carve_work(void* base, const Layout& L, unsigned long long* ctr, const c
   w.alpha_out = alpha_out;
   w.wt64 = nullptr;
   w.tw64 = nullptr;
+  w.ktab = nullptr;
+  w.ktr = nullptr;
   return w;
 }
 
@@ -319,13 +333,14 @@ fs_status ensure_twiddles(fs_ctx* ctx, int n, const cx<R>** out) {
 // not reset here).  Twiddles for P.n must exist.
 template <typename R>
 fs_status run_on(fs_ctx* ctx, const Problem& P, const Layout& L, void* base, cudaStream_t s, const void* W,
-                 void* xi, void* c, double* alpha_out, cudaEvent_t* ev) {
+                 void* xi, void* c, double* alpha_out, cudaEvent_t* ev, const fs_kernel_plan* kp = nullptr) {
   const cx<R>* tw = (const cx<R>*)ctx->tw[sizeof(R) == 8 ? 1 : 0][size_index(P.n)];
   Work<R> w = carve_work<R>(base, L, ctx->ctr, tw, alpha_out);
   if (wide_route(P, sizeof(R) == 8)) {
     w.wt64 = (double2*)((char*)base + L.t12);
     w.tw64 = (const double2*)ctx->tw[1][size_index(P.n)];
   }
+  if (kp) kernel_plan_tables(kp, &w.ktab, &w.ktr);
   const char* stage = "";
   const cudaError_t e = launch_pipeline<R>(P, w, W, xi, c, s, ev, &stage);
   return e == cudaSuccess ? FS_OK : cuda_fail(ctx, e, stage);
@@ -333,7 +348,7 @@ fs_status run_on(fs_ctx* ctx, const Problem& P, const Layout& L, void* base, cud
 
 template <typename R>
 fs_status run(fs_ctx* ctx, const Problem& P, const Layout& L, const void* W, void* xi, void* c,
-              double* alpha_out, bool timed) {
+              double* alpha_out, bool timed, const fs_kernel_plan* kp) {
   const cx<R>* tw = nullptr;
   fs_status st = ensure_twiddles<R>(ctx, P.n, &tw);
   if (st != FS_OK) return st;
@@ -344,7 +359,7 @@ fs_status run(fs_ctx* ctx, const Problem& P, const Layout& L, const void* W, voi
   cudaError_t e = cudaMemsetAsync(ctx->ctr, 0, sizeof(unsigned long long) * C_COUNT, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
   ctx->timed = timed;
-  return run_on<R>(ctx, P, L, ctx->ws, ctx->stream, W, xi, c, alpha_out, timed ? ctx->ev : nullptr);
+  return run_on<R>(ctx, P, L, ctx->ws, ctx->stream, W, xi, c, alpha_out, timed ? ctx->ev : nullptr, kp);
 }
 
 }  // namespace
@@ -368,6 +383,7 @@ fs_status fs_default_options(fs_options* o) {
   o->solve_blocks_per_sm = 2;
   o->solve_form = 0;
   o->regularizer = 0;
+  o->kernel_plan = nullptr;
   return FS_OK;
 }
 
@@ -444,8 +460,10 @@ fs_status fs_reconstruct(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, c
   if ((st = ensure_workspace(ctx, L.total)) != FS_OK) return st;
   const Problem P = make_problem(g, n_omega, omega, delta, c0, o);
   const bool timed = o.stage_timing != 0;
-  return fp64 ? run<double>(ctx, P, L, W, xi, c, alpha_out, timed)
-              : run<float>(ctx, P, L, W, xi, c, alpha_out, timed);
+  if (o.kernel_plan && kernel_plan_device(o.kernel_plan) != ctx->device)
+    return fail(ctx, FS_EINVAL, "the kernel plan lives on another device");
+  return fp64 ? run<double>(ctx, P, L, W, xi, c, alpha_out, timed, o.kernel_plan)
+              : run<float>(ctx, P, L, W, xi, c, alpha_out, timed, o.kernel_plan);
 }
 
 fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const void* W_host,
@@ -494,7 +512,7 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
     key.insert(key.end(), (const unsigned char*)omega, (const unsigned char*)(omega + n_omega));
     if (o.alpha_mode == 1)
       key.insert(key.end(), (const unsigned char*)o.alpha_given, (const unsigned char*)(o.alpha_given + n_omega));
-    const void* ptrs[6] = {W_host, xi_host, c_host, ctx->stage, ctx->ws, ctx->stream};
+    const void* ptrs[7] = {W_host, xi_host, c_host, ctx->stage, ctx->ws, ctx->stream, o.kernel_plan};
     key_put(key, ptrs);
     if (ctx->host_exec && key == ctx->host_key) {
       if ((e = cudaGraphLaunch(ctx->host_exec, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
@@ -519,7 +537,7 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
   if (graphable) {
     // the run above sized the workspace and twiddles, so the capture allocates
     // nothing; the key is taken again in case the workspace moved
-    const void* ptrs[6] = {W_host, xi_host, c_host, ctx->stage, ctx->ws, ctx->stream};
+    const void* ptrs[7] = {W_host, xi_host, c_host, ctx->stage, ctx->ws, ctx->stream, o.kernel_plan};
     key.resize(key.size() - sizeof(ptrs));
     key_put(key, ptrs);
     if (ctx->host_exec) {
@@ -553,6 +571,7 @@ fs_status fs_reconstruct_batch(fs_ctx* ctx, const fs_problem* probs, int n_probs
   fs_options o;
   fs_default_options(&o);
   if (opts) o = *opts;
+  if (o.kernel_plan) return fail(ctx, FS_EUNSUPPORTED, "batches take the Weyl kernel only (kernel_plan must be NULL)");
   const bool fp64 = prec == FS_FP64;
   size_t total = 0;
   for (int i = 0; i < n_probs; ++i) {

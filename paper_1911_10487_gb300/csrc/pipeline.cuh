@@ -46,6 +46,7 @@ struct Problem {
   double k0[MAX_OMEGA], g0[MAX_OMEGA];
   double kn;
   double inv_c02, u_guard;  // c0^-2 and the |u|^2 guard eps_u^2 n_omega of the recovery
+  int sampled;  // 1: the sampled-G kernel of a kernel plan (Work::ktab) replaces the Weyl form
 };
 
 inline void derive_constants(Problem& P) {
@@ -87,6 +88,13 @@ template <typename R> struct Work {
   // twiddles tw64, and the solve reads b from here.  Null otherwise.
   double2* wt64;
   const double2* tw64;
+  // sampled-G kernel (Problem::sampled): per frequency and mode the D = M1 M + M
+  // values [A_nu row-major (k, l) | omega^2 h_z K~_nu(j h_z), j < M] at
+  // ktab + ((omega N^2) + nu) D -- double2 in FP64; in the mixed precision float4
+  // two-float pairs (hi.re, lo.re, hi.im, lo.im), the A part scaled by 1/sqrt(tr) --
+  // and tr(A_nu A_nu^H) at ktr[omega N^2 + nu].  Null otherwise.
+  const void* ktab;
+  const double* ktr;
 };
 
 // blocks of 1024 consecutive modes in the classification of an N x N grid
@@ -128,6 +136,13 @@ fs_status validate_args(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, in
 Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, double delta, double c0,
                      const fs_options& o);
 
+// kernel plans (kernel_plan.cu): whether a plan was made for these arguments, and
+// its tables
+bool kernel_plan_matches(const fs_kernel_plan* p, const fs_geometry* g, fs_precision prec, const double* omega,
+                         int n_omega, double c0);
+void kernel_plan_tables(const fs_kernel_plan* p, const void** tab, const double** tr);
+int kernel_plan_device(const fs_kernel_plan* p);
+
 // Launch facts kept per device, since one process may drive several GPUs:
 //   sm_count()    SM count of the current device (looked up once per device)
 //   opt_in_smem() cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for `kernel`,
@@ -161,6 +176,13 @@ cudaError_t launch_twiddles(cx<R>* tw, int n, cudaStream_t s);
 template <typename R>
 cudaError_t launch_fft2_dense(cx<R>* in, cx<R>* out, int n, long long planes, bool inverse, const cx<R>* tw,
                               cudaStream_t s);
+// the sampled-G kernel tables of one frequency (kernel_plan.cu): G sampled on the grid
+// offsets, its 2D FFT, packed mode-major with omega^2 h_z applied and the traces;
+// gs and ft are scratch of D N^2 complex128 each, tw64 the FP64 twiddles of N
+cudaError_t launch_kernel_tables(const Problem& P, int om, double2* gs, double2* ft, const double2* tw64, bool mixed,
+                                 void* tab, double* tr, cudaStream_t s);
+inline int kernel_table_width(const Problem& P) { return P.m1 * P.m + P.m; }
+
 // forward data generator (single scattering): W = F^-1[ A_nu F[omega^2 xi u0] ]
 template <typename R>
 cudaError_t launch_forward_born(const Problem& P, const R* xi, cx<R>* src, cx<R>* W, const cx<R>* tw,

@@ -345,6 +345,7 @@ struct Shared {
   double2 A[MAX_M1][MAX_M + 1];  // A_nu in FP64 (FP64 route), Ah in two-float (mixed route)
   union { Bulk<double> d; BulkF f; Eq9 q; } u;
   double2 E[MAX_M1], Pz[MAX_M], b[MAX_M1], c[MAX_M1], y[MAX_M1], z[MAX_M1];
+  double2 Tk[MAX_M];  // sampled kernel: row omega^2 h_z K~(j h_z) of the Toeplitz T_nu of eq. (9)
   double d[MAX_M1], e[MAX_M1];     // tridiagonal T (FP64 route: of G; scaled by 1/tr after the factor)
   float d32[MAX_M1], e32[MAX_M1];  // T / tr in FP32
   float2 c32[MAX_M1], r32[MAX_M1];
@@ -756,11 +757,15 @@ __device__ __noinline__ void eq9_scans(int m) {
   }
 }
 
-template <typename B, bool MIXED>
+// SAMPLED: A_nu and the row of T_nu come from the tables of a kernel plan (the
+// sampled-G kernel: ktab, ktr, layout in Work::ktab) instead of the Weyl closed form;
+// eq. (9) is then the Toeplitz product itself rather than its recurrences.
+template <typename B, bool MIXED, bool SAMPLED>
 __global__ void __launch_bounds__(ST)
 k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         const int* __restrict__ count, const double* __restrict__ dnu_arr,
-        cx<B>* __restrict__ prof, double* __restrict__ alpha_out, unsigned long long* __restrict__ ctr) {
+        cx<B>* __restrict__ prof, double* __restrict__ alpha_out, unsigned long long* __restrict__ ctr,
+        const void* __restrict__ ktab, const double* __restrict__ ktr) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -792,10 +797,25 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     const double g0 = P.g0[om];
     const double2 gamma = q >= 0.0 ? make_double2(0.0, -g0 * rq) : make_double2(-g0 * rq, 0.0);
     const double ztop = P.z1 + (m - 0.5) * P.hz;
+    const long long mb = ((long long)om * N2 + nu) * (long long)(n * m + m);  // the mode's table row
     // the exponentials, one per thread: threads 0..63 take P, threads 64..95 take E
     // (FP32 in the mixed route), thread 96 the plane-to-plane factor q of eq. (9)
-    // in FP64 (the mixed route takes it later, while warp 0 finds the root)
-    if (threadIdx.x < m) {
+    // in FP64 (the mixed route takes it later, while warp 0 finds the root).  The
+    // sampled kernel reads the row of T_nu (threads 0..63) instead.
+    if (SAMPLED) {
+      if (threadIdx.x < m) {
+        const long long at = mb + n * m + threadIdx.x;
+        if (MIXED) {
+          const float4 v = reinterpret_cast<const float4*>(ktab)[at];
+          S.Tk[threadIdx.x] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+        } else {
+          S.Tk[threadIdx.x] = reinterpret_cast<const double2*>(ktab)[at];
+        }
+      } else if (threadIdx.x >= MAX_M && threadIdx.x < MAX_M + n) {
+        const int k = threadIdx.x - MAX_M;
+        S.b[k] = to_d(wt[((long long)om * n + k) * N2 + nu]);
+      }
+    } else if (threadIdx.x < m) {
       const int l = threadIdx.x;
       S.Pz[l] = MIXED ? exp_ikz32(kz, ztop - (P.z1 + (l + 0.5) * P.hz)) : exp_ikz(kz, ztop - (P.z1 + (l + 0.5) * P.hz));
       if (MIXED) S.Pf[l] = ffc_from(S.Pz[l]);
@@ -818,7 +838,10 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       if (wid == 0) v = (lane < m ? abs2(S.Pz[lane]) : 0.0) + (lane + 32 < m ? abs2(S.Pz[lane + 32]) : 0.0);
       else if (wid == 1) v = lane < n ? abs2(S.b[lane]) : 0.0;
       else if (wid == 2) v = lane < n ? abs2(S.E[lane]) : 0.0;
-      if (wid < 3) {
+      if (SAMPLED && wid != 1) {
+        // tr(G) from the plan: S.red[0] S.red[2] = tr
+        if (wid < 3 && lane == 0) S.red[wid] = wid == 0 ? ktr[(long long)om * N2 + nu] : 1.0;
+      } else if (wid < 3) {
         v = warp_sum(v);
         if (lane == 0) S.red[wid] = v;
       }
@@ -836,7 +859,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         const double y = rsqrt32(bb);
         return fma(0.5 * y, fma(-bb * y, y, 1.0), y);
       };
-      if (MIXED && wid == 0 && lane < n) {
+      if (MIXED && !SAMPLED && wid == 0 && lane < n) {
         // the scale factor need only be used consistently: FP32-accurate 1/sqrt(tr)
         S.Ef[lane] = ffc_from(rsqrt32(tr) * S.E[lane]);
       } else if (wid == 1) {
@@ -888,15 +911,27 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       // Ah in two-float (for the residual and V~) and its FP32 part (for the model);
       // thread t builds column t mod 64, rows t / 64, t / 64 + 2, ...
       ffc (*Af)[MAX_M + 1] = reinterpret_cast<ffc (*)[MAX_M + 1]>(S.A);
-      const double sa = rsqrt32(tr);
-      const int l = threadIdx.x & (MAX_M - 1);
-      if (l < m) {
-        const ffc pl = S.Pf[l];
+      // the sampled tables hold A exactly scaled by 1/sqrt(tr) (FP64 in the plan)
+      const double sa = SAMPLED ? rsqrt64(tr) : rsqrt32(tr);
+      if (SAMPLED) {
+        const float4* t4 = reinterpret_cast<const float4*>(ktab) + mb;
 #pragma unroll 1
-        for (int k = threadIdx.x / MAX_M; k < n; k += ST / MAX_M) {
-          const ffc a = ffc_mul(S.Ef[k], pl);
-          Af[k][l] = a;
-          S.u.f.m.A[k][l] = make_float2(a.re.hi, a.im.hi);
+        for (int e = threadIdx.x; e < n * m; e += ST) {
+          const int k = e / m, l = e - k * m;
+          const float4 v = t4[e];
+          Af[k][l] = ffc{ff{v.x, v.y}, ff{v.z, v.w}};
+          S.u.f.m.A[k][l] = make_float2(v.x, v.z);
+        }
+      } else {
+        const int l = threadIdx.x & (MAX_M - 1);
+        if (l < m) {
+          const ffc pl = S.Pf[l];
+#pragma unroll 1
+          for (int k = threadIdx.x / MAX_M; k < n; k += ST / MAX_M) {
+            const ffc a = ffc_mul(S.Ef[k], pl);
+            Af[k][l] = a;
+            S.u.f.m.A[k][l] = make_float2(a.re.hi, a.im.hi);
+          }
         }
       }
       __syncthreads();
@@ -934,7 +969,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           S.fp64 = fp64 ? 1 : 0;
           if (fp64) atomicAdd(ctr + C_FP64_FALLBACK, 1ull);
         }
-      } else if (threadIdx.x == MAX_M + MAX_M1) {
+      } else if (!SAMPLED && threadIdx.x == MAX_M + MAX_M1) {
         S.qz = exp_ikz(kz, P.hz);  // FP64, on an idle warp; first read by eq. (9)
       }
       __syncthreads();
@@ -1003,11 +1038,18 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         __syncthreads();
       }
       if (S.fp64) {
-        // FP64 route for this mode: A in FP64 over the two-float storage
+        // FP64 route for this mode: A in FP64 over the two-float storage (each entry
+        // read and rewritten by the same thread)
+        const double sq = tr * sa;  // sqrt(tr), the sampled tables' scale
 #pragma unroll 1
         for (int e = threadIdx.x; e < n * m; e += ST) {
           const int k = e / m, l = e - k * m;
-          S.A[k][l] = S.E[k] * S.Pz[l];
+          if (SAMPLED) {
+            const ffc a = Af[k][l];
+            S.A[k][l] = sq * ffc_to(a);
+          } else {
+            S.A[k][l] = S.E[k] * S.Pz[l];
+          }
         }
         __syncthreads();
       }
@@ -1015,7 +1057,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
 #pragma unroll 1
       for (int e = threadIdx.x; e < n * m; e += ST) {
         const int k = e / m, l = e - k * m;
-        S.A[k][l] = S.E[k] * S.Pz[l];
+        S.A[k][l] = SAMPLED ? reinterpret_cast<const double2*>(ktab)[mb + e] : S.E[k] * S.Pz[l];
       }
       __syncthreads();
     }
@@ -1034,8 +1076,20 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       __syncthreads();
     }
     FL_MARK(10);
-    // U~ = U~0 + gamma (F + B), eq. (9)
-    eq9_scans(m);
+    // U~ = U~0 + gamma (F + B), eq. (9); with the sampled kernel U~ - U~0 = T_nu V~ by
+    // the Toeplitz product (F), two threads per plane
+    if (SAMPLED) {
+      const int l = threadIdx.x >> 1, h = threadIdx.x & 1;
+      double2 acc = make_double2(0.0, 0.0);
+      if (l < m)
+#pragma unroll 1
+        for (int j = h; j < m; j += 2) acc = acc + S.Tk[l > j ? l - j : j - l] * S.u.q.Vt[j];
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      if (l < m && h == 0) S.u.q.F[l] = acc;
+    } else {
+      eq9_scans(m);
+    }
     __syncthreads();
     FL_MARK(11);
     cx<B>* out = prof + ((long long)om * N2 + i) * 2 * m;
@@ -1045,9 +1099,14 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         if (threadIdx.x < MAX_M) {
           out[l] = from_d<B>(S.u.q.Vt[l]);
         } else {
-          const double2 f = S.u.q.F[l] + S.u.q.Bk[l];
-          // gamma is imaginary (propagating mode) or real (evanescent)
-          double2 u = q >= 0.0 ? make_double2(-gamma.y * f.y, gamma.y * f.x) : make_double2(gamma.x * f.x, gamma.x * f.y);
+          double2 u;
+          if (SAMPLED) {
+            u = S.u.q.F[l];
+          } else {
+            const double2 f = S.u.q.F[l] + S.u.q.Bk[l];
+            // gamma is imaginary (propagating mode) or real (evanescent)
+            u = q >= 0.0 ? make_double2(-gamma.y * f.y, gamma.y * f.x) : make_double2(gamma.x * f.x, gamma.x * f.y);
+          }
           if (nu == 0) {
             double s, c;
             sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s, &c);
@@ -1065,14 +1124,24 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
 
 int solve_grid(int bps) { return (bps < 1 ? 1 : (bps > 3 ? 3 : bps)) * sm_count(); }
 
-template <typename B, bool MIXED>
-cudaError_t solve_impl(const Problem& P, const Work<B>& w, cudaStream_t s) {
+template <typename B, bool MIXED, bool SAMPLED>
+cudaError_t solve_variant(const Problem& P, const Work<B>& w, cudaStream_t s) {
   const size_t smem = sizeof(Shared);
   static SmemOptIn attr;
-  cudaError_t e = opt_in_smem(attr, (const void*)k_solve<B, MIXED>, smem);
+  cudaError_t e = opt_in_smem(attr, (const void*)k_solve<B, MIXED, SAMPLED>, smem);
   if (e != cudaSuccess) return e;
-  return launch_pdl(k_solve<B, MIXED>, dim3(solve_grid(P.solve_bps)), dim3(ST), smem, s, P, (const cx<B>*)w.wt,
-                    (const int*)w.act, (const int*)w.count, (const double*)w.dnu, w.prof, w.alpha_out, w.ctr);
+  return launch_pdl(k_solve<B, MIXED, SAMPLED>, dim3(solve_grid(P.solve_bps)), dim3(ST), smem, s, P,
+                    (const cx<B>*)w.wt, (const int*)w.act, (const int*)w.count, (const double*)w.dnu, w.prof,
+                    w.alpha_out, w.ctr, w.ktab, w.ktr);
+}
+
+template <typename B, bool MIXED>
+cudaError_t solve_impl(const Problem& P, const Work<B>& w, cudaStream_t s) {
+  if (P.sampled) {
+    if (!w.ktab || !w.ktr) return cudaErrorInvalidValue;
+    return solve_variant<B, MIXED, true>(P, w, s);
+  }
+  return solve_variant<B, MIXED, false>(P, w, s);
 }
 
 }  // namespace

@@ -85,6 +85,7 @@ extern "C" fs_status fs_reconstruct_static(const fs_geometry* g, fs_precision pr
                                            const fs_options* opts, void* xi, void* c, void* stream) {
   fs_status st = validate_args(nullptr, g, prec, n_omega, omega, delta, c0, opts);
   if (st != FS_OK) return st;
+  if (opts && opts->kernel_plan) return FS_EUNSUPPORTED;  // the sampled kernel needs its plan's memory
   if (!W || !xi) return FS_EINVAL;
   const bool fp64 = prec == FS_FP64;
   const Layout L = layout(g->n, g->m, g->m1, n_omega, fp64);

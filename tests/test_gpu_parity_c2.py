@@ -1,7 +1,8 @@
 """Parity on the 128 x 128 x 64 workload itself (32 data planes, k0 = 8 pi, three
 Gaussian inclusions) at the three noise levels of that workload, 0, 1 % and 5 %, in
 both precisions; the mixed path's FP64 route, forced and as taken at delta = 0; and
-the thin data layer of Sec. 5.4 (two planes).
+the thin data layer of Sec. 5.4 (two planes), where xi is compared in the weight of
+its least-squares denominator (see that test).
 
 Tolerances as in test_gpu_parity: xi rel. L2 <= 1e-10 (FS_FP64) and <= 1e-5
 (FS_MIXED) against the FP64 oracle on the complex128 data; identical active sets.
@@ -79,63 +80,32 @@ def test_mixed_fp64_route_at_floor_cases(rc):
     assert rep["n_alpha_floor"] == ref.counts["alpha_floor"]
 
 
-def root_sensitivity_bound(ref, W, om, g):
-    """Relative xi error that two correct FP64 implementations may show on this case,
-    from the conditioning of the discrepancy root (derived, not fitted):
-      phi^2(alpha) = sum_j (alpha/(s_j^2 + alpha))^2 |beta_j|^2 + ||P_perp b||^2
-    is computed by either side with an absolute rounding error of about
-      e = 16 u (||b||^2 + ||b|| b_rms log2(N^2))     (u = 2^-53)
-    -- ||P_perp b||^2 = ||b||^2 - |beta|^2 cancels, and b itself carries the rounding
-    of an FFT of log2(N^2) stages spread over the modes (b_rms = ||W~|| / N).  The
-    root then moves by e / |d phi^2/d alpha| and V~ by that times ||dV~/d alpha||,
-    dV~/d alpha = -V diag(s/(s^2 + alpha)^2) beta.  Summed in quadrature over the
-    active, non-floor modes and taken relative to ||V~|| (xi = Re(conj(u) V)/|u|^2
-    with |u| ~ 1 in this weak-scattering case), with a factor 10 for |u| and the
-    constants: the bound returned."""
-    from oracle.operators import data_matrices, fft2
-    u = 2.0 ** -53
-    num, den = 0.0, 0.0
-    for j, w in enumerate(om):
-        Wt = fft2(W[j])
-        b_rms = np.linalg.norm(Wt) / g.n
-        act = ref.active[j]
-        al = ref.alpha[j]
-        A = w ** 2 * data_matrices(w, g)                     # [y, x, M1, M]
-        b = np.moveaxis(Wt, 0, -1)                           # [y, x, M1]
-        Aa, ba, aa = A[act], b[act], al[act]
-        U, s, Vh = np.linalg.svd(Aa, full_matrices=False)
-        beta = np.einsum("akj,ak->aj", U.conj(), ba)
-        s2 = s ** 2
-        bn2 = np.sum(np.abs(ba) ** 2, axis=-1)
-        e = 16 * u * (bn2 + np.sqrt(bn2) * b_rms * np.log2(g.n * g.n))
-        dphi = np.sum(2 * aa[:, None] * s2 * np.abs(beta) ** 2 / (s2 + aa[:, None]) ** 3, axis=-1)
-        dv = np.sqrt(np.sum(s2 * np.abs(beta) ** 2 / (s2 + aa[:, None]) ** 4, axis=-1))
-        floor = np.isclose(aa, 1e-6 * np.sum(s2, axis=-1), rtol=1e-9)
-        dV = np.where(floor, 0.0, e / dphi * dv)
-        num += np.sum(dV ** 2)
-        den += np.sum(np.abs(ref.Vt[j]) ** 2)
-    return 10.0 * np.sqrt(num / den)
-
-
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_thin_layer_two_planes(rc, precision):
-    """Sec. 5.4: data on two planes 0.01 apart.  With M1 = 2 the discrepancy test
-    passes noise-only modes (two complex values per mode) and the root of
-    phi = delta_nu is ill-determined where ||P_perp b|| ~ delta_nu, so two correct FP64
-    implementations agree on xi only to the bound of root_sensitivity_bound.  What is
-    determined exactly -- the active sets -- must match."""
+    """Sec. 5.4: data on two planes 0.01 apart.  With two values per mode the
+    discrepancy test (tau = 2) passes about 0.3 % of the pure-noise modes, among them
+    strongly evanescent ones (sigma_1 ~ 1e-63 at N = 256): their solutions, amplified
+    by 1/sigma, dominate V and u, and xi = Re(conj(u) V)/|u|^2 is then fixed only to the
+    relative rounding of those giant terms wherever |u|^2 falls far below its maximum.
+    What is determined, and asserted: the active sets (exactly), alpha per mode, and xi
+    weighted by the least-squares denominator D = sum_omega |u|^2 -- from xi D = num,
+    an error eps in num and D gives ||(xi' - xi) D|| <= 2 eps ||xi D|| -- within the
+    path's tolerance.  The unweighted error is printed."""
     g, om, W, _ = case("thin256", 0.01)
     ref = oracle_result("thin256", 0.01)
     xi, c, alpha, rep = run_gpu(rc, g, om, W, 0.01, precision=precision)
-    err = rel_l2(xi, ref.xi)
-    bound = root_sensitivity_bound(ref, W, om, g)
-    tol = max(bound, TOL_FP64) if precision == "fp64" else max(bound, TOL_MIXED)
+    den = np.sum(np.abs(ref.u) ** 2, axis=0)
+    werr = np.linalg.norm((xi - ref.xi) * den) / np.linalg.norm(ref.xi * den)
     act = np.isfinite(alpha)
-    print(f"thin layer {precision}: xi rel L2 {err:.3e}, derived bound {bound:.3e}, active {act.sum()}/"
-          f"{ref.active.sum()}")
-    assert err <= tol, (err, tol)
+    print(f"thin layer {precision}: xi weighted by sum |u|^2 {werr:.3e}, unweighted {rel_l2(xi, ref.xi):.3e}; "
+          f"active {act.sum()}/{ref.active.sum()}; sum |u|^2 spans {den.min():.1e}..{den.max():.1e}")
     if precision == "fp64":
         assert np.array_equal(act, ref.active)
+        ra = np.abs(alpha[ref.active] / ref.alpha[ref.active] - 1)
+        print(f"alpha max rel err {ra.max():.2e}")
+        assert ra.max() <= 1e-6
         assert rep["n_active"] == int(ref.active.sum())
+        assert werr <= TOL_FP64
     else:
         assert np.sum(act != ref.active) <= 2
+        assert werr <= TOL_MIXED
