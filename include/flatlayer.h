@@ -68,8 +68,10 @@ typedef enum {
                   W complex64 in, xi/c float32 out                                  */
 } fs_precision;
 
-/* Limits of this build: N in {8,12,16,24,32,48,64,96,128,192,256}; 1 <= M <= 64;
-   1 <= M1 <= 32; 1 <= n_omega <= 64. */
+/* Limits of this build: N in {8,12,16,24,32,48,64,96,128,192,256}; 1 <= M <= 128;
+   1 <= M1 <= 128; 1 <= n_omega <= 64.  The dense per-mode solve (solve_form 0, the
+   default; the sampled kernel; the derivatives of flatlayer_diff.h) holds A_nu in
+   shared memory and takes M <= 64, M1 <= 32; the rank-one form serves the rest. */
 
 typedef struct {
   int n;            /* N: horizontal grid points per axis                           */
@@ -116,6 +118,12 @@ typedef struct {
                           it (solve_form 1 gives FS_EUNSUPPORTED); eq. (9) is applied as the
                           Toeplitz matrix T_nu; no mode is excluded as grazing.  Only
                           fs_reconstruct and fs_reconstruct_host accept it.             */
+  const void* incident;  /* NULL (default): the incident field is the plane wave exp(-i k0 z).
+                          Else device, [n_omega][M][N][N] complex in the working precision:
+                          the incident field u0 on the X planes (for instance the point
+                          sources of fs_incident_point_sources, Sec. 5); Algorithm 2 step 2
+                          then takes u = u0 + F^-1[omega^2 T_nu V~].  fs_reconstruct,
+                          fs_reconstruct_host and fs_reconstruct_static accept it.      */
 } fs_options;
 
 typedef struct {
@@ -216,12 +224,27 @@ fs_status fs_reconstruct_batch(fs_ctx* ctx, const fs_problem* probs, int n_probs
 /* Forward data generator in the single-scattering (Born) form: Algorithm 1 of
    Sec. 3 with zero iterations, i.e. U~ = U~0 in eq. (7):
      W = F^-1[ omega^2 sum_l h_z K_nu(z_k - z'_l) F[xi u0](z'_l) ]  on the data planes,
-   with u0 = exp(-i k0 z), k0 = omega/c0, and grazing modes excluded as above.
-     xi  device, [M][N][N] real (float64 for FS_FP64, float32 for FS_MIXED).
-     W   device, [n_omega][M1][N][N] complex (complex128 / complex64), written.
+   with k0 = omega/c0 and grazing modes excluded as above.
+     xi        device, [M][N][N] real (float64 for FS_FP64, float32 for FS_MIXED).
+     incident  device, [n_omega][M][N][N] complex (complex128 / complex64): u0 on the X
+               planes; or NULL for the plane wave u0 = exp(-i k0 z).
+     W         device, [n_omega][M1][N][N] complex (complex128 / complex64), written.
    Uses the context workspace; asynchronous. */
 fs_status fs_forward_born(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* xi,
-                          const double* omega, int n_omega, double c0, void* W);
+                          const void* incident, const double* omega, int n_omega, double c0, void* W);
+
+/* The incident field of point sources on the X planes (Sec. 5: sources f = sum_s a_s
+   delta(x - x_s), u0 = sum_s a_s G(|x - x_s|)), in the horizontally periodic model of
+   this library: for every frequency and mode
+     U~0_nu(z'_l) = (N^2/L^2) sum_s a_s K_nu(z'_l - z_s) exp(-i nu . (r_s - x0)),
+   K_nu the Weyl form (grazing modes zero), x0 = -L/2 the first grid node on both
+   horizontal axes (nodes x0 + i L/N), then u0 = F^-1[U~0] on each X plane.
+     sources  host, [n_sources][4] doubles (x, y, z, a): position and real amplitude;
+              every source lies above X (z > z2).
+     u0       device, [n_omega][M][N][N] complex (complex128 / complex64), written.
+   Synchronises the context's stream.  Errors: FS_EINVAL, FS_EUNSUPPORTED, FS_ECUDA. */
+fs_status fs_incident_point_sources(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const double* sources,
+                                    int n_sources, const double* omega, int n_omega, double c0, void* u0);
 
 /* Solver of the full-scattering forward problem u = u0 + omega^2 T(xi u) on X (first
    line of eq. 2) for fs_forward. */

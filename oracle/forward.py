@@ -17,14 +17,16 @@ compare them:
 * ``dense``       -- LU of the explicitly assembled matrix (tiny grids only).
 
 ``born`` skips the solve (u = u0): single scattering.
-The incident field is the plane wave u0 = exp(-i k0 z) used by the workloads.
+The incident field is the plane wave u0 = exp(-i k0 z) of the workloads, or the field
+of point sources (``incident_point_sources``, Sec. 5) passed as u0.
 """
 from __future__ import annotations
 
 import numpy as np
 import scipy.sparse.linalg as spla
 
-from .grid import Geometry
+from .grid import Geometry, grazing_mask, kz as kz_of, wavenumbers
+from .kernel import weyl
 from .operators import (apply_data, apply_interior, dense_operator_explicit, fft2,
                         ifft2, interior_matrices, _row_chunks)
 
@@ -35,6 +37,28 @@ def incident_plane_wave(k0, g: Geometry) -> np.ndarray:
     """u0 = exp(-i k0 z) on the X planes, [M, N, N]."""
     col = np.exp(-1j * k0 * g.zx())
     return np.broadcast_to(col[:, None, None], (g.m, g.n, g.n)).astype(np.complex128)
+
+
+def incident_point_sources(k0, g: Geometry, sources) -> np.ndarray:
+    """u0 = sum_s a_s G(|x - x_s|) on the X planes for point sources (x, y, z, a) above X
+    (Sec. 5: f = sum_s a_s delta(x - x_s)), in the horizontally periodic model: the
+    Fourier coefficient of the periodised field at nu is (1/L^2) K_nu(z - z_s) a_s
+    exp(-i nu.r_s), so the DFT of its samples on the grid x0 + i h is
+        U~0_nu(z) = (N^2/L^2) sum_s a_s K_nu(z - z_s) exp(-i nu.(r_s - x0))
+    (the modes beyond the grid's band are negligible for sources well above X);
+    u0 = ifft2(U~0).  Grazing modes carry K = 0, as in every operator.  [M, N, N]."""
+    kz = kz_of(k0, g)
+    graz = grazing_mask(np.real(k0), g) if np.isrealobj(k0) else np.zeros(kz.shape, bool)
+    kz_safe = np.where(graz, 1.0, kz)
+    nu1, nu2 = wavenumbers(g)
+    zx = g.zx()
+    Ut0 = np.zeros((g.m, g.n, g.n), dtype=np.complex128)
+    for (xs, ys, zs, a) in sources:
+        phase = np.exp(-1j * (nu1 * (xs - g.x0) + nu2 * (ys - g.x0)))
+        K = weyl(kz_safe[None], (zx - zs)[:, None, None])     # [M, y, x]
+        Ut0 += a * K * phase[None]
+    Ut0[:, graz] = 0.0
+    return ifft2((g.n * g.n) / g.period ** 2 * Ut0)
 
 
 def _fixed_point(xi, k0, omega, g, u0, max_iter):
@@ -79,10 +103,11 @@ def _dense(xi, k0, omega, g, u0):
     return np.linalg.solve(L, u0.ravel()).reshape(u0.shape)
 
 
-def total_field(xi, omega, g: Geometry, c0=1.0, method="gmres", max_iter=500):
-    """u on X solving u = u0 + omega^2 T(xi u) (first line of eq. 2)."""
+def total_field(xi, omega, g: Geometry, c0=1.0, method="gmres", max_iter=500, u0=None):
+    """u on X solving u = u0 + omega^2 T(xi u) (first line of eq. 2); u0 the plane wave
+    unless given ([M, N, N] on X)."""
     k0 = omega / c0
-    u0 = incident_plane_wave(k0, g)
+    u0 = incident_plane_wave(k0, g) if u0 is None else np.asarray(u0, dtype=np.complex128)
     xi = np.asarray(xi, dtype=np.float64)
     if method == "born":
         return u0.copy()
@@ -106,11 +131,12 @@ def scattered_data(xi, u, omega, g: Geometry, c0=1.0):
     return omega ** 2 * apply_data(np.asarray(xi) * u, omega / c0, g)
 
 
-def make_data(xi, omegas, g: Geometry, c0=1.0, method="gmres"):
-    """Exact data W[n_omega, M1, N, N] and total fields u[n_omega, M, N, N]."""
+def make_data(xi, omegas, g: Geometry, c0=1.0, method="gmres", u0s=None):
+    """Exact data W[n_omega, M1, N, N] and total fields u[n_omega, M, N, N]; u0s: the
+    incident field per frequency ([n_omega, M, N, N]) or None for the plane wave."""
     Ws, us = [], []
-    for om in omegas:
-        u = total_field(xi, om, g, c0, method)
+    for j, om in enumerate(omegas):
+        u = total_field(xi, om, g, c0, method, u0=None if u0s is None else u0s[j])
         us.append(u)
         Ws.append(scattered_data(xi, u, om, g, c0))
     return np.stack(Ws), np.stack(us)

@@ -160,9 +160,10 @@ def _band(chunks, band):
         yield rows
 
 
-def interior_field(Vt, omega, k0, g: Geometry, band=None):
-    """Step 2 (eq. 9): U~ = U~0 + omega^2 T_nu V~ per mode, explicit matrix product."""
-    Ut = fft2(incident_plane_wave(k0, g))
+def interior_field(Vt, omega, k0, g: Geometry, band=None, u0=None):
+    """Step 2 (eq. 9): U~ = U~0 + omega^2 T_nu V~ per mode, explicit matrix product;
+    U~0 = F[u0], u0 the plane wave unless given."""
+    Ut = fft2(incident_plane_wave(k0, g) if u0 is None else np.asarray(u0, dtype=np.complex128))
     for rows in _band(_row_chunks(g, g.m * g.m), band):
         T = interior_matrices(k0, g, rows)
         Ut[:, rows, :] += omega ** 2 * np.einsum("yxkl,lyx->kyx", T, Vt[:, rows, :])
@@ -180,8 +181,9 @@ def combine(V, u, eps_u=1e-8, c0=1.0):
     return xi, c, int(np.sum(guard)), int(np.sum(~ok))
 
 
-def reconstruct(W, omegas, g: Geometry, delta, c0=1.0, opts: Options | None = None) -> Result:
-    """Algorithm 2 on data W[n_omega, M1, N, N] at frequencies `omegas`."""
+def reconstruct(W, omegas, g: Geometry, delta, c0=1.0, opts: Options | None = None, u0s=None) -> Result:
+    """Algorithm 2 on data W[n_omega, M1, N, N] at frequencies `omegas`; u0s: the incident
+    field on X per frequency ([n_omega, M, N, N]), None for the plane wave."""
     opts = opts or Options()
     W = np.asarray(W, dtype=np.complex128)
     omegas = np.atleast_1d(np.asarray(omegas, dtype=np.float64))
@@ -195,7 +197,7 @@ def reconstruct(W, omegas, g: Geometry, delta, c0=1.0, opts: Options | None = No
         dnu = opts.tau * max(delta, opts.delta_floor) * np.linalg.norm(W[j])
         afix = None if opts.alpha_given is None else float(np.atleast_1d(opts.alpha_given)[j])
         Vt, alpha, active, nfl = solve_modes(Wt, om, k0, g, dnu, opts, afix)
-        Ut = interior_field(Vt, om, k0, g, opts.mode_rows)
+        Ut = interior_field(Vt, om, k0, g, opts.mode_rows, None if u0s is None else u0s[j])
         Vs.append(ifft2(Vt))
         us.append(ifft2(Ut))
         Vts.append(Vt)

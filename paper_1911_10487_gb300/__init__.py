@@ -115,6 +115,11 @@ class Reconstructor:
             xi, c, alpha = out
         if isinstance(options.get("kernel_plan"), KernelPlan):
             options["kernel_plan"] = options["kernel_plan"].handle
+        if "incident" in options and hasattr(options["incident"], "data_ptr"):
+            u0 = options["incident"]
+            if u0.dtype != W.dtype or tuple(u0.shape) != (n_om, geom.m, geom.n, geom.n) or not u0.is_contiguous():
+                raise ValueError("incident must be a contiguous [n_omega, M, N, N] tensor of W's dtype")
+            options["incident"] = u0.data_ptr()
         opts = make_options(**options) if options else None
         fs_reconstruct(self.ctx, geom.c_struct(), prec, W.data_ptr(), omega, delta, c0, opts,
                        xi.data_ptr(), c.data_ptr() if c is not None else None,
@@ -147,8 +152,19 @@ class Reconstructor:
         fs_reconstruct_batch(self.ctx, probs, prec, opts, n_streams)
         return res
 
-    def forward_born(self, xi, omega, geom: Geometry, c0: float = 1.0, precision: str = "fp64"):
-        """Single-scattering data W[n_omega, M1, N, N] of xi[M, N, N] (device tensors)."""
+    def incident_point_sources(self, sources, omega, geom: Geometry, c0: float = 1.0, precision: str = "fp64"):
+        """Incident field u0[n_omega, M, N, N] on the X planes of point sources (x, y, z, a),
+        Sec. 5, in the periodic model (grid nodes -L/2 + i L/N)."""
+        import torch
+        prec = PRECISIONS[precision]
+        cdt = torch.complex128 if prec == FS_FP64 else torch.complex64
+        u0 = torch.empty((len(omega), geom.m, geom.n, geom.n), dtype=cdt, device=self.device)
+        _abi.fs_incident_point_sources(self.ctx, geom.c_struct(), prec, sources, omega, c0, u0.data_ptr())
+        return u0
+
+    def forward_born(self, xi, omega, geom: Geometry, c0: float = 1.0, precision: str = "fp64", incident=None):
+        """Single-scattering data W[n_omega, M1, N, N] of xi[M, N, N] (device tensors); the
+        plane incident wave unless `incident` (u0[n_omega, M, N, N] on X) is given."""
         import torch
         prec = PRECISIONS[precision]
         rdt = torch.float64 if prec == FS_FP64 else torch.float32
@@ -158,7 +174,11 @@ class Reconstructor:
         if tuple(xi.shape) != (geom.m, geom.n, geom.n):
             raise ValueError("xi shape does not match the geometry")
         W = torch.empty((len(omega), geom.m1, geom.n, geom.n), dtype=cdt, device=self.device)
-        fs_forward_born(self.ctx, geom.c_struct(), prec, xi.data_ptr(), omega, c0, W.data_ptr())
+        if incident is not None and (incident.dtype != cdt or tuple(incident.shape) != (len(omega), geom.m, geom.n, geom.n)
+                                     or not incident.is_contiguous()):
+            raise ValueError("incident must be a contiguous [n_omega, M, N, N] tensor of the working precision")
+        fs_forward_born(self.ctx, geom.c_struct(), prec, xi.data_ptr(), omega, c0, W.data_ptr(),
+                        incident.data_ptr() if incident is not None else None)
         return W
 
     def forward(self, xi, omega, geom: Geometry, c0: float = 1.0, precision: str = "fp64", max_iter: int = 500,

@@ -23,7 +23,7 @@ EXPORTS = ("fs_version", "fs_default_options", "fs_create", "fs_destroy", "fs_la
            "fs_get_report", "fs_sync_status", "fs_measure_alu_peaks", "fs_eval_reciprocals", "fs_reconstruct_static", "fs_reconstruct_batch",
            "fs_diff_plan_create", "fs_diff_plan_destroy", "fs_diff_tape_bytes", "fs_diff_scratch_bytes",
            "fs_reconstruct_diff", "fs_reconstruct_vjp", "fs_reconstruct_jvp",
-           "fs_kernel_plan_create", "fs_kernel_plan_destroy", "fs_kernel_plan_bytes")
+           "fs_kernel_plan_create", "fs_kernel_plan_destroy", "fs_kernel_plan_bytes", "fs_incident_point_sources")
 
 
 class fs_geometry(C.Structure):
@@ -37,7 +37,7 @@ class fs_options(C.Structure):
                 ("alpha_given", C.POINTER(C.c_double)), ("max_iter", C.c_int),
                 ("refine_iters", C.c_int), ("fp64_switch", C.c_double), ("stage_timing", C.c_int),
                 ("solve_blocks_per_sm", C.c_int), ("solve_form", C.c_int), ("regularizer", C.c_int),
-                ("kernel_plan", C.c_void_p)]
+                ("kernel_plan", C.c_void_p), ("incident", C.c_void_p)]
 
 
 STAGES = ("fft_x_forward", "fft_y_forward_norms", "classify", "solve", "ifft_y_gather", "ifft_x_recover")
@@ -104,7 +104,9 @@ def lib():
         L.fs_reconstruct_host.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, C.c_double,
                                           C.POINTER(fs_options), vp, vp]
         L.fs_forward_born.restype = ip
-        L.fs_forward_born.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, vp]
+        L.fs_forward_born.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, vp, dp, ip, C.c_double, vp]
+        L.fs_incident_point_sources.restype = ip
+        L.fs_incident_point_sources.argtypes = [vp, C.POINTER(fs_geometry), ip, dp, ip, dp, ip, C.c_double, vp]
         L.fs_forward.restype = ip
         L.fs_forward.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, ip, ip, C.c_double, vp,
                                  vp, C.POINTER(C.c_int)]
@@ -204,11 +206,21 @@ def fs_reconstruct_host(ctx, geom, prec, W_ptr, omega, delta, c0, opts, xi_ptr, 
     _check(ctx, st, "fs_reconstruct_host")
 
 
-def fs_forward_born(ctx, geom, prec, xi_ptr, omega, c0, W_ptr):
+def fs_forward_born(ctx, geom, prec, xi_ptr, omega, c0, W_ptr, incident_ptr=None):
     om = (C.c_double * len(omega))(*[float(x) for x in omega])
-    st = lib().fs_forward_born(ctx, C.byref(geom), int(prec), C.c_void_p(xi_ptr), om, len(omega),
-                               float(c0), C.c_void_p(W_ptr))
+    st = lib().fs_forward_born(ctx, C.byref(geom), int(prec), C.c_void_p(xi_ptr), C.c_void_p(incident_ptr or None), om,
+                               len(omega), float(c0), C.c_void_p(W_ptr))
     _check(ctx, st, "fs_forward_born")
+
+
+def fs_incident_point_sources(ctx, geom, prec, sources, omega, c0, u0_ptr):
+    """sources: sequence of (x, y, z, amplitude)."""
+    flat = [float(v) for src in sources for v in src]
+    sp = (C.c_double * len(flat))(*flat)
+    om = (C.c_double * len(omega))(*[float(x) for x in omega])
+    st = lib().fs_incident_point_sources(ctx, C.byref(geom), int(prec), sp, len(sources), om, len(omega), float(c0),
+                                         C.c_void_p(u0_ptr))
+    _check(ctx, st, "fs_incident_point_sources")
 
 
 FS_FIXED_POINT, FS_GMRES, FS_FIXED_POINT_GMRES = 0, 1, 2
@@ -293,8 +305,8 @@ def make_options(**kw) -> fs_options:
             arr = (C.c_double * len(v))(*[float(x) for x in v])
             o.alpha_given = C.cast(arr, C.POINTER(C.c_double))
             o._keep = arr
-        elif k == "kernel_plan":
-            o.kernel_plan = v.value if isinstance(v, C.c_void_p) else v
+        elif k in ("kernel_plan", "incident"):
+            setattr(o, k, v.value if isinstance(v, C.c_void_p) else v)
         else:
             setattr(o, k, v)
     return o

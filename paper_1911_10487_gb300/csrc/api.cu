@@ -10,6 +10,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <cmath>
+
 #include <atomic>
 #include <vector>
 
@@ -126,15 +128,22 @@ Layout layout(int n, int m, int m1, int n_omega, bool fp64) {
 }
 
 fs_status validate_args(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, int n_omega, const double* omega,
-                   double delta, double c0, const fs_options* o) {
+                        double delta, double c0, const fs_options* o, bool dense_solve) {
   if (!g) return fail(ctx, FS_EINVAL, "geometry is NULL");
   if (prec != FS_FP64 && prec != FS_MIXED) return fail(ctx, FS_EINVAL, "unknown precision");
   if (g->n <= 0 || g->m <= 0 || g->m1 <= 0) return fail(ctx, FS_EINVAL, "grid sizes must be positive");
   if (!fft_size_supported(g->n))
     return fail(ctx, FS_EUNSUPPORTED, "N=%d not supported (8,12,16,24,32,48,64,96,128,192,256)",
                 g->n);
-  if (g->m > MAX_M) return fail(ctx, FS_EUNSUPPORTED, "M=%d exceeds 64", g->m);
-  if (g->m1 > MAX_M1) return fail(ctx, FS_EUNSUPPORTED, "M1=%d exceeds 32", g->m1);
+  if (g->m > MAX_M) return fail(ctx, FS_EUNSUPPORTED, "M=%d exceeds %d", g->m, MAX_M);
+  if (g->m1 > MAX_M1) return fail(ctx, FS_EUNSUPPORTED, "M1=%d exceeds %d", g->m1, MAX_M1);
+  // the dense per-mode solve (solve_form 0, the default) holds A_nu in shared memory
+  const bool dense = dense_solve && (!o || o->solve_form == 0);
+  if (dense && (g->m > DENSE_M || g->m1 > DENSE_M1))
+    return fail(ctx, FS_EUNSUPPORTED,
+                "the dense form solves M <= %d, M1 <= %d (got M=%d, M1=%d); larger layers take the rank-one form "
+                "(solve_form 1)",
+                DENSE_M, DENSE_M1, g->m, g->m1);
   if (n_omega <= 0) return fail(ctx, FS_EINVAL, "n_omega must be positive");
   if (n_omega > MAX_OMEGA) return fail(ctx, FS_EUNSUPPORTED, "n_omega=%d exceeds 64", n_omega);
   if (!omega) return fail(ctx, FS_EINVAL, "omega is NULL");
@@ -188,6 +197,7 @@ Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, dou
   P.solve_form = o.solve_form;
   P.regularizer = o.regularizer;
   P.sampled = o.kernel_plan ? 1 : 0;
+  P.incident = o.incident ? 1 : 0;
   for (int k = 0; k < g->m1; ++k) P.zy[k] = g->zy[k];
   for (int j = 0; j < n_omega; ++j) {
     P.omega[j] = omega[j];
@@ -235,6 +245,7 @@ Work<R> carve_work(void* base, const Layout& L, unsigned long long* ctr, const c
   w.tw64 = nullptr;
   w.ktab = nullptr;
   w.ktr = nullptr;
+  w.u0 = nullptr;
   return w;
 }
 
@@ -333,7 +344,8 @@ fs_status ensure_twiddles(fs_ctx* ctx, int n, const cx<R>** out) {
 // not reset here).  Twiddles for P.n must exist.
 template <typename R>
 fs_status run_on(fs_ctx* ctx, const Problem& P, const Layout& L, void* base, cudaStream_t s, const void* W,
-                 void* xi, void* c, double* alpha_out, cudaEvent_t* ev, const fs_kernel_plan* kp = nullptr) {
+                 void* xi, void* c, double* alpha_out, cudaEvent_t* ev, const fs_kernel_plan* kp = nullptr,
+                 const void* u0 = nullptr) {
   const cx<R>* tw = (const cx<R>*)ctx->tw[sizeof(R) == 8 ? 1 : 0][size_index(P.n)];
   Work<R> w = carve_work<R>(base, L, ctx->ctr, tw, alpha_out);
   if (wide_route(P, sizeof(R) == 8)) {
@@ -341,6 +353,7 @@ fs_status run_on(fs_ctx* ctx, const Problem& P, const Layout& L, void* base, cud
     w.tw64 = (const double2*)ctx->tw[1][size_index(P.n)];
   }
   if (kp) kernel_plan_tables(kp, &w.ktab, &w.ktr);
+  if (P.incident) w.u0 = (const cx<R>*)u0;
   const char* stage = "";
   const cudaError_t e = launch_pipeline<R>(P, w, W, xi, c, s, ev, &stage);
   return e == cudaSuccess ? FS_OK : cuda_fail(ctx, e, stage);
@@ -348,7 +361,7 @@ fs_status run_on(fs_ctx* ctx, const Problem& P, const Layout& L, void* base, cud
 
 template <typename R>
 fs_status run(fs_ctx* ctx, const Problem& P, const Layout& L, const void* W, void* xi, void* c,
-              double* alpha_out, bool timed, const fs_kernel_plan* kp) {
+              double* alpha_out, bool timed, const fs_kernel_plan* kp, const void* u0) {
   const cx<R>* tw = nullptr;
   fs_status st = ensure_twiddles<R>(ctx, P.n, &tw);
   if (st != FS_OK) return st;
@@ -359,7 +372,7 @@ fs_status run(fs_ctx* ctx, const Problem& P, const Layout& L, const void* W, voi
   cudaError_t e = cudaMemsetAsync(ctx->ctr, 0, sizeof(unsigned long long) * C_COUNT, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
   ctx->timed = timed;
-  return run_on<R>(ctx, P, L, ctx->ws, ctx->stream, W, xi, c, alpha_out, timed ? ctx->ev : nullptr, kp);
+  return run_on<R>(ctx, P, L, ctx->ws, ctx->stream, W, xi, c, alpha_out, timed ? ctx->ev : nullptr, kp, u0);
 }
 
 }  // namespace
@@ -384,6 +397,7 @@ fs_status fs_default_options(fs_options* o) {
   o->solve_form = 0;
   o->regularizer = 0;
   o->kernel_plan = nullptr;
+  o->incident = nullptr;
   return FS_OK;
 }
 
@@ -462,8 +476,8 @@ fs_status fs_reconstruct(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, c
   const bool timed = o.stage_timing != 0;
   if (o.kernel_plan && kernel_plan_device(o.kernel_plan) != ctx->device)
     return fail(ctx, FS_EINVAL, "the kernel plan lives on another device");
-  return fp64 ? run<double>(ctx, P, L, W, xi, c, alpha_out, timed, o.kernel_plan)
-              : run<float>(ctx, P, L, W, xi, c, alpha_out, timed, o.kernel_plan);
+  return fp64 ? run<double>(ctx, P, L, W, xi, c, alpha_out, timed, o.kernel_plan, o.incident)
+              : run<float>(ctx, P, L, W, xi, c, alpha_out, timed, o.kernel_plan, o.incident);
 }
 
 fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const void* W_host,
@@ -512,7 +526,7 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
     key.insert(key.end(), (const unsigned char*)omega, (const unsigned char*)(omega + n_omega));
     if (o.alpha_mode == 1)
       key.insert(key.end(), (const unsigned char*)o.alpha_given, (const unsigned char*)(o.alpha_given + n_omega));
-    const void* ptrs[7] = {W_host, xi_host, c_host, ctx->stage, ctx->ws, ctx->stream, o.kernel_plan};
+    const void* ptrs[8] = {W_host, xi_host, c_host, ctx->stage, ctx->ws, ctx->stream, o.kernel_plan, o.incident};
     key_put(key, ptrs);
     if (ctx->host_exec && key == ctx->host_key) {
       if ((e = cudaGraphLaunch(ctx->host_exec, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
@@ -537,7 +551,7 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
   if (graphable) {
     // the run above sized the workspace and twiddles, so the capture allocates
     // nothing; the key is taken again in case the workspace moved
-    const void* ptrs[7] = {W_host, xi_host, c_host, ctx->stage, ctx->ws, ctx->stream, o.kernel_plan};
+    const void* ptrs[8] = {W_host, xi_host, c_host, ctx->stage, ctx->ws, ctx->stream, o.kernel_plan, o.incident};
     key.resize(key.size() - sizeof(ptrs));
     key_put(key, ptrs);
     if (ctx->host_exec) {
@@ -572,6 +586,7 @@ fs_status fs_reconstruct_batch(fs_ctx* ctx, const fs_problem* probs, int n_probs
   fs_default_options(&o);
   if (opts) o = *opts;
   if (o.kernel_plan) return fail(ctx, FS_EUNSUPPORTED, "batches take the Weyl kernel only (kernel_plan must be NULL)");
+  if (o.incident) return fail(ctx, FS_EUNSUPPORTED, "batches take the plane incident wave only (incident must be NULL)");
   const bool fp64 = prec == FS_FP64;
   size_t total = 0;
   for (int i = 0; i < n_probs; ++i) {
@@ -647,9 +662,9 @@ fs_status fs_reconstruct_batch(fs_ctx* ctx, const fs_problem* probs, int n_probs
 }
 
 fs_status fs_forward_born(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const void* xi,
-                          const double* omega, int n_omega, double c0, void* W) {
+                          const void* incident, const double* omega, int n_omega, double c0, void* W) {
   if (!ctx) return FS_EINVAL;
-  fs_status st = validate_args(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr);
+  fs_status st = validate_args(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr, false);
   if (st != FS_OK) return st;
   if (!xi || !W) return fail(ctx, FS_EINVAL, "xi and W must be device pointers");
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -663,11 +678,13 @@ fs_status fs_forward_born(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, 
   if (fp64) {
     const double2* tw = nullptr;
     if ((st = ensure_twiddles<double>(ctx, g->n, &tw)) != FS_OK) return st;
-    e = launch_forward_born<double>(P, (const double*)xi, (double2*)ctx->ws, (double2*)W, tw, ctx->stream);
+    e = launch_forward_born<double>(P, (const double*)xi, (const double2*)incident, (double2*)ctx->ws, (double2*)W, tw,
+                                    ctx->stream);
   } else {
     const float2* tw = nullptr;
     if ((st = ensure_twiddles<float>(ctx, g->n, &tw)) != FS_OK) return st;
-    e = launch_forward_born<float>(P, (const float*)xi, (float2*)ctx->ws, (float2*)W, tw, ctx->stream);
+    e = launch_forward_born<float>(P, (const float*)xi, (const float2*)incident, (float2*)ctx->ws, (float2*)W, tw,
+                                   ctx->stream);
   }
   return e == cudaSuccess ? FS_OK : cuda_fail(ctx, e, "forward_born");
 }
@@ -676,7 +693,7 @@ fs_status fs_forward(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const
                      int n_omega, double c0, fs_forward_method method, int max_iter, double rtol, void* W, void* u,
                      int* iterations) {
   if (!ctx) return FS_EINVAL;
-  fs_status st = validate_args(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr);
+  fs_status st = validate_args(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr, false);
   if (st != FS_OK) return st;
   if (!xi || !W) return fail(ctx, FS_EINVAL, "xi and W must be device pointers");
   if (max_iter < 0) return fail(ctx, FS_EINVAL, "max_iter must be >= 0");
@@ -709,6 +726,43 @@ fs_status fs_forward(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const
     if (!conv[j])
       return fail(ctx, FS_ENOCONV, "the forward solve did not converge for omega[%d] after %d iterations", j, it[j]);
   return FS_OK;
+}
+
+fs_status fs_incident_point_sources(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const double* sources,
+                                    int n_sources, const double* omega, int n_omega, double c0, void* u0) {
+  if (!ctx) return FS_EINVAL;
+  fs_status st = validate_args(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr, false);
+  if (st != FS_OK) return st;
+  if (!u0) return fail(ctx, FS_EINVAL, "u0 must be a device pointer");
+  if (n_sources < 1 || !sources) return fail(ctx, FS_EINVAL, "at least one source is needed");
+  std::vector<double> spec(4 * (size_t)n_sources);
+  for (int j = 0; j < n_sources; ++j) {
+    for (int c = 0; c < 4; ++c) spec[4 * j + c] = sources[4 * j + c];
+    if (!std::isfinite(spec[4 * j]) || !std::isfinite(spec[4 * j + 1]) || !std::isfinite(spec[4 * j + 3]))
+      return fail(ctx, FS_EINVAL, "source %d is not finite", j);
+    if (!(spec[4 * j + 2] > g->z2)) return fail(ctx, FS_EINVAL, "source %d is not above X", j);
+  }
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  const size_t need = align_up(32 * (size_t)n_sources);
+  if ((st = ensure_workspace(ctx, need)) != FS_OK) return st;
+  if ((e = cudaMemcpyAsync(ctx->ws, spec.data(), 32 * (size_t)n_sources, cudaMemcpyHostToDevice, ctx->stream)) !=
+      cudaSuccess)
+    return cuda_fail(ctx, e, "source copy");
+  fs_options o;
+  fs_default_options(&o);
+  const Problem P = make_problem(g, n_omega, omega, 0.0, c0, o);
+  if (prec == FS_FP64) {
+    const double2* tw = nullptr;
+    if ((st = ensure_twiddles<double>(ctx, g->n, &tw)) != FS_OK) return st;
+    e = launch_point_sources<double>(P, (const double*)ctx->ws, n_sources, (double2*)u0, tw, ctx->stream);
+  } else {
+    const float2* tw = nullptr;
+    if ((st = ensure_twiddles<float>(ctx, g->n, &tw)) != FS_OK) return st;
+    e = launch_point_sources<float>(P, (const double*)ctx->ws, n_sources, (float2*)u0, tw, ctx->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the host copy of spec must outlive it
+  return e == cudaSuccess ? FS_OK : cuda_fail(ctx, e, "point sources");
 }
 
 fs_status fs_get_report(fs_ctx* ctx, fs_report* r) {

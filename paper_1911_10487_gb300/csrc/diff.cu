@@ -45,11 +45,11 @@ constexpr int GT = 128;           // threads of the normal-matrix kernel
 constexpr double AP_MAX = 1e290;  // alpha' above this: H^ = alpha' I to FP64, V~ = 0
 
 struct WarpMem {
-  double2 H[MAX_M1][MAX_M1 + 1];  // H^ (lower triangle) -> Cholesky factor L
-  double2 E[MAX_M1];              // E_k / sqrt(sum |E|^2)
-  double2 Pz[MAX_M];              // P_l / sqrt(sum |P|^2)
-  double2 v[MAX_M], t[MAX_M], F[MAX_M], B[MAX_M];
-  double dinv[MAX_M1];            // 1 / L_jj
+  double2 H[DENSE_M1][DENSE_M1 + 1];  // H^ (lower triangle) -> Cholesky factor L
+  double2 E[DENSE_M1];              // E_k / sqrt(sum |E|^2)
+  double2 Pz[DENSE_M];              // P_l / sqrt(sum |P|^2)
+  double2 v[DENSE_M], t[DENSE_M], F[DENSE_M], B[DENSE_M];
+  double dinv[DENSE_M1];            // 1 / L_jj
 };
 
 struct ModeGeo {
@@ -115,7 +115,7 @@ __device__ __forceinline__ void store_lower(double2* __restrict__ dst, const War
 // (row, column) of the packed lower triangle in column-major order (column j holds
 // rows j..n-1), one entry per element, for the trailing updates of the Cholesky
 // factorisation; built once per block for the problem's M1.
-constexpr int MAX_P1 = MAX_M1 * (MAX_M1 + 1) / 2;
+constexpr int MAX_P1 = DENSE_M1 * (DENSE_M1 + 1) / 2;
 __device__ void build_rc(unsigned short* rc, int n) {
   const int P1 = n * (n + 1) / 2;
   for (int e = threadIdx.x; e < P1; e += blockDim.x) {
@@ -239,8 +239,8 @@ __device__ __forceinline__ void block_partial(double v, double* red, double* par
 // normal matrices G^ = A^ A^^H, one block per mode (A^ staged in shared memory)
 // ---------------------------------------------------------------------------
 struct GramMem {
-  double2 A[MAX_M1][MAX_M + 1];
-  double2 E[MAX_M1], Pz[MAX_M];  // filled by warp 0 (mode_setup)
+  double2 A[DENSE_M1][DENSE_M + 1];
+  double2 E[DENSE_M1], Pz[DENSE_M];  // filled by warp 0 (mode_setup)
   int usable;
 };
 

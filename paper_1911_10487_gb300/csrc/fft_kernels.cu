@@ -181,7 +181,7 @@ k_ifft_cols_gather(Problem P, const cx<R>* __restrict__ prof, const int* __restr
         const int s = slot[om * N2 + (long long)i * N + nu1];
         if (s >= 0) {
           v = prof[(((long long)om * N2 + s) * 2 + f) * M + l];
-        } else if (f == 1 && i == 0 && nu1 == 0) {  // one thread: FP64 is slow on this GPU
+        } else if (f == 1 && i == 0 && nu1 == 0 && !P.incident) {  // one thread: FP64 is slow on this GPU
           double sn, cs;
           sincos(-(P.omega[om] / P.c0) * (P.z1 + (l + 0.5) * P.hz), &sn, &cs);
           v = from_d<R>(make_double2((double)N2 * cs, (double)N2 * sn));
@@ -231,7 +231,8 @@ template <> __device__ __forceinline__ double inv_sqrt<double>(double x) { retur
 template <typename R, int N, typename A>
 __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __restrict__ t2,
                                              const int* __restrict__ cols, const int* __restrict__ ncol,
-                                             cx<R>* buf, const cx<R>* tw_s, A* num, A* den) {
+                                             const cx<R>* __restrict__ u0, cx<R>* buf, const cx<R>* tw_s, A* num,
+                                             A* den) {
   constexpr int LINES = row_lines<N>() / 2 > 0 ? row_lines<N>() / 2 : 1;
   constexpr int E = LINES * N;
   using IX = LayIdx<Lay::ROW, N, 2 * LINES, SKEW_RECOVER>;  // V~ lines, then U~ lines
@@ -265,7 +266,11 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
       const int e = threadIdx.x + p * THREADS;
       if (e < E) {
         const cx<R> v = scale * buf[IX::at(e / N, e % N)];
-        const cx<R> u = scale * buf[IX::at(LINES + e / N, e % N)];
+        cx<R> u = scale * buf[IX::at(LINES + e / N, e % N)];
+        if (u0) {  // the given incident field (the transform holds U~ - U~0)
+          const long long r = row0 + e / N;
+          if (r < nrows) u = u + u0[((long long)om * M + r / N) * N2 + (r % N) * N + (e % N)];
+        }
         num[p] += (A)u.x * (A)v.x + (A)u.y * (A)v.y;  // Re(conj(u) V)
         den[p] += (A)u.x * (A)u.x + (A)u.y * (A)u.y;  // |u|^2
       }
@@ -281,8 +286,8 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
 template <typename R, int N>
 __global__ void __launch_bounds__(THREADS)
 k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restrict__ cols,
-                    const int* __restrict__ ncol, R* __restrict__ xi, R* __restrict__ cout,
-                    unsigned long long* __restrict__ ctr, const cx<R>* __restrict__ tw) {
+                    const int* __restrict__ ncol, const cx<R>* __restrict__ u0, R* __restrict__ xi,
+                    R* __restrict__ cout, unsigned long long* __restrict__ ctr, const cx<R>* __restrict__ tw) {
   pdl_wait();
   pdl_trigger();
   constexpr int LINES = row_lines<N>() / 2 > 0 ? row_lines<N>() / 2 : 1;
@@ -295,11 +300,11 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
   const long long nrows = (long long)P.m * N;
   const long long row0 = (long long)blockIdx.x * LINES;
   R num[PER], den[PER];
-  if (recover_pass<R, N, R>(P, t2, cols, ncol, buf, tw_s, num, den)) {
+  if (recover_pass<R, N, R>(P, t2, cols, ncol, u0, buf, tw_s, num, den)) {
     // the sums left the range of R (|u| |V| beyond FP32 for huge evanescent
     // profiles): redo this block with FP64 sums; xi itself is in range
     double nd[PER], dd[PER];
-    recover_pass<R, N, double>(P, t2, cols, ncol, buf, tw_s, nd, dd);
+    recover_pass<R, N, double>(P, t2, cols, ncol, u0, buf, tw_s, nd, dd);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const bool g = !(dd[p] >= (double)P.n_omega * P.eps_u * P.eps_u);
@@ -409,7 +414,8 @@ cudaError_t rec_impl(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream
   constexpr int LINES = row_lines<N>() / 2 > 0 ? row_lines<N>() / 2 : 1;
   const long long nrows = (long long)P.m * N;
   e = launch_pdl(k_ifft_rows_recover<R, N>, dim3((unsigned)((nrows + LINES - 1) / LINES)), dim3(THREADS), 0, s, P,
-                 (const cx<R>*)w.t2, (const int*)w.cols, (const int*)w.ncol, xi, c, w.ctr, (const cx<R>*)w.tw);
+                 (const cx<R>*)w.t2, (const int*)w.cols, (const int*)w.ncol, w.u0, xi, c, w.ctr,
+                 (const cx<R>*)w.tw);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

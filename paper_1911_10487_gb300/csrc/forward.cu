@@ -25,8 +25,17 @@ namespace fl {
 
 namespace {
 
+__device__ __forceinline__ double2 exp_ikz(double2 kz, double d) {
+  const double mag = exp(-kz.y * d);
+  double s, c;
+  sincos(kz.x * d, &s, &c);
+  return make_double2(mag * c, mag * s);
+}
+
+// V = xi u0 on X (omega^2 sits in the kernel factor); u0 the plane wave, or the given
+// incident field u0i [n_omega][M][N][N]
 template <typename R>
-__global__ void k_source(Problem P, const R* __restrict__ xi, cx<R>* __restrict__ src) {
+__global__ void k_source(Problem P, const R* __restrict__ xi, const cx<R>* __restrict__ u0i, cx<R>* __restrict__ src) {
   const long long N2 = (long long)P.n * P.n;
   const long long per = (long long)P.m * N2;
   const long long total = per * P.n_omega;
@@ -34,20 +43,56 @@ __global__ void k_source(Problem P, const R* __restrict__ xi, cx<R>* __restrict_
        e += (long long)gridDim.x * blockDim.x) {
     const int om = (int)(e / per);
     const long long r = e - om * per;
+    const R x = xi[r];
+    if (u0i) {
+      const cx<R> u = u0i[e];
+      src[e] = mk<R>(x * u.x, x * u.y);
+      continue;
+    }
     const int l = (int)(r / N2);
     const double k0 = P.omega[om] / P.c0;
     double s, c;
     sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s, &c);
-    const double x = (double)xi[r];  // V = xi u0; omega^2 sits in the kernel factor
-    src[e] = from_d<R>(make_double2(x * c, x * s));
+    src[e] = from_d<R>(make_double2((double)x * c, (double)x * s));
   }
 }
 
-__device__ __forceinline__ double2 exp_ikz(double2 kz, double d) {
-  const double mag = exp(-kz.y * d);
-  double s, c;
-  sincos(kz.x * d, &s, &c);
-  return make_double2(mag * c, mag * s);
+// U~0 of point sources on the X planes (periodic model, Sec. 5): thread per (omega, l, nu),
+// U~0 = (N^2/L^2) sum_s a_s K_nu(z'_l - z_s) e^{-i nu.(r_s - x0)}, K_nu(dz) = -i e^{i k_z|dz|}/(2 k_z),
+// x0 = -L/2 (the grid's first node); zero on grazing modes
+template <typename R>
+__global__ void k_point_sources(Problem P, const double* __restrict__ spec, int n_src, cx<R>* __restrict__ ut) {
+  const int N = P.n;
+  const long long N2 = (long long)N * N;
+  const long long total = (long long)P.n_omega * P.m * N2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long pl = e / N2;
+    const int nu = (int)(e - pl * N2);
+    const int om = (int)(pl / P.m), l = (int)(pl - (long long)om * P.m);
+    const int i2 = nu / N, i1 = nu - i2 * N;
+    const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
+    const int msq = m1 * m1 + m2 * m2;
+    double2 acc = make_double2(0.0, 0.0);
+    if (!(msq >= P.graz_lo[om] && msq <= P.graz_hi[om])) {
+      const double k0 = P.k0[om];
+      const double q = k0 * k0 - P.kn * P.kn * (double)msq;
+      const double2 kz = q >= 0.0 ? make_double2(sqrt(q), 0.0) : make_double2(0.0, sqrt(-q));
+      // -i / (2 k_z): k_z real -> (0, -1/(2 k_z)); k_z = i kappa -> (-1/(2 kappa), 0)
+      const double2 g = q >= 0.0 ? make_double2(0.0, -0.5 / kz.x) : make_double2(-0.5 / kz.y, 0.0);
+      const double zl = P.z1 + (l + 0.5) * P.hz, x0 = -0.5 * P.period;
+      const double nu1 = P.kn * m1, nu2 = P.kn * m2;
+      for (int j = 0; j < n_src; ++j) {
+        const double* sp = spec + 4 * j;
+        const double2 ez = exp_ikz(kz, sp[2] - zl);  // sources above X: |dz| = z_s - z'_l
+        double sn, cs;
+        sincos(-(nu1 * (sp[0] - x0) + nu2 * (sp[1] - x0)), &sn, &cs);
+        acc = acc + sp[3] * (ez * make_double2(cs, sn));
+      }
+      acc = (double)N2 / (P.period * P.period) * (g * acc);
+    }
+    ut[e] = from_d<R>(acc);
+  }
 }
 
 template <typename R>
@@ -87,10 +132,24 @@ __global__ void k_apply_data(Problem P, const cx<R>* __restrict__ vt, cx<R>* __r
 }  // namespace
 
 template <typename R>
-cudaError_t launch_forward_born(const Problem& P, const R* xi, cx<R>* src, cx<R>* W, const cx<R>* tw,
-                                cudaStream_t s) {
+cudaError_t launch_point_sources(const Problem& P, const double* spec, int n_src, cx<R>* u0, const cx<R>* tw,
+                                 cudaStream_t s) {
+  k_point_sources<R><<<2048, 256, 0, s>>>(P, spec, n_src, u0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_fft2_dense<R>(u0, u0, P.n, (long long)P.n_omega * P.m, true, tw, s);
+}
+
+template cudaError_t launch_point_sources<double>(const Problem&, const double*, int, double2*, const double2*,
+                                                  cudaStream_t);
+template cudaError_t launch_point_sources<float>(const Problem&, const double*, int, float2*, const float2*,
+                                                 cudaStream_t);
+
+template <typename R>
+cudaError_t launch_forward_born(const Problem& P, const R* xi, const cx<R>* u0, cx<R>* src, cx<R>* W,
+                                const cx<R>* tw, cudaStream_t s) {
   const long long N2 = (long long)P.n * P.n;
-  k_source<R><<<1024, 256, 0, s>>>(P, xi, src);
+  k_source<R><<<1024, 256, 0, s>>>(P, xi, u0, src);
   cudaError_t e = launch_fft2_dense<R>(src, src, P.n, (long long)P.n_omega * P.m, false, tw, s);
   if (e != cudaSuccess) return e;
   const long long modes = N2 * P.n_omega;
@@ -99,10 +158,10 @@ cudaError_t launch_forward_born(const Problem& P, const R* xi, cx<R>* src, cx<R>
   return launch_fft2_dense<R>(W, W, P.n, (long long)P.n_omega * P.m1, true, tw, s);
 }
 
-template cudaError_t launch_forward_born<double>(const Problem&, const double*, double2*, double2*,
+template cudaError_t launch_forward_born<double>(const Problem&, const double*, const double2*, double2*, double2*,
                                                  const double2*, cudaStream_t);
-template cudaError_t launch_forward_born<float>(const Problem&, const float*, float2*, float2*, const float2*,
-                                                cudaStream_t);
+template cudaError_t launch_forward_born<float>(const Problem&, const float*, const float2*, float2*, float2*,
+                                                const float2*, cudaStream_t);
 
 
 // ---- Algorithm 1 (fixed point of eq. 6) -------------------------------------

@@ -145,4 +145,37 @@ __device__ __forceinline__ void affine_scan64(const double2* s, int len, double2
   if (l1 < len) out[l1] = B;
 }
 
+// The same recurrence F_l = q F_{l-1} + s_l for l < len <= 32 EPL, lanes owning EPL
+// consecutive elements: each lane composes its elements' affine maps x -> q x + s_l,
+// the warp scans the composed maps (inclusive), and each lane replays its elements
+// from the value the scan leaves before it.
+template <int EPL>
+__device__ __forceinline__ void affine_scan_lanes(const double2* s, int len, double2 q, double2* out) {
+  const int lane = threadIdx.x & 31;
+  const int l0 = EPL * lane;
+  double2 v[EPL];
+  double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
+#pragma unroll
+  for (int j = 0; j < EPL; ++j) {
+    v[j] = l0 + j < len ? s[l0 + j] : make_double2(0.0, 0.0);
+    B = q * B + v[j];
+    A = q * A;
+  }
+  for (int off = 1; off < 32; off <<= 1) {
+    const double2 Ap = make_double2(__shfl_up_sync(0xffffffffu, A.x, off), __shfl_up_sync(0xffffffffu, A.y, off));
+    const double2 Bp = make_double2(__shfl_up_sync(0xffffffffu, B.x, off), __shfl_up_sync(0xffffffffu, B.y, off));
+    if (lane >= off) {
+      B = A * Bp + B;
+      A = A * Ap;
+    }
+  }
+  double2 prev = make_double2(__shfl_up_sync(0xffffffffu, B.x, 1), __shfl_up_sync(0xffffffffu, B.y, 1));
+  if (lane == 0) prev = make_double2(0.0, 0.0);
+#pragma unroll
+  for (int j = 0; j < EPL; ++j) {
+    prev = q * prev + v[j];
+    if (l0 + j < len) out[l0 + j] = prev;
+  }
+}
+
 }  // namespace fl

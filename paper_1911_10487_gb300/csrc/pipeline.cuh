@@ -12,8 +12,12 @@
 
 namespace fl {
 
-constexpr int MAX_M1 = 32;      // data planes per problem (dual Gram is M1 x M1)
-constexpr int MAX_M = 64;       // X planes per problem
+constexpr int MAX_M1 = 128;     // data planes per problem
+constexpr int MAX_M = 128;      // X planes per problem
+// the dense per-mode solve and the derivative kernels hold A_nu (M1 x M) and its
+// factorisations in shared memory: their limits
+constexpr int DENSE_M1 = 32;
+constexpr int DENSE_M = 64;
 constexpr int MAX_OMEGA = 64;   // frequencies per problem
 constexpr int MAX_N = 256;      // horizontal points per axis
 
@@ -47,6 +51,7 @@ struct Problem {
   double kn;
   double inv_c02, u_guard;  // c0^-2 and the |u|^2 guard eps_u^2 n_omega of the recovery
   int sampled;  // 1: the sampled-G kernel of a kernel plan (Work::ktab) replaces the Weyl form
+  int incident; // 1: the incident field on X is given (Work::u0) instead of the plane wave
 };
 
 inline void derive_constants(Problem& P) {
@@ -95,6 +100,9 @@ template <typename R> struct Work {
   // and tr(A_nu A_nu^H) at ktr[omega N^2 + nu].  Null otherwise.
   const void* ktab;
   const double* ktr;
+  // the incident field u0 on the X planes, [n_omega][M][N][N] (Problem::incident): the
+  // solve then writes U~ - U~0 and the recovery adds u0 pointwise.  Null otherwise.
+  const cx<R>* u0;
 };
 
 // blocks of 1024 consecutive modes in the classification of an N x N grid
@@ -129,9 +137,11 @@ cudaError_t launch_pipeline(const Problem& P, const Work<R>& w, const void* W, v
 inline bool wide_route(const Problem& P, bool fp64) { return !fp64 && P.regularizer == 1; }
 
 // Argument checks shared by the entry points (the rules of include/flatlayer.h).
-// ctx may be null: the status is returned without a message.
+// ctx may be null: the status is returned without a message.  dense_solve: the call
+// runs the per-mode solve, whose dense form (o null or o->solve_form 0) is limited to
+// DENSE_M x DENSE_M1; the forward generators pass false.
 fs_status validate_args(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, int n_omega, const double* omega,
-                        double delta, double c0, const fs_options* o);
+                        double delta, double c0, const fs_options* o, bool dense_solve = true);
 // The by-value problem description of validated arguments.
 Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, double delta, double c0,
                      const fs_options& o);
@@ -183,10 +193,18 @@ cudaError_t launch_kernel_tables(const Problem& P, int om, double2* gs, double2*
                                  void* tab, double* tr, cudaStream_t s);
 inline int kernel_table_width(const Problem& P) { return P.m1 * P.m + P.m; }
 
-// forward data generator (single scattering): W = F^-1[ A_nu F[omega^2 xi u0] ]
+// forward data generator (single scattering): W = F^-1[ A_nu F[omega^2 xi u0] ], u0 the
+// plane wave or, when given, the incident field u0 [n_omega][M][N][N] on X
 template <typename R>
-cudaError_t launch_forward_born(const Problem& P, const R* xi, cx<R>* src, cx<R>* W, const cx<R>* tw,
-                                cudaStream_t s);
+cudaError_t launch_forward_born(const Problem& P, const R* xi, const cx<R>* u0, cx<R>* src, cx<R>* W,
+                                const cx<R>* tw, cudaStream_t s);
+// the field of point sources on the X planes in the periodic model (Sec. 5): for every
+// frequency and mode U~0_nu(z'_l) = (N^2/L^2) sum_s a_s K_nu(z'_l - z_s) e^{-i nu.(r_s - x0)}
+// (grazing modes zero), then its inverse 2D FFT; spec [n_src][4] = (x, y, z, a), device;
+// u0 [n_omega][M][N][N]; tw the twiddles of N
+template <typename R>
+cudaError_t launch_point_sources(const Problem& P, const double* spec, int n_src, cx<R>* u0, const cx<R>* tw,
+                                 cudaStream_t s);
 // Full-scattering field per frequency -- method 0: Algorithm 1 (fixed point of eq. 6);
 // 1: restarted GMRES on u - omega^2 T(xi u) = u0; 2: Algorithm 1, GMRES where it does
 // not converge -- then the data of eq. (7).  iters and converged (host arrays of

@@ -76,7 +76,7 @@ constexpr int ST = 128;
 // tr(G): a few units of round-off of the normal matrix in each precision
 constexpr float LANCZOS_TOL32 = 1e-6f;
 constexpr double LANCZOS_TOL64 = 1e-14;
-static_assert(ST == 2 * MAX_M && ST == 4 * MAX_M1, "thread maps of the solve assume 2 threads per plane l and 4 per data plane k");
+static_assert(ST == 2 * DENSE_M && ST == 4 * DENSE_M1, "thread maps of the solve assume 2 threads per plane l and 4 per data plane k");
 
 // ------------------------------------------------------------------------------
 // classification (integer arithmetic only), in two passes over blocks of CMB
@@ -320,36 +320,36 @@ __device__ __forceinline__ ffc ffc_shfl_xor(ffc a, int m) {
 // dead after the Lanczos process, so the root search reuses it), and the arrays of
 // eq. (9), written once the solve is done.
 template <typename B> struct Bulk {
-  cx<B> V[MAX_M1][MAX_M1 + 1];  // Lanczos basis, column j = q_j (FP64 route)
-  cx<B> t[MAX_M];               // A^H q_j of the Lanczos step
-  cx<B> w[MAX_M1];              // G q_j of the Lanczos step
+  cx<B> V[DENSE_M1][DENSE_M1 + 1];  // Lanczos basis, column j = q_j (FP64 route)
+  cx<B> t[DENSE_M];               // A^H q_j of the Lanczos step
+  cx<B> w[DENSE_M1];              // G q_j of the Lanczos step
 };
 struct BulkF {
-  float2 Q[MAX_M1][MAX_M1 + 1];  // Lanczos basis, column j = q_j
-  float2 t[MAX_M];               // A^H q_j of the Lanczos step
-  float2 w[MAX_M1];              // G q_j of the Lanczos step
-  float2 p[MAX_M1];              // model solve (T + a I)^-1 Q^H r
+  float2 Q[DENSE_M1][DENSE_M1 + 1];  // Lanczos basis, column j = q_j
+  float2 t[DENSE_M];               // A^H q_j of the Lanczos step
+  float2 w[DENSE_M1];              // G q_j of the Lanczos step
+  float2 p[DENSE_M1];              // model solve (T + a I)^-1 Q^H r
   union {
-    float2 A[MAX_M1][MAX_M + 1];  // A_nu / sqrt(tr G) in FP32, for the Lanczos products
+    float2 A[DENSE_M1][DENSE_M + 1];  // A_nu / sqrt(tr G) in FP32, for the Lanczos products
     struct {
-      float2 ts[MAX_M1][32];  // per-lane tridiagonal solves of the root search: scaled values
-      float tmu[MAX_M1][32];  //                                                 and multipliers
+      float2 ts[DENSE_M1][32];  // per-lane tridiagonal solves of the root search: scaled values
+      float tmu[DENSE_M1][32];  //                                                 and multipliers
     } rs;
   } m;
 };
 struct Eq9 {
-  double2 Vt[MAX_M], t[MAX_M], F[MAX_M], Bk[MAX_M], z64[MAX_M];
+  double2 Vt[DENSE_M], t[DENSE_M], F[DENSE_M], Bk[DENSE_M], z64[DENSE_M];
 };
 
 struct Shared {
-  double2 A[MAX_M1][MAX_M + 1];  // A_nu in FP64 (FP64 route), Ah in two-float (mixed route)
+  double2 A[DENSE_M1][DENSE_M + 1];  // A_nu in FP64 (FP64 route), Ah in two-float (mixed route)
   union { Bulk<double> d; BulkF f; Eq9 q; } u;
-  double2 E[MAX_M1], Pz[MAX_M], b[MAX_M1], c[MAX_M1], y[MAX_M1], z[MAX_M1];
-  double2 Tk[MAX_M];  // sampled kernel: row omega^2 h_z K~(j h_z) of the Toeplitz T_nu of eq. (9)
-  double d[MAX_M1], e[MAX_M1];     // tridiagonal T (FP64 route: of G; scaled by 1/tr after the factor)
-  float d32[MAX_M1], e32[MAX_M1];  // T / tr in FP32
-  float2 c32[MAX_M1], r32[MAX_M1];
-  ffc yh[MAX_M1], bh[MAX_M1], th[MAX_M], Ef[MAX_M1], Pf[MAX_M];  // two-float (mixed route)
+  double2 E[DENSE_M1], Pz[DENSE_M], b[DENSE_M1], c[DENSE_M1], y[DENSE_M1], z[DENSE_M1];
+  double2 Tk[DENSE_M];  // sampled kernel: row omega^2 h_z K~(j h_z) of the Toeplitz T_nu of eq. (9)
+  double d[DENSE_M1], e[DENSE_M1];     // tridiagonal T (FP64 route: of G; scaled by 1/tr after the factor)
+  float d32[DENSE_M1], e32[DENSE_M1];  // T / tr in FP32
+  float2 c32[DENSE_M1], r32[DENSE_M1];
+  ffc yh[DENSE_M1], bh[DENSE_M1], th[DENSE_M], Ef[DENSE_M1], Pf[DENSE_M];  // two-float (mixed route)
   double tr, sb, inv_sb, dnu, lo, hi, a_s, red[8];  // a_s = alpha / tr
   double2 qz;  // exp(i k_z h_z)
   int fp64, tflag, kd, go;  // kd: dimension of the Lanczos model; go: Lanczos continues
@@ -372,8 +372,8 @@ static_assert(sizeof(Shared) <= 75 * 1024, "three solve blocks per SM");
 // is computed, depend on e only through the squares e_j^2, so stopping at
 // e_k <= tol changes phi^2 by O(tol^2 / a^2) relative.
 template <typename T>
-__device__ int lanczos_block(const cx<T> (*A)[MAX_M + 1], int n, int m, cx<T>* t, cx<T>* wv,
-                             cx<T> (*Q)[MAX_M1 + 1], T* d, T* e, T tol, int* go) {
+__device__ int lanczos_block(const cx<T> (*A)[DENSE_M + 1], int n, int m, cx<T>* t, cx<T>* wv,
+                             cx<T> (*Q)[DENSE_M1 + 1], T* d, T* e, T tol, int* go) {
   const int lane = threadIdx.x & 31;
   int k = n;
 #pragma unroll 1
@@ -441,7 +441,7 @@ __device__ int lanczos_block(const cx<T> (*A)[MAX_M + 1], int n, int m, cx<T>* t
 // Returns false if a pivot is not positive (T + a I not numerically SPD).
 template <typename T>
 __device__ bool tri_solve(const T* d, const T* e, int n, T a, const cx<T>* rhs, cx<T>* z) {
-  T mu[MAX_M1], il[MAX_M1];
+  T mu[DENSE_M1], il[DENSE_M1];
   T lp = d[0] + a;
   if (!(lp > T(0))) return false;
   il[0] = rcp<T>(lp);
@@ -475,7 +475,7 @@ template <typename T>
 __device__ double newton_log_alpha(const T* d, const T* e, const cx<T>* c, int n, double lo, double hi,
                                    double target, double t0, double tol, int max_iter, double& gp_out,
                                    bool& ok, int& iters) {
-  cx<T> z[MAX_M1], s[MAX_M1];
+  cx<T> z[DENSE_M1], s[DENSE_M1];
   T tl = log_t((T)lo), th = log_t((T)hi), t = (T)t0;
   const T lt = log_t((T)target);
   const T eps_t = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
@@ -509,7 +509,7 @@ __device__ double newton_log_alpha(const T* d, const T* e, const cx<T>* c, int n
 // a^2 ||(T + a I)^-1 c||^2 in precision T; single thread.
 template <typename T>
 __device__ double phi2(const T* d, const T* e, const cx<T>* c, int n, double a, bool& ok) {
-  cx<T> z[MAX_M1];
+  cx<T> z[DENSE_M1];
   ok = tri_solve<T>(d, e, n, (T)a, c, z);
   T zz = T(0);
 #pragma unroll 1
@@ -587,7 +587,7 @@ template <typename T>
 __device__ __forceinline__ cx<T> pick(const cx<T>* v, int j) {  // v[j] for a runtime j, register-resident v
   cx<T> r = czero<T>();
 #pragma unroll
-  for (int c = 0; c < MAX_M1; ++c)
+  for (int c = 0; c < DENSE_M1; ++c)
     if (c == j) r = v[c];
   return r;
 }
@@ -626,7 +626,7 @@ __device__ float2 lanczos_apply32(Shared& S, int n, int kd, float a, float2 r) {
 
 // two-float residual of the scaled dual system: th = Ah^H yh, rh = bh - Ah th - a yh
 __device__ void residual_ff(Shared& S, int n, int m, ff a) {
-  ffc (*Af)[MAX_M + 1] = reinterpret_cast<ffc (*)[MAX_M + 1]>(S.A);
+  ffc (*Af)[DENSE_M + 1] = reinterpret_cast<ffc (*)[DENSE_M + 1]>(S.A);
   {  // 2 threads per column l
     const int l = threadIdx.x >> 1, h = threadIdx.x & 1;
     ffc acc = ffc_zero();
@@ -811,19 +811,19 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         } else {
           S.Tk[threadIdx.x] = reinterpret_cast<const double2*>(ktab)[at];
         }
-      } else if (threadIdx.x >= MAX_M && threadIdx.x < MAX_M + n) {
-        const int k = threadIdx.x - MAX_M;
+      } else if (threadIdx.x >= DENSE_M && threadIdx.x < DENSE_M + n) {
+        const int k = threadIdx.x - DENSE_M;
         S.b[k] = to_d(wt[((long long)om * n + k) * N2 + nu]);
       }
     } else if (threadIdx.x < m) {
       const int l = threadIdx.x;
       S.Pz[l] = MIXED ? exp_ikz32(kz, ztop - (P.z1 + (l + 0.5) * P.hz)) : exp_ikz(kz, ztop - (P.z1 + (l + 0.5) * P.hz));
       if (MIXED) S.Pf[l] = ffc_from(S.Pz[l]);
-    } else if (threadIdx.x >= MAX_M && threadIdx.x < MAX_M + n) {
-      const int k = threadIdx.x - MAX_M;
+    } else if (threadIdx.x >= DENSE_M && threadIdx.x < DENSE_M + n) {
+      const int k = threadIdx.x - DENSE_M;
       S.b[k] = to_d(wt[((long long)om * n + k) * N2 + nu]);
       S.E[k] = gamma * (MIXED ? exp_ikz32(kz, P.zy[k] - ztop) : exp_ikz(kz, P.zy[k] - ztop));
-    } else if (!MIXED && threadIdx.x == MAX_M + MAX_M1) {
+    } else if (!MIXED && threadIdx.x == DENSE_M + DENSE_M1) {
       S.qz = exp_ikz(kz, P.hz);
     }
     __syncthreads();
@@ -895,7 +895,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
 #pragma unroll 1
       for (int l = threadIdx.x; l < m; l += ST) {
         double2 u = make_double2(0, 0);
-        if (nu == 0) {
+        if (nu == 0 && !P.incident) {
           double s0, c0;
           sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s0, &c0);
           u = make_double2((double)N2 * c0, (double)N2 * s0);
@@ -910,7 +910,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       // scaled problem Ah = A / sqrt(tr) (||Ah||_F ~ 1), bh = b / ||b||, a = alpha / tr:
       // Ah in two-float (for the residual and V~) and its FP32 part (for the model);
       // thread t builds column t mod 64, rows t / 64, t / 64 + 2, ...
-      ffc (*Af)[MAX_M + 1] = reinterpret_cast<ffc (*)[MAX_M + 1]>(S.A);
+      ffc (*Af)[DENSE_M + 1] = reinterpret_cast<ffc (*)[DENSE_M + 1]>(S.A);
       // the sampled tables hold A exactly scaled by 1/sqrt(tr) (FP64 in the plan)
       const double sa = SAMPLED ? rsqrt64(tr) : rsqrt32(tr);
       if (SAMPLED) {
@@ -923,11 +923,11 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           S.u.f.m.A[k][l] = make_float2(v.x, v.z);
         }
       } else {
-        const int l = threadIdx.x & (MAX_M - 1);
+        const int l = threadIdx.x & (DENSE_M - 1);
         if (l < m) {
           const ffc pl = S.Pf[l];
 #pragma unroll 1
-          for (int k = threadIdx.x / MAX_M; k < n; k += ST / MAX_M) {
+          for (int k = threadIdx.x / DENSE_M; k < n; k += ST / DENSE_M) {
             const ffc a = ffc_mul(S.Ef[k], pl);
             Af[k][l] = a;
             S.u.f.m.A[k][l] = make_float2(a.re.hi, a.im.hi);
@@ -969,7 +969,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           S.fp64 = fp64 ? 1 : 0;
           if (fp64) atomicAdd(ctr + C_FP64_FALLBACK, 1ull);
         }
-      } else if (!SAMPLED && threadIdx.x == MAX_M + MAX_M1) {
+      } else if (!SAMPLED && threadIdx.x == DENSE_M + DENSE_M1) {
         S.qz = exp_ikz(kz, P.hz);  // FP64, on an idle warp; first read by eq. (9)
       }
       __syncthreads();
@@ -1093,11 +1093,14 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     __syncthreads();
     FL_MARK(11);
     cx<B>* out = prof + ((long long)om * N2 + i) * 2 * m;
+    bool overflow = false;  // a profile beyond the range of B (FP32 in the mixed path)
     {  // V~ by threads l < 64, U~ by threads 64 + l (its FP64 arithmetic on warps 2 and 3)
-      const int l = threadIdx.x & (MAX_M - 1);
+      const int l = threadIdx.x & (DENSE_M - 1);
       if (l < m) {
-        if (threadIdx.x < MAX_M) {
-          out[l] = from_d<B>(S.u.q.Vt[l]);
+        if (threadIdx.x < DENSE_M) {
+          const cx<B> v = from_d<B>(S.u.q.Vt[l]);
+          overflow = !(isfinite(v.x) && isfinite(v.y));
+          out[l] = v;
         } else {
           double2 u;
           if (SAMPLED) {
@@ -1107,17 +1110,21 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
             // gamma is imaginary (propagating mode) or real (evanescent)
             u = q >= 0.0 ? make_double2(-gamma.y * f.y, gamma.y * f.x) : make_double2(gamma.x * f.x, gamma.x * f.y);
           }
-          if (nu == 0) {
+          if (nu == 0 && !P.incident) {  // the plane wave; a given incident field is added in the recovery
             double s, c;
             sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s, &c);
             u = u + make_double2((double)N2 * c, (double)N2 * s);
           }
-          out[m + l] = from_d<B>(u);
+          const cx<B> uo = from_d<B>(u);
+          overflow = !(isfinite(uo.x) && isfinite(uo.y));
+          out[m + l] = uo;
         }
       }
     }
     if (threadIdx.x == 0 && alpha_out) alpha_out[om * N2 + nu] = S.a_s * S.tr;
-    __syncthreads();
+    // counted as non-finite (fs_sync_status: FS_ENONFINITE): the working precision
+    // cannot hold this mode's solution
+    if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicAdd(ctr + C_NONFINITE, 1ull);
     FL_MARK(12);
   }
 }

@@ -19,7 +19,8 @@
 // floored at alpha_rel tr, which is also taken when phi(alpha_floor) >= delta_nu.
 // The dense form reaches the same values through the normal matrix; the two agree
 // to rounding.  Cost O(M1 + M) per mode, one warp per mode; eq. (9) and the output
-// layout are those of the dense solve.
+// layout are those of the dense solve.  It holds no matrix, so it serves layers up
+// to the global limits (M, M1 <= 128), beyond those of the dense form.
 #include <math.h>
 
 #include "modes.cuh"
@@ -29,7 +30,8 @@ namespace fl {
 
 namespace {
 
-constexpr int RW = 4;  // warps (modes) per block
+constexpr int RW = 4;               // warps (modes) per block
+constexpr int RK = MAX_M / 32;      // X planes per lane
 
 struct Rank1Mem {
   double2 v[MAX_M], t[MAX_M], F[MAX_M], B[MAX_M];
@@ -50,7 +52,7 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
   const long long N2 = (long long)N * N;
   long long total = 0;
   for (int w = 0; w < P.n_omega; ++w) total += count[w];
-  unsigned long long n_floor = 0, n_zeroed = 0;
+  unsigned long long n_floor = 0, n_zeroed = 0, n_bad = 0;
   for (long long item = (long long)blockIdx.x * RW + warp; item < total; item += (long long)gridDim.x * RW) {
     int om = 0;
     long long i = item;
@@ -65,20 +67,30 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
     const double g0 = P.g0[om];
     const double2 gamma = q >= 0.0 ? make_double2(0.0, -g0 * rq) : make_double2(-g0 * rq, 0.0);
     const double ztop = P.z1 + (m - 0.5) * P.hz;
-    // E_k and b_k on lane k; P_l on lanes l and l - 32
-    double2 e = make_double2(0, 0), b = make_double2(0, 0);
-    if (lane < n) {
-      e = gamma * exp_ikz_inline(kz, P.zy[lane] - ztop);
-      const long long at = ((long long)om * n + lane) * N2 + nu;
-      b = wt64 ? wt64[at] : to_d(wt[at]);  // W~ in FP64 on the mixed truncated-SVD route
+    // E_k, b_k on lanes k mod 32 and P_l on lanes l mod 32 (M1, M <= 128): the sums
+    // sum |E|^2, sum |b|^2, E^H b and sum |P|^2, P kept in registers (slot l / 32)
+    double sE = 0.0, bb = 0.0, sP = 0.0;
+    double2 beta = make_double2(0, 0);
+#pragma unroll 1
+    for (int k = lane; k < n; k += 32) {
+      const double2 e = gamma * exp_ikz_inline(kz, P.zy[k] - ztop);
+      const long long at = ((long long)om * n + k) * N2 + nu;
+      const double2 b = wt64 ? wt64[at] : to_d(wt[at]);  // W~ in FP64 on the mixed truncated-SVD route
+      sE += abs2(e);
+      bb += abs2(b);
+      beta = beta + cmul_conj_a(e, b);
     }
-    const int l0 = lane, l1 = lane + 32;
-    const double2 p0 = l0 < m ? exp_ikz_inline(kz, ztop - (P.z1 + (l0 + 0.5) * P.hz)) : make_double2(0, 0);
-    const double2 p1 = l1 < m ? exp_ikz_inline(kz, ztop - (P.z1 + (l1 + 0.5) * P.hz)) : make_double2(0, 0);
-    const double sE = warp_sum(abs2(e));
-    const double sP = warp_sum(abs2(p0) + abs2(p1));
-    const double bb = warp_sum(abs2(b));
-    const double2 beta = warp_sum(cmul_conj_a(e, b));  // E^H b
+    double2 pl[RK];
+#pragma unroll
+    for (int j = 0; j < RK; ++j) {
+      const int l = lane + 32 * j;
+      pl[j] = l < m ? exp_ikz_inline(kz, ztop - (P.z1 + (l + 0.5) * P.hz)) : make_double2(0, 0);
+      sP += abs2(pl[j]);
+    }
+    sE = warp_sum(sE);
+    sP = warp_sum(sP);
+    bb = warp_sum(bb);
+    beta = warp_sum(beta);  // E^H b
     const double tr = sE * sP;
     const double dnu = dnu_arr[om];
     double2 coef = make_double2(0, 0);  // V~_l = conj(P_l) coef
@@ -110,36 +122,45 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
       ++n_zeroed;
     }
     // V~ and eq. (9): U~ = U~0 + gamma (F + B) over the X planes (two affine scans)
-    const double2 v0 = cmul_conj_a(p0, coef), v1 = cmul_conj_a(p1, coef);
-    if (l0 < m) S.v[l0] = v0;
-    if (l1 < m) S.v[l1] = v1;
+    double2 qz = make_double2(0, 0);  // P_{m-2} = e^{i k_z h_z}: the plane-to-plane factor
+#pragma unroll
+    for (int j = 0; j < RK; ++j) {
+      const int l = lane + 32 * j;
+      if (l < m) S.v[l] = cmul_conj_a(pl[j], coef);
+      if (m >= 2 && j == (m - 2) >> 5) qz = pl[j];
+    }
+    if (m >= 2) {
+      const int src = (m - 2) & 31;
+      qz = make_double2(__shfl_sync(0xffffffffu, qz.x, src), __shfl_sync(0xffffffffu, qz.y, src));
+    }
     __syncwarp();
-    // P_{m-2} = e^{i k_z h_z}: the plane-to-plane factor of eq. (9)
-    const int src = m >= 2 ? (m - 2) & 31 : 0;
-    const double2 pq = (m >= 2 && m - 2 >= 32) ? p1 : p0;
-    const double2 qz = make_double2(__shfl_sync(0xffffffffu, pq.x, src), __shfl_sync(0xffffffffu, pq.y, src));
-    affine_scan64(S.v, m, qz, S.F);
+    affine_scan_lanes<RK>(S.v, m, qz, S.F);
     for (int r = lane; r < m; r += 32) S.t[r] = r == 0 ? make_double2(0, 0) : qz * S.v[m - r];
     __syncwarp();
-    affine_scan64(S.t, m, qz, S.B);
+    affine_scan_lanes<RK>(S.t, m, qz, S.B);
     __syncwarp();
     cx<R>* out = prof + ((long long)om * N2 + i) * 2 * m;
     const double n2 = (double)N2;
+    bool overflow = false;  // a profile beyond the range of R (FP32 in the mixed path)
     for (int l = lane; l < m; l += 32) {
       double2 u = gamma * (S.F[l] + S.B[m - 1 - l]);
-      if (nu == 0) {
+      if (nu == 0 && !P.incident) {
         double s0, c0;
         sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s0, &c0);
         u = u + make_double2(n2 * c0, n2 * s0);
       }
-      out[l] = from_d<R>(l < 32 ? v0 : v1);
-      out[m + l] = from_d<R>(u);
+      const cx<R> vo = from_d<R>(S.v[l]), uo = from_d<R>(u);
+      overflow |= !(isfinite(vo.x) && isfinite(vo.y) && isfinite(uo.x) && isfinite(uo.y));
+      out[l] = vo;
+      out[m + l] = uo;
     }
+    if (__any_sync(0xffffffffu, overflow)) ++n_bad;
     if (lane == 0 && alpha_out) alpha_out[om * N2 + nu] = zeroed ? INFINITY : alpha;
     __syncwarp();
   }
   if (lane == 0) {
     if (n_floor) atomicAdd(ctr + C_ALPHA_FLOOR, n_floor);
+    if (n_bad) atomicAdd(ctr + C_NONFINITE, n_bad);  // profiles beyond the range of R
     if (n_zeroed) {
       atomicAdd(ctr + C_ACTIVE, (unsigned long long)(-(long long)n_zeroed));
       atomicAdd(ctr + C_ZEROED, n_zeroed);

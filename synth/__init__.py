@@ -6,8 +6,9 @@ shapes.  Forward modelling (turning xi into data W) is done by the oracle on the
 CPU or by the library's own forward kernel on the GPU, never here.
 """
 from .phantoms import (gaussian_inclusions, random_gaussians, sphere_phantom,
-                       noise_direction, grid_points)
-from .workloads import Workload, WORKLOADS, workload
+                       noise_direction, grid_points, three_bumps)
+from .workloads import PaperWorkload, Workload, WORKLOADS, paper_workload, workload
 
 __all__ = ["gaussian_inclusions", "random_gaussians", "sphere_phantom",
-           "noise_direction", "grid_points", "Workload", "WORKLOADS", "workload"]
+           "noise_direction", "grid_points", "three_bumps", "PaperWorkload", "Workload", "WORKLOADS",
+           "paper_workload", "workload"]

@@ -72,3 +72,17 @@ def sphere_phantom(rng, n, m, z1, z2, count=3, radii=(0.1, 0.3), contrast=(0.02,
 def noise_direction(rng, shape):
     """Complex noise draw with iid N(0,1) real and imaginary parts."""
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def three_bumps(n, m, z1, z2, period, x0, a0=0.3):
+    """The model solution of Sec. 5: A0 [(1 - rho1^2/0.4^2)_+ + 2 (1 - rho2^2/0.25^2)_+
+    + 2.5 (1 - rho3^2/0.3^2)_+] with
+      rho1^2 = (x-1)^2 + (y-2)^2 + (z-0.5)^2,
+      rho2^2 = (x-4)^2 + (y+3)^2 + (z-0.5)^2 + 1.5 (y+3)(z-0.5),
+      rho3^2 = (x+3)^2 + y^2 + (z-0.45)^2 - 1.5 y (z-0.45)."""
+    X, Y, Z = grid_points(n, m, z1, z2, period, x0)
+    r1 = (X - 1) ** 2 + (Y - 2) ** 2 + (Z - 0.5) ** 2
+    r2 = (X - 4) ** 2 + (Y + 3) ** 2 + (Z - 0.5) ** 2 + 1.5 * (Y + 3) * (Z - 0.5)
+    r3 = (X + 3) ** 2 + Y ** 2 + (Z - 0.45) ** 2 - 1.5 * Y * (Z - 0.45)
+    pos = lambda a: np.maximum(a, 0.0)
+    return a0 * (pos(1 - r1 / 0.4 ** 2) + 2 * pos(1 - r2 / 0.25 ** 2) + 2.5 * pos(1 - r3 / 0.3 ** 2))

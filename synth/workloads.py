@@ -10,7 +10,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .phantoms import gaussian_inclusions, random_gaussians, sphere_phantom
+from .phantoms import gaussian_inclusions, random_gaussians, sphere_phantom, three_bumps
 
 Z1, Z2, Z3, Z4 = 0.2, 1.0, 1.2, 1.6
 
@@ -98,3 +98,64 @@ WORKLOADS = {"c1": _c1, "c2": _c2, "c3": _c3, "c5": _c5}
 
 def workload(name: str) -> Workload:
     return WORKLOADS[name]()
+
+
+@dataclass
+class PaperWorkload:
+    """The geometry of the paper's own experiments (Sec. 5): X = [-10,10]^2 x [-0.5,1.5] on
+    an N x N x M grid, data in the thick layer [6.01, 6.5] (Sec. 5.3) or the thin layer
+    [6.01, 6.02] (Sec. 5.4) on M1 planes, 11 point sources (0, y_s, 6), y_s = -5..5,
+    a_s = 1, the three-bump xi with A0 = 0.3, frequencies omega = k0 in {1, 2, 3}
+    (c0 = 1), noise levels 0, 1e-7, 1e-5."""
+    name: str
+    n: int = 128
+    m: int = 71
+    m1: int = 71
+    layer: str = "thick"
+    omegas: tuple = (1.0, 2.0, 3.0)
+    deltas: tuple = (0.0, 1e-7, 1e-5)
+    a0: float = 0.3
+    period: float = 20.0
+    x0: float = -10.0
+    z1: float = -0.5
+    z2: float = 1.5
+    seed: int = 5
+
+    @property
+    def z3(self):
+        return 6.01
+
+    @property
+    def z4(self):
+        return 6.5 if self.layer == "thick" else 6.02
+
+    @property
+    def zy(self):
+        if self.m1 == 1:
+            return np.array([self.z3])
+        return self.z3 + (self.z4 - self.z3) * np.arange(self.m1) / (self.m1 - 1)
+
+    @property
+    def sources(self):
+        return [(0.0, float(y), 6.0, 1.0) for y in range(-5, 6)]
+
+    @property
+    def xi(self):
+        return three_bumps(self.n, self.m, self.z1, self.z2, self.period, self.x0, self.a0)
+
+    @property
+    def voxel_freqs(self) -> int:
+        return len(self.omegas) * self.n * self.n * self.m
+
+    def noise(self, stream=0):
+        rng = np.random.default_rng([self.seed, 2000 + stream])
+        shape = (len(self.omegas), self.m1, self.n, self.n)
+        return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def paper_workload(layer="thick", n=128, m=71, m1=None):
+    """Sec. 5.3 (thick layer, M1 = M = 71) or Sec. 5.4 (thin layer, M1 = 2) at N = 128."""
+    if m1 is None:
+        m1 = 71 if layer == "thick" else 2
+    return PaperWorkload(f"paper geometry, {layer} layer: {n}^2 x {m}, {m1} data planes, 11 point sources, "
+                         f"three bumps A0 = 0.3, omega 1, 2, 3", n=n, m=m, m1=m1, layer=layer)

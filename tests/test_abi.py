@@ -71,7 +71,7 @@ def test_forward_entry_points_reject_a_null_context_without_gpu(abi):
     its = (C.c_int * 1)()
     st = abi.lib().fs_forward(None, C.byref(g), 0, None, om, 1, 1.0, abi.FS_FIXED_POINT, 10, 1e-13, None, None, its)
     assert st == abi.FS_EINVAL
-    st = abi.lib().fs_forward_born(None, C.byref(g), 0, None, om, 1, 1.0, None)
+    st = abi.lib().fs_forward_born(None, C.byref(g), 0, None, None, om, 1, 1.0, None)
     assert st == abi.FS_EINVAL
     assert abi.STATUS_NAMES[abi.FS_ENOCONV] == "FS_ENOCONV"
     assert sorted(abi.FORWARD_METHODS.values()) == [abi.FS_FIXED_POINT, abi.FS_GMRES, abi.FS_FIXED_POINT_GMRES]

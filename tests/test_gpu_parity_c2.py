@@ -90,7 +90,8 @@ def test_thin_layer_two_planes(rc, precision):
     What is determined, and asserted: the active sets (exactly), alpha per mode, and xi
     weighted by the least-squares denominator D = sum_omega |u|^2 -- from xi D = num,
     an error eps in num and D gives ||(xi' - xi) D|| <= 2 eps ||xi D|| -- within the
-    path's tolerance.  The unweighted error is printed."""
+    FP64 tolerance.  The unweighted error is printed.  Those profiles exceed the FP32
+    range, which the mixed path must report (FS_ENONFINITE)."""
     g, om, W, _ = case("thin256", 0.01)
     ref = oracle_result("thin256", 0.01)
     xi, c, alpha, rep = run_gpu(rc, g, om, W, 0.01, precision=precision)
@@ -107,5 +108,9 @@ def test_thin_layer_two_planes(rc, precision):
         assert rep["n_active"] == int(ref.active.sum())
         assert werr <= TOL_FP64
     else:
+        # the noise-mode profiles (|V~| up to ~1e61 here) leave the FP32 range of the mixed
+        # path's profiles: the path must say so (FS_ENONFINITE), not return silently
+        from paper_1911_10487_gb300._abi import FS_ENONFINITE
         assert np.sum(act != ref.active) <= 2
-        assert werr <= TOL_MIXED
+        assert rc.sync_status() == FS_ENONFINITE
+        assert rc.report()["n_nonfinite"] > 0
