@@ -598,6 +598,147 @@ def run_diff(args, local, flush, world):
     return out
 
 
+def graph_time(stream, flush, fn, steps, warmup, world):
+    """Capture fn() as a CUDA graph on `stream` and time `steps` replays (L2 flushed
+    before each) with CUDA events; returns ms per replay, max over ranks."""
+    import torch
+    with torch.cuda.stream(stream):
+        fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        fn()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            flush.zero_()
+            g.replay()
+    torch.cuda.synchronize()
+    barrier(world)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+    torch.cuda.synchronize()
+    return max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, world)
+
+
+def run_sampled(args, local, flush, world):
+    """The sampled-G kernel (Sec. 5: G~ from the FFT of sampled G) on the headline
+    workload: kernel plan build once per precision, then the reconstruction with the
+    dense per-mode solve on the tabulated A_nu (numerically full rank) and the Toeplitz
+    eq. (9), replayed as a CUDA graph.  Same data as the headline (the library's
+    single-scattering kernel plus seeded noise)."""
+    import torch
+    from paper_1911_10487_gb300 import Geometry, KernelPlan, Reconstructor
+    from synth import workload
+    wl = workload(WORKLOAD)
+    geom = Geometry(wl.n, wl.m, wl.z1, wl.z2, tuple(wl.zy))
+    om = [float(x) for x in wl.omegas]
+    stream = torch.cuda.Stream()
+    rc = Reconstructor(local, stream=stream)
+    with torch.cuda.stream(stream):
+        W64 = make_inputs(rc, wl, geom)
+    torch.cuda.synchronize()
+    out = {"workload": "128x128x64 X grid, 32 data planes, k0=8pi, 1% noise; sampled-G kernel, dense form",
+           "voxel_freqs": wl.voxel_freqs, "steps": args.steps}
+    xis = {}
+    for prec, W, rdt in (("fp64", W64, torch.float64), ("mixed", W64.to(torch.complex64), torch.float32)):
+        t0 = time.perf_counter()
+        plan = KernelPlan(rc, geom, om, prec)
+        torch.cuda.synchronize()
+        plan_ms = 1e3 * (time.perf_counter() - t0)
+        xi = torch.empty((wl.m, wl.n, wl.n), dtype=rdt, device=rc.device)
+        c = torch.empty_like(xi)
+        torch.cuda.synchronize()  # inputs made on the default stream
+
+        def step():
+            rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, c, None), kernel_plan=plan)
+
+        ms = graph_time(stream, flush, step, args.steps, args.warmup, world)
+        with torch.cuda.stream(stream):
+            step()
+        rep = rc.report()
+        out[prec] = {"value": world * wl.voxel_freqs / (ms * 1e-3), "ms_per_step": ms, "plan_ms": plan_ms,
+                     "plan_bytes": plan.nbytes, "n_active": rep["n_active"],
+                     "n_fp64_fallback": rep["n_fp64_fallback"], "n_refine_iters": rep["n_refine_iters"]}
+        xis[prec] = xi.double().cpu().numpy()
+        plan.close()
+    out["_check"] = (wl, W64.cpu().numpy(), om, xis)
+    rc.close()
+    return out
+
+
+def delta_l2_planes(xi, xi_true):
+    """Delta_L2(z) of Sec. 5.3 per X plane (NaN where xi_true vanishes on the plane)."""
+    m = xi_true.shape[0]
+    d = np.linalg.norm((xi - xi_true).reshape(m, -1), axis=1)
+    n = np.linalg.norm(xi_true.reshape(m, -1), axis=1)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(n > 0, d / n, np.nan)
+
+
+def run_paper(args, local, flush, world):
+    """The paper's own experiment (Sec. 5, 5.3, 5.4) at full size: X = [-10,10]^2 x
+    [-0.5,1.5] on 128 x 128 x 71, data on 71 planes of [6.01, 6.5] (thick) or 2 of
+    [6.01, 6.02] (thin), 11 point sources (0, y, 6), the three-bump xi (A0 = 0.3),
+    omega = 1, 2, 3 solved together (least squares over omega), noise 0, 1e-7, 1e-5
+    (delta_floor 1e-10).  Data: the library's point-source incident field and its
+    single-scattering kernel.  M1 = 71 is solved in the rank-one form.  Reports the
+    time of one reconstruction (CUDA graph) and Delta_L2(z) against the true xi."""
+    import torch
+    from paper_1911_10487_gb300 import Geometry, Reconstructor
+    from synth import paper_workload
+    stream = torch.cuda.Stream()
+    rc = Reconstructor(local, stream=stream)
+    res = {"workload": "paper geometry (Sec. 5): 128^2 x 71 X grid, 11 point sources, three bumps A0=0.3, "
+                       "omega 1,2,3; thick layer 71 planes, thin layer 2 planes; rank-one form; delta_floor 1e-10"}
+    for layer in ("thick", "thin"):
+        pw = paper_workload(layer)
+        geom = Geometry(pw.n, pw.m, pw.z1, pw.z2, tuple(pw.zy), pw.period)
+        om = [float(x) for x in pw.omegas]
+        with torch.cuda.stream(stream):
+            u0 = rc.incident_point_sources(pw.sources, om, geom, precision="fp64")
+            xi_t = torch.from_numpy(np.ascontiguousarray(pw.xi)).to(rc.device)
+            W0 = rc.forward_born(xi_t, om, geom, precision="fp64", incident=u0)
+            nz = torch.from_numpy(pw.noise()).to(rc.device)
+        torch.cuda.synchronize()
+        lr = {"voxel_freqs": pw.voxel_freqs, "m1": pw.m1}
+        for delta in (pw.deltas if layer == "thick" else (0.0, 1e-7)):
+            W = W0.clone()
+            if delta > 0:
+                for j in range(W.shape[0]):
+                    W[j] += delta * torch.linalg.vector_norm(W0[j]) * nz[j] / torch.linalg.vector_norm(nz[j])
+            entry = {}
+            for prec in ("fp64", "mixed"):
+                cdt = torch.complex128 if prec == "fp64" else torch.complex64
+                rdt = torch.float64 if prec == "fp64" else torch.float32
+                Wp, up = W.to(cdt), u0.to(cdt)
+                xi = torch.empty((pw.m, pw.n, pw.n), dtype=rdt, device=rc.device)
+                c = torch.empty_like(xi)
+                torch.cuda.synchronize()  # inputs made on the default stream
+
+                def step():
+                    rc.reconstruct(Wp, om, geom, delta, precision=prec, out=(xi, c, None), solve_form=1,
+                                   incident=up, delta_floor=1e-10)
+
+                ms = graph_time(stream, flush, step, max(3, min(args.steps, 10)), args.warmup, world)
+                dz = delta_l2_planes(xi.double().cpu().numpy(), pw.xi)
+                rep = rc.report()
+                entry[prec] = {"value": world * pw.voxel_freqs / (ms * 1e-3), "ms_per_step": ms,
+                               "n_active": rep["n_active"], "n_nonfinite": rep["n_nonfinite"],
+                               "delta_l2_z": {"min": float(np.nanmin(dz)), "median": float(np.nanmedian(dz)),
+                                              "max": float(np.nanmax(dz)),
+                                              "per_plane": [round(float(x), 5) for x in dz]}}
+            lr[f"delta={delta:g}"] = entry
+        res[layer] = lr
+    rc.close()
+    return res
+
+
 def cpu_baseline(wl, W_np, om, rows=None):
     from oracle import inverse
     from oracle.grid import Geometry as OG
@@ -618,6 +759,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batch measurement")
     ap.add_argument("--no-diff", action="store_true", help="skip the derivative measurement")
     ap.add_argument("--no-forward", action="store_true", help="skip the full-scattering forward measurement")
+    ap.add_argument("--no-sampled", action="store_true", help="skip the sampled-G kernel measurement")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper-geometry workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":  # host cores only: no device is touched
@@ -637,6 +780,17 @@ def main():
         result["differentiation"] = run_diff(args, local, flush, world)
     if not args.no_forward:
         result["forward_fixed_point"] = run_forward(rc, wl, geom, om)
+    sampled_check = None
+    if not args.no_sampled:
+        import torch
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=rc.device)
+        sp = run_sampled(args, local, flush, world)
+        sampled_check = sp.pop("_check")
+        result["sampled_kernel"] = sp
+    if not args.no_paper:
+        import torch
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=rc.device)
+        result["paper_geometry"] = run_paper(args, local, flush, world)
     if rank == 0:
         import torch
         W_np = W64.cpu().numpy()
@@ -663,6 +817,15 @@ def main():
             for p in ("mixed", "fp64"):
                 result["rank1_form"][p]["rel_err_vs_oracle"] = rel_l2(outs[p + "_r1"][0].double().cpu().numpy(),
                                                                      ref.xi)
+            if sampled_check is not None:
+                from oracle import inverse
+                from oracle.grid import Geometry as OG
+                swl, sW, som, sxis = sampled_check
+                sg = OG(swl.n, swl.m, swl.z1, swl.z2, tuple(swl.zy), kernel="sampled")
+                t0 = time.perf_counter()
+                sref = inverse.reconstruct(sW, som, sg, DELTA)
+                result["sampled_kernel"]["oracle_s"] = time.perf_counter() - t0
+                result["sampled_kernel"]["rel_err_vs_oracle"] = {p: rel_l2(x, sref.xi) for p, x in sxis.items()}
             if batch is not None:
                 swl, sW, som, sxm, sx64 = spot
                 _, sref = cpu_baseline(swl, sW, som)

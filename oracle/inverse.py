@@ -117,7 +117,11 @@ def solve_modes(Wt, omega, k0, g: Geometry, delta_nu, opts: Options, alpha_fixed
         bnorm = np.linalg.norm(b, axis=-1)
         U, s, Vh = np.linalg.svd(A, full_matrices=False)
         beta = np.einsum("yxkj,yxk->yxj", U.conj(), b)
-        perp2 = np.maximum(bnorm ** 2 - np.sum(np.abs(beta) ** 2, axis=-1), 0.0)
+        # ||P_perp b||^2 of phi^2, as the norm of the projection residual b - U U* b
+        # itself: the difference of squares ||b||^2 - ||U* b||^2 would leave a rounding
+        # error of order eps ||b||^2 in phi^2, which decides alpha once delta_nu^2 is
+        # not far above it (the tiny noise levels of Sec. 5.3)
+        perp2 = np.sum(np.abs(b - np.einsum("yxkj,yxj->yxk", U, beta)) ** 2, axis=-1)
         s2 = s ** 2
         # a mode whose matrix underflowed to zero carries no information: V~ = 0
         usable = ~graz[rows] & (np.sum(s ** 2, axis=-1) > 0)

@@ -71,14 +71,20 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
     // sum |E|^2, sum |b|^2, E^H b and sum |P|^2, P kept in registers (slot l / 32)
     double sE = 0.0, bb = 0.0, sP = 0.0;
     double2 beta = make_double2(0, 0);
-#pragma unroll 1
-    for (int k = lane; k < n; k += 32) {
-      const double2 e = gamma * exp_ikz_inline(kz, P.zy[k] - ztop);
-      const long long at = ((long long)om * n + k) * N2 + nu;
-      const double2 b = wt64 ? wt64[at] : to_d(wt[at]);  // W~ in FP64 on the mixed truncated-SVD route
-      sE += abs2(e);
-      bb += abs2(b);
-      beta = beta + cmul_conj_a(e, b);
+    double2 ek[RK], bk[RK];  // E_k and b_k of k = lane + 32 j
+#pragma unroll
+    for (int j = 0; j < RK; ++j) {
+      const int k = lane + 32 * j;
+      ek[j] = make_double2(0, 0);
+      bk[j] = make_double2(0, 0);
+      if (k < n) {
+        ek[j] = gamma * exp_ikz_inline(kz, P.zy[k] - ztop);
+        const long long at = ((long long)om * n + k) * N2 + nu;
+        bk[j] = wt64 ? wt64[at] : to_d(wt[at]);  // W~ in FP64 on the mixed truncated-SVD route
+      }
+      sE += abs2(ek[j]);
+      bb += abs2(bk[j]);
+      beta = beta + cmul_conj_a(ek[j], bk[j]);
     }
     double2 pl[RK];
 #pragma unroll
@@ -93,6 +99,16 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
     beta = warp_sum(beta);  // E^H b
     const double tr = sE * sP;
     const double dnu = dnu_arr[om];
+    // ||b - E (E^H b)/||E||^2||^2, the part of ||b||^2 outside the range of A, as the norm
+    // of that residual (not ||b||^2 - |E^H b|^2/||E||^2, whose rounding of order
+    // eps ||b||^2 decides alpha when delta_nu << ||b||)
+    double p = 0.0;
+    if (tr > 0.0) {
+      const double2 pr = rcp64(sE) * beta;
+#pragma unroll
+      for (int j = 0; j < RK; ++j) p += abs2(bk[j] - ek[j] * pr);
+      p = warp_sum(p);
+    }
     double2 coef = make_double2(0, 0);  // V~_l = conj(P_l) coef
     const bool zeroed = !(tr > 0.0) || (P.alpha_mode == 0 && !(bb > dnu * dnu));
     double alpha = INFINITY;
@@ -105,7 +121,6 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
           alpha = P.alpha_given[om];
         } else {
           const double c = abs2(beta) * rcp64(sE);  // |u^H b|^2, u = E / ||E||
-          const double p = fmax(bb - c, 0.0);
           const double afl = P.alpha_rel * tr;
           const double rf = afl * rcp64(tr + afl);
           if (rf * rf * c + p >= dnu * dnu) {
