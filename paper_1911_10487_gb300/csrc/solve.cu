@@ -847,6 +847,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       }
     }
     __syncthreads();
+    FL_MARK(3);
     {
       // the scalars of the mode, and in the mixed route the scaled factors of A and b in
       // two-float (warp 0: E, warp 1: b, warp 3: the root bracket)
@@ -880,6 +881,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
       }
     }
     __syncthreads();
+    FL_MARK(16);
     const double tr = S.tr, bb = S.red[1];
     const double dnu0 = S.dnu;
     // A_nu underflowed to zero (the mode carries no information), or, under the
