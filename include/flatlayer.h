@@ -56,8 +56,10 @@ typedef enum {
   FS_ECUDA = 3,       /* a CUDA call failed; see fs_last_error                   */
   FS_EUNSUPPORTED = 4, /* size outside the compiled limits (see below)           */
   FS_ENOCONV = 5,      /* fs_forward: the fixed point did not converge            */
-  FS_ENONFINITE = 6    /* fs_sync_status: the last reconstruction met a non-finite
+  FS_ENONFINITE = 6,   /* fs_sync_status: the last reconstruction met a non-finite
                           value (NaN or Inf in W, or in a recovered xi)            */
+  FS_ETIMEOUT = 7      /* fs_sync_status: a device-side wait of the last
+                          reconstruction gave up after its poll limit               */
 } fs_status;
 
 typedef enum {
@@ -118,6 +120,13 @@ typedef struct {
                           it (solve_form 1 gives FS_EUNSUPPORTED); eq. (9) is applied as the
                           Toeplitz matrix T_nu; no mode is excluded as grazing.  Only
                           fs_reconstruct and fs_reconstruct_host accept it.             */
+  int classify_single_pass; /* 1 (default): the norms of the modes, the discrepancy test and the
+                          active list in one cooperative launch whose blocks meet at two
+                          bounded device-side barriers (a wait that runs out is reported by
+                          fs_sync_status as FS_ETIMEOUT); used when the device holds the grid
+                          co-resident, else the three-kernel form is taken.  0: always the
+                          three-kernel form.  Results are identical up to the rounding of the
+                          sum ||W||^2 (its terms are grouped differently).                 */
   const void* incident;  /* NULL (default): the incident field is the plane wave exp(-i k0 z).
                           Else device, [n_omega][M][N][N] complex in the working precision:
                           the incident field u0 on the X planes (for instance the point
@@ -140,8 +149,11 @@ typedef struct {
   long long n_columns;       /* columns nu1 holding a nonzero mode, summed over omega:
                                 the inverse transform along y runs on these only       */
   long long n_nonfinite;     /* modes whose ||W~_nu||^2 is not finite (W holds a NaN or
-                                Inf) plus voxels whose recovered xi is not finite; when
-                                nonzero the outputs of the call are unspecified         */
+                                Inf) plus voxels whose recovered xi is not finite plus
+                                modes whose solution leaves the range of the working
+                                precision; when nonzero the outputs are unspecified     */
+  long long n_timeouts;      /* device-side waits that ran out (the single-pass
+                                classification); when nonzero the outputs are unspecified */
   float ms_stage[6];         /* with stage_timing: device milliseconds of the kernels
                                 [0] forward FFT along x, [1] forward FFT along y + mode
                                 norms, [2] mode classification, [3] per-mode solve,
@@ -340,10 +352,11 @@ fs_status fs_get_report(fs_ctx* ctx, fs_report* report);
 /* Device-side status of the last fs_reconstruct (or fs_reconstruct_batch) call on
    this context.  The calls return once their work is enqueued, so what the
    kernels find is reported here: synchronises the context's stream, then returns
-   FS_ECUDA if the stream reports an error, FS_ENONFINITE if the call met a
-   non-finite value (fs_report.n_nonfinite > 0: a NaN or Inf in W makes delta_nu
-   undefined, so no mode is solved and xi, c are unspecified), and FS_OK
-   otherwise.  The message of fs_last_error says what was found. */
+   FS_ECUDA if the stream reports an error, FS_ETIMEOUT if a device-side wait ran
+   out (fs_report.n_timeouts > 0), FS_ENONFINITE if the call met a non-finite value
+   (fs_report.n_nonfinite > 0: a NaN or Inf in W makes delta_nu undefined, so no mode
+   is solved and xi, c are unspecified; or a solution beyond the range of the working
+   precision), and FS_OK otherwise.  The message of fs_last_error says what was found. */
 fs_status fs_sync_status(fs_ctx* ctx);
 
 #ifdef __cplusplus

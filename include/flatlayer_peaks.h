@@ -37,6 +37,15 @@ int fs_measure_alu_peaks(int device, fs_alu_peaks* out);
    Returns 0 on success, 1 for a bad argument, 3 on a launch error. */
 int fs_eval_reciprocals(const double* x, int n, double* out, void* stream);
 
+/* The bounded device-side wait of the single-pass classification, made to run out:
+   `blocks` (1..64) blocks arrive at a barrier whose target is blocks + 1, so no wait is
+   ever satisfied, and each gives up after `polls` (1..2^20) polls of about 64 ns and
+   counts a timeout.  *timeouts receives the count (blocks when the limit works).
+   Synchronous on the current device; allocates and frees a few bytes.  Returns 0 on
+   success, 1 for a bad argument, 2 if allocation fails, 3 on a CUDA error.  The paper
+   has no counterpart. */
+int fs_check_bounded_wait(int blocks, unsigned polls, long long* timeouts);
+
 #ifdef __cplusplus
 }
 #endif

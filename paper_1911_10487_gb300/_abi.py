@@ -12,15 +12,15 @@ import os
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libflatlayer.so")
 _lib = None
 
-FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED, FS_ENOCONV, FS_ENONFINITE = 0, 1, 2, 3, 4, 5, 6
+FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED, FS_ENOCONV, FS_ENONFINITE, FS_ETIMEOUT = range(8)
 FS_FP64, FS_MIXED = 0, 1
 STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_EUNSUPPORTED", 5: "FS_ENOCONV",
-                6: "FS_ENONFINITE"}
+                6: "FS_ENONFINITE", 7: "FS_ETIMEOUT"}
 
 # every function declared in include/*.h
 EXPORTS = ("fs_version", "fs_default_options", "fs_create", "fs_destroy", "fs_last_error",
            "fs_workspace_size", "fs_reconstruct", "fs_reconstruct_host", "fs_forward_born", "fs_forward",
-           "fs_get_report", "fs_sync_status", "fs_measure_alu_peaks", "fs_eval_reciprocals", "fs_reconstruct_static", "fs_reconstruct_batch",
+           "fs_get_report", "fs_sync_status", "fs_measure_alu_peaks", "fs_eval_reciprocals", "fs_check_bounded_wait", "fs_reconstruct_static", "fs_reconstruct_batch",
            "fs_diff_plan_create", "fs_diff_plan_destroy", "fs_diff_tape_bytes", "fs_diff_scratch_bytes",
            "fs_reconstruct_diff", "fs_reconstruct_vjp", "fs_reconstruct_jvp",
            "fs_kernel_plan_create", "fs_kernel_plan_destroy", "fs_kernel_plan_bytes", "fs_incident_point_sources")
@@ -37,7 +37,7 @@ class fs_options(C.Structure):
                 ("alpha_given", C.POINTER(C.c_double)), ("max_iter", C.c_int),
                 ("refine_iters", C.c_int), ("fp64_switch", C.c_double), ("stage_timing", C.c_int),
                 ("solve_blocks_per_sm", C.c_int), ("solve_form", C.c_int), ("regularizer", C.c_int),
-                ("kernel_plan", C.c_void_p), ("incident", C.c_void_p)]
+                ("kernel_plan", C.c_void_p), ("classify_single_pass", C.c_int), ("incident", C.c_void_p)]
 
 
 STAGES = ("fft_x_forward", "fft_y_forward_norms", "classify", "solve", "ifft_y_gather", "ifft_x_recover")
@@ -52,7 +52,7 @@ class fs_problem(C.Structure):
 class fs_report(C.Structure):
     _fields_ = [(k, C.c_longlong) for k in (
         "n_modes", "n_active", "n_zeroed", "n_grazing", "n_alpha_floor", "n_root_capped",
-        "n_u_guard", "n_nan_c", "n_fp64_fallback", "n_refine_iters", "n_columns", "n_nonfinite")] + \
+        "n_u_guard", "n_nan_c", "n_fp64_fallback", "n_refine_iters", "n_columns", "n_nonfinite", "n_timeouts")] + \
         [("ms_stage", C.c_float * 6)]
 
     def as_dict(self):
@@ -129,6 +129,8 @@ def lib():
         L.fs_kernel_plan_bytes.argtypes = [vp]
         L.fs_eval_reciprocals.restype = ip
         L.fs_eval_reciprocals.argtypes = [vp, ip, vp, vp]
+        L.fs_check_bounded_wait.restype = ip
+        L.fs_check_bounded_wait.argtypes = [ip, C.c_uint, C.POINTER(C.c_longlong)]
         L.fs_diff_plan_create.restype = ip
         L.fs_diff_plan_create.argtypes = [vp, C.POINTER(fs_geometry), ip, dp, ip, C.c_double, C.c_double,
                                           C.POINTER(vp)]
@@ -286,6 +288,15 @@ def fs_sync_status(ctx) -> int:
 def fs_eval_reciprocals(x_ptr, n, out_ptr, stream=0) -> int:
     """The library's reciprocal helpers beside CUDA's 1/x and rsqrt (device pointers)."""
     return int(lib().fs_eval_reciprocals(C.c_void_p(x_ptr), int(n), C.c_void_p(out_ptr), C.c_void_p(stream or None)))
+
+
+def fs_check_bounded_wait(blocks, polls) -> int:
+    """Timeouts counted by a device-side barrier that nothing completes (see the header)."""
+    t = C.c_longlong()
+    st = lib().fs_check_bounded_wait(int(blocks), int(polls), C.byref(t))
+    if st != 0:
+        raise FlatLayerError(FS_ECUDA, f"fs_check_bounded_wait returned {st}")
+    return int(t.value)
 
 
 def make_geometry(n, m, z1, z2, zy, period=2.0):

@@ -123,6 +123,7 @@ Layout layout(int n, int m, int m1, int n_omega, bool fp64) {
   L.ncol = off; off = align_up(off + 4 * (size_t)n_omega);
   L.count = off; off = align_up(off + 4 * (size_t)n_omega);
   L.dnu = off; off = align_up(off + 8 * (size_t)n_omega);
+  L.bar = off; off = align_up(off + 4 * (size_t)n_omega);
   L.total = off;
   return L;
 }
@@ -169,6 +170,8 @@ fs_status validate_args(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, in
     if (o->solve_blocks_per_sm < 1 || o->solve_blocks_per_sm > 3)
       return fail(ctx, FS_EINVAL, "solve_blocks_per_sm must be 1, 2 or 3");
     if (o->solve_form != 0 && o->solve_form != 1) return fail(ctx, FS_EINVAL, "solve_form must be 0 or 1");
+    if (o->classify_single_pass != 0 && o->classify_single_pass != 1)
+      return fail(ctx, FS_EINVAL, "classify_single_pass must be 0 or 1");
     if (o->regularizer != 0 && o->regularizer != 1) return fail(ctx, FS_EINVAL, "regularizer must be 0 or 1");
     if (o->regularizer == 1 && o->solve_form != 1)
       return fail(ctx, FS_EUNSUPPORTED, "the truncated SVD is implemented in the rank-one form (solve_form 1)");
@@ -198,6 +201,7 @@ Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, dou
   P.regularizer = o.regularizer;
   P.sampled = o.kernel_plan ? 1 : 0;
   P.incident = o.incident ? 1 : 0;
+  P.classify_single = o.classify_single_pass;
   for (int k = 0; k < g->m1; ++k) P.zy[k] = g->zy[k];
   for (int j = 0; j < n_omega; ++j) {
     P.omega[j] = omega[j];
@@ -238,6 +242,7 @@ Work<R> carve_work(void* base, const Layout& L, unsigned long long* ctr, const c
   w.ncol = (int*)(b + L.ncol);
   w.count = (int*)(b + L.count);
   w.dnu = (double*)(b + L.dnu);
+  w.bar = (unsigned*)(b + L.bar);
   w.ctr = ctr;
   w.tw = tw;
   w.alpha_out = alpha_out;
@@ -256,12 +261,25 @@ template <typename R>
 cudaError_t launch_pipeline(const Problem& P, const Work<R>& w, const void* W, void* xi, void* c, cudaStream_t s,
                             cudaEvent_t* ev, const char** stage) {
   cudaError_t e;
+  // the single-pass classification computes the norms itself; the mixed truncated-SVD
+  // route (W~ in FP64) keeps the separate norms kernel
+  const bool fused = w.wt64 == nullptr && classify_fused_ok(P);
   if (ev) cudaEventRecord(ev[0], s);
   *stage = "fft2_forward";
-  if ((e = launch_fft2_forward<R>((const cx<R>*)W, P, w, s, ev ? ev[1] : nullptr)) != cudaSuccess) return e;
+  if ((e = launch_fft2_forward<R>((const cx<R>*)W, P, w, s, ev ? ev[1] : nullptr, !fused)) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], s);
   *stage = "classify";
-  if ((e = launch_classify<R>(P, w, s)) != cudaSuccess) return e;
+  if (fused) {
+    e = launch_classify_fused<R>(P, w, s);
+    if (e != cudaSuccess) {  // not co-resident on this device: norms, then the two-kernel classification
+      cudaGetLastError();
+      if ((e = launch_mode_norms<R>(P, w, s)) != cudaSuccess) return e;
+      e = launch_classify<R>(P, w, s);
+    }
+  } else {
+    e = launch_classify<R>(P, w, s);
+  }
+  if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[3], s);
   *stage = "solve";
   if (P.solve_form == 1) e = launch_solve_rank1<R>(P, w, s);
@@ -398,6 +416,7 @@ fs_status fs_default_options(fs_options* o) {
   o->regularizer = 0;
   o->kernel_plan = nullptr;
   o->incident = nullptr;
+  o->classify_single_pass = 1;
   return FS_OK;
 }
 
@@ -786,6 +805,7 @@ fs_status fs_get_report(fs_ctx* ctx, fs_report* r) {
   r->n_refine_iters = (long long)h[C_REFINE_ITERS];
   r->n_columns = (long long)h[C_COLUMNS];
   r->n_nonfinite = (long long)h[C_NONFINITE];
+  r->n_timeouts = (long long)h[C_TIMEOUT];
   for (int i = 0; i < 6; ++i) {
     float ms = 0.f;
     if (ctx->timed && cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) ms = 0.f;
@@ -802,6 +822,8 @@ fs_status fs_sync_status(fs_ctx* ctx) {
                         ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fs_sync_status");
+  const unsigned long long to = ctx->ctr_host[C_TIMEOUT];
+  if (to) return fail(ctx, FS_ETIMEOUT, "%llu device-side waits ran out (results unspecified)", to);
   const unsigned long long nf = ctx->ctr_host[C_NONFINITE];
   if (nf) return fail(ctx, FS_ENONFINITE, "%llu non-finite values (modes of W~ or voxels of xi)", nf);
   return FS_OK;

@@ -75,11 +75,15 @@ k_fft_rows(const TI* __restrict__ in, cx<R>* __restrict__ out, long long nrows,
 }
 
 // ---- dense pass along y (columns), in place; grid (ceil(N/TC), planes) ---------
+// clear (may be null): nclear counters zeroed by block (0, 0) -- the barrier counters
+// of the classification kernel that follows
 template <typename R, int N, bool INV>
 __global__ void __launch_bounds__(THREADS)
-k_fft_cols(cx<R>* __restrict__ data, const cx<R>* __restrict__ tw) {
+k_fft_cols(cx<R>* __restrict__ data, const cx<R>* __restrict__ tw, unsigned* __restrict__ clear, int nclear) {
   pdl_wait();
   pdl_trigger();
+  if (clear && blockIdx.x == 0 && blockIdx.y == 0)
+    for (int i = threadIdx.x; i < nclear; i += THREADS) clear[i] = 0u;
   constexpr int TC = Cfg<R>::TC;
   constexpr int E = N * TC;
   __shared__ cx<R> buf[E];
@@ -228,7 +232,7 @@ template <typename R> __device__ __forceinline__ R inv_sqrt(R x);
 template <> __device__ __forceinline__ float inv_sqrt<float>(float x) { return 1.0f / sqrtf(x); }
 template <> __device__ __forceinline__ double inv_sqrt<double>(double x) { return rsqrt64(x); }
 
-template <typename R, int N, typename A>
+template <typename R, int N, typename A, bool INC>
 __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __restrict__ t2,
                                              const int* __restrict__ cols, const int* __restrict__ ncol,
                                              const cx<R>* __restrict__ u0, cx<R>* buf, const cx<R>* tw_s, A* num,
@@ -267,7 +271,7 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
       if (e < E) {
         const cx<R> v = scale * buf[IX::at(e / N, e % N)];
         cx<R> u = scale * buf[IX::at(LINES + e / N, e % N)];
-        if (u0) {  // the given incident field (the transform holds U~ - U~0)
+        if (INC) {  // the given incident field (the transform holds U~ - U~0)
           const long long r = row0 + e / N;
           if (r < nrows) u = u + u0[((long long)om * M + r / N) * N2 + (r % N) * N + (e % N)];
         }
@@ -283,7 +287,9 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
   return __syncthreads_or(bad) != 0;
 }
 
-template <typename R, int N>
+// INC: u0 (the incident field on X) is given and added to u; otherwise the transform
+// already holds the plane wave
+template <typename R, int N, bool INC>
 __global__ void __launch_bounds__(THREADS)
 k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restrict__ cols,
                     const int* __restrict__ ncol, const cx<R>* __restrict__ u0, R* __restrict__ xi,
@@ -300,11 +306,11 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
   const long long nrows = (long long)P.m * N;
   const long long row0 = (long long)blockIdx.x * LINES;
   R num[PER], den[PER];
-  if (recover_pass<R, N, R>(P, t2, cols, ncol, u0, buf, tw_s, num, den)) {
+  if (recover_pass<R, N, R, INC>(P, t2, cols, ncol, u0, buf, tw_s, num, den)) {
     // the sums left the range of R (|u| |V| beyond FP32 for huge evanescent
     // profiles): redo this block with FP64 sums; xi itself is in range
     double nd[PER], dd[PER];
-    recover_pass<R, N, double>(P, t2, cols, ncol, u0, buf, tw_s, nd, dd);
+    recover_pass<R, N, double, INC>(P, t2, cols, ncol, u0, buf, tw_s, nd, dd);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const bool g = !(dd[p] >= (double)P.n_omega * P.eps_u * P.eps_u);
@@ -373,7 +379,7 @@ cudaError_t fwd_wide_impl(const float2* W, const Problem& P, const Work<float>& 
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
   const dim3 g2((N + Cfg<double>::TC - 1) / Cfg<double>::TC, (unsigned)(P.n_omega * P.m1));
-  e = launch_pdl(k_fft_cols<double, N, false>, g2, dim3(THREADS), 0, s, w.wt64, w.tw64);
+  e = launch_pdl(k_fft_cols<double, N, false>, g2, dim3(THREADS), 0, s, w.wt64, w.tw64, (unsigned*)nullptr, 0);
   if (e != cudaSuccess) return e;
   const dim3 gn((unsigned)w.n_partial, (unsigned)P.n_omega);
   e = launch_pdl(k_mode_norms<double>, gn, dim3(NORM_T), 0, s, (const double2*)w.wt64, w.norms, w.partial, P.m1,
@@ -383,7 +389,8 @@ cudaError_t fwd_wide_impl(const float2* W, const Problem& P, const Work<float>& 
 }
 
 template <typename R, int N>
-cudaError_t fwd_impl(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStream_t s, cudaEvent_t mid) {
+cudaError_t fwd_impl(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStream_t s, cudaEvent_t mid,
+                     bool norms) {
   if constexpr (std::is_same<R, float>::value) {
     if (w.wt64) return fwd_wide_impl<N>(W, P, w, s, mid);
   }
@@ -395,13 +402,11 @@ cudaError_t fwd_impl(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStr
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
   const dim3 g2((N + Cfg<R>::TC - 1) / Cfg<R>::TC, (unsigned)(P.n_omega * P.m1));
-  e = launch_pdl(k_fft_cols<R, N, false>, g2, dim3(THREADS), 0, s, w.wt, (const cx<R>*)w.tw);
+  e = launch_pdl(k_fft_cols<R, N, false>, g2, dim3(THREADS), 0, s, w.wt, (const cx<R>*)w.tw,
+                 norms ? (unsigned*)nullptr : w.bar, P.n_omega);
   if (e != cudaSuccess) return e;
-  const dim3 gn((unsigned)w.n_partial, (unsigned)P.n_omega);
-  e = launch_pdl(k_mode_norms<R>, gn, dim3(NORM_T), 0, s, (const cx<R>*)w.wt, w.norms, w.partial, P.m1, N * N,
-                 w.ctr);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  if (!norms) return cudaGetLastError();
+  return launch_mode_norms<R>(P, w, s);
 }
 
 template <typename R, int N>
@@ -413,9 +418,13 @@ cudaError_t rec_impl(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream
   if (mid) cudaEventRecord(mid, s);
   constexpr int LINES = row_lines<N>() / 2 > 0 ? row_lines<N>() / 2 : 1;
   const long long nrows = (long long)P.m * N;
-  e = launch_pdl(k_ifft_rows_recover<R, N>, dim3((unsigned)((nrows + LINES - 1) / LINES)), dim3(THREADS), 0, s, P,
-                 (const cx<R>*)w.t2, (const int*)w.cols, (const int*)w.ncol, w.u0, xi, c, w.ctr,
-                 (const cx<R>*)w.tw);
+  const dim3 gr((unsigned)((nrows + LINES - 1) / LINES));
+  if (w.u0)
+    e = launch_pdl(k_ifft_rows_recover<R, N, true>, gr, dim3(THREADS), 0, s, P, (const cx<R>*)w.t2,
+                   (const int*)w.cols, (const int*)w.ncol, w.u0, xi, c, w.ctr, (const cx<R>*)w.tw);
+  else
+    e = launch_pdl(k_ifft_rows_recover<R, N, false>, gr, dim3(THREADS), 0, s, P, (const cx<R>*)w.t2,
+                   (const int*)w.cols, (const int*)w.ncol, w.u0, xi, c, w.ctr, (const cx<R>*)w.tw);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -430,8 +439,8 @@ cudaError_t dense_impl(cx<R>* in, cx<R>* out, long long planes, bool inverse, co
     for (long long p0 = 0; p0 < planes; p0 += MAX_Y) {
       const long long np = planes - p0 < MAX_Y ? planes - p0 : MAX_Y;
       const dim3 gc((N + Cfg<R>::TC - 1) / Cfg<R>::TC, (unsigned)np);
-      if (inv) k_fft_cols<R, N, true><<<gc, THREADS, 0, s>>>(buf + p0 * N * N, tw);
-      else k_fft_cols<R, N, false><<<gc, THREADS, 0, s>>>(buf + p0 * N * N, tw);
+      if (inv) k_fft_cols<R, N, true><<<gc, THREADS, 0, s>>>(buf + p0 * N * N, tw, nullptr, 0);
+      else k_fft_cols<R, N, false><<<gc, THREADS, 0, s>>>(buf + p0 * N * N, tw, nullptr, 0);
     }
   };
   if (!inverse) {
@@ -456,10 +465,21 @@ bool fft_size_supported(int n) {
 }
 
 template <typename R>
+cudaError_t launch_mode_norms(const Problem& P, const Work<R>& w, cudaStream_t s) {
+  const dim3 gn((unsigned)w.n_partial, (unsigned)P.n_omega);
+  cudaError_t e = launch_pdl(k_mode_norms<R>, gn, dim3(NORM_T), 0, s, (const cx<R>*)w.wt, w.norms, w.partial, P.m1,
+                             P.n * P.n, w.ctr);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+template cudaError_t launch_mode_norms<double>(const Problem&, const Work<double>&, cudaStream_t);
+template cudaError_t launch_mode_norms<float>(const Problem&, const Work<float>&, cudaStream_t);
+
+template <typename R>
 cudaError_t launch_fft2_forward(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStream_t s,
-                                cudaEvent_t mid) {
+                                cudaEvent_t mid, bool norms) {
   switch (P.n) {
-#define FL_CASE(K) case K: return fwd_impl<R, K>(W, P, w, s, mid);
+#define FL_CASE(K) case K: return fwd_impl<R, K>(W, P, w, s, mid, norms);
     FL_SIZES(FL_CASE)
 #undef FL_CASE
     default: return cudaErrorInvalidValue;
@@ -496,9 +516,9 @@ cudaError_t launch_twiddles(cx<R>* tw, int n, cudaStream_t s) {
 }
 
 template cudaError_t launch_fft2_forward<double>(const double2*, const Problem&, const Work<double>&, cudaStream_t,
-                                                 cudaEvent_t);
+                                                 cudaEvent_t, bool);
 template cudaError_t launch_fft2_forward<float>(const float2*, const Problem&, const Work<float>&, cudaStream_t,
-                                                cudaEvent_t);
+                                                cudaEvent_t, bool);
 template cudaError_t launch_recover<double>(const Problem&, const Work<double>&, double*, double*, cudaStream_t,
                                             cudaEvent_t);
 template cudaError_t launch_recover<float>(const Problem&, const Work<float>&, float*, float*, cudaStream_t,

@@ -24,7 +24,7 @@ constexpr int MAX_N = 256;      // horizontal points per axis
 // Device counters (index into Work::ctr); summed over the call.
 enum Ctr {
   C_MODES = 0, C_ACTIVE, C_ZEROED, C_GRAZING, C_ALPHA_FLOOR, C_ROOT_CAPPED,
-  C_U_GUARD, C_NAN_C, C_FP64_FALLBACK, C_NONFINITE, C_REFINE_ITERS, C_COLUMNS, C_COUNT
+  C_U_GUARD, C_NAN_C, C_FP64_FALLBACK, C_NONFINITE, C_REFINE_ITERS, C_COLUMNS, C_TIMEOUT, C_COUNT
 };
 
 // Scalars of one problem, passed by value to every kernel.
@@ -52,7 +52,10 @@ struct Problem {
   double inv_c02, u_guard;  // c0^-2 and the |u|^2 guard eps_u^2 n_omega of the recovery
   int sampled;  // 1: the sampled-G kernel of a kernel plan (Work::ktab) replaces the Weyl form
   int incident; // 1: the incident field on X is given (Work::u0) instead of the plane wave
+  int classify_single;  // 1: single-pass classification (one cooperative launch)
 };
+
+inline bool classify_fused_ok(const Problem& P) { return P.classify_single != 0; }
 
 inline void derive_constants(Problem& P) {
   P.kn = 2.0 * M_PI / P.period;
@@ -83,6 +86,7 @@ template <typename R> struct Work {
   int* ncol;        // [n_omega]
   int* count;       // [n_omega] active modes
   double* dnu;      // [n_omega] delta_nu
+  unsigned* bar;    // [n_omega] barrier counters of the single-pass classification
   unsigned long long* ctr;  // [C_COUNT]
   const cx<R>* tw;  // [N] twiddles exp(-2 pi i j/N)
   double* alpha_out;  // [n_omega][N*N] or null
@@ -112,7 +116,7 @@ inline int classify_blocks(int n) { return (n * n + 1023) / 1024; }
 // from the base of the workspace, and its total size.  The context entry points
 // and the allocation-free entry point carve their workspace from this one layout.
 struct Layout {
-  size_t t12, prof, norms, partial, slot, act, flagbits, blkcnt, blkgz, colblk, cols, ncol, count, dnu, total;
+  size_t t12, prof, norms, partial, slot, act, flagbits, blkcnt, blkgz, colblk, cols, ncol, count, dnu, bar, total;
   int n_partial;
 };
 // (the W~ part of the t12 region is sized for complex128 in both precisions, so
@@ -166,11 +170,21 @@ cudaError_t opt_in_smem(SmemOptIn& flag, const void* kernel, size_t bytes);
 
 // Launchers (return the launch error).
 // `mid` (may be null) is recorded on `s` between the two kernels of the stage
+// norms: also the per-mode norms and their block sums (k_mode_norms); without them the
+// column pass zeroes the barrier counters of the single-pass classification instead
 template <typename R>
 cudaError_t launch_fft2_forward(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStream_t s,
-                                cudaEvent_t mid = nullptr);
+                                cudaEvent_t mid = nullptr, bool norms = true);
+template <typename R>
+cudaError_t launch_mode_norms(const Problem& P, const Work<R>& w, cudaStream_t s);
+// classification from the norms: two kernels (flags, scatter)
 template <typename R>
 cudaError_t launch_classify(const Problem& P, const Work<R>& w, cudaStream_t s);
+// classification in one cooperative launch that computes the norms itself (forward
+// transform run with norms = false); returns an error without enqueueing anything
+// when the device cannot hold the grid co-resident (the caller then falls back)
+template <typename R>
+cudaError_t launch_classify_fused(const Problem& P, const Work<R>& w, cudaStream_t s);
 cudaError_t launch_solve_fp64(const Problem& P, const Work<double>& w, cudaStream_t s);
 cudaError_t launch_solve_mixed(const Problem& P, const Work<float>& w, cudaStream_t s);
 // rank-one closed form of the per-mode problem (Problem::solve_form == 1), either precision

@@ -42,6 +42,8 @@
 //            fp64_switch, floor cases and FP32 breakdowns take the FS_FP64 route.
 #include <math.h>
 
+#include <atomic>
+
 #include "modes.cuh"
 #include "pipeline.cuh"
 
@@ -245,6 +247,226 @@ k_classify_scatter(Problem P, const unsigned* __restrict__ flagbits, const int* 
       count[om] = total;
       atomicAdd(ctr + C_MODES, (unsigned long long)N2);
       atomicAdd(ctr + C_COLUMNS, (unsigned long long)base);
+      atomicAdd(ctr + C_ACTIVE, (unsigned long long)total);
+      atomicAdd(ctr + C_GRAZING, (unsigned long long)gz);
+      atomicAdd(ctr + C_ZEROED, (unsigned long long)(N2 - total - gz));
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------
+// single-pass classification: one cooperative launch, grid (CB, n_omega), blocks of
+// CMB modes as above, in three phases separated by barriers over the blocks of a
+// frequency:
+//   1. the norms ||W~_nu||^2 of the block's modes (summed over the data planes in
+//      plane order, in the working precision, kept in registers) and their block sum;
+//   2. delta_nu from the CB block sums (every block adds them in the same order), the
+//      active-mode bitmask (shared memory), the block's active and grazing counts and
+//      column mask;
+//   3. slots and the ascending active list from the prefix of the block counts;
+//      block 0 compacts the columns and adds the counters.
+// It replaces k_mode_norms, k_classify_flags and k_classify_scatter (three launches and
+// their tails).  The barrier counters (Work::bar) are zeroed by the forward column
+// pass.  Each wait polls at most BAR_POLLS times (about a quarter of a second); a wait
+// that runs out adds to C_TIMEOUT and its block stops (fs_sync_status: FS_ETIMEOUT).
+// ------------------------------------------------------------------------------
+constexpr unsigned BAR_POLLS = 1u << 22;
+
+// arrive at the barrier `bar` and wait until `target` blocks have arrived; false when
+// the wait ran out (uniform over the block)
+__device__ __forceinline__ bool grid_wait(unsigned* bar, unsigned target, unsigned polls_max,
+                                          unsigned long long* ctr, int* ok_s) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's writes before its arrival
+    atomicAdd(bar, 1u);
+    unsigned polls = 0;
+    int ok = 1;
+    while (*(volatile unsigned*)bar < target) {
+      if (++polls > polls_max) {
+        ok = 0;
+        atomicAdd(ctr + C_TIMEOUT, 1ull);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();  // the other blocks' writes after the wait
+    *ok_s = ok;
+  }
+  __syncthreads();
+  return *ok_s != 0;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(CT)
+k_classify_fused(Problem P, const cx<R>* __restrict__ wt, double* __restrict__ partial, unsigned* __restrict__ bar,
+                 int* __restrict__ blkcnt, int* __restrict__ blkgz, unsigned* __restrict__ colblk,
+                 int* __restrict__ slot, int* __restrict__ act, int* __restrict__ cols, int* __restrict__ ncol,
+                 int* __restrict__ count, double* __restrict__ dnu_out, unsigned long long* __restrict__ ctr) {
+  pdl_wait();
+  pdl_trigger();
+  const int om = blockIdx.y, b = blockIdx.x, CB = gridDim.x;
+  const int N = P.n, N2 = N * N, M1 = P.m1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int K = CMB / CT;  // modes per thread
+  __shared__ double red[CT / 32];
+  __shared__ double thr_s;
+  __shared__ unsigned cm[NWC];
+  __shared__ int wc[CT / 32], wg[CT / 32];
+  __shared__ unsigned words[CWB];
+  __shared__ int wpre[CWB];
+  __shared__ int base_s, total_s, ok_s;
+  if (threadIdx.x < NWC) cm[threadIdx.x] = 0u;
+  // phase 1: norms, eight planes' loads in flight per mode
+  R nrm[K];
+  double mine = 0.0;
+  int bad = 0;
+  const cx<R>* base = wt + (long long)om * M1 * N2;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int v = b * CMB + k * CT + threadIdx.x;
+    R acc = R(0);
+    if (v < N2) {
+      int p = 0;
+      for (; p + 8 <= M1; p += 8) {
+        cx<R> q[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) q[j] = base[(long long)(p + j) * N2 + v];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc += q[j].x * q[j].x + q[j].y * q[j].y;
+      }
+      for (; p < M1; ++p) {
+        const cx<R> q = base[(long long)p * N2 + v];
+        acc += q.x * q.x + q.y * q.y;
+      }
+      bad += !isfinite(acc);
+    }
+    nrm[k] = acc;
+    mine += (double)acc;
+  }
+  mine = warp_sum(mine);
+  if (lane == 0) red[wid] = mine;
+  const int n_bad = __syncthreads_count(bad);
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < CT / 32; ++w) t += red[w];
+    partial[om * CB + b] = t;
+    if (n_bad) atomicAdd(ctr + C_NONFINITE, (unsigned long long)n_bad);
+  }
+  if (!grid_wait(bar + om, (unsigned)CB, BAR_POLLS, ctr, &ok_s)) return;
+  // phase 2: delta_nu from the block sums (||W||^2 = sum_nu ||W~_nu||^2 / N^2, Parseval),
+  // the same order in every block, then the bitmask
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int i = lane; i < CB; i += 32) t += __ldcg(partial + om * CB + i);
+    t = warp_sum(t);
+    if (lane == 0) {
+      const double dnu = P.tau * fmax(P.delta, P.delta_floor) * sqrt(t / (double)N2);
+      if (b == 0) dnu_out[om] = dnu;
+      // a non-finite ||W|| (W holds a NaN or Inf) leaves delta_nu undefined: no mode passes
+      thr_s = isfinite(dnu) ? dnu * dnu : INFINITY;
+    }
+  }
+  __syncthreads();
+  const double thr = thr_s;
+  const int glo = P.graz_lo[om], ghi = P.graz_hi[om];
+  int cnt = 0, ngz = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int v = b * CMB + k * CT + threadIdx.x;
+    bool on = false;
+    if (v < N2) {
+      const int i2 = v / N, i1 = v - i2 * N;
+      const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
+      const int msq = m1 * m1 + m2 * m2;
+      const bool graz = msq >= glo && msq <= ghi;
+      ngz += graz;
+      on = !graz && (P.alpha_mode == 1 || (double)nrm[k] > thr);
+      if (on) atomicOr(&cm[i1 >> 5], 1u << (i1 & 31));
+    }
+    const unsigned word = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) {
+      words[k * (CT / 32) + wid] = word;
+      cnt += __popc(word);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) ngz += __shfl_xor_sync(0xffffffffu, ngz, o);
+  if (lane == 0) {
+    wc[wid] = cnt;
+    wg[wid] = ngz;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int c = 0, g = 0;
+    for (int w = 0; w < CT / 32; ++w) {
+      c += wc[w];
+      g += wg[w];
+    }
+    blkcnt[om * CB + b] = c;
+    blkgz[om * CB + b] = g;
+  }
+  if (threadIdx.x < NWC) colblk[((long long)om * CB + b) * NWC + threadIdx.x] = cm[threadIdx.x];
+  if (!grid_wait(bar + om, 2u * (unsigned)CB, BAR_POLLS, ctr, &ok_s)) return;
+  // phase 3: slots and the active list (as k_classify_scatter, the words from shared memory)
+  if (wid == 0) {
+    const int c0 = lane < CB ? __ldcg(blkcnt + om * CB + lane) : 0;
+    const int c1 = lane + 32 < CB ? __ldcg(blkcnt + om * CB + lane + 32) : 0;
+    int before = (lane < b ? c0 : 0) + (lane + 32 < b ? c1 : 0), all = c0 + c1;
+    for (int o = 16; o > 0; o >>= 1) {
+      before += __shfl_xor_sync(0xffffffffu, before, o);
+      all += __shfl_xor_sync(0xffffffffu, all, o);
+    }
+    const unsigned w = words[lane];
+    const int c = __popc(w);
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    wpre[lane] = incl - c;
+    if (lane == 0) {
+      base_s = before;
+      total_s = all;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int v = b * CMB + k * CT + threadIdx.x;
+    if (v < N2) {
+      const int j = k * (CT / 32) + wid;
+      const unsigned w = words[j];
+      if (w >> lane & 1u) {
+        const int pos = base_s + wpre[j] + __popc(w & ((1u << lane) - 1u));
+        slot[(long long)om * N2 + v] = pos;
+        act[(long long)om * N2 + pos] = v;
+      } else {
+        slot[(long long)om * N2 + v] = -1;
+      }
+    }
+  }
+  if (b == 0 && wid == 0) {  // columns holding an active mode, in order, and the counters
+    int gz = 0;
+    for (int i = lane; i < CB; i += 32) gz += __ldcg(blkgz + om * CB + i);
+    for (int o = 16; o > 0; o >>= 1) gz += __shfl_xor_sync(0xffffffffu, gz, o);
+    int cbase = 0;
+    for (int j0 = 0; j0 < N; j0 += 32) {
+      unsigned cmw = 0u;
+      for (int i = lane; i < CB; i += 32) cmw |= __ldcg(colblk + ((long long)om * CB + i) * NWC + (j0 >> 5));
+      cmw = __reduce_or_sync(0xffffffffu, cmw);
+      if (j0 == 0) cmw |= 1u;  // the incident plane wave lives at nu = 0
+      const int j = j0 + lane;
+      const bool f = j < N && (cmw >> lane & 1u);
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (f) cols[om * N + cbase + __popc(bal & ((1u << lane) - 1u))] = j;
+      cbase += __popc(bal);
+    }
+    if (lane == 0) {
+      const int total = total_s;
+      ncol[om] = cbase;
+      count[om] = total;
+      atomicAdd(ctr + C_MODES, (unsigned long long)N2);
+      atomicAdd(ctr + C_COLUMNS, (unsigned long long)cbase);
       atomicAdd(ctr + C_ACTIVE, (unsigned long long)total);
       atomicAdd(ctr + C_GRAZING, (unsigned long long)gz);
       atomicAdd(ctr + C_ZEROED, (unsigned long long)(N2 - total - gz));
@@ -1166,6 +1388,82 @@ cudaError_t launch_classify(const Problem& P, const Work<R>& w, cudaStream_t s) 
 }
 template cudaError_t launch_classify<double>(const Problem&, const Work<double>&, cudaStream_t);
 template cudaError_t launch_classify<float>(const Problem&, const Work<float>&, cudaStream_t);
+
+template <typename R>
+cudaError_t launch_classify_fused(const Problem& P, const Work<R>& w, cudaStream_t s) {
+  const int cb = classify_blocks(P.n);
+  if (cb * CMB < P.n * P.n || cb > 64) return cudaErrorInvalidValue;
+  // every block of the grid must be resident at once (they wait on one another): the
+  // resident blocks per SM of this kernel, looked up once per device; a device on
+  // which the launch failed once takes the two-kernel classification from then on
+  static std::atomic<int> occ[MAX_DEVICES], refused[MAX_DEVICES];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const bool known = dev >= 0 && dev < MAX_DEVICES;
+  if (known && refused[dev].load(std::memory_order_relaxed)) return cudaErrorNotSupported;
+  int per_sm = known ? occ[dev].load(std::memory_order_relaxed) : 0;
+  if (per_sm <= 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_classify_fused<R>, CT, 0);
+    if (e != cudaSuccess) return e;
+    if (known) occ[dev].store(per_sm, std::memory_order_relaxed);
+  }
+  if ((long long)per_sm * sm_count() < (long long)cb * P.n_omega) return cudaErrorCooperativeLaunchTooLarge;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cb, P.n_omega);
+  cfg.blockDim = dim3(CT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_classify_fused<R>, P, (const cx<R>*)w.wt, w.partial, w.bar,
+                                           w.blkcnt, w.blkgz, w.colblk, w.slot, w.act, w.cols, w.ncol, w.count,
+                                           w.dnu, w.ctr);
+  if (e != cudaSuccess && known) refused[dev].store(1, std::memory_order_relaxed);
+  return e;
+}
+template cudaError_t launch_classify_fused<double>(const Problem&, const Work<double>&, cudaStream_t);
+template cudaError_t launch_classify_fused<float>(const Problem&, const Work<float>&, cudaStream_t);
+
+namespace {
+// every block arrives at a barrier whose target is one more than the grid: nothing
+// ever completes it, so each wait runs out after `polls` polls
+__global__ void k_wait_never(unsigned* bar, unsigned target, unsigned polls, unsigned long long* ctr) {
+  __shared__ int ok_s;
+  grid_wait(bar, target, polls, ctr, &ok_s);
+}
+}  // namespace
+
+}  // namespace fl
+
+extern "C" int fs_check_bounded_wait(int blocks, unsigned polls, long long* timeouts) {
+  using namespace fl;
+  if (blocks < 1 || blocks > 64 || polls < 1 || polls > (1u << 20) || !timeouts) return 1;
+  // one buffer: the barrier counter (bytes 0-3), the counters [C_COUNT] from byte 16
+  constexpr size_t CTR_OFF = 16, BYTES = CTR_OFF + sizeof(unsigned long long) * C_COUNT;
+  unsigned char* mem = nullptr;
+  if (cudaMalloc(&mem, BYTES) != cudaSuccess) return 2;
+  unsigned* bar = reinterpret_cast<unsigned*>(mem);
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(mem + CTR_OFF);
+  cudaError_t e = cudaMemset(mem, 0, BYTES);
+  if (e == cudaSuccess) {
+    k_wait_never<<<blocks, 32>>>(bar, (unsigned)blocks + 1u, polls, ctr);
+    e = cudaGetLastError();
+  }
+  unsigned long long h[C_COUNT] = {};
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(h, ctr, sizeof(unsigned long long) * C_COUNT, cudaMemcpyDeviceToHost);
+  cudaFree(mem);
+  if (e != cudaSuccess) return 3;
+  *timeouts = (long long)h[C_TIMEOUT];
+  return 0;
+}
+
+namespace fl {
 
 cudaError_t launch_solve_fp64(const Problem& P, const Work<double>& w, cudaStream_t s) {
   return solve_impl<double, false>(P, w, s);

@@ -30,14 +30,15 @@ namespace fl {
 
 namespace {
 
-constexpr int RW = 4;               // warps (modes) per block
-constexpr int RK = MAX_M / 32;      // X planes per lane
+constexpr int RW = 4;  // warps (modes) per block
 
-struct Rank1Mem {
-  double2 v[MAX_M], t[MAX_M], F[MAX_M], B[MAX_M];
+// RKE data planes and RK X planes per lane: (1, 2) for up to 32 data and 64 X planes,
+// (4, 4) up to 128 of each; the register arrays and per-warp shared memory are sized by them
+template <int RK> struct Rank1Mem {
+  double2 v[32 * RK], t[32 * RK], F[32 * RK], B[32 * RK];
 };
 
-template <typename R>
+template <typename R, int RKE, int RK>
 __global__ void __launch_bounds__(RW * 32)
 k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict__ wt64,
               const int* __restrict__ act, const int* __restrict__ count,
@@ -45,9 +46,9 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
               unsigned long long* __restrict__ ctr) {
   pdl_wait();
   pdl_trigger();
-  __shared__ Rank1Mem mem[RW];
+  __shared__ Rank1Mem<RK> mem[RW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Rank1Mem& S = mem[warp];
+  Rank1Mem<RK>& S = mem[warp];
   const int N = P.n, n = P.m1, m = P.m;
   const long long N2 = (long long)N * N;
   long long total = 0;
@@ -71,9 +72,9 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
     // sum |E|^2, sum |b|^2, E^H b and sum |P|^2, P kept in registers (slot l / 32)
     double sE = 0.0, bb = 0.0, sP = 0.0;
     double2 beta = make_double2(0, 0);
-    double2 ek[RK], bk[RK];  // E_k and b_k of k = lane + 32 j
+    double2 ek[RKE], bk[RKE];  // E_k and b_k of k = lane + 32 j
 #pragma unroll
-    for (int j = 0; j < RK; ++j) {
+    for (int j = 0; j < RKE; ++j) {
       const int k = lane + 32 * j;
       ek[j] = make_double2(0, 0);
       bk[j] = make_double2(0, 0);
@@ -106,7 +107,7 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
     if (tr > 0.0) {
       const double2 pr = rcp64(sE) * beta;
 #pragma unroll
-      for (int j = 0; j < RK; ++j) p += abs2(bk[j] - ek[j] * pr);
+      for (int j = 0; j < RKE; ++j) p += abs2(bk[j] - ek[j] * pr);
       p = warp_sum(p);
     }
     double2 coef = make_double2(0, 0);  // V~_l = conj(P_l) coef
@@ -192,9 +193,13 @@ cudaError_t launch_solve_rank1(const Problem& P, const Work<R>& w, cudaStream_t 
   const long long want = (modes + RW - 1) / RW;
   const long long cap = 8LL * sms;
   const unsigned grid = (unsigned)(want < cap ? want : cap);
-  return launch_pdl(k_solve_rank1<R>, dim3(grid), dim3(RW * 32), 0, s, P, (const cx<R>*)w.wt,
-                    (const double2*)w.wt64, (const int*)w.act,
-                    (const int*)w.count, (const double*)w.dnu, w.prof, w.alpha_out, w.ctr);
+  if (P.m <= 64 && P.m1 <= 32)
+    return launch_pdl(k_solve_rank1<R, 1, 2>, dim3(grid), dim3(RW * 32), 0, s, P, (const cx<R>*)w.wt,
+                      (const double2*)w.wt64, (const int*)w.act, (const int*)w.count, (const double*)w.dnu, w.prof,
+                      w.alpha_out, w.ctr);
+  return launch_pdl(k_solve_rank1<R, 4, 4>, dim3(grid), dim3(RW * 32), 0, s, P, (const cx<R>*)w.wt,
+                    (const double2*)w.wt64, (const int*)w.act, (const int*)w.count, (const double*)w.dnu, w.prof,
+                    w.alpha_out, w.ctr);
 }
 
 template cudaError_t launch_solve_rank1<double>(const Problem&, const Work<double>&, cudaStream_t);

@@ -116,3 +116,40 @@ def test_reciprocals_match_cuda():
     assert rel32s.max() <= 2.5e-7, rel32s.max()
     # negative inputs: rsqrt64 and rsqrt32 return what 1/sqrt(x) gives (NaN)
     assert np.all(np.isnan(rsq64[pos.size:])) and np.all(np.isnan(rsq32[pos.size:]))
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(rc):
+    """A device-side barrier that nothing completes (its target exceeds the grid): each
+    block's wait gives up after its poll limit and counts a timeout; the GPU context is
+    usable afterwards (a reconstruction runs and reports FS_OK)."""
+    import torch
+    from paper_1911_10487_gb300._abi import FS_OK, fs_check_bounded_wait
+    assert fs_check_bounded_wait(4, 2000) == 4
+    g, om, W, _ = case("r24", 0.01)
+    Wd = torch.from_numpy(np.ascontiguousarray(W)).to(rc.device)
+    rc.reconstruct(Wd, list(om), _geom(g), 0.01)
+    assert rc.sync_status() == FS_OK
+    assert rc.report()["n_timeouts"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["c1", "r12", "r48", "r256"])
+def test_single_pass_classification_equals_three_kernel_form(rc, name, precision):
+    """The cooperative single-pass classification and the three-kernel form decide the
+    same modes; xi agrees to the rounding of ||W||^2 (grouped differently)."""
+    import torch
+    g, om, W, _ = case(name, 0.01)
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    Wd = torch.from_numpy(np.ascontiguousarray(W)).to(device=rc.device, dtype=dt)
+    out = []
+    for single in (1, 0):
+        xi, _, alpha = rc.reconstruct(Wd, list(om), _geom(g), 0.01, precision=precision, want_alpha=True,
+                                      classify_single_pass=single)
+        torch.cuda.synchronize()
+        out.append((xi.double().cpu().numpy(), np.isfinite(alpha.cpu().numpy()), rc.report()))
+    (x1, a1, r1), (x0, a0, r0) = out
+    assert np.array_equal(a1, a0)
+    assert r1["n_active"] == r0["n_active"] and r1["n_columns"] == r0["n_columns"]
+    assert r1["n_timeouts"] == 0
+    from oracle.metrics import rel_l2
+    assert rel_l2(x1, x0) <= (1e-12 if precision == "fp64" else 1e-6)
