@@ -487,8 +487,18 @@ def run_batch(args, local, flush, world):
                 e.record(stream)
         torch.cuda.synchronize()
         ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in ev) / K, world)
+        # the batch's compulsory HBM traffic: every problem's data W read once and xi, c
+        # written once (a lower bound of the algorithmic bytes: the intermediates of
+        # this workload's 4-16 MB problems stay in the 129 MB L2 between kernels)
+        sc = 16 if prec == "fp64" else 8
+        byt = sum(len(wl.omegas) * wl.m1 * wl.n * wl.n * sc + 2 * wl.m * wl.n * wl.n * (sc // 2) for wl in wls)
+        hbm, src = peaks()
+        gbs = byt / (ms * 1e-3) / 1e9
         res[prec] = {"value": world * vox / (ms * 1e-3), "ms_per_step": ms,
-                     "tuned": {"n_streams": cfgs[prec][0], "solve_blocks_per_sm": cfgs[prec][1]}}
+                     "tuned": {"n_streams": cfgs[prec][0], "solve_blocks_per_sm": cfgs[prec][1]},
+                     "roofline": {"bound": "hbm", "compulsory_bytes": byt, "achieved": gbs, "peak": hbm,
+                                  "unit": "GB/s", "frac": gbs / hbm, "peak_source": src,
+                                  "note": "W read once, xi and c written once per problem"}}
     grids = {}
     for wl in wls:
         k = f"{wl.n}^2x{wl.m}"

@@ -297,8 +297,10 @@ __device__ __forceinline__ bool grid_wait(unsigned* bar, unsigned target, unsign
   return *ok_s != 0;
 }
 
+constexpr int FT = CMB / 2;  // threads per block of the single-pass classification: two modes each
+
 template <typename R>
-__global__ void __launch_bounds__(CT)
+__global__ void __launch_bounds__(FT)
 k_classify_fused(Problem P, const cx<R>* __restrict__ wt, double* __restrict__ partial, unsigned* __restrict__ bar,
                  int* __restrict__ blkcnt, int* __restrict__ blkgz, unsigned* __restrict__ colblk,
                  int* __restrict__ slot, int* __restrict__ act, int* __restrict__ cols, int* __restrict__ ncol,
@@ -308,48 +310,49 @@ k_classify_fused(Problem P, const cx<R>* __restrict__ wt, double* __restrict__ p
   const int om = blockIdx.y, b = blockIdx.x, CB = gridDim.x;
   const int N = P.n, N2 = N * N, M1 = P.m1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  constexpr int K = CMB / CT;  // modes per thread
-  __shared__ double red[CT / 32];
+  constexpr int K = CMB / FT;  // modes per thread
+  constexpr int BATCH = sizeof(R) == 4 ? 16 : 8;  // plane loads in flight per thread
+  __shared__ double red[FT / 32];
   __shared__ double thr_s;
   __shared__ unsigned cm[NWC];
-  __shared__ int wc[CT / 32], wg[CT / 32];
+  __shared__ int wc[FT / 32], wg[FT / 32];
   __shared__ unsigned words[CWB];
   __shared__ int wpre[CWB];
   __shared__ int base_s, total_s, ok_s;
   if (threadIdx.x < NWC) cm[threadIdx.x] = 0u;
-  // phase 1: norms, eight planes' loads in flight per mode
+  // phase 1: norms, BATCH planes' loads in flight, summed in plane order
   R nrm[K];
   double mine = 0.0;
   int bad = 0;
   const cx<R>* base = wt + (long long)om * M1 * N2;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int v = b * CMB + k * CT + threadIdx.x;
-    R acc = R(0);
-    if (v < N2) {
-      int p = 0;
-      for (; p + 8 <= M1; p += 8) {
-        cx<R> q[8];
+  for (int k = 0; k < K; ++k) nrm[k] = R(0);
+  for (int p = 0; p < M1; p += BATCH) {  // the K modes' loads of BATCH planes all in flight
+    cx<R> q[K][BATCH];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) q[j] = base[(long long)(p + j) * N2 + v];
+    for (int k = 0; k < K; ++k) {
+      const int v = b * CMB + k * FT + threadIdx.x;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc += q[j].x * q[j].x + q[j].y * q[j].y;
-      }
-      for (; p < M1; ++p) {
-        const cx<R> q = base[(long long)p * N2 + v];
-        acc += q.x * q.x + q.y * q.y;
-      }
-      bad += !isfinite(acc);
+      for (int j = 0; j < BATCH; ++j)
+        q[k][j] = (v < N2 && p + j < M1) ? base[(long long)(p + j) * N2 + v] : czero<R>();
     }
-    nrm[k] = acc;
-    mine += (double)acc;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int j = 0; j < BATCH; ++j) nrm[k] += q[k][j].x * q[k][j].x + q[k][j].y * q[k][j].y;
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int v = b * CMB + k * FT + threadIdx.x;
+    if (v < N2) bad += !isfinite(nrm[k]);
+    mine += (double)nrm[k];
   }
   mine = warp_sum(mine);
   if (lane == 0) red[wid] = mine;
   const int n_bad = __syncthreads_count(bad);
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < CT / 32; ++w) t += red[w];
+    for (int w = 0; w < FT / 32; ++w) t += red[w];
     partial[om * CB + b] = t;
     if (n_bad) atomicAdd(ctr + C_NONFINITE, (unsigned long long)n_bad);
   }
@@ -373,7 +376,7 @@ k_classify_fused(Problem P, const cx<R>* __restrict__ wt, double* __restrict__ p
   int cnt = 0, ngz = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int v = b * CMB + k * CT + threadIdx.x;
+    const int v = b * CMB + k * FT + threadIdx.x;
     bool on = false;
     if (v < N2) {
       const int i2 = v / N, i1 = v - i2 * N;
@@ -386,7 +389,7 @@ k_classify_fused(Problem P, const cx<R>* __restrict__ wt, double* __restrict__ p
     }
     const unsigned word = __ballot_sync(0xffffffffu, on);
     if (lane == 0) {
-      words[k * (CT / 32) + wid] = word;
+      words[k * (FT / 32) + wid] = word;
       cnt += __popc(word);
     }
   }
@@ -398,7 +401,7 @@ k_classify_fused(Problem P, const cx<R>* __restrict__ wt, double* __restrict__ p
   __syncthreads();
   if (threadIdx.x == 0) {
     int c = 0, g = 0;
-    for (int w = 0; w < CT / 32; ++w) {
+    for (int w = 0; w < FT / 32; ++w) {
       c += wc[w];
       g += wg[w];
     }
@@ -432,9 +435,9 @@ k_classify_fused(Problem P, const cx<R>* __restrict__ wt, double* __restrict__ p
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int v = b * CMB + k * CT + threadIdx.x;
+    const int v = b * CMB + k * FT + threadIdx.x;
     if (v < N2) {
-      const int j = k * (CT / 32) + wid;
+      const int j = k * (FT / 32) + wid;
       const unsigned w = words[j];
       if (w >> lane & 1u) {
         const int pos = base_s + wpre[j] + __popc(w & ((1u << lane) - 1u));
@@ -1403,14 +1406,14 @@ cudaError_t launch_classify_fused(const Problem& P, const Work<R>& w, cudaStream
   if (known && refused[dev].load(std::memory_order_relaxed)) return cudaErrorNotSupported;
   int per_sm = known ? occ[dev].load(std::memory_order_relaxed) : 0;
   if (per_sm <= 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_classify_fused<R>, CT, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_classify_fused<R>, FT, 0);
     if (e != cudaSuccess) return e;
     if (known) occ[dev].store(per_sm, std::memory_order_relaxed);
   }
   if ((long long)per_sm * sm_count() < (long long)cb * P.n_omega) return cudaErrorCooperativeLaunchTooLarge;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cb, P.n_omega);
-  cfg.blockDim = dim3(CT);
+  cfg.blockDim = dim3(FT);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[2];
