@@ -459,13 +459,14 @@ def run_batch(args, local, flush, world):
         cfgs[prec] = tuner.best(rc, items[prec], prec, repeats=2, outs=outs[prec])
     graphs = {}
     for prec in ("fp64", "mixed"):
-        s_, b_ = cfgs[prec]
+        s_, b_, t_, c_ = cfgs[prec]
+        kw = dict(n_streams=s_, outs=outs[prec], solve_blocks_per_sm=b_, fft_tile=t_, classify_single_pass=c_)
         with torch.cuda.stream(stream):
-            rc.reconstruct_batch(items[prec], prec, n_streams=s_, outs=outs[prec], solve_blocks_per_sm=b_)
+            rc.reconstruct_batch(items[prec], prec, **kw)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
-            rc.reconstruct_batch(items[prec], prec, n_streams=s_, outs=outs[prec], solve_blocks_per_sm=b_)
+            rc.reconstruct_batch(items[prec], prec, **kw)
         torch.cuda.synchronize()
         graphs[prec] = g
     vox = sum(wl.voxel_freqs for wl in wls)
@@ -495,7 +496,8 @@ def run_batch(args, local, flush, world):
         hbm, src = peaks()
         gbs = byt / (ms * 1e-3) / 1e9
         res[prec] = {"value": world * vox / (ms * 1e-3), "ms_per_step": ms,
-                     "tuned": {"n_streams": cfgs[prec][0], "solve_blocks_per_sm": cfgs[prec][1]},
+                     "tuned": {"n_streams": cfgs[prec][0], "solve_blocks_per_sm": cfgs[prec][1],
+                               "fft_tile": cfgs[prec][2], "classify_single_pass": cfgs[prec][3]},
                      "roofline": {"bound": "hbm", "compulsory_bytes": byt, "achieved": gbs, "peak": hbm,
                                   "unit": "GB/s", "frac": gbs / hbm, "peak_source": src,
                                   "note": "W read once, xi and c written once per problem"}}

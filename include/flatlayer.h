@@ -120,13 +120,20 @@ typedef struct {
                           it (solve_form 1 gives FS_EUNSUPPORTED); eq. (9) is applied as the
                           Toeplitz matrix T_nu; no mode is excluded as grazing.  Only
                           fs_reconstruct and fs_reconstruct_host accept it.             */
-  int classify_single_pass; /* 1 (default): the norms of the modes, the discrepancy test and the
-                          active list in one cooperative launch whose blocks meet at two
-                          bounded device-side barriers (a wait that runs out is reported by
-                          fs_sync_status as FS_ETIMEOUT); used when the device holds the grid
-                          co-resident, else the three-kernel form is taken.  0: always the
-                          three-kernel form.  Results are identical up to the rounding of the
-                          sum ||W||^2 (its terms are grouped differently).                 */
+  int classify_single_pass; /* 0 (default): the norms of the modes, the discrepancy test and the
+                          active list in three kernels.  1: in one cooperative launch whose
+                          blocks meet at two bounded device-side barriers (a wait that runs
+                          out is reported by fs_sync_status as FS_ETIMEOUT); taken when the
+                          device holds the grid co-resident, else the three-kernel form.
+                          Fewer launches (batches); on one 128^2 problem the three kernels,
+                          overlapped by programmatic dependent launch, are faster (measured).
+                          Results are identical up to the rounding of the sum ||W||^2 (its
+                          terms are grouped differently).                                  */
+  int fft_tile;        /* tile shape of the transform passes, a tuning knob: 0 (default)
+                          shared-memory tiles of 2048 elements, 16 (FP32) / 8 (FP64) columns
+                          per column tile, radix cap 16; 1: tiles of 1024 elements, 8 / 4
+                          columns, radix cap 8 (twice the blocks, half the shared memory
+                          each).  Results are identical.                                 */
   const void* incident;  /* NULL (default): the incident field is the plane wave exp(-i k0 z).
                           Else device, [n_omega][M][N][N] complex in the working precision:
                           the incident field u0 on the X planes (for instance the point

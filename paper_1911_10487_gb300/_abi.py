@@ -37,7 +37,8 @@ class fs_options(C.Structure):
                 ("alpha_given", C.POINTER(C.c_double)), ("max_iter", C.c_int),
                 ("refine_iters", C.c_int), ("fp64_switch", C.c_double), ("stage_timing", C.c_int),
                 ("solve_blocks_per_sm", C.c_int), ("solve_form", C.c_int), ("regularizer", C.c_int),
-                ("kernel_plan", C.c_void_p), ("classify_single_pass", C.c_int), ("incident", C.c_void_p)]
+                ("kernel_plan", C.c_void_p), ("classify_single_pass", C.c_int), ("fft_tile", C.c_int),
+                ("incident", C.c_void_p)]
 
 
 STAGES = ("fft_x_forward", "fft_y_forward_norms", "classify", "solve", "ifft_y_gather", "ifft_x_recover")

@@ -172,6 +172,7 @@ fs_status validate_args(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, in
     if (o->solve_form != 0 && o->solve_form != 1) return fail(ctx, FS_EINVAL, "solve_form must be 0 or 1");
     if (o->classify_single_pass != 0 && o->classify_single_pass != 1)
       return fail(ctx, FS_EINVAL, "classify_single_pass must be 0 or 1");
+    if (o->fft_tile != 0 && o->fft_tile != 1) return fail(ctx, FS_EINVAL, "fft_tile must be 0 or 1");
     if (o->regularizer != 0 && o->regularizer != 1) return fail(ctx, FS_EINVAL, "regularizer must be 0 or 1");
     if (o->regularizer == 1 && o->solve_form != 1)
       return fail(ctx, FS_EUNSUPPORTED, "the truncated SVD is implemented in the rank-one form (solve_form 1)");
@@ -202,6 +203,7 @@ Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, dou
   P.sampled = o.kernel_plan ? 1 : 0;
   P.incident = o.incident ? 1 : 0;
   P.classify_single = o.classify_single_pass;
+  P.fft_tile = o.fft_tile;
   for (int k = 0; k < g->m1; ++k) P.zy[k] = g->zy[k];
   for (int j = 0; j < n_omega; ++j) {
     P.omega[j] = omega[j];
@@ -416,7 +418,8 @@ fs_status fs_default_options(fs_options* o) {
   o->regularizer = 0;
   o->kernel_plan = nullptr;
   o->incident = nullptr;
-  o->classify_single_pass = 1;
+  o->classify_single_pass = 0;
+  o->fft_tile = 0;
   return FS_OK;
 }
 
@@ -535,8 +538,8 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
   std::vector<unsigned char> key;
   if (graphable) {
     // values only (no struct padding, no pointers to argument arrays)
-    const int ints[12] = {g->n, g->m, g->m1, n_omega, (int)prec, o.alpha_mode, o.max_iter, o.refine_iters,
-                          o.solve_blocks_per_sm, o.solve_form, o.regularizer, 0};
+    const int ints[13] = {g->n, g->m, g->m1, n_omega, (int)prec, o.alpha_mode, o.max_iter, o.refine_iters,
+                          o.solve_blocks_per_sm, o.solve_form, o.regularizer, o.classify_single_pass, o.fft_tile};
     const double dbl[10] = {g->period, g->z1, g->z2, delta, c0, o.tau, o.delta_floor, o.alpha_rel, o.eps_u,
                             o.fp64_switch};
     key_put(key, ints);

@@ -53,6 +53,7 @@ struct Problem {
   int sampled;  // 1: the sampled-G kernel of a kernel plan (Work::ktab) replaces the Weyl form
   int incident; // 1: the incident field on X is given (Work::u0) instead of the plane wave
   int classify_single;  // 1: single-pass classification (one cooperative launch)
+  int fft_tile;         // tile shape of the transform passes (0 large, 1 small)
 };
 
 inline bool classify_fused_ok(const Problem& P) { return P.classify_single != 0; }

@@ -2,16 +2,22 @@
 
 For a batch signature (the sorted multiset of (N, M, M1, n_omega) and the
 precision) it times the candidate launch configurations -- the number of
-concurrent streams the batch is dealt over and the resident blocks per SM of the
-per-mode solve -- with CUDA events on the library's stream, and keeps the fastest.
-Results are cached in memory and, if a path is given, in a JSON file.
+concurrent streams the batch is dealt over, the resident blocks per SM of the
+per-mode solve, the tile shape of the transform passes (fs_options.fft_tile:
+2048-element tiles with radix cap 16, or 1024-element tiles with radix cap 8) and
+the form of the classification (fs_options.classify_single_pass: three kernels, or
+one cooperative launch) --
+with CUDA events on the library's stream, and keeps the fastest.  The signature
+ignores the plane heights and the noise level: they change neither the launch
+shapes nor the work per mode of the transforms.  Results are cached in memory and,
+if a path is given, in a JSON file.
 """
 from __future__ import annotations
 
 import json
 import os
 
-CANDIDATES = [(s, b) for s in (1, 2, 4, 8, 16) for b in (1, 2, 3)]
+CANDIDATES = [(s, b, t, c) for s in (1, 2, 4, 8, 16) for b in (1, 2, 3) for t in (0, 1) for c in (0, 1)]
 
 
 def signature(items, precision):
@@ -28,22 +34,24 @@ class BatchTuner:
                 self.cache = json.load(f)
 
     def best(self, rc, items, precision="mixed", repeats=3, outs=None):
-        """(n_streams, solve_blocks_per_sm) for this batch, timing it if unseen."""
+        """(n_streams, solve_blocks_per_sm, fft_tile, classify_single_pass) for this batch,
+        timing it if unseen."""
         import torch
         key = signature(items, precision)
         if key in self.cache:
             return tuple(self.cache[key]["config"])
         timings = {}
         with torch.cuda.stream(rc.stream):
-            for s, b in CANDIDATES:
-                rc.reconstruct_batch(items, precision, n_streams=s, outs=outs, solve_blocks_per_sm=b)  # warm
+            for s, b, t, c in CANDIDATES:
+                kw = dict(n_streams=s, outs=outs, solve_blocks_per_sm=b, fft_tile=t, classify_single_pass=c)
+                rc.reconstruct_batch(items, precision, **kw)  # warm
                 t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 t0.record(rc.stream)
                 for _ in range(repeats):
-                    rc.reconstruct_batch(items, precision, n_streams=s, outs=outs, solve_blocks_per_sm=b)
+                    rc.reconstruct_batch(items, precision, **kw)
                 t1.record(rc.stream)
                 t1.synchronize()
-                timings[f"{s},{b}"] = t0.elapsed_time(t1) / repeats
+                timings[f"{s},{b},{t},{c}"] = t0.elapsed_time(t1) / repeats
         best = min(timings, key=timings.get)
         cfg = tuple(int(x) for x in best.split(","))
         self.cache[key] = {"config": list(cfg), "ms": timings}

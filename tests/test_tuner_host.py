@@ -28,13 +28,16 @@ def test_cached_configuration_needs_no_timing(tmp_path):
     items = [_item(128, 32, 8, 2), _item(64, 16, 4, 1)]
     path = tmp_path / "tuner.json"
     key = signature(items, "mixed")
-    path.write_text(json.dumps({key: {"config": [8, 3], "ms": {"8,3": 1.0}}}))
+    path.write_text(json.dumps({key: {"config": [8, 3, 1, 0], "ms": {"8,3,1,0": 1.0}}}))
     t = BatchTuner(str(path))
-    assert t.best(_NoGPU(), items, "mixed") == (8, 3)
+    assert t.best(_NoGPU(), items, "mixed") == (8, 3, 1, 0)
     # a fresh tuner without the file has nothing cached
     assert key not in BatchTuner(None).cache
 
 
-def test_candidates_cover_streams_and_blocks_per_sm():
-    assert sorted({s for s, _ in CANDIDATES}) == [1, 2, 4, 8, 16]
-    assert sorted({b for _, b in CANDIDATES}) == [1, 2, 3]
+def test_candidates_cover_streams_blocks_per_sm_tiles_and_classification():
+    assert sorted({s for s, _, _, _ in CANDIDATES}) == [1, 2, 4, 8, 16]
+    assert sorted({b for _, b, _, _ in CANDIDATES}) == [1, 2, 3]
+    assert sorted({t for _, _, t, _ in CANDIDATES}) == [0, 1]
+    assert sorted({c for _, _, _, c in CANDIDATES}) == [0, 1]
+    assert len(CANDIDATES) == len(set(CANDIDATES)) == 60
