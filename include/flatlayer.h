@@ -283,6 +283,10 @@ typedef enum {
    restart.  Either way the data of eq. (7) follow from the converged field.  Each
    frequency is solved on its own.
      xi        device, [M][N][N] real (float64 for FS_FP64, float32 for FS_MIXED).
+     incident  device, [n_omega][M][N][N] complex: the incident field u0 on X (for
+               instance fs_incident_point_sources), whose U~0 = F_r[u0] starts
+               Algorithm 1 and enters each step; or NULL for the plane wave.  The
+               stopping rule then takes ||U~0|| of that field.
      omega     host, n_omega values > 0.
      max_iter  >= 0: iterations of Algorithm 1, or operator applications of GMRES (each
                method of FS_FIXED_POINT_GMRES gets max_iter); FS_FIXED_POINT with 0
@@ -300,8 +304,8 @@ typedef enum {
    stream at each stopping test and GMRES inner product, so it cannot be captured in a
    graph. */
 fs_status fs_forward(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* xi,
-                     const double* omega, int n_omega, double c0, fs_forward_method method, int max_iter,
-                     double rtol, void* W, void* u, int* iterations);
+                     const void* incident, const double* omega, int n_omega, double c0, fs_forward_method method,
+                     int max_iter, double rtol, void* W, void* u, int* iterations);
 
 /* Sampled-G kernel (Sec. 5: the discrete analogue of G~ computed from the values of G
    by the FFT), the alternative to the Weyl closed form.  For every frequency and mode

@@ -182,13 +182,14 @@ class Reconstructor:
         return W
 
     def forward(self, xi, omega, geom: Geometry, c0: float = 1.0, precision: str = "fp64", max_iter: int = 500,
-                rtol: float = None, want_u: bool = False, method: str = "fixed_point"):
+                rtol: float = None, want_u: bool = False, method: str = "fixed_point", incident=None):
         """Data W[n_omega, M1, N, N] of xi[M, N, N] with full scattering: method
         "fixed_point" (Algorithm 1, the fixed point of eq. 6, to ||U~_{n+1} - U~_n|| <=
         rtol ||U~0||), "gmres" (restarted GMRES to a relative residual rtol) or
         "fixed_point_gmres" (GMRES where Algorithm 1 fails); rtol defaults to 1e-13 in
         FP64 and 1e-6 in the mixed precision.  Returns (W, u or None, iterations per
-        frequency); raises FlatLayerError (FS_ENOCONV) when a frequency does not converge."""
+        frequency); raises FlatLayerError (FS_ENOCONV) when a frequency does not converge.  The
+        plane incident wave unless `incident` (u0[n_omega, M, N, N] on X) is given."""
         import torch
         prec = PRECISIONS[precision]
         rdt = torch.float64 if prec == FS_FP64 else torch.float32
@@ -201,8 +202,12 @@ class Reconstructor:
             rtol = 1e-13 if prec == FS_FP64 else 1e-6
         W = torch.empty((len(omega), geom.m1, geom.n, geom.n), dtype=cdt, device=self.device)
         u = torch.empty((len(omega), geom.m, geom.n, geom.n), dtype=cdt, device=self.device) if want_u else None
+        if incident is not None and (incident.dtype != cdt or tuple(incident.shape) != (len(omega), geom.m, geom.n, geom.n)
+                                     or not incident.is_contiguous()):
+            raise ValueError("incident must be a contiguous [n_omega, M, N, N] tensor of the working precision")
         its = fs_forward(self.ctx, geom.c_struct(), prec, xi.data_ptr(), omega, c0, FORWARD_METHODS[method], max_iter,
-                         rtol, W.data_ptr(), u.data_ptr() if u is not None else None)
+                         rtol, W.data_ptr(), u.data_ptr() if u is not None else None,
+                         incident.data_ptr() if incident is not None else None)
         return W, u, its
 
     def report(self) -> dict:

@@ -109,7 +109,7 @@ def lib():
         L.fs_incident_point_sources.restype = ip
         L.fs_incident_point_sources.argtypes = [vp, C.POINTER(fs_geometry), ip, dp, ip, dp, ip, C.c_double, vp]
         L.fs_forward.restype = ip
-        L.fs_forward.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, dp, ip, C.c_double, ip, ip, C.c_double, vp,
+        L.fs_forward.argtypes = [vp, C.POINTER(fs_geometry), ip, vp, vp, dp, ip, C.c_double, ip, ip, C.c_double, vp,
                                  vp, C.POINTER(C.c_int)]
         L.fs_reconstruct_batch.restype = ip
         L.fs_reconstruct_batch.argtypes = [vp, C.POINTER(fs_problem), ip, ip, C.POINTER(fs_options), ip]
@@ -230,13 +230,13 @@ FS_FIXED_POINT, FS_GMRES, FS_FIXED_POINT_GMRES = 0, 1, 2
 FORWARD_METHODS = {"fixed_point": FS_FIXED_POINT, "gmres": FS_GMRES, "fixed_point_gmres": FS_FIXED_POINT_GMRES}
 
 
-def fs_forward(ctx, geom, prec, xi_ptr, omega, c0, method, max_iter, rtol, W_ptr, u_ptr=None):
+def fs_forward(ctx, geom, prec, xi_ptr, omega, c0, method, max_iter, rtol, W_ptr, u_ptr=None, incident_ptr=None):
     """Returns the iterations each frequency took."""
     om = (C.c_double * len(omega))(*[float(x) for x in omega])
     its = (C.c_int * len(omega))()
-    st = lib().fs_forward(ctx, C.byref(geom), int(prec), C.c_void_p(xi_ptr), om, len(omega), float(c0),
-                          int(method), int(max_iter), float(rtol), C.c_void_p(W_ptr), C.c_void_p(u_ptr or None),
-                          its)
+    st = lib().fs_forward(ctx, C.byref(geom), int(prec), C.c_void_p(xi_ptr), C.c_void_p(incident_ptr or None), om,
+                          len(omega), float(c0), int(method), int(max_iter), float(rtol), C.c_void_p(W_ptr),
+                          C.c_void_p(u_ptr or None), its)
     _check(ctx, st, "fs_forward")
     return [int(x) for x in its]
 

@@ -711,9 +711,9 @@ fs_status fs_forward_born(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, 
   return e == cudaSuccess ? FS_OK : cuda_fail(ctx, e, "forward_born");
 }
 
-fs_status fs_forward(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const void* xi, const double* omega,
-                     int n_omega, double c0, fs_forward_method method, int max_iter, double rtol, void* W, void* u,
-                     int* iterations) {
+fs_status fs_forward(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const void* xi, const void* incident,
+                     const double* omega, int n_omega, double c0, fs_forward_method method, int max_iter, double rtol,
+                     void* W, void* u, int* iterations) {
   if (!ctx) return FS_EINVAL;
   fs_status st = validate_args(ctx, g, prec, n_omega, omega, 0.0, c0, nullptr, false);
   if (st != FS_OK) return st;
@@ -733,13 +733,13 @@ fs_status fs_forward(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const
   if (fp64) {
     const double2* tw = nullptr;
     if ((st = ensure_twiddles<double>(ctx, g->n, &tw)) != FS_OK) return st;
-    e = forward_solve<double>(P, (const double*)xi, (double2*)W, (double2*)u, ctx->ws, (int)method, rtol, max_iter,
-                              tw, ctx->stream, it.data(), conv.data());
+    e = forward_solve<double>(P, (const double*)xi, (const double2*)incident, (double2*)W, (double2*)u, ctx->ws,
+                              (int)method, rtol, max_iter, tw, ctx->stream, it.data(), conv.data());
   } else {
     const float2* tw = nullptr;
     if ((st = ensure_twiddles<float>(ctx, g->n, &tw)) != FS_OK) return st;
-    e = forward_solve<float>(P, (const float*)xi, (float2*)W, (float2*)u, ctx->ws, (int)method, rtol, max_iter, tw,
-                             ctx->stream, it.data(), conv.data());
+    e = forward_solve<float>(P, (const float*)xi, (const float2*)incident, (float2*)W, (float2*)u, ctx->ws,
+                             (int)method, rtol, max_iter, tw, ctx->stream, it.data(), conv.data());
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "forward");
   if (iterations)

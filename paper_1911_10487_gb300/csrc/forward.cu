@@ -196,10 +196,12 @@ __global__ void k_times_xi(long long count, const R* __restrict__ xi, cx<R>* __r
 // F_l = q F_{l-1} + V~_l, B_l = q (B_{l+1} + V~_{l+1}) (fbuf holds F).  One thread per mode.
 // STEP (a step of Algorithm 1): ut <- U~0 + gamma (F + B) and the block partial of
 // ||U~_{n+1} - U~_n||^2 in a fixed order; otherwise ut <- gamma (F + B).
+// u0t (STEP only, may be null): U~0 of a given incident field on every mode; null for the
+// plane wave, whose U~0 is N^2 exp(-i k0 z'_l) at nu = 0 alone
 template <typename R, bool STEP>
 __global__ void __launch_bounds__(FP_T)
 k_interior(Problem P, const cx<R>* __restrict__ vt, cx<R>* __restrict__ ut, cx<R>* __restrict__ fbuf,
-           double* __restrict__ partial) {
+           double* __restrict__ partial, const cx<R>* __restrict__ u0t) {
   __shared__ double red[FP_T];
   const int N = P.n, M = P.m;
   const long long N2 = (long long)N * N;
@@ -227,7 +229,9 @@ k_interior(Problem P, const cx<R>* __restrict__ vt, cx<R>* __restrict__ ut, cx<R
     cx<R> b = czero<R>();
     for (int l = M - 1; l >= 0; --l) {
       cx<R> un = gr * (fbuf[l * N2 + nu] + b);
-      if (STEP && nu == 0) {
+      if (STEP && u0t) {
+        un = un + u0t[l * N2 + nu];
+      } else if (STEP && nu == 0) {
         double s, c;
         sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s, &c);
         un = un + from_d<R>(make_double2(n2 * c, n2 * s));
@@ -349,8 +353,9 @@ template <typename R> struct FwdLayout {
   explicit FwdLayout(const Problem& P, void* ws) {
     N2 = (long long)P.n * P.n;
     MN2 = (long long)P.m * N2;
-    // fixed point: ut, fb, sc; GMRES: sc, tv, fb, x, u0, GM_RESTART + 1 Krylov vectors
-    const long long fp = 3 * MN2;
+    // fixed point: ut, fb, sc, U~0 of a given incident field; GMRES: sc, tv, fb, x, u0,
+    // GM_RESTART + 1 Krylov vectors
+    const long long fp = 4 * MN2;
     const long long gm = (6 + GM_RESTART) * MN2;
     vec_elems = fp > gm ? fp : gm;
     base = reinterpret_cast<cx<R>*>(ws);
@@ -373,22 +378,35 @@ Problem one_frequency(const Problem& P, int om) {
 
 // Algorithm 1 for one frequency; on convergence u (physical, M planes) is written to uo
 // (which may be the scratch sc).  The stopping test is taken on the host each iteration.
+// ||a||^2 of count complex values: block partials of k_dots summed on the host in a fixed order
 template <typename R>
-cudaError_t fixed_point_one(const Problem& Q, const R* xi, const FwdLayout<R>& L, const cx<R>* tw, double rtol,
-                            int max_iter, cudaStream_t s, cx<R>* uo_user, cx<R>** uo, int* iters, bool* conv) {
+cudaError_t norm2_host(const cx<R>* a, long long count, double2* partial, cudaStream_t s, double* out);
+
+template <typename R>
+cudaError_t fixed_point_one(const Problem& Q, const R* xi, const cx<R>* u0, const FwdLayout<R>& L, const cx<R>* tw,
+                            double rtol, int max_iter, cudaStream_t s, cx<R>* uo_user, cx<R>** uo, int* iters,
+                            bool* conv) {
   const long long N2 = L.N2, MN2 = L.MN2;
   cx<R>* ut = L.base;
   cx<R>* fb = ut + MN2;
   cx<R>* sc = fb + MN2;
+  cx<R>* u0t = u0 ? sc + MN2 : nullptr;  // U~0 of the given incident field
   double* partial = reinterpret_cast<double*>(L.reals());
   const int nblk = (int)((N2 + FP_T - 1) / FP_T);
   std::vector<double> host(nblk);
-  const double nrm0 = (double)N2 * sqrt((double)Q.m);  // ||U~0||: N^2 |e^{-i k0 z}| on M planes
+  double nrm0 = (double)N2 * sqrt((double)Q.m);  // ||U~0||: N^2 |e^{-i k0 z}| on M planes (plane wave)
   const unsigned gx = (unsigned)((MN2 + FP_T - 1) / FP_T < 4096 ? (MN2 + FP_T - 1) / FP_T : 4096);
-  cudaError_t e = cudaMemsetAsync(ut, 0, sizeof(cx<R>) * MN2, s);
-  if (e != cudaSuccess) return e;
-  k_incident<R><<<(Q.m + 63) / 64, 64, 0, s>>>(Q, ut);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaError_t e;
+  if (u0) {  // U~1 = U~0 = F_r[u0], and its norm for the stopping rule
+    if ((e = launch_fft2_dense<R>(const_cast<cx<R>*>(u0), u0t, Q.n, Q.m, false, tw, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(ut, u0t, sizeof(cx<R>) * MN2, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    if ((e = norm2_host<R>(u0t, MN2, L.reals(), s, &nrm0)) != cudaSuccess) return e;
+    nrm0 = sqrt(nrm0);
+  } else {
+    if ((e = cudaMemsetAsync(ut, 0, sizeof(cx<R>) * MN2, s)) != cudaSuccess) return e;
+    k_incident<R><<<(Q.m + 63) / 64, 64, 0, s>>>(Q, ut);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   int it = 0;
   bool ok = max_iter == 0;
   while (it < max_iter) {
@@ -398,7 +416,7 @@ cudaError_t fixed_point_one(const Problem& Q, const R* xi, const FwdLayout<R>& L
     if ((e = launch_fft2_dense<R>(sc, sc, Q.n, Q.m, true, tw, s)) != cudaSuccess) return e;
     k_times_xi<R><<<gx, FP_T, 0, s>>>(MN2, xi, sc);
     if ((e = launch_fft2_dense<R>(sc, sc, Q.n, Q.m, false, tw, s)) != cudaSuccess) return e;
-    k_interior<R, true><<<nblk, FP_T, 0, s>>>(Q, sc, ut, fb, partial);
+    k_interior<R, true><<<nblk, FP_T, 0, s>>>(Q, sc, ut, fb, partial, u0t);
     if ((e = cudaMemcpyAsync(host.data(), partial, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
       return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
@@ -435,7 +453,7 @@ template <typename R> struct Krylov {
     k_xi_times<R><<<gx, FP_T, 0, s>>>(MN2, xi, x, sc);
     cudaError_t e = launch_fft2_dense<R>(sc, sc, Q.n, Q.m, false, tw, s);
     if (e != cudaSuccess) return e;
-    k_interior<R, false><<<(unsigned)((N2 + FP_T - 1) / FP_T), FP_T, 0, s>>>(Q, sc, tv, fb, nullptr);
+    k_interior<R, false><<<(unsigned)((N2 + FP_T - 1) / FP_T), FP_T, 0, s>>>(Q, sc, tv, fb, nullptr, nullptr);
     if ((e = launch_fft2_dense<R>(tv, tv, Q.n, Q.m, true, tw, s)) != cudaSuccess) return e;
     k_sub<R><<<gx, FP_T, 0, s>>>(MN2, x, tv, y);
     return cudaGetLastError();
@@ -474,8 +492,22 @@ template <typename R> struct Krylov {
 // rotations, from x = 0, to ||u0 - A x|| <= rtol ||u0|| (the residual of each cycle's
 // start is computed, not estimated); iters counts the operator applications.
 template <typename R>
-cudaError_t gmres_one(const Problem& Q, const R* xi, const FwdLayout<R>& L, const cx<R>* tw, double rtol, int max_iter,
-                      cudaStream_t s, cx<R>** uo, int* iters, bool* conv) {
+cudaError_t norm2_host(const cx<R>* a, long long count, double2* partial, cudaStream_t s, double* out) {
+  k_dots<R><<<dim3(GM_BLOCKS, 1), FP_T, 0, s>>>(count, a, count, a, partial);
+  cudaError_t e = cudaGetLastError();
+  std::vector<double2> h(GM_BLOCKS);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), partial, sizeof(double2) * GM_BLOCKS, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  double t = 0.0;
+  for (int b = 0; b < GM_BLOCKS; ++b) t += h[b].x;
+  *out = t;
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t gmres_one(const Problem& Q, const R* xi, const cx<R>* u0, const FwdLayout<R>& L, const cx<R>* tw,
+                      double rtol, int max_iter, cudaStream_t s, cx<R>** uo, int* iters, bool* conv) {
   using cd = std::complex<double>;
   const long long N2 = L.N2, MN2 = L.MN2;
   Krylov<R> K{Q, xi, tw, s};
@@ -491,7 +523,11 @@ cudaError_t gmres_one(const Problem& Q, const R* xi, const FwdLayout<R>& L, cons
   K.partial = L.reals();
   K.coef = K.partial + (size_t)(GM_RESTART + 1) * GM_BLOCKS;
   cudaError_t e;
-  k_plane_wave<R><<<K.gx, FP_T, 0, s>>>(Q, bv);
+  if (u0) {
+    if ((e = cudaMemcpyAsync(bv, u0, sizeof(cx<R>) * MN2, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+  } else {
+    k_plane_wave<R><<<K.gx, FP_T, 0, s>>>(Q, bv);
+  }
   if ((e = cudaMemsetAsync(x, 0, sizeof(cx<R>) * MN2, s)) != cudaSuccess) return e;
   std::vector<cd> d;
   if ((e = K.dots(bv, 1, bv, d)) != cudaSuccess) return e;
@@ -579,8 +615,9 @@ size_t forward_bytes(const Problem& P) {
 }
 
 template <typename R>
-cudaError_t forward_solve(const Problem& P, const R* xi, cx<R>* W, cx<R>* u_out, void* ws, int method, double rtol,
-                          int max_iter, const cx<R>* tw, cudaStream_t s, int* iters, int* converged) {
+cudaError_t forward_solve(const Problem& P, const R* xi, const cx<R>* incident, cx<R>* W, cx<R>* u_out, void* ws,
+                          int method, double rtol, int max_iter, const cx<R>* tw, cudaStream_t s, int* iters,
+                          int* converged) {
   const FwdLayout<R> L(P, ws);
   const long long N2 = L.N2, MN2 = L.MN2;
   const unsigned gx = (unsigned)((MN2 + FP_T - 1) / FP_T < 4096 ? (MN2 + FP_T - 1) / FP_T : 4096);
@@ -591,12 +628,14 @@ cudaError_t forward_solve(const Problem& P, const R* xi, cx<R>* W, cx<R>* u_out,
     cx<R>* u = nullptr;
     int it = 0;
     bool conv = false;
+    const cx<R>* u0 = incident ? incident + (long long)om * MN2 : nullptr;
     if (method != 1) {  // Algorithm 1 (method 0, or the first try of method 2)
-      if ((e = fixed_point_one<R>(Q, xi, L, tw, rtol, max_iter, s, uo_user, &u, &it, &conv)) != cudaSuccess) return e;
+      if ((e = fixed_point_one<R>(Q, xi, u0, L, tw, rtol, max_iter, s, uo_user, &u, &it, &conv)) != cudaSuccess)
+        return e;
     }
     if (!conv && method != 0) {  // GMRES (method 1, or the fallback of method 2)
       int it2 = 0;
-      if ((e = gmres_one<R>(Q, xi, L, tw, rtol, max_iter, s, &u, &it2, &conv)) != cudaSuccess) return e;
+      if ((e = gmres_one<R>(Q, xi, u0, L, tw, rtol, max_iter, s, &u, &it2, &conv)) != cudaSuccess) return e;
       it += it2;
       if (conv && uo_user &&
           (e = cudaMemcpyAsync(uo_user, u, sizeof(cx<R>) * MN2, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
@@ -620,9 +659,9 @@ cudaError_t forward_solve(const Problem& P, const R* xi, cx<R>* W, cx<R>* u_out,
 
 template size_t forward_bytes<double>(const Problem&);
 template size_t forward_bytes<float>(const Problem&);
-template cudaError_t forward_solve<double>(const Problem&, const double*, double2*, double2*, void*, int, double, int,
-                                           const double2*, cudaStream_t, int*, int*);
-template cudaError_t forward_solve<float>(const Problem&, const float*, float2*, float2*, void*, int, double, int,
-                                          const float2*, cudaStream_t, int*, int*);
+template cudaError_t forward_solve<double>(const Problem&, const double*, const double2*, double2*, double2*, void*,
+                                           int, double, int, const double2*, cudaStream_t, int*, int*);
+template cudaError_t forward_solve<float>(const Problem&, const float*, const float2*, float2*, float2*, void*, int,
+                                          double, int, const float2*, cudaStream_t, int*, int*);
 
 }  // namespace fl

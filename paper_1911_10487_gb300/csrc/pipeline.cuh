@@ -227,9 +227,11 @@ cudaError_t launch_point_sources(const Problem& P, const double* spec, int n_src
 // Synchronises the stream at each stopping test and inner product.
 template <typename R>
 size_t forward_bytes(const Problem& P);
+// incident: u0 [n_omega][M][N][N] on X, or null for the plane wave
 template <typename R>
-cudaError_t forward_solve(const Problem& P, const R* xi, cx<R>* W, cx<R>* u_out, void* ws, int method, double rtol,
-                          int max_iter, const cx<R>* tw, cudaStream_t s, int* iters, int* converged);
+cudaError_t forward_solve(const Problem& P, const R* xi, const cx<R>* incident, cx<R>* W, cx<R>* u_out, void* ws,
+                          int method, double rtol, int max_iter, const cx<R>* tw, cudaStream_t s, int* iters,
+                          int* converged);
 
 bool fft_size_supported(int n);
 

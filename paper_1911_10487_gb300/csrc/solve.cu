@@ -51,8 +51,15 @@
 // boundaries of the first mode of block 0; it is compiled out otherwise.
 #ifdef FL_PHASE_TIMING
 __device__ long long g_phase[24];
+__device__ long long g_mode_cycles[4096];
+__device__ int g_mode_sweeps[4096];
 extern "C" int fs_debug_phases(long long* out) {
   return (int)cudaMemcpyFromSymbol(out, g_phase, sizeof(long long) * 24);
+}
+extern "C" int fs_debug_modes(long long* cycles, int* sweeps) {
+  int e = (int)cudaMemcpyFromSymbol(cycles, g_mode_cycles, sizeof(long long) * 4096);
+  if (e) return e;
+  return (int)cudaMemcpyFromSymbol(sweeps, g_mode_sweeps, sizeof(int) * 4096);
 }
 #define FL_MARK(i) \
   if (blockIdx.x == 0 && (threadIdx.x & 31) == 0 && item == 0) g_phase[i] = clock64()
@@ -1009,6 +1016,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     FL_MARK(0);
 #ifdef FL_PHASE_TIMING
     if (threadIdx.x == 0) S.tflag = blockIdx.x == 0 && item == 0;
+    const long long t_mode0 = clock64();
 #endif
     const int i2 = nu / N, i1 = nu - i2 * N;
     const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
@@ -1245,6 +1253,9 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         }
         if (!conv) conv = rel <= 1e-18f || (sweeps >= 2 && rel * rel <= 1e-18f * prev);
         if (threadIdx.x == 0) {
+#ifdef FL_PHASE_TIMING
+          if (item < 4096) g_mode_sweeps[item] = sweeps;
+#endif
           atomicAdd(ctr + C_REFINE_ITERS, (unsigned long long)sweeps);
           if (!conv) {
             S.fp64 = 1;
@@ -1353,6 +1364,9 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
     // cannot hold this mode's solution
     if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicAdd(ctr + C_NONFINITE, 1ull);
     FL_MARK(12);
+#ifdef FL_PHASE_TIMING
+    if (threadIdx.x == 0 && item < 4096) g_mode_cycles[item] = clock64() - t_mode0;
+#endif
   }
 }
 

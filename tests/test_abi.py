@@ -69,7 +69,8 @@ def test_forward_entry_points_reject_a_null_context_without_gpu(abi):
     g = abi.make_geometry(32, 16, 0.2, 1.0, [1.3])
     om = (C.c_double * 1)(1.0)
     its = (C.c_int * 1)()
-    st = abi.lib().fs_forward(None, C.byref(g), 0, None, om, 1, 1.0, abi.FS_FIXED_POINT, 10, 1e-13, None, None, its)
+    st = abi.lib().fs_forward(None, C.byref(g), 0, None, None, om, 1, 1.0, abi.FS_FIXED_POINT, 10, 1e-13, None, None,
+                              its)
     assert st == abi.FS_EINVAL
     st = abi.lib().fs_forward_born(None, C.byref(g), 0, None, None, om, 1, 1.0, None)
     assert st == abi.FS_EINVAL
