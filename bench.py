@@ -9,9 +9,10 @@ single-scattering forward kernel (synthetic; no dataset).
 A step = one full reconstruction W -> (xi, c): 2D FFT of the data planes, mode
 norms, discrepancy classification, per-mode Tikhonov solve + eq. (9), inverse FFTs
 and the pointwise xi/c recovery, replayed as one CUDA graph.  The headline is the
-mixed-precision path; the plain FP64 path is measured in the same run, and both
-again with the rank-one closed form of the per-mode problem (`rank1_form`).  L2 is
-flushed (256 MiB write) before every timed step.
+mixed-precision path with the rank-one closed form of the per-mode problem (exact
+for the Weyl kernel); the plain FP64 path is measured in the same run, and both
+again with the dense per-mode solve (`dense_form`).  L2 is flushed (256 MiB write)
+before every timed step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,11 +39,19 @@ WORKLOAD = "c2"
 DELTA = 0.01
 FLUSH_BYTES = 256 << 20
 STAGES = ("fft_x_forward", "fft_y_forward_norms", "classify", "solve", "ifft_y_gather", "ifft_x_recover")
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the mixed
-# per-mode solve on this workload, from one ncu capture of the current kernel; to be
-# measured again whenever that kernel changes
-SOLVE_DRAM_BYTES = 245504
-KERNELS_PER_STEP = 8  # rows FFT, columns FFT, mode norms, classify (flags, scatter), solve, gather+y-IFFT, x-IFFT+recover
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch on this workload,
+# from one ncu capture of the current kernels (None: not captured since the kernel
+# changed); to be measured again whenever a kernel changes
+SOLVE_DRAM_BYTES = None  # k_solve<float> (dense form, mixed)
+STAGE_DRAM_BYTES = {}
+STAGE_KERNELS = {"fft_x_forward": "k_fft2_plane<float>", "fft_y_forward_norms": "k_mode_norms<float>",
+                 "classify": "k_classify_flags + k_classify_scatter", "ifft_y_gather": "k_ifft_cols_gather<float>",
+                 "ifft_x_recover": "k_ifft_rows_recover<float>"}
+HEAD_FORM = 1  # the headline's per-mode solver: the rank-one closed form
+# kernels of one mixed step: 2D FFT (one pass), mode norms, classify (flags, scatter),
+# solve, gather + y-IFFT, x-IFFT + recover; the plain FP64 path transforms in two passes
+KERNELS_PER_STEP_MIXED = 7
+KERNELS_PER_STEP = 8
 
 
 def peaks():
@@ -152,8 +161,10 @@ def make_inputs(rc, wl, geom):
     return W
 
 
-def algorithmic_bytes(stage, wl, rep, sc):
-    """Bytes a stage must move at minimum (one launch), sc = bytes per complex."""
+def algorithmic_bytes(stage, wl, rep, sc, single=False):
+    """Bytes a stage must move at minimum (one launch), sc = bytes per complex; single:
+    the forward 2D transform in one pass (the mixed path), so that its first stage is the
+    whole transform and the second the mode norms alone."""
     F, N2, M, M1 = len(wl.omegas), wl.n * wl.n, wl.m, wl.m1
     sr = sc // 2
     act, cols = rep["n_active"], rep["n_columns"]
@@ -161,7 +172,7 @@ def algorithmic_bytes(stage, wl, rep, sc):
     if stage == "fft_x_forward":
         return 2 * data
     if stage == "fft_y_forward_norms":
-        return 2 * data + data + 8 * F * N2
+        return (0 if single else 2 * data) + data + 8 * F * N2
     if stage == "classify":
         return 8 * F * N2 + 4 * F * N2 + 4 * act
     if stage == "solve":
@@ -173,13 +184,16 @@ def algorithmic_bytes(stage, wl, rep, sc):
     raise KeyError(stage)
 
 
-def stage_flops(stage, wl, rep):
+def stage_flops(stage, wl, rep, single=False):
     """Real flops of a stage's transforms for one launch (5 L log2 L per complex line of
-    length L); the solve's count is solve_flops; classification does no flops."""
+    length L); the solve's count is solve_flops; classification does no flops.  single:
+    as in algorithmic_bytes."""
     F, N, M, M1 = len(wl.omegas), wl.n, wl.m, wl.m1
     line = 5.0 * N * np.log2(N)
-    if stage in ("fft_x_forward", "fft_y_forward_norms"):
-        return F * M1 * N * line
+    if stage == "fft_x_forward":
+        return (2 if single else 1) * F * M1 * N * line
+    if stage == "fft_y_forward_norms":
+        return 0.0 if single else F * M1 * N * line
     if stage == "ifft_y_gather":
         return F * 2 * M * rep["n_columns"] * line
     if stage == "ifft_x_recover":
@@ -202,6 +216,7 @@ def solve_flops(wl, rep, iters=8):
 def run_ours(args, rank, world, local):
     import torch
     from paper_1911_10487_gb300 import Geometry, Reconstructor, fs_reconstruct_host, FS_MIXED, build
+    from paper_1911_10487_gb300._abi import make_options
     from synth import workload
     build.build()
     wl = workload(WORKLOAD)
@@ -217,31 +232,25 @@ def run_ours(args, rank, world, local):
     outs = {}
     graphs = {}
     cases = (("mixed", W32, torch.float32), ("fp64", W64, torch.float64))
+    # the headline takes the rank-one closed form of the per-mode problem (solve_form 1,
+    # exact for the Weyl kernel); the dense form (solve_form 0) is measured beside it
+    forms = {"": HEAD_FORM, "_dense": 0}
     for prec, W, rdt in cases[::-1]:  # size the workspace (largest first) before any capture
-        xi = torch.empty((wl.m, wl.n, wl.n), dtype=rdt, device=rc.device)
-        outs[prec] = (xi, torch.empty_like(xi))
-        with torch.cuda.stream(stream):
-            rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, outs[prec][1], None))
-        torch.cuda.synchronize()
+        for tag, form in forms.items():
+            xi = torch.empty((wl.m, wl.n, wl.n), dtype=rdt, device=rc.device)
+            outs[prec + tag] = (xi, torch.empty_like(xi))
+            with torch.cuda.stream(stream):
+                rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, outs[prec + tag][1], None),
+                               solve_form=form)
+            torch.cuda.synchronize()
     for prec, W, rdt in cases:
-        xi, c = outs[prec]
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=stream):
-            rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, c, None))
-        torch.cuda.synchronize()
-        graphs[prec] = g
-    # the same step with the rank-one closed form of the per-mode problem (solve_form 1)
-    for prec, W, rdt in cases:
-        xi = torch.empty((wl.m, wl.n, wl.n), dtype=rdt, device=rc.device)
-        outs[prec + "_r1"] = (xi, torch.empty_like(xi))
-        with torch.cuda.stream(stream):
-            rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, outs[prec + "_r1"][1], None), solve_form=1)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=stream):
-            rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, outs[prec + "_r1"][1], None), solve_form=1)
-        torch.cuda.synchronize()
-        graphs[prec + "_r1"] = g
+        for tag, form in forms.items():
+            xi, c = outs[prec + tag]
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, c, None), solve_form=form)
+            torch.cuda.synchronize()
+            graphs[prec + tag] = g
 
     def timed(prec, K, Wm, clocks=None):
         g = graphs[prec]
@@ -275,23 +284,25 @@ def run_ours(args, rank, world, local):
     vox = wl.voxel_freqs
     value, ms_mixed = job_value(vox, ms_mixed, world)
     value_fp64, ms_fp64 = job_value(vox, ms_fp64, world)
-    ms_r1 = {p: max_over_ranks(timed(p + "_r1", args.steps, args.warmup)[0], world) for p in ("mixed", "fp64")}
+    ms_dense = {p: max_over_ranks(timed(p + "_dense", args.steps, args.warmup)[0], world) for p in ("mixed", "fp64")}
 
     # per-kernel durations (CUDA events recorded by the library between its kernels)
     stage_ms = {}
     reps = {}
     for prec, W in (("mixed", W32), ("fp64", W64)):
-        xi, c = outs[prec]
-        acc = np.zeros(6)
-        n = max(3, min(args.steps, 20))
-        for _ in range(n):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-                rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, c, None), stage_timing=1)
-            rep = rc.report()
-            acc += np.array([rep["ms_stage"][s] for s in STAGES])
-        stage_ms[prec] = dict(zip(STAGES, (acc / n).tolist()))
-        reps[prec] = rep
+        for tag, form in forms.items():
+            xi, c = outs[prec + tag]
+            acc = np.zeros(6)
+            n = max(3, min(args.steps, 20))
+            for _ in range(n):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                    rc.reconstruct(W, om, geom, DELTA, precision=prec, out=(xi, c, None), stage_timing=1,
+                                   solve_form=form)
+                rep = rc.report()
+                acc += np.array([rep["ms_stage"][s] for s in STAGES])
+            stage_ms[prec + tag] = dict(zip(STAGES, (acc / n).tolist()))
+            reps[prec + tag] = rep
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     W_h = W32.cpu().pin_memory()
@@ -299,8 +310,11 @@ def run_ours(args, rank, world, local):
     xi_h = torch.empty((wl.m, wl.n, wl.n), dtype=torch.float32).pin_memory()
     gstruct = geom.c_struct()
 
+    e2e_opts = make_options(solve_form=HEAD_FORM)
+
     def e2e_once():
-        fs_reconstruct_host(rc.ctx, gstruct, FS_MIXED, W_h.data_ptr(), om, DELTA, 1.0, None, xi_h.data_ptr(), None)
+        fs_reconstruct_host(rc.ctx, gstruct, FS_MIXED, W_h.data_ptr(), om, DELTA, 1.0, e2e_opts, xi_h.data_ptr(),
+                            None)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -320,14 +334,20 @@ def run_ours(args, rank, world, local):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "128x128x64 X grid, 32 data planes, k0=8pi, 3 Gaussian inclusions, 1% noise",
                    "n": wl.n, "m": wl.m, "m1": wl.m1, "n_omega": len(om), "delta": DELTA,
-                   "precision": "mixed (FP32 FFT/assembly/reduction, FP64 root-find + refinement)",
+                   "precision": "mixed (FP32 transforms and kernel factors, FP64 scalars, sums and eq. (9))",
+                   "solve_form": "rank-one closed form of the per-mode Tikhonov problem (exact for the Weyl "
+                                 "kernel; the dense form is reported under dense_form)",
                    "cuda_graph": True, "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
-        "fp64_path": {"value": value_fp64, "ms_per_step": ms_fp64, "dtype": "f64"},
-        "rank1_form": {p: {"value": world * wl.voxel_freqs / (ms_r1[p] * 1e-3), "ms_per_step": ms_r1[p]}
+        "gpu_launches": KERNELS_PER_STEP_MIXED * args.steps,
+        "fp64_path": {"value": value_fp64, "ms_per_step": ms_fp64, "dtype": "f64",
+                      "stage_ms": stage_ms["fp64"]},
+        "dense_form": {p: {"value": world * wl.voxel_freqs / (ms_dense[p] * 1e-3), "ms_per_step": ms_dense[p],
+                           "stage_ms": stage_ms[p + "_dense"],
+                           "n_refine_iters": reps[p + "_dense"]["n_refine_iters"],
+                           "n_fp64_fallback": reps[p + "_dense"]["n_fp64_fallback"]}
                        for p in ("mixed", "fp64")},
-        "stage_ms": stage_ms,
+        "stage_ms": stage_ms["mixed"],
         "e2e": {"value": world * vox / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(W_h.numel() * 8), "d2h_bytes_per_step": int(xi_h.numel() * 4)},
         "clocks": ck,
@@ -343,8 +363,10 @@ def run_ours(args, rank, world, local):
     for prec, sc, pk in (("mixed", 8, alu["fp32_tflops"]), ("fp64", 16, alu["fp64_tflops"])):
         stage_roof[prec] = {}
         for stg, ms in stage_ms[prec].items():
-            byt = algorithmic_bytes(stg, wl, reps[prec], sc)
-            fl = stage_flops(stg, wl, reps[prec])
+            if stg == "solve":
+                continue  # a latency-bound chain per mode: no stream of bytes or flops to rate
+            byt = algorithmic_bytes(stg, wl, reps[prec], sc, prec == "mixed")
+            fl = stage_flops(stg, wl, reps[prec], prec == "mixed")
             gbs = byt / (ms * 1e-3) / 1e9
             tfl = fl / (ms * 1e-3) / 1e12
             stage_roof[prec][stg] = {"ms": ms, "bytes": byt, "gbs": gbs, "hbm_frac": gbs / hbm, "flops": fl,
@@ -354,24 +376,28 @@ def run_ours(args, rank, world, local):
                                           "alu_source": "measured (fs_measure_alu_peaks)"},
                                 "note": "stage times from the library's event timers, launch gaps included",
                                 **stage_roof}
-    # roofline of the dominant kernel of the headline (mixed) path
-    sm = stage_ms["mixed"]
+    # roofline of the dominant kernel of the headline (mixed) path: the transform pass
+    # with the largest time, against the measured copy bandwidth (its algorithmic bytes:
+    # what it must read and write once)
+    sm = {k: v for k, v in stage_ms["mixed"].items() if k != "solve"}
     dom = max(sm, key=sm.get)
-    if dom == "solve":
-        # per-mode dense solve: bound by the plain ALUs (FP32 pipe in the mixed path);
-        # peak = the library's own FP32 FMA microbenchmark on this GPU
-        flops = solve_flops(wl, reps["mixed"])
-        ach = flops / (sm[dom] * 1e-3) / 1e12
-        result["roofline"] = {"kernel": "solve", "bound": "alu", "achieved": ach, "peak": alu["fp32_tflops"],
-                              "unit": "TFLOP/s", "frac": ach / alu["fp32_tflops"], "traffic": SOLVE_DRAM_BYTES,
-                              "peak_source": "measured (fs_measure_alu_peaks, FP32 FMA)",
-                              "algorithmic_flops": flops, "fp64_peak_tflops": alu["fp64_tflops"]}
-    else:
-        byt = algorithmic_bytes(dom, wl, reps["mixed"], 8)
-        ach = byt / (sm[dom] * 1e-3) / 1e9
-        result["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                              "frac": ach / hbm, "traffic": None, "peak_source": src,
-                              "algorithmic_bytes": byt}
+    byt = algorithmic_bytes(dom, wl, reps["mixed"], 8, True)
+    ach = byt / (sm[dom] * 1e-3) / 1e9
+    result["roofline"] = {"kernel": STAGE_KERNELS[dom], "stage": dom, "bound": "hbm", "achieved": ach, "peak": hbm,
+                          "unit": "GB/s", "frac": ach / hbm, "traffic": STAGE_DRAM_BYTES.get(dom), "peak_source": src,
+                          "algorithmic_bytes": byt,
+                          "note": "the rank-one solve (" + f"{stage_ms['mixed']['solve'] * 1e3:.1f}" +
+                                  " us) is a per-mode latency chain of O(M + M1) work"}
+    # the dense per-mode solve: bound by the plain ALUs (the FP32 pipe in the mixed
+    # path); peak = the library's own FP32 FMA microbenchmark on this GPU
+    flops = solve_flops(wl, reps["mixed_dense"])
+    t_solve = stage_ms["mixed_dense"]["solve"]
+    ach = flops / (t_solve * 1e-3) / 1e12
+    result["dense_form"]["mixed"]["roofline"] = {
+        "kernel": "k_solve<float>", "bound": "alu", "achieved": ach, "peak": alu["fp32_tflops"], "unit": "TFLOP/s",
+        "frac": ach / alu["fp32_tflops"], "traffic": SOLVE_DRAM_BYTES,
+        "peak_source": "measured (fs_measure_alu_peaks, FP32 FMA)", "algorithmic_flops": flops,
+        "fp64_peak_tflops": alu["fp64_tflops"]}
     result["counts"] = {k: v for k, v in reps["mixed"].items() if k != "ms_stage"}
     return result, rc, wl, geom, om, W64, outs
 
@@ -456,11 +482,12 @@ def run_batch(args, local, flush, world):
     res = {}
     cfgs = {}
     for prec in ("fp64", "mixed"):  # FP64 first: it sizes the workspace for both
-        cfgs[prec] = tuner.best(rc, items[prec], prec, repeats=2, outs=outs[prec])
+        cfgs[prec] = tuner.best(rc, items[prec], prec, repeats=2, outs=outs[prec], options={"solve_form": HEAD_FORM})
     graphs = {}
     for prec in ("fp64", "mixed"):
         s_, b_, t_, c_ = cfgs[prec]
-        kw = dict(n_streams=s_, outs=outs[prec], solve_blocks_per_sm=b_, fft_tile=t_, classify_single_pass=c_)
+        kw = dict(n_streams=s_, outs=outs[prec], solve_blocks_per_sm=b_, fft_tile=t_, classify_single_pass=c_,
+                  solve_form=HEAD_FORM)
         with torch.cuda.stream(stream):
             rc.reconstruct_batch(items[prec], prec, **kw)
         torch.cuda.synchronize()
@@ -497,7 +524,8 @@ def run_batch(args, local, flush, world):
         gbs = byt / (ms * 1e-3) / 1e9
         res[prec] = {"value": world * vox / (ms * 1e-3), "ms_per_step": ms,
                      "tuned": {"n_streams": cfgs[prec][0], "solve_blocks_per_sm": cfgs[prec][1],
-                               "fft_tile": cfgs[prec][2], "classify_single_pass": cfgs[prec][3]},
+                               "fft_tile": cfgs[prec][2], "classify_single_pass": cfgs[prec][3],
+                               "solve_form": HEAD_FORM},
                      "roofline": {"bound": "hbm", "compulsory_bytes": byt, "achieved": gbs, "peak": hbm,
                                   "unit": "GB/s", "frac": gbs / hbm, "peak_source": src,
                                   "note": "W read once, xi and c written once per problem"}}
@@ -510,7 +538,7 @@ def run_batch(args, local, flush, world):
            "voxel_freqs": vox, "steps": K, "cuda_graph": True, "unit": UNIT,
            "l2": "flushed (256 MiB write) before every timed step",
            "mixed": res["mixed"], "fp64": res["fp64"],
-           "gpu_launches_per_step": KERNELS_PER_STEP * len(wls)}
+           "gpu_launches_per_step": KERNELS_PER_STEP_MIXED * len(wls)}
     # smallest problem of the batch against the oracle (a parity spot check at full batch)
     j = min(range(len(wls)), key=lambda i: wls[i].voxel_freqs * wls[i].m1)
     out["spot_problem"] = wls[j].name
@@ -703,6 +731,7 @@ def run_paper(args, local, flush, world):
     time of one reconstruction (CUDA graph) and Delta_L2(z) against the true xi."""
     import torch
     from paper_1911_10487_gb300 import Geometry, Reconstructor
+    from paper_1911_10487_gb300._abi import FS_MIXED_MIN_NOISE
     from synth import paper_workload
     stream = torch.cuda.Stream()
     rc = Reconstructor(local, stream=stream)
@@ -726,6 +755,10 @@ def run_paper(args, local, flush, world):
                     W[j] += delta * torch.linalg.vector_norm(W0[j]) * nz[j] / torch.linalg.vector_norm(nz[j])
             entry = {}
             for prec in ("fp64", "mixed"):
+                if prec == "mixed" and max(delta, 1e-10) < FS_MIXED_MIN_NOISE:
+                    entry[prec] = {"unsupported": f"noise level below the mixed path's FP32 data resolution "
+                                                  f"(FS_MIXED_MIN_NOISE = {FS_MIXED_MIN_NOISE:g}): FS_FP64 only"}
+                    continue
                 cdt = torch.complex128 if prec == "fp64" else torch.complex64
                 rdt = torch.float64 if prec == "fp64" else torch.float32
                 Wp, up = W.to(cdt), u0.to(cdt)
@@ -827,8 +860,8 @@ def main():
                 **{k: {"min": float(np.nanmin(v)), "median": float(np.nanmedian(v)), "max": float(np.nanmax(v)),
                        "per_plane": [round(float(x), 6) for x in v]} for k, v in dz.items()}}
             for p in ("mixed", "fp64"):
-                result["rank1_form"][p]["rel_err_vs_oracle"] = rel_l2(outs[p + "_r1"][0].double().cpu().numpy(),
-                                                                     ref.xi)
+                result["dense_form"][p]["rel_err_vs_oracle"] = rel_l2(
+                    outs[p + "_dense"][0].double().cpu().numpy(), ref.xi)
             if sampled_check is not None:
                 from oracle import inverse
                 from oracle.grid import Geometry as OG

@@ -70,6 +70,15 @@ typedef enum {
                   W complex64 in, xi/c float32 out                                  */
 } fs_precision;
 
+/* Smallest noise level max(delta, delta_floor) the FS_MIXED reconstruction accepts
+   when alpha comes from the discrepancy principle: the FP32 transform of W rounds
+   each mode to about 1e-7 of ||W||, and the test ||b|| <= delta_nu needs delta_nu well
+   above that.  Below it (the paper's noise levels 0 and 1e-7 of Sec. 5 with a small
+   delta_floor) fs_reconstruct returns FS_EUNSUPPORTED: FS_FP64 is the path for such
+   data.  Given alpha (alpha_mode 1) and the truncated SVD (whose route transforms W
+   in FP64) are not limited. */
+#define FS_MIXED_MIN_NOISE 1e-6
+
 /* Limits of this build: N in {8,12,16,24,32,48,64,96,128,192,256}; 1 <= M <= 128;
    1 <= M1 <= 128; 1 <= n_omega <= 64.  The dense per-mode solve (solve_form 0, the
    default; the sampled kernel; the derivatives of flatlayer_diff.h) holds A_nu in
@@ -133,7 +142,25 @@ typedef struct {
                           shared-memory tiles of 2048 elements, 16 (FP32) / 8 (FP64) columns
                           per column tile, radix cap 16; 1: tiles of 1024 elements, 8 / 4
                           columns, radix cap 8 (twice the blocks, half the shared memory
-                          each).  Results are identical.                                 */
+                          each).  Applies to the two-pass transforms.  Results agree to
+                          rounding.                                                      */
+  int forward_single_pass; /* FS_MIXED: 1 (default): the forward 2D transform of W in one pass,
+                          a cluster of CTAs per data plane exchanging rows and columns
+                          through distributed shared memory; 0: two passes (rows, then
+                          columns) through global memory.  FS_FP64 always takes the two
+                          passes.  The results agree to rounding.                       */
+  int inverse_single_pass; /* FS_MIXED, N <= 128 except 96: 1: the inverse transform along y,
+                          along x and the recovery of xi and c in one pass, a cluster of
+                          CTAs per X plane (the transformed active columns go to the CTAs
+                          that own their rows through distributed shared memory); 0
+                          (default, measured faster on one 128^2 problem): two passes (the
+                          column pass writes the transformed active columns to global
+                          memory, the row pass reads them).  FS_FP64 always takes the two
+                          passes.  The results agree to rounding.                       */
+  int fp64_sums;        /* FS_MIXED: the least-squares sums of Sec. 5.2 (step 3 of Algorithm 2)
+                          over the frequencies: 0 (default) in FP32, redone in FP64 for the
+                          rows where they overflow; 1: in FP64 from the start.  FS_FP64
+                          always sums in FP64.                                          */
   const void* incident;  /* NULL (default): the incident field is the plane wave exp(-i k0 z).
                           Else device, [n_omega][M][N][N] complex in the working precision:
                           the incident field u0 on the X planes (for instance the point

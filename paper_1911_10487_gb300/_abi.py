@@ -14,6 +14,7 @@ _lib = None
 
 FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED, FS_ENOCONV, FS_ENONFINITE, FS_ETIMEOUT = range(8)
 FS_FP64, FS_MIXED = 0, 1
+FS_MIXED_MIN_NOISE = 1e-6  # include/flatlayer.h: smallest max(delta, delta_floor) of a mixed reconstruction
 STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_EUNSUPPORTED", 5: "FS_ENOCONV",
                 6: "FS_ENONFINITE", 7: "FS_ETIMEOUT"}
 
@@ -38,7 +39,8 @@ class fs_options(C.Structure):
                 ("refine_iters", C.c_int), ("fp64_switch", C.c_double), ("stage_timing", C.c_int),
                 ("solve_blocks_per_sm", C.c_int), ("solve_form", C.c_int), ("regularizer", C.c_int),
                 ("kernel_plan", C.c_void_p), ("classify_single_pass", C.c_int), ("fft_tile", C.c_int),
-                ("incident", C.c_void_p)]
+                ("forward_single_pass", C.c_int), ("inverse_single_pass", C.c_int),
+                ("fp64_sums", C.c_int), ("incident", C.c_void_p)]
 
 
 STAGES = ("fft_x_forward", "fft_y_forward_norms", "classify", "solve", "ifft_y_gather", "ifft_x_recover")
@@ -312,7 +314,10 @@ def make_geometry(n, m, z1, z2, zy, period=2.0):
 def make_options(**kw) -> fs_options:
     """Defaults of fs_default_options, overridden by keyword (alpha_given: sequence)."""
     o = fs_default_options()
+    known = {name for name, _ in fs_options._fields_}
     for k, v in kw.items():
+        if k not in known:
+            raise TypeError(f"unknown fs_options field {k!r}")
         if k == "alpha_given":
             arr = (C.c_double * len(v))(*[float(x) for x in v])
             o.alpha_given = C.cast(arr, C.POINTER(C.c_double))

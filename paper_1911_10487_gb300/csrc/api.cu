@@ -173,11 +173,20 @@ fs_status validate_args(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, in
     if (o->classify_single_pass != 0 && o->classify_single_pass != 1)
       return fail(ctx, FS_EINVAL, "classify_single_pass must be 0 or 1");
     if (o->fft_tile != 0 && o->fft_tile != 1) return fail(ctx, FS_EINVAL, "fft_tile must be 0 or 1");
+    if ((o->forward_single_pass != 0 && o->forward_single_pass != 1) ||
+        (o->inverse_single_pass != 0 && o->inverse_single_pass != 1) || (o->fp64_sums != 0 && o->fp64_sums != 1))
+      return fail(ctx, FS_EINVAL, "forward_single_pass, inverse_single_pass and fp64_sums must be 0 or 1");
     if (o->regularizer != 0 && o->regularizer != 1) return fail(ctx, FS_EINVAL, "regularizer must be 0 or 1");
     if (o->regularizer == 1 && o->solve_form != 1)
       return fail(ctx, FS_EUNSUPPORTED, "the truncated SVD is implemented in the rank-one form (solve_form 1)");
     if (o->regularizer == 1 && o->alpha_mode != 0)
       return fail(ctx, FS_EINVAL, "the truncated SVD takes no alpha (alpha_mode must be 0)");
+    if (dense_solve && prec == FS_MIXED && o->alpha_mode == 0 && o->regularizer == 0 &&
+        !(delta >= FS_MIXED_MIN_NOISE || o->delta_floor >= FS_MIXED_MIN_NOISE))
+      return fail(ctx, FS_EUNSUPPORTED,
+                  "the mixed path transforms W in FP32: its discrepancy test resolves noise levels down to %g "
+                  "(delta=%g, delta_floor=%g); take FS_FP64",
+                  FS_MIXED_MIN_NOISE, delta, o->delta_floor);
     if (o->kernel_plan) {
       if (!kernel_plan_matches(o->kernel_plan, g, prec, omega, n_omega, c0))
         return fail(ctx, FS_EINVAL, "the kernel plan was made for another geometry, precision, frequency list or c0");
@@ -204,6 +213,9 @@ Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, dou
   P.incident = o.incident ? 1 : 0;
   P.classify_single = o.classify_single_pass;
   P.fft_tile = o.fft_tile;
+  P.forward_single = o.forward_single_pass;
+  P.inverse_single = o.inverse_single_pass;
+  P.sums64 = o.fp64_sums;
   for (int k = 0; k < g->m1; ++k) P.zy[k] = g->zy[k];
   for (int j = 0; j < n_omega; ++j) {
     P.omega[j] = omega[j];
@@ -314,13 +326,15 @@ int sm_count() {
   return v;
 }
 
-cudaError_t opt_in_smem(SmemOptIn& flag, const void* kernel, size_t bytes) {
+cudaError_t opt_in_smem(SmemOptIn& flag, const void* kernel, size_t bytes, bool max_shared) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const unsigned long long bit = (dev >= 0 && dev < MAX_DEVICES) ? 1ull << dev : 0ull;
   if (bit && (flag.done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && max_shared)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess && bit) flag.done.fetch_or(bit, std::memory_order_acq_rel);
   return e;
 }
@@ -420,6 +434,9 @@ fs_status fs_default_options(fs_options* o) {
   o->incident = nullptr;
   o->classify_single_pass = 0;
   o->fft_tile = 0;
+  o->forward_single_pass = 1;
+  o->inverse_single_pass = 0;
+  o->fp64_sums = 0;
   return FS_OK;
 }
 
@@ -538,8 +555,9 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
   std::vector<unsigned char> key;
   if (graphable) {
     // values only (no struct padding, no pointers to argument arrays)
-    const int ints[13] = {g->n, g->m, g->m1, n_omega, (int)prec, o.alpha_mode, o.max_iter, o.refine_iters,
-                          o.solve_blocks_per_sm, o.solve_form, o.regularizer, o.classify_single_pass, o.fft_tile};
+    const int ints[16] = {g->n, g->m, g->m1, n_omega, (int)prec, o.alpha_mode, o.max_iter, o.refine_iters,
+                          o.solve_blocks_per_sm, o.solve_form, o.regularizer, o.classify_single_pass, o.fft_tile,
+                          o.forward_single_pass, o.inverse_single_pass, o.fp64_sums};
     const double dbl[10] = {g->period, g->z1, g->z2, delta, c0, o.tau, o.delta_floor, o.alpha_rel, o.eps_u,
                             o.fp64_switch};
     key_put(key, ints);

@@ -27,6 +27,96 @@ __global__ void k_twiddles(cx<R>* tw, int n) {
   }
 }
 
+// ---- single-pass forward 2D transform: one data plane per cluster ------------------
+// grid (C, planes), clusters of C = plane_cluster<N>() CTAs along x.  CTA r of the
+// cluster of plane p loads rows r RB .. r RB + RB - 1 (RB = N / C) of the plane into
+// its shared memory and transforms them along x; after a cluster barrier it reads
+// columns r RB .. r RB + RB - 1 of all N rows from the CTAs that hold them
+// (distributed shared memory), transforms them along y and writes them to W~.  The
+// plane crosses global memory once each way, in one launch.
+// clear (may be null): nclear counters zeroed by CTA (0, 0), as in k_fft_cols.
+template <typename R, int N> __host__ __device__ constexpr size_t plane_fwd_smem() {
+  constexpr int RB = N / plane_cluster<N>();
+  return sizeof(cx<R>) * ((size_t)LayIdx<Lay::ROW, N, RB, 16>::ELEMS + (size_t)RB * N + N);
+}
+
+template <typename R, int N>
+__global__ void __launch_bounds__(THREADS)
+k_fft2_plane(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, const cx<R>* __restrict__ tw,
+             unsigned* __restrict__ clear, int nclear) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int C = plane_cluster<N>(), RB = N / C;
+  using IA = LayIdx<Lay::ROW, N, RB, 16>;  // this CTA's rows
+  constexpr int E = RB * N;                // elements of the row tile and of the column tile
+  constexpr int PER = (E + THREADS - 1) / THREADS;
+  extern __shared__ __align__(16) unsigned char plane_smem[];
+  cx<R>* rows = reinterpret_cast<cx<R>*>(plane_smem);
+  cx<R>* colt = rows + IA::ELEMS;  // column tile: element i of column b at i RB + b
+  cx<R>* tw_s = colt + E;
+  const unsigned r = cluster_rank();
+  if (clear && blockIdx.x == 0 && blockIdx.y == 0)
+    for (int i = threadIdx.x; i < nclear; i += THREADS) clear[i] = 0u;
+  load_twiddles<R, N>(tw_s, tw);
+  const long long pb = (long long)blockIdx.y * N * N;
+  const cx<R>* src = in + pb + (long long)r * E;
+  cx<R> v[PER];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * THREADS;
+    if (E % THREADS == 0 || e < E) v[p] = src[e];
+  }
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * THREADS;
+    if (E % THREADS == 0 || e < E) rows[IA::at(e / N, e % N)] = v[p];
+  }
+  __syncthreads();
+  fft_lines<R, N, false, RB, THREADS, Lay::ROW, 16, 16>(rows, tw_s);
+  cluster_sync();  // every CTA's rows are transformed
+  // row i of column r RB + b sits in row i % RB of CTA i / RB: all loads first, then
+  // the stores, so that the remote loads overlap
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * THREADS;
+    if (E % THREADS == 0 || e < E) {
+      const int i = e / RB, b = e - (e / RB) * RB;
+      v[p] = dsmem_ld(dsmem_addr(rows + IA::at(i % RB, (int)r * RB + b), (unsigned)(i / RB)), v[p]);
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * THREADS;
+    if (E % THREADS == 0 || e < E) colt[e] = v[p];
+  }
+  cluster_arrive();  // this CTA has read the others' rows
+  __syncthreads();
+  fft_lines<R, N, false, RB, THREADS, Lay::COL, 16>(colt, tw_s);
+  cx<R>* dst = out + pb + (long long)r * RB;
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * THREADS;
+    if (E % THREADS == 0 || e < E) dst[(long long)(e / RB) * N + e % RB] = colt[e];
+  }
+  cluster_wait();  // no CTA leaves while another may still read its rows
+}
+
+template <typename R, int N>
+cudaError_t fwd_plane(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStream_t s, cudaEvent_t mid,
+                      bool norms) {
+  constexpr size_t smem = plane_fwd_smem<R, N>();
+  static SmemOptIn attr;
+  cudaError_t e = opt_in_smem(attr, (const void*)k_fft2_plane<R, N>, smem, true);
+  if (e != cudaSuccess) return e;
+  constexpr int C = plane_cluster<N>();
+  e = launch_pdl_cluster(k_fft2_plane<R, N>, dim3(C, (unsigned)(P.n_omega * P.m1)), dim3(THREADS), C, smem, s, W,
+                         w.wt, (const cx<R>*)w.tw, norms ? (unsigned*)nullptr : w.bar, P.n_omega);
+  if (e != cudaSuccess) return e;
+  if (mid) cudaEventRecord(mid, s);
+  if (!norms) return cudaGetLastError();
+  return launch_mode_norms<R>(P, w, s);
+}
+
 // W (complex64) -> W~ (complex128 in w.wt64) and the norms: the forward transform
 // of the mixed truncated-SVD route, in FP64
 template <int N>
@@ -72,6 +162,7 @@ cudaError_t fwd_impl(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStr
                      bool norms) {
   if constexpr (std::is_same<R, float>::value) {
     if (w.wt64) return fwd_wide_impl<N>(W, P, w, s, mid);
+    if (P.forward_single) return fwd_plane<R, N>(W, P, w, s, mid, norms);
   }
   return P.fft_tile == 1 ? fwd_tiled<R, N, 1>(W, P, w, s, mid, norms) : fwd_tiled<R, N, 0>(W, P, w, s, mid, norms);
 }

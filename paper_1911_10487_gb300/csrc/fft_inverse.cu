@@ -155,37 +155,14 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
   return __syncthreads_or(bad) != 0;
 }
 
-// INC: u0 (the incident field on X) is given and added to u; otherwise the transform
-// already holds the plane wave
-template <typename R, int N, bool INC, int T>
-__global__ void __launch_bounds__(THREADS)
-k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restrict__ cols,
-                    const int* __restrict__ ncol, const cx<R>* __restrict__ u0, R* __restrict__ xi,
-                    R* __restrict__ cout, unsigned long long* __restrict__ ctr, const cx<R>* __restrict__ tw) {
-  pdl_wait();
-  pdl_trigger();
-  constexpr int LINES = row_lines<N, T>() / 2 > 0 ? row_lines<N, T>() / 2 : 1;
-  constexpr int E = LINES * N;            // elements of one field
-  constexpr int PER = (E + THREADS - 1) / THREADS;
-  __shared__ cx<R> buf[LayIdx<Lay::ROW, N, 2 * LINES, Tile<T>::SKEW_RECOVER>::ELEMS];
-  __shared__ cx<R> tw_s[N];
-  __shared__ unsigned red[THREADS / 32];
-  load_twiddles<R, N>(tw_s, tw);
-  const long long nrows = (long long)P.m * N;
-  const long long row0 = (long long)blockIdx.x * LINES;
-  R num[PER], den[PER];
-  if (recover_pass<R, N, R, INC, T>(P, t2, cols, ncol, u0, buf, tw_s, num, den)) {
-    // the sums left the range of R (|u| |V| beyond FP32 for huge evanescent
-    // profiles): redo this block with FP64 sums; xi itself is in range
-    double nd[PER], dd[PER];
-    recover_pass<R, N, double, INC, T>(P, t2, cols, ncol, u0, buf, tw_s, nd, dd);
-#pragma unroll
-    for (int p = 0; p < PER; ++p) {
-      const bool g = !(dd[p] >= (double)P.n_omega * P.eps_u * P.eps_u);
-      num[p] = g ? R(0) : R(nd[p] / dd[p]);
-      den[p] = g ? R(0) : R(1);
-    }
-  }
+// xi and c of the elements e = threadIdx.x + p THREADS < E of rows row0 + e / N (below
+// nrows) from the least-squares sums, and the counters of guarded, NaN-c and non-finite
+// voxels (almost always zero, so one barrier decides)
+template <typename R, int PER, int N>
+__device__ __forceinline__ void recover_epilogue(const Problem& P, const R* num, const R* den, long long row0,
+                                                 long long nrows, int E, R* __restrict__ xi,
+                                                 R* __restrict__ cout, unsigned long long* __restrict__ ctr,
+                                                 unsigned* red) {
   const R guard = R(P.u_guard);  // host-derived: no FP64 division on the device
   const R inv_c02 = R(P.inv_c02);
   unsigned n_guard = 0, n_nan = 0, n_bad = 0;
@@ -225,6 +202,223 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
   }
 }
 
+// INC: u0 (the incident field on X) is given and added to u; otherwise the transform
+// already holds the plane wave
+template <typename R, int N, bool INC, int T>
+__global__ void __launch_bounds__(THREADS)
+k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restrict__ cols,
+                    const int* __restrict__ ncol, const cx<R>* __restrict__ u0, R* __restrict__ xi,
+                    R* __restrict__ cout, unsigned long long* __restrict__ ctr, const cx<R>* __restrict__ tw) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int LINES = row_lines<N, T>() / 2 > 0 ? row_lines<N, T>() / 2 : 1;
+  constexpr int E = LINES * N;            // elements of one field
+  constexpr int PER = (E + THREADS - 1) / THREADS;
+  __shared__ cx<R> buf[LayIdx<Lay::ROW, N, 2 * LINES, Tile<T>::SKEW_RECOVER>::ELEMS];
+  __shared__ cx<R> tw_s[N];
+  __shared__ unsigned red[THREADS / 32];
+  load_twiddles<R, N>(tw_s, tw);
+  const long long nrows = (long long)P.m * N;
+  const long long row0 = (long long)blockIdx.x * LINES;
+  R num[PER], den[PER];
+  if (P.sums64 || recover_pass<R, N, R, INC, T>(P, t2, cols, ncol, u0, buf, tw_s, num, den)) {
+    // the sums left the range of R (|u| |V| beyond FP32 for huge evanescent
+    // profiles): redo this block with FP64 sums; xi itself is in range
+    double nd[PER], dd[PER];
+    recover_pass<R, N, double, INC, T>(P, t2, cols, ncol, u0, buf, tw_s, nd, dd);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const bool g = !(dd[p] >= (double)P.n_omega * P.eps_u * P.eps_u);
+      num[p] = g ? R(0) : R(nd[p] / dd[p]);
+      den[p] = g ? R(0) : R(1);
+    }
+  }
+  recover_epilogue<R, PER, N>(P, num, den, row0, nrows, E, xi, cout, ctr, red);
+}
+
+// ---- single-pass inverse transform and recovery: one X plane per cluster ---------
+// grid (C, M), clusters of C = plane_cluster<N>() CTAs along x; CTA r of the cluster
+// of plane l owns rows r RB .. r RB + RB - 1 (RB = N / C) of both fields (V and u) in
+// its shared memory.  For every frequency the cluster splits the 2 nc active columns
+// (V~ and U~ columns nu1 of cols) among its CTAs; each gathers its columns' profiles
+// (as k_ifft_cols_gather), transforms them along y and stores every value in the row
+// tile of the CTA that owns its row (distributed shared memory).  After a cluster
+// barrier each CTA transforms its rows along x and accumulates the least-squares sums
+// (as recover_pass).  No intermediate array goes through global memory, and one launch
+// replaces two.
+constexpr int REC_CL = 8;  // column lines per chunk (a divisor of THREADS)
+
+template <typename R, int N> __host__ __device__ constexpr size_t plane_rec_smem() {
+  constexpr int RB = N / plane_cluster<N>();
+  return sizeof(cx<R>) * ((size_t)LayIdx<Lay::ROW, N, 2 * RB, 8>::ELEMS + (size_t)REC_CL * N + N);
+}
+
+// The sums of the elements p0 .. p0 + G - 1 (of threadIdx.x + p THREADS < RB N) over
+// the frequencies, in the accumulator type A.  Called by every thread of every CTA of
+// the cluster (it holds cluster barriers).
+template <typename R, int N, bool INC, typename A, int G>
+__device__ __forceinline__ void plane_rec_pass(const Problem& P, const cx<R>* __restrict__ prof,
+                                               const int* __restrict__ slot, const int* __restrict__ cols,
+                                               const int* __restrict__ ncol, const cx<R>* __restrict__ u0, int l,
+                                               unsigned r, cx<R>* rt, cx<R>* ct, const cx<R>* tw_s, int p0, A* num,
+                                               A* den) {
+  constexpr int C = plane_cluster<N>(), RB = N / C;
+  using IX = LayIdx<Lay::ROW, N, 2 * RB, 8>;  // V rows, then u rows
+  constexpr int E = RB * N;
+  const int M = P.m;
+  const long long N2 = (long long)N * N;
+  const R scale = R(1.0 / (double)N2);
+#pragma unroll
+  for (int k = 0; k < G; ++k) { num[k] = A(0); den[k] = A(0); }
+  for (int om = 0; om < P.n_omega; ++om) {
+    for (int e = threadIdx.x; e < IX::ELEMS; e += THREADS) rt[e] = czero<R>();
+    cluster_sync();  // every row tile is cleared (and was read) before any CTA stores into it
+    const int nc = ncol[om];
+    const int* cl = cols + om * N;
+    const int nl = 2 * nc, lpc = (nl + C - 1) / C;  // line q: field q / nc, column cl[q % nc]
+    const int q0 = min(nl, (int)r * lpc), q1 = min(nl, q0 + lpc);
+    // thread t handles line b = t % REC_CL of each chunk, rows i = t / REC_CL + p THREADS / REC_CL:
+    // one column per thread, its CPER values' loads issued together
+    constexpr int CPER = (REC_CL * N + THREADS - 1) / THREADS;
+    const int b = threadIdx.x % REC_CL;
+    for (int c0 = q0; c0 < q1; c0 += REC_CL) {
+      const int q = c0 + b;
+      const int f = q >= nc ? 1 : 0;
+      const int nu1 = q < q1 ? cl[q - f * nc] : -1;
+      int sl[CPER];
+#pragma unroll
+      for (int p = 0; p < CPER; ++p) {
+        const int i = threadIdx.x / REC_CL + p * (THREADS / REC_CL);
+        sl[p] = (nu1 >= 0 && i < N) ? slot[om * N2 + (long long)i * N + nu1] : -1;
+      }
+#pragma unroll
+      for (int p = 0; p < CPER; ++p) {
+        const int i = threadIdx.x / REC_CL + p * (THREADS / REC_CL);
+        if (i < N) {
+          cx<R> v = czero<R>();
+          if (sl[p] >= 0) {
+            v = prof[(((long long)om * N2 + sl[p]) * 2 + f) * M + l];
+          } else if (!INC && f == 1 && i == 0 && nu1 == 0) {
+            // the plane wave's U~0 = N^2 exp(-i k0 z'_l) at nu = 0: the phase reduced to
+            // [-pi, pi] in FP64, its sine and cosine in FP32 (the precision of R)
+            const double ph = -(P.omega[om] / P.c0) * (P.z1 + (l + 0.5) * P.hz);
+            const double red = fma(-6.283185307179586, rint(ph * 0.15915494309189535), ph);
+            float sn, cs;
+            sincosf((float)red, &sn, &cs);
+            v = mk<R>(R(N2) * R(cs), R(N2) * R(sn));
+          }
+          ct[i * REC_CL + b] = v;  // element i of line b
+        }
+      }
+      __syncthreads();
+      fft_lines<R, N, true, REC_CL, THREADS, Lay::COL, 8>(ct, tw_s);
+      if (nu1 >= 0) {  // value i of the line -> row i % RB of CTA i / RB
+#pragma unroll
+        for (int p = 0; p < CPER; ++p) {
+          const int i = threadIdx.x / REC_CL + p * (THREADS / REC_CL);
+          if (i < N) dsmem_st(dsmem_addr(rt + IX::at(f * RB + i % RB, nu1), (unsigned)(i / RB)), ct[i * REC_CL + b]);
+        }
+      }
+      __syncthreads();
+    }
+    cluster_sync();  // every active column has reached its rows
+    fft_lines<R, N, true, 2 * RB, THREADS, Lay::ROW, 8, 8>(rt, tw_s);
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      const int e = threadIdx.x + (p0 + k) * THREADS;
+      if (e < E) {
+        const cx<R> v = scale * rt[IX::at(e / N, e % N)];
+        cx<R> u = scale * rt[IX::at(RB + e / N, e % N)];
+        if (INC) u = u + u0[((long long)om * M + l) * N2 + (long long)((int)r * RB + e / N) * N + (e % N)];
+        num[k] += (A)u.x * (A)v.x + (A)u.y * (A)v.y;  // Re(conj(u) V)
+        den[k] += (A)u.x * (A)u.x + (A)u.y * (A)u.y;  // |u|^2
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R, int N, bool INC>
+__global__ void __launch_bounds__(THREADS, 2)
+k_ifft2_plane_recover(Problem P, const cx<R>* __restrict__ prof, const int* __restrict__ slot,
+                      const int* __restrict__ cols, const int* __restrict__ ncol, const cx<R>* __restrict__ u0,
+                      R* __restrict__ xi, R* __restrict__ cout, unsigned long long* __restrict__ ctr,
+                      const cx<R>* __restrict__ tw) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int C = plane_cluster<N>(), RB = N / C;
+  constexpr int E = RB * N;
+  constexpr int PER = (E + THREADS - 1) / THREADS;
+  static_assert(PER <= 32, "one bit per element in the redo mask");
+  constexpr int G = 2;  // elements per thread of one redo pass
+  extern __shared__ __align__(16) unsigned char plane_smem[];
+  cx<R>* rt = reinterpret_cast<cx<R>*>(plane_smem);
+  cx<R>* ct = rt + LayIdx<Lay::ROW, N, 2 * RB, 8>::ELEMS;
+  cx<R>* tw_s = ct + REC_CL * N;
+  __shared__ unsigned red[THREADS / 32];
+  __shared__ unsigned vote[8];
+  load_twiddles<R, N>(tw_s, tw);
+  const unsigned r = cluster_rank();
+  const int l = blockIdx.y;
+  const long long row0 = (long long)l * N + (long long)r * RB;
+  R num[PER], den[PER];
+  unsigned any = 1;
+  if (!P.sums64) {
+    plane_rec_pass<R, N, INC, R, PER>(P, prof, slot, cols, ncol, u0, l, r, rt, ct, tw_s, 0, num, den);
+    bool bad = false;
+#pragma unroll
+    for (int p = 0; p < PER; ++p) bad |= !(isfinite(num[p]) && isfinite(den[p]));
+    const unsigned mine = __syncthreads_or(bad) ? 1u : 0u;
+    // every CTA of the cluster learns whether any of them overflowed
+    if (threadIdx.x < C) dsmem_st(dsmem_addr(&vote[r], threadIdx.x), mine);
+    cluster_sync();
+    any = 0;
+#pragma unroll
+    for (int q = 0; q < C; ++q) any |= vote[q];
+  }
+  if (any) {
+    // the sums left the range of R (|u| |V| beyond FP32 for huge evanescent profiles):
+    // the cluster redoes the plane with FP64 sums, G elements per thread at a time;
+    // the quotient goes through xi (written and read back by the same thread)
+    unsigned gated = 0;
+    for (int p0 = 0; p0 < PER; p0 += G) {
+      double nd[G], dd[G];
+      plane_rec_pass<R, N, INC, double, G>(P, prof, slot, cols, ncol, u0, l, r, rt, ct, tw_s, p0, nd, dd);
+#pragma unroll
+      for (int k = 0; k < G; ++k) {
+        const int e = threadIdx.x + (p0 + k) * THREADS;
+        if (p0 + k < PER && e < E) {
+          const bool g = !(dd[k] >= (double)P.n_omega * P.eps_u * P.eps_u);
+          gated |= (g ? 1u : 0u) << (p0 + k);
+          xi[(row0 + e / N) * N + (e % N)] = g ? R(0) : R(nd[k] / dd[k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int e = threadIdx.x + p * THREADS;
+      const bool g = (gated >> p) & 1u;
+      num[p] = (g || e >= E) ? R(0) : xi[(row0 + e / N) * N + (e % N)];
+      den[p] = g ? R(0) : R(1);
+    }
+  }
+  recover_epilogue<R, PER, N>(P, num, den, row0, (long long)P.m * N, E, xi, cout, ctr, red);
+}
+
+template <typename R, int N, bool INC>
+cudaError_t rec_plane(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream_t s) {
+  constexpr size_t smem = plane_rec_smem<R, N>();
+  static SmemOptIn attr;
+  cudaError_t e = opt_in_smem(attr, (const void*)k_ifft2_plane_recover<R, N, INC>, smem, true);
+  if (e != cudaSuccess) return e;
+  constexpr int C = plane_cluster<N>();
+  e = launch_pdl_cluster(k_ifft2_plane_recover<R, N, INC>, dim3(C, (unsigned)P.m), dim3(THREADS), C, smem, s, P,
+                         (const cx<R>*)w.prof, (const int*)w.slot, (const int*)w.cols, (const int*)w.ncol, w.u0, xi,
+                         c, w.ctr, (const cx<R>*)w.tw);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 template <typename R, int N, int T>
 cudaError_t rec_tiled(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream_t s, cudaEvent_t mid) {
   constexpr int TC = tile_cols<R, T>();
@@ -248,6 +442,14 @@ cudaError_t rec_tiled(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStrea
 
 template <typename R, int N>
 cudaError_t rec_impl(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream_t s, cudaEvent_t mid) {
+  // the mixed path: one pass unless asked otherwise (N = 96, 192 and 256 hold too many
+  // values per thread for the cluster pass: two passes)
+  if constexpr (sizeof(R) == 4 && N <= 128 && N != 96) {
+    if (P.inverse_single) {
+      if (mid) cudaEventRecord(mid, s);
+      return w.u0 ? rec_plane<R, N, true>(P, w, xi, c, s) : rec_plane<R, N, false>(P, w, xi, c, s);
+    }
+  }
   return P.fft_tile == 1 ? rec_tiled<R, N, 1>(P, w, xi, c, s, mid) : rec_tiled<R, N, 0>(P, w, xi, c, s, mid);
 }
 

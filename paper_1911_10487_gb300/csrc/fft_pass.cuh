@@ -44,6 +44,15 @@ template <int N, int T> __host__ __device__ constexpr int row_lines() {
   return Tile<T>::ELEMS / N > 0 ? Tile<T>::ELEMS / N : 1;
 }
 
+// CTAs per plane of the single-pass (cluster) transforms: the smallest power of two,
+// at most 8 (the portable cluster size), that leaves each CTA at most 16 rows (24 for
+// N = 192, 32 for N = 256)
+template <int N> __host__ __device__ constexpr int plane_cluster() {
+  int c = 1;
+  while (c < 8 && N / c > 16 && N % (2 * c) == 0) c *= 2;
+  return c;
+}
+
 template <typename R, int N>
 __device__ __forceinline__ void load_twiddles(cx<R>* tw_s, const cx<R>* __restrict__ tw) {
   for (int j = threadIdx.x; j < N; j += THREADS) tw_s[j] = tw[j];

@@ -121,6 +121,23 @@ static __device__ __noinline__ double2 exp_ikz(double2 kz, double d) {
   return make_double2(mag * c, mag * s);
 }
 
+// exp(i kz d) for the mixed route: the phase is reduced to [-pi, pi] in FP64
+// (three FP64 operations) and the sine, cosine and exponential are taken in FP32
+// (FP64 where the decay leaves the FP32 range).  Relative error ~1e-7, the
+// precision of the FP32 data; A = E P^T built from the
+// rounded factors is still exactly rank one, and the refinement converges to the
+// solution of that A, so the rounding enters V~ at ~1e-7 without amplification.
+__device__ __forceinline__ double2 exp_ikz32(double2 kz, double d) {
+  if (kz.y * d > 80.0) return exp_ikz(kz, d);  // e^-80: the FP32 exponential nears underflow
+  const double ph = kz.x * d;
+  const double red = fma(-6.283185307179586, rint(ph * 0.15915494309189535), ph);
+  float sn, cs;
+  sincosf((float)red, &sn, &cs);
+  const float mag = expf((float)(-kz.y * d));
+  return make_double2((double)(mag * cs), (double)(mag * sn));
+}
+
+
 // F_l = sum_{l' <= l} q^(l - l') s_l' for l < len <= 64, one warp, lanes own two
 // consecutive elements; an inclusive scan of the affine maps x -> A x + B.
 __device__ __forceinline__ void affine_scan64(const double2* s, int len, double2 q, double2* out) {

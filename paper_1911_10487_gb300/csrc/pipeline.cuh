@@ -54,6 +54,9 @@ struct Problem {
   int incident; // 1: the incident field on X is given (Work::u0) instead of the plane wave
   int classify_single;  // 1: single-pass classification (one cooperative launch)
   int fft_tile;         // tile shape of the transform passes (0 large, 1 small)
+  int forward_single;   // 1: the mixed path's forward 2D transform in one pass (clusters)
+  int inverse_single;   // 1: the mixed path's inverse transform and recovery in one pass
+  int sums64;           // 1: the mixed path's least-squares sums of step 3 in FP64 from the start
 };
 
 inline bool classify_fused_ok(const Problem& P) { return P.classify_single != 0; }
@@ -160,14 +163,16 @@ int kernel_plan_device(const fs_kernel_plan* p);
 
 // Launch facts kept per device, since one process may drive several GPUs:
 //   sm_count()    SM count of the current device (looked up once per device)
-//   opt_in_smem() cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for `kernel`,
-//                 done once per device; `flag` is the call site's own record
+//   opt_in_smem() cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for `kernel`
+//                 (and, max_shared, the largest shared-memory carveout of the unified
+//                 L1/shared array, so that as many CTAs as the registers allow stay
+//                 resident), done once per device; `flag` is the call site's own record
 constexpr int MAX_DEVICES = 64;
 int sm_count();
 struct SmemOptIn {
   std::atomic<unsigned long long> done{0};  // bit d: set on device d
 };
-cudaError_t opt_in_smem(SmemOptIn& flag, const void* kernel, size_t bytes);
+cudaError_t opt_in_smem(SmemOptIn& flag, const void* kernel, size_t bytes, bool max_shared = false);
 
 // Launchers (return the launch error).
 // `mid` (may be null) is recorded on `s` between the two kernels of the stage

@@ -535,6 +535,42 @@ __device__ __forceinline__ ffc ffc_mul(ffc a, ffc b) {
 __device__ __forceinline__ ffc ffc_conj_mul(ffc a, ffc b) {  // conj(a) b
   return ffc{ff_add(ff_mul(a.re, b.re), ff_mul(a.im, b.im)), ff_add(ff_mul(a.re, b.im), ff_neg(ff_mul(a.im, b.re)))};
 }
+// Compensated dot products of two-float operands (the Dot2 scheme of Ogita, Rump and
+// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005): the rounded
+// products hi*hi are summed exactly by TwoSum into s, and every rounding error (of
+// those sums, of the products, and the cross terms hi*lo + lo*hi) is summed in plain
+// FP32 into e.  As accurate as summing in two-float (the errors are O(u) terms summed
+// with relative error O(n u)), for two thirds of the operations.
+struct dot2 { float s, e; };
+struct dot2c { dot2 re, im; };
+__device__ __forceinline__ void dot2_add(dot2& d, float p, float ep) {  // d += p + ep
+  const float t = d.s + p;
+  const float bb = t - d.s;
+  d.e += ((d.s - (t - bb)) + (p - bb)) + ep;
+  d.s = t;
+}
+__device__ __forceinline__ void dot2_mac(dot2& d, ff a, ff b) {  // d += a b
+  const float p = a.hi * b.hi;
+  dot2_add(d, p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p))));
+}
+__device__ __forceinline__ void dot2_msub(dot2& d, ff a, ff b) { dot2_mac(d, ff_neg(a), b); }  // d -= a b
+__device__ __forceinline__ void dot2c_conj_mac(dot2c& d, ffc a, ffc b) {  // d += conj(a) b
+  dot2_mac(d.re, a.re, b.re);
+  dot2_mac(d.re, a.im, b.im);
+  dot2_mac(d.im, a.re, b.im);
+  dot2_msub(d.im, a.im, b.re);
+}
+__device__ __forceinline__ void dot2c_mac(dot2c& d, ffc a, ffc b) {  // d += a b
+  dot2_mac(d.re, a.re, b.re);
+  dot2_msub(d.re, a.im, b.im);
+  dot2_mac(d.im, a.re, b.im);
+  dot2_mac(d.im, a.im, b.re);
+}
+__device__ __forceinline__ dot2c dot2c_zero() { return dot2c{dot2{0.f, 0.f}, dot2{0.f, 0.f}}; }
+__device__ __forceinline__ ffc dot2c_ffc(dot2c d) {
+  return ffc{fast_two_sum(d.re.s, d.re.e), fast_two_sum(d.im.s, d.im.e)};
+}
+
 __device__ __forceinline__ ffc ffc_shfl_xor(ffc a, int m) {
   ffc r;
   r.re.hi = __shfl_xor_sync(0xffffffffu, a.re.hi, m);
@@ -856,27 +892,44 @@ __device__ float2 lanczos_apply32(Shared& S, int n, int kd, float a, float2 r) {
   return y;
 }
 
+// Ah^H yh (two-float, m columns): two threads per column l, lanes 8 apart (l = t mod 8 +
+// 8 (t / 16)), each summing every other row in two compensated chains.  Eight
+// consecutive threads read eight consecutive columns of one row: the 16-byte loads of a
+// quarter warp fall on distinct banks.  Returns the column sum on both threads.
+__device__ __forceinline__ ffc colsum_ff(const ffc (*Af)[DENSE_M + 1], const ffc* yh, int n, int l, int h) {
+  dot2c a0 = dot2c_zero(), a1 = dot2c_zero();
+#pragma unroll 1
+  for (int k = h; k < n; k += 4) {
+    dot2c_conj_mac(a0, Af[k][l], yh[k]);
+    if (k + 2 < n) dot2c_conj_mac(a1, Af[k + 2][l], yh[k + 2]);
+  }
+  ffc acc = ffc_add(dot2c_ffc(a0), dot2c_ffc(a1));
+  return ffc_add(acc, ffc_shfl_xor(acc, 8));
+}
+
 // two-float residual of the scaled dual system: th = Ah^H yh, rh = bh - Ah th - a yh
 __device__ void residual_ff(Shared& S, int n, int m, ff a) {
-  ffc (*Af)[DENSE_M + 1] = reinterpret_cast<ffc (*)[DENSE_M + 1]>(S.A);
+  const ffc (*Af)[DENSE_M + 1] = reinterpret_cast<const ffc (*)[DENSE_M + 1]>(S.A);
   {  // 2 threads per column l
-    const int l = threadIdx.x >> 1, h = threadIdx.x & 1;
-    ffc acc = ffc_zero();
-    if (l < m)
-#pragma unroll 4
-      for (int k = h; k < n; k += 2) acc = ffc_add(acc, ffc_conj_mul(Af[k][l], S.yh[k]));
-    acc = ffc_add(acc, ffc_shfl_xor(acc, 1));
-    if (l < m && h == 0) S.th[l] = acc;
+    const int t = threadIdx.x, l = (t & 7) + 8 * (t >> 4), h = (t >> 3) & 1;
+    const bool on = l < m;
+    const ffc acc = colsum_ff(Af, S.yh, on ? n : 0, l, h);
+    if (on && h == 0) S.th[l] = acc;
   }
   __syncthreads();
-  {  // 4 threads per row k
-    const int k = threadIdx.x >> 2, h = threadIdx.x & 3;
-    ffc acc = ffc_zero();
+  {  // 4 threads per row k (lanes 8 apart): eight consecutive rows at one column per
+     // quarter warp, distinct banks (row stride 65 entries)
+    const int t = threadIdx.x, k = (t & 7) + 8 * (t >> 5), h = (t >> 3) & 3;
+    dot2c a0 = dot2c_zero(), a1 = dot2c_zero();
     if (k < n)
-#pragma unroll 4
-      for (int l = h; l < m; l += 4) acc = ffc_add(acc, ffc_mul(Af[k][l], S.th[l]));
-    acc = ffc_add(acc, ffc_shfl_xor(acc, 1));
-    acc = ffc_add(acc, ffc_shfl_xor(acc, 2));
+#pragma unroll 1
+      for (int l = h; l < m; l += 8) {
+        dot2c_mac(a0, Af[k][l], S.th[l]);
+        if (l + 4 < m) dot2c_mac(a1, Af[k][l + 4], S.th[l + 4]);
+      }
+    ffc acc = ffc_add(dot2c_ffc(a0), dot2c_ffc(a1));
+    acc = ffc_add(acc, ffc_shfl_xor(acc, 8));
+    acc = ffc_add(acc, ffc_shfl_xor(acc, 16));
     if (k < n && h == 0) {
       const ffc ay = ffc{ff_mul(a, S.yh[k].re), ff_mul(a, S.yh[k].im)};
       const ffc r = ffc_sub(ffc_sub(S.bh[k], acc), ay);
@@ -942,22 +995,6 @@ __device__ float root32_warp(Shared& S, int n, float lo, float hi, float target,
   }
   const float t = gh > gl ? tl + (th - tl) * (-gl / (gh - gl)) : 0.5f * (tl + th);
   return expf(t);
-}
-
-// exp(i kz d) for the mixed route: the phase is reduced to [-pi, pi] in FP64
-// (three FP64 operations) and the sine, cosine and exponential are taken in FP32
-// (FP64 where the decay leaves the FP32 range).  Relative error ~1e-7, the
-// precision of the FP32 data; A = E P^T built from the
-// rounded factors is still exactly rank one, and the refinement converges to the
-// solution of that A, so the rounding enters V~ at ~1e-7 without amplification.
-__device__ __forceinline__ double2 exp_ikz32(double2 kz, double d) {
-  if (kz.y * d > 80.0) return exp_ikz(kz, d);  // e^-80: the FP32 exponential nears underflow
-  const double ph = kz.x * d;
-  const double red = fma(-6.283185307179586, rint(ph * 0.15915494309189535), ph);
-  float sn, cs;
-  sincosf((float)red, &sn, &cs);
-  const float mag = expf((float)(-kz.y * d));
-  return make_double2((double)(mag * cs), (double)(mag * sn));
 }
 
 // The block's shared state through the dynamic shared-memory symbol, so that an
@@ -1217,6 +1254,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           S.r32[k] = make_float2(S.bh[k].re.hi, S.bh[k].im.hi);
         }
         __syncthreads();
+        FL_MARK(17);
         const float a32 = (float)S.a_s;
         const ff a_ff = ff{a32, 0.f};  // the FP32 root is exact in two-float
         // stop once the next correction, predicted from the contraction of the last
@@ -1234,6 +1272,7 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           }
           prev = rel;
           if (sweeps) residual_ff(S, n, m, a_ff);
+          if (sweeps == 1) FL_MARK(19);
           if (threadIdx.x < 32) {
             const int j = threadIdx.x;
             const float2 dy = lanczos_apply32(S, n, kd, a32, j < n ? S.r32[j] : make_float2(0.f, 0.f));
@@ -1250,6 +1289,8 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
           }
           __syncthreads();
           rel = (float)S.red[4];
+          if (sweeps == 0) FL_MARK(18);
+          if (sweeps == 1) FL_MARK(20);
         }
         if (!conv) conv = rel <= 1e-18f || (sweeps >= 2 && rel * rel <= 1e-18f * prev);
         if (threadIdx.x == 0) {
@@ -1265,13 +1306,10 @@ k_solve(Problem P, const cx<B>* __restrict__ wt, const int* __restrict__ act,
         FL_MARK(8);
         if (conv) {
           // V~ = A^H y = (||b|| / sqrt(tr)) Ah^H yh, two-float, 2 threads per column
-          const int l = threadIdx.x >> 1, h = threadIdx.x & 1;
-          ffc acc = ffc_zero();
-          if (l < m)
-#pragma unroll 1
-            for (int k = h; k < n; k += 2) acc = ffc_add(acc, ffc_conj_mul(Af[k][l], S.yh[k]));
-          acc = ffc_add(acc, ffc_shfl_xor(acc, 1));
-          if (l < m && h == 0) S.u.q.Vt[l] = (S.sb * sa) * ffc_to(acc);
+          const int t = threadIdx.x, l = (t & 7) + 8 * (t >> 4), h = (t >> 3) & 1;
+          const bool on = l < m;
+          const ffc acc = colsum_ff(Af, S.yh, on ? n : 0, l, h);
+          if (on && h == 0) S.u.q.Vt[l] = (S.sb * sa) * ffc_to(acc);
         }
         __syncthreads();
       }

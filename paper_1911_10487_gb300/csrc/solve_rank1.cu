@@ -38,6 +38,16 @@ template <int RK> struct Rank1Mem {
   double2 v[32 * RK], t[32 * RK], F[32 * RK], B[32 * RK];
 };
 
+// The factors E_k and P_l: FP64 exponentials in the FP64 path; in the mixed path the
+// phase reduced in FP64 and the exponentials taken in FP32 (exp_ikz32), a relative
+// error of ~1e-7, the precision of the FP32 data, instead of FP64 exponentials at the
+// FP64 rate (the bulk of this kernel otherwise).  A = E P^T from the rounded factors
+// is still exactly rank one, so the closed form below stays exact for that A.
+template <typename R> __device__ __forceinline__ double2 exp_mode(double2 kz, double d) {
+  if constexpr (sizeof(R) == 4) return exp_ikz32(kz, d);
+  else return exp_ikz_inline(kz, d);
+}
+
 template <typename R, int RKE, int RK>
 __global__ void __launch_bounds__(RW * 32)
 k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict__ wt64,
@@ -54,7 +64,10 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
   long long total = 0;
   for (int w = 0; w < P.n_omega; ++w) total += count[w];
   unsigned long long n_floor = 0, n_zeroed = 0, n_bad = 0;
-  for (long long item = (long long)blockIdx.x * RW + warp; item < total; item += (long long)gridDim.x * RW) {
+  // item w G + b on warp w of block b (G = gridDim.x): consecutive modes on different
+  // blocks, so that a few active modes spread over the SMs instead of filling the
+  // warps of the first blocks
+  for (long long item = (long long)warp * gridDim.x + blockIdx.x; item < total; item += (long long)gridDim.x * RW) {
     int om = 0;
     long long i = item;
     while (i >= count[om]) { i -= count[om]; ++om; }
@@ -79,7 +92,7 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
       ek[j] = make_double2(0, 0);
       bk[j] = make_double2(0, 0);
       if (k < n) {
-        ek[j] = gamma * exp_ikz_inline(kz, P.zy[k] - ztop);
+        ek[j] = gamma * exp_mode<R>(kz, P.zy[k] - ztop);
         const long long at = ((long long)om * n + k) * N2 + nu;
         bk[j] = wt64 ? wt64[at] : to_d(wt[at]);  // W~ in FP64 on the mixed truncated-SVD route
       }
@@ -91,7 +104,7 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
 #pragma unroll
     for (int j = 0; j < RK; ++j) {
       const int l = lane + 32 * j;
-      pl[j] = l < m ? exp_ikz_inline(kz, ztop - (P.z1 + (l + 0.5) * P.hz)) : make_double2(0, 0);
+      pl[j] = l < m ? exp_mode<R>(kz, ztop - (P.z1 + (l + 0.5) * P.hz)) : make_double2(0, 0);
       sP += abs2(pl[j]);
     }
     sE = warp_sum(sE);

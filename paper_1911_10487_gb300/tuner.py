@@ -33,17 +33,22 @@ class BatchTuner:
             with open(path) as f:
                 self.cache = json.load(f)
 
-    def best(self, rc, items, precision="mixed", repeats=3, outs=None):
+    def best(self, rc, items, precision="mixed", repeats=3, outs=None, options=None):
         """(n_streams, solve_blocks_per_sm, fft_tile, classify_single_pass) for this batch,
-        timing it if unseen."""
+        timing it if unseen.  options: further fs_options fields, fixed for every
+        candidate (part of the cache key)."""
         import torch
+        options = dict(options or {})
         key = signature(items, precision)
+        if options:
+            key += "|" + ",".join(f"{k}={v}" for k, v in sorted(options.items()))
         if key in self.cache:
             return tuple(self.cache[key]["config"])
         timings = {}
         with torch.cuda.stream(rc.stream):
             for s, b, t, c in CANDIDATES:
-                kw = dict(n_streams=s, outs=outs, solve_blocks_per_sm=b, fft_tile=t, classify_single_pass=c)
+                kw = dict(n_streams=s, outs=outs, solve_blocks_per_sm=b, fft_tile=t, classify_single_pass=c,
+                          **options)
                 rc.reconstruct_batch(items, precision, **kw)  # warm
                 t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 t0.record(rc.stream)

@@ -76,3 +76,31 @@ def test_forward_entry_points_reject_a_null_context_without_gpu(abi):
     assert st == abi.FS_EINVAL
     assert abi.STATUS_NAMES[abi.FS_ENOCONV] == "FS_ENOCONV"
     assert sorted(abi.FORWARD_METHODS.values()) == [abi.FS_FIXED_POINT, abi.FS_GMRES, abi.FS_FIXED_POINT_GMRES]
+
+
+def test_transform_options_and_strict_option_names(abi):
+    o = abi.fs_default_options()
+    assert (o.forward_single_pass, o.inverse_single_pass, o.fp64_sums) == (1, 0, 0)
+    with pytest.raises(TypeError):
+        abi.make_options(forward_single=1)  # a misspelt field is an error, not a no-op
+
+
+def test_mixed_noise_limit_is_checked_before_any_device_work(abi):
+    """FS_MIXED with the discrepancy principle below FS_MIXED_MIN_NOISE is refused by the
+    argument checks (the allocation-free entry runs them before touching the device)."""
+    text = open(os.path.join(ROOT, "include", "flatlayer.h")).read()
+    assert float(re.search(r"#define FS_MIXED_MIN_NOISE ([0-9.e+-]+)", text).group(1)) == abi.FS_MIXED_MIN_NOISE
+    g = abi.make_geometry(32, 16, 0.2, 1.0, [1.2 + 0.05 * k for k in range(8)])
+    om = (C.c_double * 1)(1.0)
+    L = abi.lib()
+    for delta, floor in ((0.0, 1e-10), (0.5 * abi.FS_MIXED_MIN_NOISE, 0.0)):
+        o = abi.make_options(delta_floor=floor)
+        st = L.fs_reconstruct_static(C.byref(g), abi.FS_MIXED, None, om, 1, delta, 1.0, C.byref(o), None, None, None)
+        assert st == abi.FS_EUNSUPPORTED
+    # the same arguments pass that check in FP64, and with a given alpha (then fail on the NULL W)
+    o = abi.make_options(delta_floor=1e-10)
+    assert L.fs_reconstruct_static(C.byref(g), abi.FS_FP64, None, om, 1, 0.0, 1.0, C.byref(o), None, None,
+                                   None) == abi.FS_EINVAL
+    o = abi.make_options(delta_floor=1e-10, alpha_mode=1, alpha_given=[1e-3])
+    assert L.fs_reconstruct_static(C.byref(g), abi.FS_MIXED, None, om, 1, 0.0, 1.0, C.byref(o), None, None,
+                                   None) == abi.FS_EINVAL
