@@ -65,8 +65,9 @@ typedef enum {
 typedef enum {
   FS_FP64 = 0, /* every step in FP64: W complex128 in, xi/c float64 out               */
   FS_MIXED = 1 /* FFTs, kernel assembly, normal matrix and its reduction in FP32;
-                  alpha root-find and an FP64-residual refinement of the solve in
-                  FP64 (FP64 factorisation when alpha/tr(A A^H) < fp64_switch);
+                  the dense solve's alpha root-find and its refinement against a
+                  two-float residual (FP64 factorisation when alpha/tr(A A^H) <
+                  fp64_switch); the rank-one form in two-float arithmetic;
                   W complex64 in, xi/c float32 out                                  */
 } fs_precision;
 
@@ -114,8 +115,10 @@ typedef struct {
                           (default); 1: rank-one closed form.  Every data plane lies above
                           X, so K_nu(z_k - z'_l) factors and A_nu = E P^T has rank one
                           exactly: the Tikhonov solution is conj(P) (E^H b)/(tr + alpha) and
-                          the discrepancy root is explicit, O(M1 + M) per mode.  The two
-                          forms agree to rounding.                                        */
+                          the discrepancy root is explicit, O(M1 + M) per mode.  FS_MIXED:
+                          the factors E, P rounded to FP32, every sum, the root, V~ and
+                          eq. (9) in two-float arithmetic on the FP32 pipe.  The two forms
+                          agree to rounding.                                              */
   int regularizer;     /* 0: Tikhonov (default); 1: truncated SVD (Sec. 5: the paper's best
                           regularising algorithm), truncation rank by the discrepancy
                           principle -- rank one on these kernels, i.e. the pseudo-inverse on

@@ -217,6 +217,8 @@ Problem make_problem(const fs_geometry* g, int n_omega, const double* omega, dou
   P.inverse_single = o.inverse_single_pass;
   P.sums64 = o.fp64_sums;
   for (int k = 0; k < g->m1; ++k) P.zy[k] = g->zy[k];
+  P.zy_min = g->zy[0];
+  for (int k = 1; k < g->m1; ++k) P.zy_min = fmin(P.zy_min, g->zy[k]);
   for (int j = 0; j < n_omega; ++j) {
     P.omega[j] = omega[j];
     P.alpha_given[j] = (o.alpha_mode == 1) ? o.alpha_given[j] : 0.0;

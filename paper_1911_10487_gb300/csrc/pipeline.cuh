@@ -40,6 +40,7 @@ struct Problem {
   double delta, tau, delta_floor, alpha_rel, eps_u;
   double fp64_switch; // mixed precision: FP64 factor when alpha/tr(Gram) is below this
   double zy[MAX_M1];
+  double zy_min;  // the lowest data plane
   double omega[MAX_OMEGA];
   double alpha_given[MAX_OMEGA];
   // grazing modes |nu| = k0: integer window [graz_lo, graz_hi] of m1^2 + m2^2, the

@@ -46,6 +46,7 @@
 
 #include "modes.cuh"
 #include "pipeline.cuh"
+#include "twofloat.cuh"
 
 // FL_PHASE_TIMING (development builds only) records clock64() at phase
 // boundaries of the first mode of block 0; it is compiled out otherwise.
@@ -487,98 +488,6 @@ k_classify_fused(Problem P, const cx<R>* __restrict__ wt, double* __restrict__ p
 // ------------------------------------------------------------------------------
 // scalar helpers
 // ------------------------------------------------------------------------------
-
-// ------------------------------------------------------------------------------
-// two-float arithmetic: a value is hi + lo (|lo| <= ulp(hi)/2); sums and products
-// use the error-free transformations TwoSum (Knuth) and TwoProd (with fma), which
-// gives about 48 significant bits on the FP32 pipe.  The mixed route computes its
-// refinement residual and V~ = A^H y this way: FP64-class accuracy without the
-// FP64 pipe, which runs at 1/64 of the FP32 rate on this GPU.
-// ------------------------------------------------------------------------------
-struct ff { float hi, lo; };
-struct ffc { ff re, im; };
-
-__device__ __forceinline__ ff ff_from(double x) {
-  ff r;
-  r.hi = (float)x;
-  r.lo = (float)(x - (double)r.hi);
-  return r;
-}
-__device__ __forceinline__ double ff_to(ff a) { return (double)a.hi + (double)a.lo; }
-__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // requires |a| >= |b| (or a == 0)
-  ff r;
-  r.hi = a + b;
-  r.lo = b - (r.hi - a);
-  return r;
-}
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  const float e = (a.hi - (s - bb)) + (b.hi - bb);
-  return fast_two_sum(s, e + (a.lo + b.lo));
-}
-__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-  const float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-  return fast_two_sum(p, e);
-}
-__device__ __forceinline__ ffc ffc_from(double2 z) { return ffc{ff_from(z.x), ff_from(z.y)}; }
-__device__ __forceinline__ double2 ffc_to(ffc z) { return make_double2(ff_to(z.re), ff_to(z.im)); }
-__device__ __forceinline__ ffc ffc_zero() { return ffc{ff{0.f, 0.f}, ff{0.f, 0.f}}; }
-__device__ __forceinline__ ffc ffc_add(ffc a, ffc b) { return ffc{ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
-__device__ __forceinline__ ffc ffc_sub(ffc a, ffc b) { return ffc{ff_add(a.re, ff_neg(b.re)), ff_add(a.im, ff_neg(b.im))}; }
-__device__ __forceinline__ ffc ffc_mul(ffc a, ffc b) {
-  return ffc{ff_add(ff_mul(a.re, b.re), ff_neg(ff_mul(a.im, b.im))), ff_add(ff_mul(a.re, b.im), ff_mul(a.im, b.re))};
-}
-__device__ __forceinline__ ffc ffc_conj_mul(ffc a, ffc b) {  // conj(a) b
-  return ffc{ff_add(ff_mul(a.re, b.re), ff_mul(a.im, b.im)), ff_add(ff_mul(a.re, b.im), ff_neg(ff_mul(a.im, b.re)))};
-}
-// Compensated dot products of two-float operands (the Dot2 scheme of Ogita, Rump and
-// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005): the rounded
-// products hi*hi are summed exactly by TwoSum into s, and every rounding error (of
-// those sums, of the products, and the cross terms hi*lo + lo*hi) is summed in plain
-// FP32 into e.  As accurate as summing in two-float (the errors are O(u) terms summed
-// with relative error O(n u)), for two thirds of the operations.
-struct dot2 { float s, e; };
-struct dot2c { dot2 re, im; };
-__device__ __forceinline__ void dot2_add(dot2& d, float p, float ep) {  // d += p + ep
-  const float t = d.s + p;
-  const float bb = t - d.s;
-  d.e += ((d.s - (t - bb)) + (p - bb)) + ep;
-  d.s = t;
-}
-__device__ __forceinline__ void dot2_mac(dot2& d, ff a, ff b) {  // d += a b
-  const float p = a.hi * b.hi;
-  dot2_add(d, p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p))));
-}
-__device__ __forceinline__ void dot2_msub(dot2& d, ff a, ff b) { dot2_mac(d, ff_neg(a), b); }  // d -= a b
-__device__ __forceinline__ void dot2c_conj_mac(dot2c& d, ffc a, ffc b) {  // d += conj(a) b
-  dot2_mac(d.re, a.re, b.re);
-  dot2_mac(d.re, a.im, b.im);
-  dot2_mac(d.im, a.re, b.im);
-  dot2_msub(d.im, a.im, b.re);
-}
-__device__ __forceinline__ void dot2c_mac(dot2c& d, ffc a, ffc b) {  // d += a b
-  dot2_mac(d.re, a.re, b.re);
-  dot2_msub(d.re, a.im, b.im);
-  dot2_mac(d.im, a.re, b.im);
-  dot2_mac(d.im, a.im, b.re);
-}
-__device__ __forceinline__ dot2c dot2c_zero() { return dot2c{dot2{0.f, 0.f}, dot2{0.f, 0.f}}; }
-__device__ __forceinline__ ffc dot2c_ffc(dot2c d) {
-  return ffc{fast_two_sum(d.re.s, d.re.e), fast_two_sum(d.im.s, d.im.e)};
-}
-
-__device__ __forceinline__ ffc ffc_shfl_xor(ffc a, int m) {
-  ffc r;
-  r.re.hi = __shfl_xor_sync(0xffffffffu, a.re.hi, m);
-  r.re.lo = __shfl_xor_sync(0xffffffffu, a.re.lo, m);
-  r.im.hi = __shfl_xor_sync(0xffffffffu, a.im.hi, m);
-  r.im.lo = __shfl_xor_sync(0xffffffffu, a.im.lo, m);
-  return r;
-}
 
 // ------------------------------------------------------------------------------
 // shared state of one block

@@ -25,6 +25,7 @@
 
 #include "modes.cuh"
 #include "pipeline.cuh"
+#include "twofloat.cuh"
 
 namespace fl {
 
@@ -38,21 +39,11 @@ template <int RK> struct Rank1Mem {
   double2 v[32 * RK], t[32 * RK], F[32 * RK], B[32 * RK];
 };
 
-// The factors E_k and P_l: FP64 exponentials in the FP64 path; in the mixed path the
-// phase reduced in FP64 and the exponentials taken in FP32 (exp_ikz32), a relative
-// error of ~1e-7, the precision of the FP32 data, instead of FP64 exponentials at the
-// FP64 rate (the bulk of this kernel otherwise).  A = E P^T from the rounded factors
-// is still exactly rank one, so the closed form below stays exact for that A.
-template <typename R> __device__ __forceinline__ double2 exp_mode(double2 kz, double d) {
-  if constexpr (sizeof(R) == 4) return exp_ikz32(kz, d);
-  else return exp_ikz_inline(kz, d);
-}
-
-template <typename R, int RKE, int RK>
+// The FP64 path (k_solve_rank1_mixed below is the mixed one).
+template <int RKE, int RK>
 __global__ void __launch_bounds__(RW * 32)
-k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict__ wt64,
-              const int* __restrict__ act, const int* __restrict__ count,
-              const double* __restrict__ dnu_arr, cx<R>* __restrict__ prof, double* __restrict__ alpha_out,
+k_solve_rank1(Problem P, const double2* __restrict__ wt, const int* __restrict__ act, const int* __restrict__ count,
+              const double* __restrict__ dnu_arr, double2* __restrict__ prof, double* __restrict__ alpha_out,
               unsigned long long* __restrict__ ctr) {
   pdl_wait();
   pdl_trigger();
@@ -92,9 +83,8 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
       ek[j] = make_double2(0, 0);
       bk[j] = make_double2(0, 0);
       if (k < n) {
-        ek[j] = gamma * exp_mode<R>(kz, P.zy[k] - ztop);
-        const long long at = ((long long)om * n + k) * N2 + nu;
-        bk[j] = wt64 ? wt64[at] : to_d(wt[at]);  // W~ in FP64 on the mixed truncated-SVD route
+        ek[j] = gamma * exp_ikz_inline(kz, P.zy[k] - ztop);
+        bk[j] = wt[((long long)om * n + k) * N2 + nu];
       }
       sE += abs2(ek[j]);
       bb += abs2(bk[j]);
@@ -104,7 +94,7 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
 #pragma unroll
     for (int j = 0; j < RK; ++j) {
       const int l = lane + 32 * j;
-      pl[j] = l < m ? exp_mode<R>(kz, ztop - (P.z1 + (l + 0.5) * P.hz)) : make_double2(0, 0);
+      pl[j] = l < m ? exp_ikz_inline(kz, ztop - (P.z1 + (l + 0.5) * P.hz)) : make_double2(0, 0);
       sP += abs2(pl[j]);
     }
     sE = warp_sum(sE);
@@ -168,9 +158,9 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
     __syncwarp();
     affine_scan_lanes<RK>(S.t, m, qz, S.B);
     __syncwarp();
-    cx<R>* out = prof + ((long long)om * N2 + i) * 2 * m;
+    double2* out = prof + ((long long)om * N2 + i) * 2 * m;
     const double n2 = (double)N2;
-    bool overflow = false;  // a profile beyond the range of R (FP32 in the mixed path)
+    bool overflow = false;  // a profile beyond the FP64 range
     for (int l = lane; l < m; l += 32) {
       double2 u = gamma * (S.F[l] + S.B[m - 1 - l]);
       if (nu == 0 && !P.incident) {
@@ -178,10 +168,9 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
         sincos(-k0 * (P.z1 + (l + 0.5) * P.hz), &s0, &c0);
         u = u + make_double2(n2 * c0, n2 * s0);
       }
-      const cx<R> vo = from_d<R>(S.v[l]), uo = from_d<R>(u);
-      overflow |= !(isfinite(vo.x) && isfinite(vo.y) && isfinite(uo.x) && isfinite(uo.y));
-      out[l] = vo;
-      out[m + l] = uo;
+      overflow |= !(isfinite(S.v[l].x) && isfinite(S.v[l].y) && isfinite(u.x) && isfinite(u.y));
+      out[l] = S.v[l];
+      out[m + l] = u;
     }
     if (__any_sync(0xffffffffu, overflow)) ++n_bad;
     if (lane == 0 && alpha_out) alpha_out[om * N2 + nu] = zeroed ? INFINITY : alpha;
@@ -189,7 +178,253 @@ k_solve_rank1(Problem P, const cx<R>* __restrict__ wt, const double2* __restrict
   }
   if (lane == 0) {
     if (n_floor) atomicAdd(ctr + C_ALPHA_FLOOR, n_floor);
-    if (n_bad) atomicAdd(ctr + C_NONFINITE, n_bad);  // profiles beyond the range of R
+    if (n_bad) atomicAdd(ctr + C_NONFINITE, n_bad);  // profiles beyond the FP64 range
+    if (n_zeroed) {
+      atomicAdd(ctr + C_ACTIVE, (unsigned long long)(-(long long)n_zeroed));
+      atomicAdd(ctr + C_ZEROED, n_zeroed);
+    }
+  }
+}
+
+// ---- the mixed path: two-float arithmetic on the FP32 pipe ---------------------
+// The same closed form with the factors rounded to FP32 and every sum, the
+// discrepancy root, V~ and the scans of eq. (9) in two-float arithmetic (about 48
+// bits, the exponent range of FP32).  To keep that range, E is written as
+//   E_k = s gn e_k,  e_k = e^{i k_z (z_k - z_min)}  (|e_k| <= 1, 1 on the lowest data
+//   plane z_min),  s gn = gamma e^{i k_z (z_min - z_top)},  s > 0,  |gn| = 1,
+// and the problem is solved for the scaled unknown: with tr_n = ||e||^2 ||p||^2
+// (tr = s^2 tr_n), beta_n = conj(gn) e^H b (beta = s beta_n) and alpha = s^2 alpha_n,
+//   V~ = conj(p) beta_n / (s (tr_n + alpha_n)),
+// and the discrepancy root t (of c = |e^H b|^2 / ||e||^2 and the residual part p,
+// which s and gn leave unchanged) gives alpha_n = tr_n t / (1 - t).  s, a decay of up
+// to e^-(k_z (z_min - z_top)) on evanescent modes, stays in FP64 (its mantissa from an
+// FP32 power of two); FP64 is left to k_z and s (a few operations per mode): at the
+// FP64 rate of this GPU the FP64 form of this kernel spends most of its time on its
+// sums, root and scans.
+__device__ __forceinline__ float2 exp_ikz32f(double2 kz, double d) {
+  const double ph = kz.x * d;
+  const double red = fma(-6.283185307179586, rint(ph * 0.15915494309189535), ph);
+  float sn, cs;
+  sincosf((float)red, &sn, &cs);
+  const float mag = expf((float)(-kz.y * d));  // below the FP32 range: 0
+  return make_float2(mag * cs, mag * sn);
+}
+
+__device__ __forceinline__ ffc ffc_shfl_up(ffc a, int off) {
+  ffc r;
+  r.re.hi = __shfl_up_sync(0xffffffffu, a.re.hi, off);
+  r.re.lo = __shfl_up_sync(0xffffffffu, a.re.lo, off);
+  r.im.hi = __shfl_up_sync(0xffffffffu, a.im.hi, off);
+  r.im.lo = __shfl_up_sync(0xffffffffu, a.im.lo, off);
+  return r;
+}
+
+// F_l = sum_{l' <= l} q^(l - l') s_l' for l < len <= 32 EPL in two-float, one warp,
+// lanes own EPL consecutive elements (the scan of affine maps of affine_scan_lanes)
+template <int EPL>
+__device__ __forceinline__ void affine_scan_lanes_ff(const ffc* s, int len, float2 q, ffc* out) {
+  const int lane = threadIdx.x & 31;
+  const int l0 = EPL * lane;
+  ffc v[EPL];
+  ffc A = ffc{ff{1.f, 0.f}, ff{0.f, 0.f}}, B = ffc_zero();
+#pragma unroll
+  for (int j = 0; j < EPL; ++j) {
+    v[j] = l0 + j < len ? s[l0 + j] : ffc_zero();
+    B = ffc_add(ffc_mul_f2(B, q), v[j]);
+    A = ffc_mul_f2(A, q);
+  }
+  for (int off = 1; off < 32; off <<= 1) {
+    const ffc Ap = ffc_shfl_up(A, off), Bp = ffc_shfl_up(B, off);
+    if (lane >= off) {
+      B = ffc_add(ffc_mul(A, Bp), B);
+      A = ffc_mul(A, Ap);
+    }
+  }
+  ffc prev = ffc_shfl_up(B, 1);
+  if (lane == 0) prev = ffc_zero();
+#pragma unroll
+  for (int j = 0; j < EPL; ++j) {
+    prev = ffc_add(ffc_mul_f2(prev, q), v[j]);
+    if (l0 + j < len) out[l0 + j] = prev;
+  }
+}
+
+template <int RK> struct Rank1MemF {
+  ffc v[32 * RK], t[32 * RK], F[32 * RK], B[32 * RK];
+};
+
+// gamma z for gamma = -i g (propagating modes) or -g (evanescent), g > 0
+__device__ __forceinline__ ffc gamma_mul(bool prop, ff g, ffc z) {
+  return prop ? ffc{ff_mul(g, z.im), ff_neg(ff_mul(g, z.re))} : ffc{ff_neg(ff_mul(g, z.re)), ff_neg(ff_mul(g, z.im))};
+}
+template <int RKE, int RK>
+__global__ void __launch_bounds__(RW * 32)
+k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __restrict__ wt64,
+                    const int* __restrict__ act, const int* __restrict__ count, const double* __restrict__ dnu_arr,
+                    float2* __restrict__ prof, double* __restrict__ alpha_out, unsigned long long* __restrict__ ctr) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ Rank1MemF<RK> mem[RW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Rank1MemF<RK>& S = mem[warp];
+  const int N = P.n, n = P.m1, m = P.m;
+  const long long N2 = (long long)N * N;
+  long long total = 0;
+  for (int w = 0; w < P.n_omega; ++w) total += count[w];
+  unsigned long long n_floor = 0, n_zeroed = 0, n_bad = 0;
+  // item w G + b on warp w of block b, as in k_solve_rank1
+  for (long long item = (long long)warp * gridDim.x + blockIdx.x; item < total; item += (long long)gridDim.x * RW) {
+    int om = 0;
+    long long i = item;
+    while (i >= count[om]) { i -= count[om]; ++om; }
+    const int nu = act[om * N2 + i];
+    const int i2 = nu / N, i1 = nu - i2 * N;
+    const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
+    const double k0 = P.k0[om], kn = P.kn;
+    const double q = k0 * k0 - kn * kn * (double)(m1 * m1 + m2 * m2);
+    const double rq = rsqrt64(fabs(q));  // active modes are never grazing: q != 0
+    const bool prop = q >= 0.0;
+    const double2 kz = prop ? make_double2(fabs(q) * rq, 0.0) : make_double2(0.0, fabs(q) * rq);
+    const double gd = P.g0[om] * rq;  // |gamma|
+    const ff g = ff_from(gd);
+    const double ztop = P.z1 + (m - 0.5) * P.hz;
+    const double d0 = P.zy_min - ztop;  // > 0: the data lie above X
+    // s and gn: propagating, s = |gamma| and gn = -i e^{i k_z d0}; evanescent, gn = -1
+    // and s = |gamma| e^{-|k_z| d0} = sm 2^ns (sm = |gamma| 2^f, f in [0, 1))
+    double sm = gd, inv_sm = rcp64(gd);
+    int ns = 0;
+    float2 gn = make_float2(-1.f, 0.f);
+    if (prop) {
+      const float2 ph = exp_ikz32f(kz, d0);
+      gn = make_float2(ph.y, -ph.x);
+    } else {
+      const double x = -kz.y * d0 * 1.4426950408889634;  // log2 of the decay
+      const double fl = floor(x);
+      const float f2 = exp2f((float)(x - fl));
+      ns = (int)fl;
+      sm = gd * (double)f2;
+      inv_sm = inv_sm * (double)(1.0f / f2);
+    }
+    const float inv_s = (float)ldexp(inv_sm, -ns);  // 1/s (inf beyond the FP32 range: an overflowing profile)
+    const double s2 = ldexp(sm * sm, 2 * ns);
+    // e_k, b_k on lanes k mod 32, p_l on lanes l mod 32: ||e||^2, ||b||^2, e^H b, ||p||^2
+    ff se = ff{0.f, 0.f}, bb = ff{0.f, 0.f}, sp = ff{0.f, 0.f};
+    ffc eb = ffc_zero();
+    float2 ek[RKE];
+    ffc bk[RKE];
+#pragma unroll
+    for (int j = 0; j < RKE; ++j) {
+      const int k = lane + 32 * j;
+      ek[j] = make_float2(0.f, 0.f);
+      bk[j] = ffc_zero();
+      if (k < n) {
+        ek[j] = exp_ikz32f(kz, P.zy[k] - P.zy_min);
+        const long long at = ((long long)om * n + k) * N2 + nu;
+        if (wt64) {
+          bk[j] = ffc_from(wt64[at]);  // W~ in FP64 on the truncated-SVD route
+        } else {
+          const float2 w = wt[at];
+          bk[j] = ffc{ff{w.x, 0.f}, ff{w.y, 0.f}};
+        }
+      }
+      se = ff_add(se, ff_add(two_prod(ek[j].x, ek[j].x), two_prod(ek[j].y, ek[j].y)));
+      bb = ff_add(bb, ffc_abs2(bk[j]));
+      eb = ffc_add(eb, ffc_conj_f2_mul(ek[j], bk[j]));
+    }
+    float2 pl[RK];
+#pragma unroll
+    for (int j = 0; j < RK; ++j) {
+      const int l = lane + 32 * j;
+      pl[j] = l < m ? exp_ikz32f(kz, ztop - (P.z1 + (l + 0.5) * P.hz)) : make_float2(0.f, 0.f);
+      sp = ff_add(sp, ff_add(two_prod(pl[j].x, pl[j].x), two_prod(pl[j].y, pl[j].y)));
+    }
+    se = ff_warp_sum(se);
+    sp = ff_warp_sum(sp);
+    bb = ff_warp_sum(bb);
+    eb = ffc_warp_sum(eb);
+    const ff tr = ff_mul(se, sp);  // tr_n
+    const ff dnu = ff_from(dnu_arr[om]);
+    const ff dnu2 = ff_mul(dnu, dnu);
+    // ||b - e (e^H b)/||e||^2||^2, the part of ||b||^2 outside the range of A, as the
+    // norm of that residual (its rounding does not grow with ||b||)
+    ff pres = ff{0.f, 0.f};
+    if (se.hi > 0.f) {
+      const ffc pr = ffc{ff_div(eb.re, se), ff_div(eb.im, se)};
+#pragma unroll
+      for (int j = 0; j < RKE; ++j) pres = ff_add(pres, ffc_abs2(ffc_sub(bk[j], ffc_mul_f2(pr, ek[j]))));
+      pres = ff_warp_sum(pres);
+    }
+    ffc coef = ffc_zero();  // V~_l = conj(p_l) coef
+    const bool zeroed = !(tr.hi > 0.f) || (P.alpha_mode == 0 && !ff_gt(bb, dnu2));
+    ff alpha = ff{0.f, 0.f};
+    if (!zeroed) {
+      const ffc beta = ffc_conj_f2_mul(gn, eb);  // beta_n
+      if (P.regularizer == 1) {
+        coef = ffc{ff_div(beta.re, tr), ff_div(beta.im, tr)};
+      } else {
+        if (P.alpha_mode == 1) {
+          const double an = P.alpha_given[om] * rcp64(s2);  // alpha / s^2
+          alpha = ff_from(an < 1e30 ? an : 1e30);  // beyond: V~ is 0 to FP32 precision
+        } else {
+          const ff c = ff_div(ffc_abs2(eb), se);  // |e^H b|^2 / ||e||^2
+          const ff afl = ff_mul(ff_from(P.alpha_rel), tr);
+          const ff rf = ff_div(afl, ff_add(tr, afl));
+          if (!ff_gt(dnu2, ff_add(ff_mul(ff_mul(rf, rf), c), pres))) {
+            alpha = afl;
+            ++n_floor;
+          } else {
+            const ff t = ff_sqrt(ff_div(ff_sub(dnu2, pres), c));
+            alpha = ff_div(ff_mul(tr, t), ff_sub(ff{1.f, 0.f}, t));
+            if (ff_gt(afl, alpha)) alpha = afl;
+          }
+        }
+        const ff den = ff_add(tr, alpha);
+        coef = ffc{ff_div(beta.re, den), ff_div(beta.im, den)};
+      }
+      coef = ffc{ff_mul_f(coef.re, inv_s), ff_mul_f(coef.im, inv_s)};
+    } else {
+      ++n_zeroed;
+    }
+    // V~ and eq. (9): U~ = U~0 + gamma (F + B) over the X planes (two affine scans)
+    float2 qz = make_float2(0.f, 0.f);  // p_{m-2} = e^{i k_z h_z}: the plane-to-plane factor
+#pragma unroll
+    for (int j = 0; j < RK; ++j) {
+      const int l = lane + 32 * j;
+      if (l < m) S.v[l] = ffc_conj_f2_mul(pl[j], coef);
+      if (m >= 2 && j == (m - 2) >> 5) qz = pl[j];
+    }
+    if (m >= 2) {
+      const int src = (m - 2) & 31;
+      qz = make_float2(__shfl_sync(0xffffffffu, qz.x, src), __shfl_sync(0xffffffffu, qz.y, src));
+    }
+    __syncwarp();
+    affine_scan_lanes_ff<RK>(S.v, m, qz, S.F);
+    for (int r = lane; r < m; r += 32) S.t[r] = r == 0 ? ffc_zero() : ffc_mul_f2(S.v[m - r], qz);
+    __syncwarp();
+    affine_scan_lanes_ff<RK>(S.t, m, qz, S.B);
+    __syncwarp();
+    float2* out = prof + ((long long)om * N2 + i) * 2 * m;
+    const float n2 = (float)N2;
+    bool overflow = false;  // a profile beyond the FP32 range
+    for (int l = lane; l < m; l += 32) {
+      float2 u = ffc_to_f2(gamma_mul(prop, g, ffc_add(S.F[l], S.B[m - 1 - l])));
+      if (nu == 0 && !P.incident) {  // the plane wave's U~0 = N^2 exp(-i k0 z'_l)
+        const float2 w = exp_ikz32f(make_double2(k0, 0.0), -(P.z1 + (l + 0.5) * P.hz));
+        u = make_float2(u.x + n2 * w.x, u.y + n2 * w.y);
+      }
+      const float2 vo = ffc_to_f2(S.v[l]);
+      overflow |= !(isfinite(vo.x) && isfinite(vo.y) && isfinite(u.x) && isfinite(u.y));
+      out[l] = vo;
+      out[m + l] = u;
+    }
+    if (__any_sync(0xffffffffu, overflow)) ++n_bad;
+    if (lane == 0 && alpha_out)
+      alpha_out[om * N2 + nu] = zeroed ? INFINITY : (P.regularizer == 1 ? 0.0 : s2 * ff_to(alpha));
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (n_floor) atomicAdd(ctr + C_ALPHA_FLOOR, n_floor);
+    if (n_bad) atomicAdd(ctr + C_NONFINITE, n_bad);  // profiles beyond the FP32 range
     if (n_zeroed) {
       atomicAdd(ctr + C_ACTIVE, (unsigned long long)(-(long long)n_zeroed));
       atomicAdd(ctr + C_ZEROED, n_zeroed);
@@ -206,13 +441,23 @@ cudaError_t launch_solve_rank1(const Problem& P, const Work<R>& w, cudaStream_t 
   const long long want = (modes + RW - 1) / RW;
   const long long cap = 8LL * sms;
   const unsigned grid = (unsigned)(want < cap ? want : cap);
-  if (P.m <= 64 && P.m1 <= 32)
-    return launch_pdl(k_solve_rank1<R, 1, 2>, dim3(grid), dim3(RW * 32), 0, s, P, (const cx<R>*)w.wt,
-                      (const double2*)w.wt64, (const int*)w.act, (const int*)w.count, (const double*)w.dnu, w.prof,
-                      w.alpha_out, w.ctr);
-  return launch_pdl(k_solve_rank1<R, 4, 4>, dim3(grid), dim3(RW * 32), 0, s, P, (const cx<R>*)w.wt,
-                    (const double2*)w.wt64, (const int*)w.act, (const int*)w.count, (const double*)w.dnu, w.prof,
-                    w.alpha_out, w.ctr);
+  if constexpr (sizeof(R) == 4) {
+    if (P.m <= 64 && P.m1 <= 32)
+      return launch_pdl(k_solve_rank1_mixed<1, 2>, dim3(grid), dim3(RW * 32), 0, s, P, (const float2*)w.wt,
+                        (const double2*)w.wt64, (const int*)w.act, (const int*)w.count, (const double*)w.dnu,
+                        (float2*)w.prof, w.alpha_out, w.ctr);
+    return launch_pdl(k_solve_rank1_mixed<4, 4>, dim3(grid), dim3(RW * 32), 0, s, P, (const float2*)w.wt,
+                      (const double2*)w.wt64, (const int*)w.act, (const int*)w.count, (const double*)w.dnu,
+                      (float2*)w.prof, w.alpha_out, w.ctr);
+  } else {
+    if (P.m <= 64 && P.m1 <= 32)
+      return launch_pdl(k_solve_rank1<1, 2>, dim3(grid), dim3(RW * 32), 0, s, P, (const double2*)w.wt,
+                        (const int*)w.act, (const int*)w.count, (const double*)w.dnu, (double2*)w.prof, w.alpha_out,
+                        w.ctr);
+    return launch_pdl(k_solve_rank1<4, 4>, dim3(grid), dim3(RW * 32), 0, s, P, (const double2*)w.wt,
+                      (const int*)w.act, (const int*)w.count, (const double*)w.dnu, (double2*)w.prof, w.alpha_out,
+                      w.ctr);
+  }
 }
 
 template cudaError_t launch_solve_rank1<double>(const Problem&, const Work<double>&, cudaStream_t);

@@ -63,7 +63,11 @@ def test_single_pass_transforms_match_two_pass(rc, name):
 
 def test_single_pass_with_given_incident_field(rc):
     """The incident field of the paper's point sources (Sec. 5) added after the inverse
-    transform (the INC form of the recovery), N = 64 (clusters of 4)."""
+    transform (the INC form of the recovery), N = 64 (clusters of 4).  The interference
+    of the eleven sources leaves near-zeros of u on X, where xi = Re(sum conj(u) V) /
+    sum |u|^2 is fixed only to the rounding of the transforms amplified by 1 / |u|: the
+    two forms (radix 8 and 16 column passes) agree to the mixed path's bound (1e-5), and
+    to 1e-6 in the weight of the least-squares denominator."""
     import torch
     from synth import paper_workload
     from paper_1911_10487_gb300 import Geometry
@@ -79,12 +83,15 @@ def test_single_pass_with_given_incident_field(rc):
     kw = dict(solve_form=1, incident=u0)
     x0, a0, r0 = _run(rc, W, om, geom, 1e-2, forward_single_pass=0, inverse_single_pass=0, **kw)
     assert a0.sum() > 0
+    den = (u0.abs() ** 2).sum(0).double().cpu().numpy()  # sum over the frequencies of |u0|^2
     for fwd, inv, s64 in ((1, 1, 0), (1, 1, 1), (0, 1, 0)):
         x, a, r = _run(rc, W, om, geom, 1e-2, forward_single_pass=fwd, inverse_single_pass=inv, fp64_sums=s64, **kw)
         err = rel_l2(x, x0)
-        print(f"incident field: forward {fwd} inverse {inv} fp64 sums {s64}: xi vs two-pass {err:.2e}")
+        werr = np.sqrt(np.sum(den * (x - x0) ** 2) / np.sum(den * x0 ** 2))
+        print(f"incident field: forward {fwd} inverse {inv} fp64 sums {s64}: xi vs two-pass {err:.2e}, "
+              f"weighted {werr:.2e}")
         assert np.array_equal(a, a0)
-        assert err <= 1e-6
+        assert err <= 1e-5 and werr <= 1e-6
 
 
 def test_mixed_path_refuses_noise_below_its_resolution(rc):
