@@ -110,7 +110,7 @@ Layout layout(int n, int m, int m1, int n_omega, bool fp64) {
   L.t12 = off; off = align_up(off + (a > b ? a : b));  // W~, later the y-inverse pass output
   L.prof = off; off = align_up(off + cxs * (size_t)n_omega * N2 * 2 * m);
   L.norms = off; off = align_up(off + 8 * (size_t)n_omega * N2);
-  L.n_partial = (int)((N2 + 255) / 256);
+  L.n_partial = (int)((N2 + 63) / 64);  // blocks of the norms kernel (64 modes each)
   L.partial = off; off = align_up(off + 8 * (size_t)n_omega * L.n_partial);
   L.slot = off; off = align_up(off + 4 * (size_t)n_omega * N2);
   L.act = off; off = align_up(off + 4 * (size_t)n_omega * N2);

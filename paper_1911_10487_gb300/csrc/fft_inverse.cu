@@ -41,23 +41,30 @@ k_ifft_cols_gather(Problem P, const cx<R>* __restrict__ prof, const int* __restr
   load_twiddles<R, N>(tw_s, tw);
   const long long N2 = (long long)N * N;
   const int M = P.m;
+  // element e = t + p THREADS is row i = e / TC of line b = t mod TC (THREADS is a
+  // multiple of TC): one column per thread, its PER slot loads and then its profile
+  // loads issued together
+  static_assert(THREADS % TC == 0, "one column per thread");
+  const int b = threadIdx.x % TC;
+  const int nu1 = cb + b < nc ? cols[om * N + cb + b] : -1;
+  int sl[PER];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * THREADS, i = e / TC;
+    sl[p] = (nu1 >= 0 && e < E) ? slot[om * N2 + (long long)i * N + nu1] : -1;
+  }
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * THREADS;
     if (e < E) {
-      const int i = e / TC, b = e % TC;
-      const int c = cb + b;
+      const int i = e / TC;
       cx<R> v = czero<R>();
-      if (c < nc) {
-        const int nu1 = cols[om * N + c];
-        const int s = slot[om * N2 + (long long)i * N + nu1];
-        if (s >= 0) {
-          v = prof[(((long long)om * N2 + s) * 2 + f) * M + l];
-        } else if (f == 1 && i == 0 && nu1 == 0 && !P.incident) {  // one thread: FP64 is slow on this GPU
-          double sn, cs;
-          sincos(-(P.omega[om] / P.c0) * (P.z1 + (l + 0.5) * P.hz), &sn, &cs);
-          v = from_d<R>(make_double2((double)N2 * cs, (double)N2 * sn));
-        }
+      if (sl[p] >= 0) {
+        v = prof[(((long long)om * N2 + sl[p]) * 2 + f) * M + l];
+      } else if (f == 1 && i == 0 && nu1 == 0 && !P.incident) {  // one thread: FP64 is slow on this GPU
+        double sn, cs;
+        sincos(-(P.omega[om] / P.c0) * (P.z1 + (l + 0.5) * P.hz), &sn, &cs);
+        v = from_d<R>(make_double2((double)N2 * cs, (double)N2 * sn));
       }
       buf[e] = v;
     }
@@ -68,10 +75,7 @@ k_ifft_cols_gather(Problem P, const cx<R>* __restrict__ prof, const int* __restr
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * THREADS;
-    if (e < E) {
-      const int i = e / TC, b = e % TC;
-      if (cb + b < nc) t2[ob + (long long)i * N + cb + b] = buf[e];
-    }
+    if (e < E && nu1 >= 0) t2[ob + (long long)(e / TC) * N + cb + b] = buf[e];
   }
 }
 

@@ -120,10 +120,12 @@ k_fft_cols(cx<R>* __restrict__ data, const cx<R>* __restrict__ tw, unsigned* __r
   }
 }
 
-// ---- per-mode norms ||W~_nu||^2 = sum_k |W~_k(nu)|^2, summed in plane order ------
-// grid (n_partial, n_omega), one mode per thread; each block also writes the sum
-// of its modes' norms (fixed-order tree) for ||W||.
-constexpr int NORM_T = 256;
+// ---- per-mode norms ||W~_nu||^2 = sum_k |W~_k(nu)|^2 ----------------------------
+// grid (n_partial, n_omega), NORM_MB modes per block and NORM_Q threads per mode: warp
+// w sums the planes of quarter q = w / 2 (a contiguous quarter of the planes, its loads
+// in flight together) for 32 consecutive modes, and the quarters are added in a fixed
+// order; each block also writes the sum of its modes' norms (fixed-order tree) for ||W||.
+constexpr int NORM_T = 256, NORM_Q = 4, NORM_MB = NORM_T / NORM_Q;
 
 template <typename R>
 __global__ void __launch_bounds__(NORM_T)
@@ -131,34 +133,43 @@ k_mode_norms(const cx<R>* __restrict__ wt, double* __restrict__ norms, double* _
              int N2, unsigned long long* __restrict__ ctr) {
   pdl_wait();
   pdl_trigger();
-  __shared__ double red[NORM_T];
+  __shared__ R part[NORM_Q][NORM_MB];
+  __shared__ double red[NORM_MB];
   const int om = blockIdx.y;
-  const int nu = blockIdx.x * NORM_T + threadIdx.x;
+  const int q = threadIdx.x / NORM_MB, j = threadIdx.x % NORM_MB;
+  const int nu = blockIdx.x * NORM_MB + j;
   // summed in the working precision R (FP32 in the mixed path: FP64 arithmetic
   // here would run on the slow FP64 pipe for every mode)
   R acc = R(0);
+  const int k0 = q * m1 / NORM_Q, k1 = (q + 1) * m1 / NORM_Q;
   if (nu < N2) {
     const cx<R>* p = wt + (long long)om * m1 * N2 + nu;
-    int k = 0;
-    for (; k + 8 <= m1; k += 8) {  // eight independent loads in flight, summed in plane order
+    int k = k0;
+    for (; k + 8 <= k1; k += 8) {  // eight independent loads in flight, summed in plane order
       cx<R> v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = p[(long long)(k + q) * N2];
+      for (int t = 0; t < 8; ++t) v[t] = p[(long long)(k + t) * N2];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc += v[q].x * v[q].x + v[q].y * v[q].y;
+      for (int t = 0; t < 8; ++t) acc += v[t].x * v[t].x + v[t].y * v[t].y;
     }
-    for (; k < m1; ++k) {
+    for (; k < k1; ++k) {
       const cx<R> v = p[(long long)k * N2];
       acc += v.x * v.x + v.y * v.y;
     }
-    norms[(long long)om * N2 + nu] = (double)acc;
   }
-  red[threadIdx.x] = (double)acc;
+  part[q][j] = acc;
+  __syncthreads();
+  R nrm = R(0);
+  if (q == 0) {
+    nrm = (part[0][j] + part[1][j]) + (part[2][j] + part[3][j]);
+    if (nu < N2) norms[(long long)om * N2 + nu] = (double)nrm;
+    red[j] = (double)nrm;
+  }
   // modes whose norm is not finite (a NaN or Inf in W), counted at the barrier
   // the reduction needs anyway
-  const int n_bad = __syncthreads_count(nu < N2 && !isfinite(acc));
+  const int n_bad = __syncthreads_count(q == 0 && nu < N2 && !isfinite(nrm));
   if (n_bad && threadIdx.x == 0) atomicAdd(ctr + C_NONFINITE, (unsigned long long)n_bad);
-  for (int h = NORM_T / 2; h > 0; h >>= 1) {
+  for (int h = NORM_MB / 2; h > 0; h >>= 1) {
     if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
     __syncthreads();
   }

@@ -187,9 +187,9 @@ k_solve_rank1(Problem P, const double2* __restrict__ wt, const int* __restrict__
 }
 
 // ---- the mixed path: two-float arithmetic on the FP32 pipe ---------------------
-// The same closed form with the factors rounded to FP32 and every sum, the
-// discrepancy root, V~ and the scans of eq. (9) in two-float arithmetic (about 48
-// bits, the exponent range of FP32).  To keep that range, E is written as
+// The same closed form with the factors rounded to FP32, every sum, the discrepancy
+// root and V~ in two-float arithmetic (about 48 bits, the exponent range of FP32), and
+// eq. (9) in closed form (below) in FP32, the precision of the output.  To keep that range, E is written as
 //   E_k = s gn e_k,  e_k = e^{i k_z (z_k - z_min)}  (|e_k| <= 1, 1 on the lowest data
 //   plane z_min),  s gn = gamma e^{i k_z (z_min - z_top)},  s > 0,  |gn| = 1,
 // and the problem is solved for the scaled unknown: with tr_n = ||e||^2 ||p||^2
@@ -210,53 +210,6 @@ __device__ __forceinline__ float2 exp_ikz32f(double2 kz, double d) {
   return make_float2(mag * cs, mag * sn);
 }
 
-__device__ __forceinline__ ffc ffc_shfl_up(ffc a, int off) {
-  ffc r;
-  r.re.hi = __shfl_up_sync(0xffffffffu, a.re.hi, off);
-  r.re.lo = __shfl_up_sync(0xffffffffu, a.re.lo, off);
-  r.im.hi = __shfl_up_sync(0xffffffffu, a.im.hi, off);
-  r.im.lo = __shfl_up_sync(0xffffffffu, a.im.lo, off);
-  return r;
-}
-
-// F_l = sum_{l' <= l} q^(l - l') s_l' for l < len <= 32 EPL in two-float, one warp,
-// lanes own EPL consecutive elements (the scan of affine maps of affine_scan_lanes)
-template <int EPL>
-__device__ __forceinline__ void affine_scan_lanes_ff(const ffc* s, int len, float2 q, ffc* out) {
-  const int lane = threadIdx.x & 31;
-  const int l0 = EPL * lane;
-  ffc v[EPL];
-  ffc A = ffc{ff{1.f, 0.f}, ff{0.f, 0.f}}, B = ffc_zero();
-#pragma unroll
-  for (int j = 0; j < EPL; ++j) {
-    v[j] = l0 + j < len ? s[l0 + j] : ffc_zero();
-    B = ffc_add(ffc_mul_f2(B, q), v[j]);
-    A = ffc_mul_f2(A, q);
-  }
-  for (int off = 1; off < 32; off <<= 1) {
-    const ffc Ap = ffc_shfl_up(A, off), Bp = ffc_shfl_up(B, off);
-    if (lane >= off) {
-      B = ffc_add(ffc_mul(A, Bp), B);
-      A = ffc_mul(A, Ap);
-    }
-  }
-  ffc prev = ffc_shfl_up(B, 1);
-  if (lane == 0) prev = ffc_zero();
-#pragma unroll
-  for (int j = 0; j < EPL; ++j) {
-    prev = ffc_add(ffc_mul_f2(prev, q), v[j]);
-    if (l0 + j < len) out[l0 + j] = prev;
-  }
-}
-
-template <int RK> struct Rank1MemF {
-  ffc v[32 * RK], t[32 * RK], F[32 * RK], B[32 * RK];
-};
-
-// gamma z for gamma = -i g (propagating modes) or -g (evanescent), g > 0
-__device__ __forceinline__ ffc gamma_mul(bool prop, ff g, ffc z) {
-  return prop ? ffc{ff_mul(g, z.im), ff_neg(ff_mul(g, z.re))} : ffc{ff_neg(ff_mul(g, z.re)), ff_neg(ff_mul(g, z.im))};
-}
 template <int RKE, int RK>
 __global__ void __launch_bounds__(RW * 32)
 k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __restrict__ wt64,
@@ -264,9 +217,7 @@ k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __r
                     float2* __restrict__ prof, double* __restrict__ alpha_out, unsigned long long* __restrict__ ctr) {
   pdl_wait();
   pdl_trigger();
-  __shared__ Rank1MemF<RK> mem[RW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Rank1MemF<RK>& S = mem[warp];
   const int N = P.n, n = P.m1, m = P.m;
   const long long N2 = (long long)N * N;
   long long total = 0;
@@ -286,7 +237,6 @@ k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __r
     const bool prop = q >= 0.0;
     const double2 kz = prop ? make_double2(fabs(q) * rq, 0.0) : make_double2(0.0, fabs(q) * rq);
     const double gd = P.g0[om] * rq;  // |gamma|
-    const ff g = ff_from(gd);
     const double ztop = P.z1 + (m - 0.5) * P.hz;
     const double d0 = P.zy_min - ztop;  // > 0: the data lie above X
     // s and gn: propagating, s = |gamma| and gn = -i e^{i k_z d0}; evanescent, gn = -1
@@ -385,42 +335,60 @@ k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __r
     } else {
       ++n_zeroed;
     }
-    // V~ and eq. (9): U~ = U~0 + gamma (F + B) over the X planes (two affine scans)
-    float2 qz = make_float2(0.f, 0.f);  // p_{m-2} = e^{i k_z h_z}: the plane-to-plane factor
+    // V~ and eq. (9) in closed form.  With uniform X planes p_l = q^n, n = M - 1 - l,
+    // q = e^{i k_z h_z}, so v_l = conj(p_l) coef and the two sums of eq. (9),
+    // F_l = sum_{l' <= l} q^(l - l') v_l' and B_l = sum_{l' > l} q^(l' - l) v_l', are
+    // geometric:
+    //   propagating (|q| = 1, theta = k_z h_z): F_l = (l + 1) v_l,
+    //     B_l = coef q sin(n theta) / sin(theta), sin(n theta) = Im p_l;
+    //   evanescent (q = e^-a, a = |k_z| h_z): F_l = v_l (1 - q^(2(l+1))) / (1 - q^2),
+    //     B_l = n v_l;
+    // U~_l = U~0_l + gamma (F_l + B_l), evaluated in FP32 (the precision of the output).
+    float2 qz = make_float2(1.f, 0.f);  // p_{M-2} = q
 #pragma unroll
-    for (int j = 0; j < RK; ++j) {
-      const int l = lane + 32 * j;
-      if (l < m) S.v[l] = ffc_conj_f2_mul(pl[j], coef);
+    for (int j = 0; j < RK; ++j)
       if (m >= 2 && j == (m - 2) >> 5) qz = pl[j];
-    }
     if (m >= 2) {
       const int src = (m - 2) & 31;
       qz = make_float2(__shfl_sync(0xffffffffu, qz.x, src), __shfl_sync(0xffffffffu, qz.y, src));
     }
-    __syncwarp();
-    affine_scan_lanes_ff<RK>(S.v, m, qz, S.F);
-    for (int r = lane; r < m; r += 32) S.t[r] = r == 0 ? ffc_zero() : ffc_mul_f2(S.v[m - r], qz);
-    __syncwarp();
-    affine_scan_lanes_ff<RK>(S.t, m, qz, S.B);
-    __syncwarp();
+    const float2 cf = ffc_to_f2(coef);
+    const float gf = (float)gd;
+    const float a2 = (float)(2.0 * kz.y * P.hz);  // evanescent: 2a
+    const float den_e = prop ? 1.f : expm1f(-a2);  // q^2 - 1
     float2* out = prof + ((long long)om * N2 + i) * 2 * m;
     const float n2 = (float)N2;
     bool overflow = false;  // a profile beyond the FP32 range
-    for (int l = lane; l < m; l += 32) {
-      float2 u = ffc_to_f2(gamma_mul(prop, g, ffc_add(S.F[l], S.B[m - 1 - l])));
-      if (nu == 0 && !P.incident) {  // the plane wave's U~0 = N^2 exp(-i k0 z'_l)
-        const float2 w = exp_ikz32f(make_double2(k0, 0.0), -(P.z1 + (l + 0.5) * P.hz));
-        u = make_float2(u.x + n2 * w.x, u.y + n2 * w.y);
+#pragma unroll
+    for (int j = 0; j < RK; ++j) {
+      const int l = lane + 32 * j;
+      if (l < m) {
+        const float2 p = pl[j];
+        const float2 v = make_float2(p.x * cf.x + p.y * cf.y, p.x * cf.y - p.y * cf.x);  // conj(p) coef
+        const int nn = m - 1 - l;
+        float2 x;
+        if (prop) {
+          const float d = nn > 0 ? p.y / qz.y : 0.f;  // sin(n theta) / sin(theta)
+          const float2 cq = make_float2(cf.x * qz.x - cf.y * qz.y, cf.x * qz.y + cf.y * qz.x);
+          x = make_float2((float)(l + 1) * v.x + d * cq.x, (float)(l + 1) * v.y + d * cq.y);
+        } else {
+          const float gsum = expm1f(-a2 * (float)(l + 1)) / den_e + (float)nn;
+          x = make_float2(gsum * v.x, gsum * v.y);
+        }
+        // gamma x: gamma = -i g (propagating), -g (evanescent)
+        float2 u = prop ? make_float2(gf * x.y, -gf * x.x) : make_float2(-gf * x.x, -gf * x.y);
+        if (nu == 0 && !P.incident) {  // the plane wave's U~0 = N^2 exp(-i k0 z'_l)
+          const float2 w = exp_ikz32f(make_double2(k0, 0.0), -(P.z1 + (l + 0.5) * P.hz));
+          u = make_float2(u.x + n2 * w.x, u.y + n2 * w.y);
+        }
+        overflow |= !(isfinite(v.x) && isfinite(v.y) && isfinite(u.x) && isfinite(u.y));
+        out[l] = v;
+        out[m + l] = u;
       }
-      const float2 vo = ffc_to_f2(S.v[l]);
-      overflow |= !(isfinite(vo.x) && isfinite(vo.y) && isfinite(u.x) && isfinite(u.y));
-      out[l] = vo;
-      out[m + l] = u;
     }
     if (__any_sync(0xffffffffu, overflow)) ++n_bad;
     if (lane == 0 && alpha_out)
       alpha_out[om * N2 + nu] = zeroed ? INFINITY : (P.regularizer == 1 ? 0.0 : s2 * ff_to(alpha));
-    __syncwarp();
   }
   if (lane == 0) {
     if (n_floor) atomicAdd(ctr + C_ALPHA_FLOOR, n_floor);

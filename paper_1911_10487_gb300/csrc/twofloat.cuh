@@ -1,6 +1,6 @@
 // Two-float arithmetic for the mixed-precision per-mode kernels (the dense solve's
-// refinement, the rank-one closed form, eq. (9)): FP64-class accuracy on the FP32 pipe,
-// which this GPU runs at 64 times its FP64 rate.
+// refinement residual and V~, the rank-one closed form's sums and root): FP64-class
+// accuracy on the FP32 pipe, which this GPU runs at 64 times its FP64 rate.
 #pragma once
 
 #include "common.cuh"
