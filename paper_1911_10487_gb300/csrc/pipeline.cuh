@@ -58,9 +58,20 @@ struct Problem {
   int forward_single;   // 1: the mixed path's forward 2D transform in one pass (clusters)
   int inverse_single;   // 1: the mixed path's inverse transform and recovery in one pass
   int sums64;           // 1: the mixed path's least-squares sums of step 3 in FP64 from the start
+  // two-float (hi, lo) copies of the constants the mixed rank-one solve needs, so that
+  // its per-mode set-up runs on the FP32 pipe: k0, k0^2, g0 per frequency, kn^2, h_z,
+  // z1, alpha_rel, zy[k] - zy_min and zy_min - z_top (z_top = z1 + (M - 1/2) h_z)
+  float2 k0_f[MAX_OMEGA], k0sq_f[MAX_OMEGA], g0_f[MAX_OMEGA];
+  float2 knsq_f, hz_f, z1_f, alpha_rel_f, d0_f;
+  float2 zyd_f[MAX_M1];
 };
 
 inline bool classify_fused_ok(const Problem& P) { return P.classify_single != 0; }
+
+inline float2 two_float(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
 
 inline void derive_constants(Problem& P) {
   P.kn = 2.0 * M_PI / P.period;
@@ -70,7 +81,16 @@ inline void derive_constants(Problem& P) {
     const double om2 = P.omega[j] * P.omega[j];
     P.k0[j] = P.omega[j] / P.c0;
     P.g0[j] = 0.5 * om2 * P.hz;
+    P.k0_f[j] = two_float(P.k0[j]);
+    P.k0sq_f[j] = two_float(P.k0[j] * P.k0[j]);
+    P.g0_f[j] = two_float(P.g0[j]);
   }
+  P.knsq_f = two_float(P.kn * P.kn);
+  P.hz_f = two_float(P.hz);
+  P.z1_f = two_float(P.z1);
+  P.alpha_rel_f = two_float(P.alpha_rel);
+  P.d0_f = two_float(P.zy_min - (P.z1 + (P.m - 0.5) * P.hz));
+  for (int k = 0; k < P.m1; ++k) P.zyd_f[k] = two_float(P.zy[k] - P.zy_min);
 }
 
 // Workspace views (device pointers).  R = bulk real type (double / float).

@@ -197,18 +197,27 @@ k_solve_rank1(Problem P, const double2* __restrict__ wt, const int* __restrict__
 //   V~ = conj(p) beta_n / (s (tr_n + alpha_n)),
 // and the discrepancy root t (of c = |e^H b|^2 / ||e||^2 and the residual part p,
 // which s and gn leave unchanged) gives alpha_n = tr_n t / (1 - t).  s, a decay of up
-// to e^-(k_z (z_min - z_top)) on evanescent modes, stays in FP64 (its mantissa from an
-// FP32 power of two); FP64 is left to k_z and s (a few operations per mode): at the
-// FP64 rate of this GPU the FP64 form of this kernel spends most of its time on its
-// sums, root and scans.
-__device__ __forceinline__ float2 exp_ikz32f(double2 kz, double d) {
-  const double ph = kz.x * d;
-  const double red = fma(-6.283185307179586, rint(ph * 0.15915494309189535), ph);
-  float sn, cs;
-  sincosf((float)red, &sn, &cs);
-  const float mag = expf((float)(-kz.y * d));  // below the FP32 range: 0
-  return make_float2(mag * cs, mag * sn);
+// to e^-(k_z (z_min - z_top)) on evanescent modes, is kept as an FP32 mantissa and a
+// power of two.  k_z, |gamma|, the phases and s come from two-float copies of the
+// problem's constants; FP64 is left to the conversion of delta_nu and to alpha as an
+// output: at the FP64 rate of this GPU (one warp instruction per 64 cycles) the FP64
+// form of this kernel spends most of its time on FP64 set-up, sums, root and scans.
+// e^{i k_z d} from two-float |k_z| and d: propagating, the phase |k_z| d reduced by
+// the nearest multiple of 2 pi in two-float and its sine and cosine in FP32;
+// evanescent, e^{-|k_z| d} from the FP32 exponential of the leading part and the first
+// order of the trailing part
+__device__ __forceinline__ float2 exp_mode_ff(bool prop, ff kz, ff d) {
+  const ff x = ff_mul(kz, d);
+  if (prop) {
+    const float n = rintf(x.hi * 0.159154943f);
+    const ff red = ff_sub(ff_sub(x, two_prod(n, 6.28318548f)), two_prod(n, -1.74845553e-7f));
+    float sn, cs;
+    sincosf(red.hi + red.lo, &sn, &cs);
+    return make_float2(cs, sn);
+  }
+  return make_float2(expf(-x.hi) * (1.f - x.lo), 0.f);
 }
+
 
 template <int RKE, int RK>
 __global__ void __launch_bounds__(RW * 32)
@@ -231,32 +240,28 @@ k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __r
     const int nu = act[om * N2 + i];
     const int i2 = nu / N, i1 = nu - i2 * N;
     const int m1 = i1 < N / 2 ? i1 : i1 - N, m2 = i2 < N / 2 ? i2 : i2 - N;
-    const double k0 = P.k0[om], kn = P.kn;
-    const double q = k0 * k0 - kn * kn * (double)(m1 * m1 + m2 * m2);
-    const double rq = rsqrt64(fabs(q));  // active modes are never grazing: q != 0
-    const bool prop = q >= 0.0;
-    const double2 kz = prop ? make_double2(fabs(q) * rq, 0.0) : make_double2(0.0, fabs(q) * rq);
-    const double gd = P.g0[om] * rq;  // |gamma|
-    const double ztop = P.z1 + (m - 0.5) * P.hz;
-    const double d0 = P.zy_min - ztop;  // > 0: the data lie above X
-    // s and gn: propagating, s = |gamma| and gn = -i e^{i k_z d0}; evanescent, gn = -1
-    // and s = |gamma| e^{-|k_z| d0} = sm 2^ns (sm = |gamma| 2^f, f in [0, 1))
-    double sm = gd, inv_sm = rcp64(gd);
-    int ns = 0;
+    // k_z, |gamma| and the scale s of E = s gn e in two-float (the FP32 pipe)
+    const ff k2 = ff_sub(ff{P.k0sq_f[om].x, P.k0sq_f[om].y},
+                         ff_mul_f(ff{P.knsq_f.x, P.knsq_f.y}, (float)(m1 * m1 + m2 * m2)));  // k0^2 - |nu|^2
+    const bool prop = k2.hi >= 0.f;  // active modes are never grazing: k2 != 0
+    const ff kz = ff_sqrt(prop ? k2 : ff_neg(k2));  // |k_z|
+    const ff gdf = ff_div(ff{P.g0_f[om].x, P.g0_f[om].y}, kz);  // |gamma| = g0 / |k_z|
+    const ff d0 = ff{P.d0_f.x, P.d0_f.y}, hz = ff{P.hz_f.x, P.hz_f.y};
+    // propagating: s = |gamma|, gn = -i e^{i k_z d0}; evanescent: gn = -1 and
+    // s = |gamma| e^{-|k_z| d0} = |gamma| 2^f 2^ns, f in [0, 1)
     float2 gn = make_float2(-1.f, 0.f);
+    float smf = gdf.hi + gdf.lo;  // s 2^-ns
+    int ns = 0;
     if (prop) {
-      const float2 ph = exp_ikz32f(kz, d0);
+      const float2 ph = exp_mode_ff(true, kz, d0);
       gn = make_float2(ph.y, -ph.x);
     } else {
-      const double x = -kz.y * d0 * 1.4426950408889634;  // log2 of the decay
-      const double fl = floor(x);
-      const float f2 = exp2f((float)(x - fl));
+      const ff y = ff_mul(ff_mul(kz, d0), ff{-1.44269502f, -1.92596299e-8f});  // -|k_z| d0 log2(e)
+      const float fl = floorf(y.hi);
       ns = (int)fl;
-      sm = gd * (double)f2;
-      inv_sm = inv_sm * (double)(1.0f / f2);
+      smf *= exp2f((y.hi - fl) + y.lo);
     }
-    const float inv_s = (float)ldexp(inv_sm, -ns);  // 1/s (inf beyond the FP32 range: an overflowing profile)
-    const double s2 = ldexp(sm * sm, 2 * ns);
+    const float inv_s = ldexpf(1.f / smf, -ns);  // 1/s (inf beyond the FP32 range: an overflowing profile)
     // e_k, b_k on lanes k mod 32, p_l on lanes l mod 32: ||e||^2, ||b||^2, e^H b, ||p||^2
     ff se = ff{0.f, 0.f}, bb = ff{0.f, 0.f}, sp = ff{0.f, 0.f};
     ffc eb = ffc_zero();
@@ -268,7 +273,7 @@ k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __r
       ek[j] = make_float2(0.f, 0.f);
       bk[j] = ffc_zero();
       if (k < n) {
-        ek[j] = exp_ikz32f(kz, P.zy[k] - P.zy_min);
+        ek[j] = exp_mode_ff(prop, kz, ff{P.zyd_f[k].x, P.zyd_f[k].y});
         const long long at = ((long long)om * n + k) * N2 + nu;
         if (wt64) {
           bk[j] = ffc_from(wt64[at]);  // W~ in FP64 on the truncated-SVD route
@@ -285,7 +290,7 @@ k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __r
 #pragma unroll
     for (int j = 0; j < RK; ++j) {
       const int l = lane + 32 * j;
-      pl[j] = l < m ? exp_ikz32f(kz, ztop - (P.z1 + (l + 0.5) * P.hz)) : make_float2(0.f, 0.f);
+      pl[j] = l < m ? exp_mode_ff(prop, kz, ff_mul_f(hz, (float)(m - 1 - l))) : make_float2(0.f, 0.f);
       sp = ff_add(sp, ff_add(two_prod(pl[j].x, pl[j].x), two_prod(pl[j].y, pl[j].y)));
     }
     se = ff_warp_sum(se);
@@ -313,11 +318,12 @@ k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __r
         coef = ffc{ff_div(beta.re, tr), ff_div(beta.im, tr)};
       } else {
         if (P.alpha_mode == 1) {
+          const double s2 = ldexp((double)smf * (double)smf, 2 * ns);
           const double an = P.alpha_given[om] * rcp64(s2);  // alpha / s^2
           alpha = ff_from(an < 1e30 ? an : 1e30);  // beyond: V~ is 0 to FP32 precision
         } else {
           const ff c = ff_div(ffc_abs2(eb), se);  // |e^H b|^2 / ||e||^2
-          const ff afl = ff_mul(ff_from(P.alpha_rel), tr);
+          const ff afl = ff_mul(ff{P.alpha_rel_f.x, P.alpha_rel_f.y}, tr);
           const ff rf = ff_div(afl, ff_add(tr, afl));
           if (!ff_gt(dnu2, ff_add(ff_mul(ff_mul(rf, rf), c), pres))) {
             alpha = afl;
@@ -353,8 +359,8 @@ k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __r
       qz = make_float2(__shfl_sync(0xffffffffu, qz.x, src), __shfl_sync(0xffffffffu, qz.y, src));
     }
     const float2 cf = ffc_to_f2(coef);
-    const float gf = (float)gd;
-    const float a2 = (float)(2.0 * kz.y * P.hz);  // evanescent: 2a
+    const float gf = gdf.hi + gdf.lo;
+    const float a2 = 2.f * ((kz.hi + kz.lo) * (hz.hi + hz.lo));  // evanescent: 2a
     const float den_e = prop ? 1.f : expm1f(-a2);  // q^2 - 1
     float2* out = prof + ((long long)om * N2 + i) * 2 * m;
     const float n2 = (float)N2;
@@ -378,8 +384,9 @@ k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __r
         // gamma x: gamma = -i g (propagating), -g (evanescent)
         float2 u = prop ? make_float2(gf * x.y, -gf * x.x) : make_float2(-gf * x.x, -gf * x.y);
         if (nu == 0 && !P.incident) {  // the plane wave's U~0 = N^2 exp(-i k0 z'_l)
-          const float2 w = exp_ikz32f(make_double2(k0, 0.0), -(P.z1 + (l + 0.5) * P.hz));
-          u = make_float2(u.x + n2 * w.x, u.y + n2 * w.y);
+          const ff zl = ff_add(ff{P.z1_f.x, P.z1_f.y}, ff_mul_f(hz, (float)l + 0.5f));
+          const float2 w = exp_mode_ff(true, ff{P.k0_f[om].x, P.k0_f[om].y}, zl);  // e^{+i k0 z'_l}
+          u = make_float2(u.x + n2 * w.x, u.y - n2 * w.y);
         }
         overflow |= !(isfinite(v.x) && isfinite(v.y) && isfinite(u.x) && isfinite(u.y));
         out[l] = v;
@@ -388,7 +395,9 @@ k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __r
     }
     if (__any_sync(0xffffffffu, overflow)) ++n_bad;
     if (lane == 0 && alpha_out)
-      alpha_out[om * N2 + nu] = zeroed ? INFINITY : (P.regularizer == 1 ? 0.0 : s2 * ff_to(alpha));
+      alpha_out[om * N2 + nu] =
+          zeroed ? INFINITY
+                 : (P.regularizer == 1 ? 0.0 : ldexp((double)smf * (double)smf, 2 * ns) * ff_to(alpha));
   }
   if (lane == 0) {
     if (n_floor) atomicAdd(ctr + C_ALPHA_FLOOR, n_floor);
