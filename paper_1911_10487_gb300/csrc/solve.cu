@@ -117,16 +117,36 @@ k_classify_flags(Problem P, const double* __restrict__ norms, const double* __re
   __shared__ long long thr_bits;
   __shared__ unsigned cm[NWC];
   __shared__ int wc[CT / 32], wg[CT / 32];
+  __shared__ double psum[CT / 32];
   if (threadIdx.x < NWC) cm[threadIdx.x] = 0u;
-  if (threadIdx.x < 32) {
+  {
     // ||W||^2 = sum_nu ||W~_nu||^2 / N^2 (Parseval): the block partial sums of the
-    // norms kernel, lane-strided then a tree (the same order in every block)
+    // norms kernel, thread-strided (up to eight loads of a thread in flight together),
+    // then a tree over the lanes and the warps (the same order in every block)
     double s = 0.0;
-    for (int i = lane; i < n_partial; i += 32) s += partial[(long long)om * n_partial + i];
+    for (int i0 = threadIdx.x; i0 < n_partial; i0 += 8 * CT) {
+      double v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = i0 + t * CT;
+        v[t] = i < n_partial ? partial[(long long)om * n_partial + i] : 0.0;
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) s += v[t];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) psum[wid] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = lane < CT / 32 ? psum[lane] : 0.0;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
-      const double wnorm = sqrt(s / (double)N2);
-      const double dnu = P.tau * fmax(P.delta, P.delta_floor) * wnorm;
+      // ||W|| = sqrt(s / N^2) by the Newton reciprocal square root (no FP64 division or
+      // square root on this block's critical path); every block computes it alike
+      const double sn = s * P.inv_n2;
+      const double wnorm = (sn > 0.0 && isfinite(sn)) ? sn * rsqrt64(sn) : sqrt(sn);
+      const double dnu = P.dscale * wnorm;
       if (b == 0) dnu_out[om] = dnu;
       // a non-finite ||W|| (W holds a NaN or Inf, counted by the norms kernel) leaves
       // delta_nu undefined: no mode passes the test
@@ -235,19 +255,32 @@ k_classify_scatter(Problem P, const unsigned* __restrict__ flagbits, const int* 
     int gz = 0;
     for (int i = lane; i < CB; i += 32) gz += blkgz[om * CB + i];
     for (int o = 16; o > 0; o >>= 1) gz += __shfl_xor_sync(0xffffffffu, gz, o);
+    // OR of the blocks' column masks: lanes i and i + 32 load every word of blocks i and
+    // i + 32 (all these loads in flight together), then one warp reduction per word
+    static_assert(NWC <= 8 && 64 >= (MAX_N * MAX_N + CMB - 1) / CMB, "column words and blocks of one warp");
+    const int nw = (N + 31) >> 5;
+    unsigned cw[NWC];
+#pragma unroll
+    for (int w = 0; w < NWC; ++w) {
+      unsigned a = 0u;
+      if (w < nw) {
+        if (lane < CB) a |= colblk[((long long)om * CB + lane) * NWC + w];
+        if (lane + 32 < CB) a |= colblk[((long long)om * CB + lane + 32) * NWC + w];
+      }
+      cw[w] = a;
+    }
     int base = 0;
-    for (int j0 = 0; j0 < N; j0 += 32) {
-      // OR of the blocks' column masks: lane i loads block i's (the loads in flight
-      // together), then a warp reduction
-      unsigned cmw = 0u;
-      for (int i = lane; i < CB; i += 32) cmw |= colblk[((long long)om * CB + i) * NWC + (j0 >> 5)];
-      cmw = __reduce_or_sync(0xffffffffu, cmw);
-      if (j0 == 0) cmw |= 1u;  // the incident plane wave lives at nu = 0
-      const int j = j0 + lane;
-      const bool f = j < N && (cmw >> lane & 1u);
-      const unsigned bal = __ballot_sync(0xffffffffu, f);
-      if (f) cols[om * N + base + __popc(bal & ((1u << lane) - 1u))] = j;
-      base += __popc(bal);
+#pragma unroll
+    for (int w = 0; w < NWC; ++w) {
+      if (w < nw) {
+        unsigned cmw = __reduce_or_sync(0xffffffffu, cw[w]);
+        if (w == 0) cmw |= 1u;  // the incident plane wave lives at nu = 0
+        const int j = 32 * w + lane;
+        const bool f = j < N && (cmw >> lane & 1u);
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (f) cols[om * N + base + __popc(bal & ((1u << lane) - 1u))] = j;
+        base += __popc(bal);
+      }
     }
     if (lane == 0) {
       const int total = total_s;
@@ -372,7 +405,8 @@ k_classify_fused(Problem P, const cx<R>* __restrict__ wt, double* __restrict__ p
     for (int i = lane; i < CB; i += 32) t += __ldcg(partial + om * CB + i);
     t = warp_sum(t);
     if (lane == 0) {
-      const double dnu = P.tau * fmax(P.delta, P.delta_floor) * sqrt(t / (double)N2);
+      const double sn = t * P.inv_n2;  // as k_classify_flags
+      const double dnu = P.dscale * ((sn > 0.0 && isfinite(sn)) ? sn * rsqrt64(sn) : sqrt(sn));
       if (b == 0) dnu_out[om] = dnu;
       // a non-finite ||W|| (W holds a NaN or Inf) leaves delta_nu undefined: no mode passes
       thr_s = isfinite(dnu) ? dnu * dnu : INFINITY;
