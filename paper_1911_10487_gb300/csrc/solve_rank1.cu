@@ -202,18 +202,35 @@ k_solve_rank1(Problem P, const double2* __restrict__ wt, const int* __restrict__
 // problem's constants; FP64 is left to the conversion of delta_nu and to alpha as an
 // output: at the FP64 rate of this GPU (one warp instruction per 64 cycles) the FP64
 // form of this kernel spends most of its time on FP64 set-up, sums, root and scans.
-// e^{i k_z d} from two-float |k_z| and d: propagating, the phase |k_z| d reduced by
-// the nearest multiple of 2 pi in two-float and its sine and cosine in FP32;
-// evanescent, e^{-|k_z| d} from the FP32 exponential of the leading part and the first
-// order of the trailing part
+// cos and sin of y, |y| <= pi/4 (+ rounding): their Taylor series to y^10 and y^9
+// (truncation below 2e-9), Horner form
+__device__ __forceinline__ float2 cos_sin_octant(float y) {
+  const float y2 = y * y;
+  const float c = fmaf(y2, fmaf(y2, fmaf(y2, fmaf(y2, fmaf(y2, -2.75573192e-7f, 2.48015873e-5f), -1.38888889e-3f),
+                                       4.16666667e-2f), -0.5f), 1.f);
+  const float sn = y * fmaf(y2, fmaf(y2, fmaf(y2, fmaf(y2, 2.75573192e-6f, -1.98412698e-4f), 8.33333333e-3f),
+                                     -1.66666667e-1f), 1.f);
+  return make_float2(c, sn);
+}
+
+// e^{i k_z d} from two-float |k_z| and d: propagating, the phase x = |k_z| d less the
+// nearest multiple q of pi/2 in two-float (Cody-Waite with a two-float pi/2), the
+// octant's cosine and sine by their series, then the quarter turns q; evanescent,
+// e^{-|k_z| d} from the FP32 exponential of the leading part and the first order of
+// the trailing part.  Short straight-line code: each of the kernel's calls is inlined
+// and runs once per mode, so its size matters (instruction fetch).
 __device__ __forceinline__ float2 exp_mode_ff(bool prop, ff kz, ff d) {
   const ff x = ff_mul(kz, d);
   if (prop) {
-    const float n = rintf(x.hi * 0.159154943f);
-    const ff red = ff_sub(ff_sub(x, two_prod(n, 6.28318548f)), two_prod(n, -1.74845553e-7f));
-    float sn, cs;
-    sincosf(red.hi + red.lo, &sn, &cs);
-    return make_float2(cs, sn);
+    const float q = rintf(x.hi * 0.636619772f);  // 2 / pi
+    const ff red = ff_sub(ff_sub(x, two_prod(q, 1.57079637f)), two_prod(q, -4.37113883e-8f));
+    const float2 cs = cos_sin_octant(red.hi + red.lo);
+    switch ((int)q & 3) {
+      case 0: return cs;
+      case 1: return make_float2(-cs.y, cs.x);
+      case 2: return make_float2(-cs.x, -cs.y);
+      default: return make_float2(cs.y, -cs.x);
+    }
   }
   return make_float2(expf(-x.hi) * (1.f - x.lo), 0.f);
 }
@@ -293,10 +310,16 @@ k_solve_rank1_mixed(Problem P, const float2* __restrict__ wt, const double2* __r
       pl[j] = l < m ? exp_mode_ff(prop, kz, ff_mul_f(hz, (float)(m - 1 - l))) : make_float2(0.f, 0.f);
       sp = ff_add(sp, ff_add(two_prod(pl[j].x, pl[j].x), two_prod(pl[j].y, pl[j].y)));
     }
-    se = ff_warp_sum(se);
-    sp = ff_warp_sum(sp);
-    bb = ff_warp_sum(bb);
-    eb = ffc_warp_sum(eb);
+    // the four warp sums together: one loop, their shuffles and additions interleaved
+#pragma unroll 1
+    for (int o = 16; o > 0; o >>= 1) {
+      const ff a = ff_shfl_xor(se, o), b2 = ff_shfl_xor(sp, o), c2 = ff_shfl_xor(bb, o);
+      const ffc d = ffc_shfl_xor(eb, o);
+      se = ff_add(se, a);
+      sp = ff_add(sp, b2);
+      bb = ff_add(bb, c2);
+      eb = ffc_add(eb, d);
+    }
     const ff tr = ff_mul(se, sp);  // tr_n
     const ff dnu = ff_from(dnu_arr[om]);
     const ff dnu2 = ff_mul(dnu, dnu);
