@@ -17,8 +17,8 @@ namespace fl {
 namespace {
 
 // ---- inverse pass 1: gather active profiles, columns (along y) ----------------
-// grid (ceil(N/TC), M, 2 n_omega).  Column chunk `blockIdx.x` of the compact column
-// list of frequency om; field f = 0 (V~) or 1 (U~).  Inactive modes are zero in
+// Column chunk `blockIdx.z` of the compact column list of frequency om (grid below);
+// field f = 0 (V~) or 1 (U~).  Inactive modes are zero in
 // V~ and equal the incident field U~0 in U~; the plane wave exp(-i k0 z) has
 // U~0 = N^2 exp(-i k0 z'_l) at nu = 0 and zero elsewhere.
 template <typename R, int N, int T>
@@ -31,10 +31,13 @@ k_ifft_cols_gather(Problem P, const cx<R>* __restrict__ prof, const int* __restr
   constexpr int TC = tile_cols<R, T>();
   constexpr int E = N * TC;
   constexpr int PER = (E + THREADS - 1) / THREADS;
-  const int om = blockIdx.z >> 1, f = blockIdx.z & 1;
-  const int l = blockIdx.y;
+  // grid (M, 2 n_omega, ceil(N / TC)): the column chunk is the slowest index, so that
+  // the chunks that hold active columns (the first ceil(ncol / TC)) are dispatched first
+  // and the rest, which return at once, last
+  const int om = blockIdx.y >> 1, f = blockIdx.y & 1;
+  const int l = blockIdx.x;
   const int nc = ncol[om];
-  const int cb = blockIdx.x * TC;
+  const int cb = blockIdx.z * TC;
   if (cb >= nc) return;
   __shared__ cx<R> buf[E];
   __shared__ cx<R> tw_s[N];
@@ -426,7 +429,7 @@ cudaError_t rec_plane(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStrea
 template <typename R, int N, int T>
 cudaError_t rec_tiled(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream_t s, cudaEvent_t mid) {
   constexpr int TC = tile_cols<R, T>();
-  dim3 g1((N + TC - 1) / TC, P.m, 2 * P.n_omega);
+  dim3 g1(P.m, 2 * P.n_omega, (N + TC - 1) / TC);
   cudaError_t e = launch_pdl(k_ifft_cols_gather<R, N, T>, g1, dim3(THREADS), 0, s, P, (const cx<R>*)w.prof,
                              (const int*)w.slot, (const int*)w.cols, (const int*)w.ncol, w.t2, (const cx<R>*)w.tw);
   if (e != cudaSuccess) return e;
