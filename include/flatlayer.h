@@ -261,7 +261,7 @@ typedef struct {
 /* Many independent problems of uneven size in one call (the paper reconstructs one
    problem at a time; batching is a throughput device).  Each problem is solved
    exactly as by fs_reconstruct; the problems are dealt, largest first, over
-   n_streams (1..16) streams forked from the context's stream and joined back to
+   n_streams (1..64) streams forked from the context's stream and joined back to
    it, so independent problems run concurrently.  The workspace is the sum of the
    problems' workspaces.  Fork and join use events only, so the call can be
    captured into a CUDA graph once the workspace has been sized by an earlier call.

@@ -53,7 +53,7 @@ struct fs_ctx {
   cudaEvent_t ev[7] = {};
   bool timed = false;
   // batches: side streams forked from `stream` and joined back with events
-  static constexpr int MAX_SIDE = 16;
+  static constexpr int MAX_SIDE = 64;
   cudaStream_t side[MAX_SIDE] = {};
   cudaEvent_t fork_ev = nullptr, join_ev[MAX_SIDE] = {};
   // fs_reconstruct_host: the last call captured as a CUDA graph, replayed while the

@@ -2,8 +2,8 @@
 
 For a batch signature (the sorted multiset of (N, M, M1, n_omega) and the
 precision) it times the candidate launch configurations -- the number of
-concurrent streams the batch is dealt over, the resident blocks per SM of the
-per-mode solve, the tile shape of the transform passes (fs_options.fft_tile:
+concurrent streams the batch is dealt over (1 to 64), the resident blocks per SM of
+the dense per-mode solve, the tile shape of the transform passes (fs_options.fft_tile:
 2048-element tiles with radix cap 16, or 1024-element tiles with radix cap 8) and
 the form of the classification (fs_options.classify_single_pass: three kernels, or
 one cooperative launch) --
@@ -17,7 +17,17 @@ from __future__ import annotations
 import json
 import os
 
-CANDIDATES = [(s, b, t, c) for s in (1, 2, 4, 8, 16) for b in (1, 2, 3) for t in (0, 1) for c in (0, 1)]
+STREAMS = (1, 2, 4, 8, 16, 32, 64)
+CANDIDATES = [(s, b, t, c) for s in STREAMS for b in (1, 2, 3) for t in (0, 1) for c in (0, 1)]
+
+
+def candidates(options=None):
+    """The candidate configurations for a batch; resident blocks per SM only matter to
+    the dense per-mode solve, so with the rank-one form (solve_form 1) they are not
+    varied."""
+    if (options or {}).get("solve_form") == 1:
+        return [(s, 1, t, c) for s in STREAMS for t in (0, 1) for c in (0, 1)]
+    return list(CANDIDATES)
 
 
 def signature(items, precision):
@@ -46,7 +56,7 @@ class BatchTuner:
             return tuple(self.cache[key]["config"])
         timings = {}
         with torch.cuda.stream(rc.stream):
-            for s, b, t, c in CANDIDATES:
+            for s, b, t, c in candidates(options):
                 kw = dict(n_streams=s, outs=outs, solve_blocks_per_sm=b, fft_tile=t, classify_single_pass=c,
                           **options)
                 rc.reconstruct_batch(items, precision, **kw)  # warm

@@ -36,8 +36,15 @@ def test_cached_configuration_needs_no_timing(tmp_path):
 
 
 def test_candidates_cover_streams_blocks_per_sm_tiles_and_classification():
-    assert sorted({s for s, _, _, _ in CANDIDATES}) == [1, 2, 4, 8, 16]
+    assert sorted({s for s, _, _, _ in CANDIDATES}) == [1, 2, 4, 8, 16, 32, 64]
     assert sorted({b for _, b, _, _ in CANDIDATES}) == [1, 2, 3]
     assert sorted({t for _, _, t, _ in CANDIDATES}) == [0, 1]
     assert sorted({c for _, _, _, c in CANDIDATES}) == [0, 1]
-    assert len(CANDIDATES) == len(set(CANDIDATES)) == 60
+    assert len(CANDIDATES) == len(set(CANDIDATES)) == 84
+
+
+def test_rank_one_candidates_do_not_vary_the_dense_solve_blocks():
+    from paper_1911_10487_gb300.tuner import candidates
+    r1 = candidates({"solve_form": 1})
+    assert {b for _, b, _, _ in r1} == {1} and len(r1) == len(set(r1)) == 28
+    assert candidates() == CANDIDATES
