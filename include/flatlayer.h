@@ -147,7 +147,7 @@ typedef struct {
                           columns, radix cap 8 (twice the blocks, half the shared memory
                           each).  Applies to the two-pass transforms.  Results agree to
                           rounding.                                                      */
-  int forward_single_pass; /* FS_MIXED: 1 (default): the forward 2D transform of W in one pass,
+  int forward_single_pass; /* FS_MIXED, N <= 128: 1 (default): the forward 2D transform of W in one pass,
                           a cluster of CTAs per data plane exchanging rows and columns
                           through distributed shared memory; 0: two passes (rows, then
                           columns) through global memory.  FS_FP64 always takes the two
@@ -211,11 +211,27 @@ fs_status fs_default_options(fs_options* opts);
    that grows on demand and is released by fs_destroy.  *ctx receives the handle.
    A growth reallocates the workspace: CUDA graphs captured earlier around calls on
    this context refer to the old one and must be captured again after any call that
-   needed more (a larger problem, fs_forward_born, fs_forward). */
+   needed more (a larger problem, fs_forward_born, fs_forward); fs_reserve sizes it up
+   front, fs_workspace_generation tells whether it has moved, and a growth during a
+   capture is refused (FS_EUNSUPPORTED). */
 fs_status fs_create(fs_ctx** ctx, int device, void* stream);
 
 /* Release the context and its workspace (synchronises its stream).  NULL is a no-op. */
 void fs_destroy(fs_ctx* ctx);
+
+/* Grow the context's workspace now (synchronously) to what fs_reconstruct needs for
+   this geometry, frequency count and precision, and make the twiddle tables of N, so
+   that later calls up to that size allocate nothing and can be captured into CUDA
+   graphs.  A call that would have to
+   grow the workspace while the context's stream is being captured returns
+   FS_EUNSUPPORTED instead (nothing is enqueued).  Errors: FS_EINVAL, FS_EUNSUPPORTED,
+   FS_ENOMEM, FS_ECUDA. */
+fs_status fs_reserve(fs_ctx* ctx, const fs_geometry* geom, int n_omega, fs_precision prec);
+
+/* How many times the context's workspace has been reallocated (0 for NULL).  A graph
+   captured when this count was g refers to freed memory once it has changed: compare
+   before replaying. */
+unsigned long long fs_workspace_generation(const fs_ctx* ctx);
 
 /* Message describing the last error of this context (never NULL). */
 const char* fs_last_error(const fs_ctx* ctx);

@@ -14,12 +14,14 @@ from dataclasses import dataclass
 from . import _abi
 from ._abi import (FORWARD_METHODS, FS_FP64, FS_MIXED, FlatLayerError, fs_create, fs_default_options, fs_destroy,
                    fs_forward, fs_forward_born, fs_get_report, fs_last_error, fs_reconstruct, fs_reconstruct_batch,
-                   fs_reconstruct_host, fs_reconstruct_static, fs_sync_status, fs_version, fs_workspace_size,
+                   fs_reconstruct_host, fs_reconstruct_static, fs_reserve, fs_sync_status, fs_version,
+                   fs_workspace_generation, fs_workspace_size,
                    make_geometry, make_options, make_problem)
 
 __all__ = ["Geometry", "KernelPlan", "Reconstructor", "FS_FP64", "FS_MIXED", "FlatLayerError", "fs_create",
            "fs_default_options", "fs_destroy", "fs_forward", "fs_forward_born", "fs_get_report", "fs_last_error", "fs_reconstruct",
-           "fs_reconstruct_batch", "fs_reconstruct_host", "fs_reconstruct_static", "fs_sync_status", "fs_version",
+           "fs_reconstruct_batch", "fs_reconstruct_host", "fs_reconstruct_static", "fs_reserve", "fs_sync_status",
+           "fs_version", "fs_workspace_generation",
            "fs_workspace_size", "make_geometry", "make_options", "make_problem"]
 
 PRECISIONS = {"fp64": FS_FP64, "mixed": FS_MIXED}
@@ -216,3 +218,11 @@ class Reconstructor:
     def sync_status(self) -> int:
         """fs_status of what the kernels of the last reconstruction found (synchronises)."""
         return fs_sync_status(self.ctx)
+
+    def reserve(self, geom: Geometry, n_omega: int, precision: str = "fp64"):
+        """Size the workspace for reconstructions up to this problem (before graph capture)."""
+        fs_reserve(self.ctx, geom.c_struct(), n_omega, PRECISIONS[precision])
+
+    def workspace_generation(self) -> int:
+        """Reallocations of the workspace so far (a captured graph is stale once it changes)."""
+        return fs_workspace_generation(self.ctx)

@@ -24,7 +24,8 @@ EXPORTS = ("fs_version", "fs_default_options", "fs_create", "fs_destroy", "fs_la
            "fs_get_report", "fs_sync_status", "fs_measure_alu_peaks", "fs_eval_reciprocals", "fs_check_bounded_wait", "fs_reconstruct_static", "fs_reconstruct_batch",
            "fs_diff_plan_create", "fs_diff_plan_destroy", "fs_diff_tape_bytes", "fs_diff_scratch_bytes",
            "fs_reconstruct_diff", "fs_reconstruct_vjp", "fs_reconstruct_jvp",
-           "fs_kernel_plan_create", "fs_kernel_plan_destroy", "fs_kernel_plan_bytes", "fs_incident_point_sources")
+           "fs_kernel_plan_create", "fs_kernel_plan_destroy", "fs_kernel_plan_bytes", "fs_incident_point_sources",
+           "fs_reserve", "fs_workspace_generation")
 
 
 class fs_geometry(C.Structure):
@@ -124,6 +125,10 @@ def lib():
         L.fs_get_report.argtypes = [vp, C.POINTER(fs_report)]
         L.fs_sync_status.restype = ip
         L.fs_sync_status.argtypes = [vp]
+        L.fs_reserve.restype = ip
+        L.fs_reserve.argtypes = [vp, C.POINTER(fs_geometry), ip, ip]
+        L.fs_workspace_generation.restype = C.c_ulonglong
+        L.fs_workspace_generation.argtypes = [vp]
         L.fs_kernel_plan_create.restype = ip
         L.fs_kernel_plan_create.argtypes = [vp, C.POINTER(fs_geometry), ip, dp, ip, C.c_double, C.POINTER(vp)]
         L.fs_kernel_plan_destroy.restype = None
@@ -286,6 +291,18 @@ def fs_kernel_plan_bytes(plan) -> int:
 def fs_sync_status(ctx) -> int:
     """Device-side status of the last reconstruction (synchronises); returns the fs_status."""
     return int(lib().fs_sync_status(ctx))
+
+
+def fs_reserve(ctx, geom, n_omega, prec):
+    """Size the context's workspace for fs_reconstruct on this problem (raises on error)."""
+    st = lib().fs_reserve(ctx, C.byref(geom), int(n_omega), int(prec))
+    if st != FS_OK:
+        raise FlatLayerError(st, fs_last_error(ctx))
+
+
+def fs_workspace_generation(ctx) -> int:
+    """Reallocations of the context's workspace so far."""
+    return int(lib().fs_workspace_generation(ctx))
 
 
 def fs_eval_reciprocals(x_ptr, n, out_ptr, stream=0) -> int:

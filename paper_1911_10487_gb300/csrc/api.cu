@@ -44,6 +44,7 @@ struct fs_ctx {
   cudaStream_t stream = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  unsigned long long ws_generation = 0;  // reallocations of ws so far
   void* tw[2][N_SIZES] = {};  // [fp64?][size]
   unsigned long long* ctr = nullptr;
   unsigned long long* ctr_host = nullptr;
@@ -347,6 +348,14 @@ namespace {
 
 fs_status ensure_workspace(fs_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_bytes) return FS_OK;
+  // a growth frees the workspace a graph being captured (or captured before) refers
+  // to: refused during a capture, counted otherwise (fs_workspace_generation)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return fail(ctx, FS_EUNSUPPORTED,
+                "the workspace must grow to %lld bytes during a stream capture: size it first (fs_reserve, or "
+                "an uncaptured call on the largest problem)",
+                (long long)bytes);
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
   if (ctx->ws) cudaFree(ctx->ws);
@@ -358,6 +367,7 @@ fs_status ensure_workspace(fs_ctx* ctx, size_t bytes) {
     return fail(ctx, FS_ENOMEM, "workspace allocation of %lld bytes failed", (long long)bytes);
   }
   ctx->ws_bytes = bytes;
+  ++ctx->ws_generation;
   return FS_OK;
 }
 
@@ -366,6 +376,11 @@ fs_status ensure_twiddles(fs_ctx* ctx, int n, const cx<R>** out) {
   const int fp = sizeof(R) == 8 ? 1 : 0;
   const int si = size_index(n);
   if (!ctx->tw[fp][si]) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      return fail(ctx, FS_EUNSUPPORTED,
+                  "the twiddle table of N=%d must be made during a stream capture: make it first (fs_reserve, or "
+                  "an uncaptured call of that size)", n);
     void* p = nullptr;
     if (cudaMalloc(&p, sizeof(cx<R>) * n) != cudaSuccess) return fail(ctx, FS_ENOMEM, "twiddle table");
     cudaError_t e = launch_twiddles<R>((cx<R>*)p, n, ctx->stream);
@@ -497,6 +512,27 @@ fs_status fs_workspace_size(const fs_geometry* g, int n_omega, fs_precision prec
   *bytes = layout(g->n, g->m, g->m1, n_omega, prec == FS_FP64).total;
   return FS_OK;
 }
+
+extern "C" fs_status fs_reserve(fs_ctx* ctx, const fs_geometry* g, int n_omega, fs_precision prec) {
+  if (!ctx) return FS_EINVAL;
+  if (!g || g->n <= 0 || g->m <= 0 || g->m1 <= 0 || n_omega <= 0 || (prec != FS_FP64 && prec != FS_MIXED))
+    return fail(ctx, FS_EINVAL, "fs_reserve: geometry, n_omega or precision out of range");
+  if (!fft_size_supported(g->n) || g->m > MAX_M || g->m1 > MAX_M1 || n_omega > MAX_OMEGA)
+    return fail(ctx, FS_EUNSUPPORTED, "fs_reserve: N=%d, M=%d, M1=%d, n_omega=%d beyond this build's limits", g->n,
+                g->m, g->m1, n_omega);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  fs_status st = ensure_workspace(ctx, layout(g->n, g->m, g->m1, n_omega, prec == FS_FP64).total);
+  // the twiddle tables of N in both real types (FP64 also serves the mixed truncated-SVD route)
+  const double2* t64;
+  const float2* t32;
+  if (st == FS_OK) st = ensure_twiddles<double>(ctx, g->n, &t64);
+  if (st == FS_OK) st = ensure_twiddles<float>(ctx, g->n, &t32);
+  if (st == FS_OK && (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sync");
+  return st;
+}
+
+extern "C" unsigned long long fs_workspace_generation(const fs_ctx* ctx) { return ctx ? ctx->ws_generation : 0; }
 
 fs_status fs_reconstruct(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, const void* W, const double* omega,
                          int n_omega, double delta, double c0, const fs_options* opts, void* xi, void* c,

@@ -104,3 +104,9 @@ def test_mixed_noise_limit_is_checked_before_any_device_work(abi):
     o = abi.make_options(delta_floor=1e-10, alpha_mode=1, alpha_given=[1e-3])
     assert L.fs_reconstruct_static(C.byref(g), abi.FS_MIXED, None, om, 1, 0.0, 1.0, C.byref(o), None, None,
                                    None) == abi.FS_EINVAL
+
+
+def test_reserve_and_generation_without_a_context(abi):
+    g = abi.make_geometry(32, 16, 0.2, 1.0, [1.3])
+    assert abi.lib().fs_reserve(None, C.byref(g), 1, abi.FS_MIXED) == abi.FS_EINVAL
+    assert abi.fs_workspace_generation(None) == 0

@@ -153,3 +153,38 @@ def test_single_pass_classification_equals_three_kernel_form(rc, name, precision
     assert r1["n_timeouts"] == 0
     from oracle.metrics import rel_l2
     assert rel_l2(x1, x0) <= (1e-12 if precision == "fp64" else 1e-6)
+
+
+def test_workspace_reserve_generation_and_growth_during_capture():
+    """fs_reserve sizes the workspace once (the generation counts the reallocation), calls
+    up to that size allocate nothing, and a call that would grow the workspace while the
+    stream is captured is refused with FS_EUNSUPPORTED instead of freeing memory a graph
+    refers to."""
+    import torch
+    from paper_1911_10487_gb300 import FlatLayerError, Reconstructor
+    from paper_1911_10487_gb300._abi import FS_EUNSUPPORTED
+    rc = Reconstructor(0, stream=torch.cuda.Stream())
+    try:
+        g_small, om_s, W_s, _ = case("r24", 0.01)
+        g_big, om_b, W_b, _ = case("r48", 0.01)
+        gen0 = rc.workspace_generation()
+        rc.reserve(_geom(g_small), len(om_s), "mixed")
+        assert rc.workspace_generation() == gen0 + 1
+        rc.reserve(_geom(g_small), len(om_s), "mixed")  # already large enough
+        assert rc.workspace_generation() == gen0 + 1
+        Ws = torch.from_numpy(np.ascontiguousarray(W_s)).to(rc.device, torch.complex64)
+        Wb = torch.from_numpy(np.ascontiguousarray(W_b)).to(rc.device, torch.complex64)
+        xi = torch.empty((g_big.m, g_big.n, g_big.n), dtype=torch.float32, device=rc.device)
+        with torch.cuda.stream(rc.stream):
+            rc.reconstruct(Ws, list(om_s), _geom(g_small), 0.01, precision="mixed")
+        torch.cuda.synchronize()
+        assert rc.workspace_generation() == gen0 + 1
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=rc.stream):
+            with pytest.raises(FlatLayerError) as ei:
+                rc.reconstruct(Wb, list(om_b), _geom(g_big), 0.01, precision="mixed", out=(xi, None, None))
+        assert ei.value.status == FS_EUNSUPPORTED
+        assert rc.workspace_generation() == gen0 + 1
+        torch.cuda.synchronize()
+    finally:
+        rc.close()

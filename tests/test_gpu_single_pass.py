@@ -8,8 +8,9 @@ two-pass forms, through the C ABI:
                        route the FP32 sums take where they overflow).
 Every combination decides the same active modes and gives xi within FP32 rounding
 (1e-6) of the two-pass form, over the sizes that select each cluster size (1, 2, 4 and 8
-CTAs; N = 96, 192 and 256, whose inverse stays two-pass, for the forward pass), with the
-plane wave and with a given incident field.  Also: the mixed path refuses noise levels
+CTAs; N = 96, whose inverse stays two-pass, for the forward pass; at N = 192 and 256 both
+passes stay two-pass and the options must change nothing), with the plane wave and with a
+given incident field.  Also: the mixed path refuses noise levels
 below its FP32 data resolution (FS_MIXED_MIN_NOISE)."""
 import numpy as np
 import pytest
