@@ -155,6 +155,7 @@ def test_single_pass_classification_equals_three_kernel_form(rc, name, precision
     assert rel_l2(x1, x0) <= (1e-12 if precision == "fp64" else 1e-6)
 
 
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
 def test_workspace_reserve_generation_and_growth_during_capture():
     """fs_reserve sizes the workspace once (the generation counts the reallocation), calls
     up to that size allocate nothing, and a call that would grow the workspace while the
