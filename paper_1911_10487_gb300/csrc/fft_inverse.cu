@@ -104,17 +104,31 @@ template <typename R> __device__ __forceinline__ R quot(R a, R b);
 template <> __device__ __forceinline__ float quot<float>(float a, float b) { return a / b; }
 template <> __device__ __forceinline__ double quot<double>(double a, double b) { return a * rcp64(b); }
 template <typename R> __device__ __forceinline__ R inv_sqrt(R x);
-template <> __device__ __forceinline__ float inv_sqrt<float>(float x) { return 1.0f / sqrtf(x); }
+template <> __device__ __forceinline__ float inv_sqrt<float>(float x) { return rsqrtf(x); }  // <= 2 ulp
 template <> __device__ __forceinline__ double inv_sqrt<double>(double x) { return rsqrt64(x); }
+
+// The recovery pass's tile: for the FP32 large-tile form at N = 2^k, 4096 elements (the
+// V and u rows of 4096 / (2N) rows of X) with radix-16 stages, so that a 128-point row
+// takes two stages (16, 8) with every thread busy in both; otherwise the tile of
+// fs_options.fft_tile
+template <typename R, int N, int T> struct RecTile {
+  static constexpr bool BIG = sizeof(R) == 4 && T == 0 && N % 3 != 0;  // radix-3 sizes: too many registers
+  static constexpr int ELEMS = BIG ? 4096 : Tile<T>::ELEMS;
+  static constexpr int RADIX = BIG ? 16 : Tile<T>::RADIX_RECOVER;
+  static constexpr int SKEW = BIG ? 16 : Tile<T>::SKEW_RECOVER;
+};
+template <typename R, int N, int T> __host__ __device__ constexpr int rec_lines() {
+  return RecTile<R, N, T>::ELEMS / N / 2 > 0 ? RecTile<R, N, T>::ELEMS / N / 2 : 1;
+}
 
 template <typename R, int N, typename A, bool INC, int T>
 __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __restrict__ t2,
                                              const int* __restrict__ cols, const int* __restrict__ ncol,
                                              const cx<R>* __restrict__ u0, cx<R>* buf, const cx<R>* tw_s, A* num,
                                              A* den) {
-  constexpr int LINES = row_lines<N, T>() / 2 > 0 ? row_lines<N, T>() / 2 : 1;
+  constexpr int LINES = rec_lines<R, N, T>();
   constexpr int E = LINES * N;
-  using IX = LayIdx<Lay::ROW, N, 2 * LINES, Tile<T>::SKEW_RECOVER>;  // V~ lines, then U~ lines
+  using IX = LayIdx<Lay::ROW, N, 2 * LINES, RecTile<R, N, T>::SKEW>;  // V~ lines, then U~ lines
   constexpr int PER = (E + THREADS - 1) / THREADS;
   const int M = P.m;
   const long long N2 = (long long)N * N;
@@ -139,7 +153,7 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
       }
     }
     __syncthreads();
-    fft_lines<R, N, true, 2 * LINES, THREADS, Lay::ROW, Tile<T>::RADIX_RECOVER, Tile<T>::SKEW_RECOVER>(buf, tw_s);
+    fft_lines<R, N, true, 2 * LINES, THREADS, Lay::ROW, RecTile<R, N, T>::RADIX, RecTile<R, N, T>::SKEW>(buf, tw_s);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const int e = threadIdx.x + p * THREADS;
@@ -218,10 +232,10 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
                     R* __restrict__ cout, unsigned long long* __restrict__ ctr, const cx<R>* __restrict__ tw) {
   pdl_wait();
   pdl_trigger();
-  constexpr int LINES = row_lines<N, T>() / 2 > 0 ? row_lines<N, T>() / 2 : 1;
+  constexpr int LINES = rec_lines<R, N, T>();
   constexpr int E = LINES * N;            // elements of one field
   constexpr int PER = (E + THREADS - 1) / THREADS;
-  __shared__ cx<R> buf[LayIdx<Lay::ROW, N, 2 * LINES, Tile<T>::SKEW_RECOVER>::ELEMS];
+  __shared__ cx<R> buf[LayIdx<Lay::ROW, N, 2 * LINES, RecTile<R, N, T>::SKEW>::ELEMS];
   __shared__ cx<R> tw_s[N];
   __shared__ unsigned red[THREADS / 32];
   load_twiddles<R, N>(tw_s, tw);
@@ -434,7 +448,7 @@ cudaError_t rec_tiled(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStrea
                              (const int*)w.slot, (const int*)w.cols, (const int*)w.ncol, w.t2, (const cx<R>*)w.tw);
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
-  constexpr int LINES = row_lines<N, T>() / 2 > 0 ? row_lines<N, T>() / 2 : 1;
+  constexpr int LINES = rec_lines<R, N, T>();
   const long long nrows = (long long)P.m * N;
   const dim3 gr((unsigned)((nrows + LINES - 1) / LINES));
   if (w.u0)
