@@ -384,6 +384,9 @@ fs_status ensure_twiddles(fs_ctx* ctx, int n, const cx<R>** out) {
     void* p = nullptr;
     if (cudaMalloc(&p, sizeof(cx<R>) * n) != cudaSuccess) return fail(ctx, FS_ENOMEM, "twiddle table");
     cudaError_t e = launch_twiddles<R>((cx<R>*)p, n, ctx->stream);
+    // complete before any transform: those read the table before their programmatic
+    // dependency wait
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) { cudaFree(p); return cuda_fail(ctx, e, "twiddles"); }
     ctx->tw[fp][si] = p;
   }

@@ -72,8 +72,9 @@ template <typename R> __host__ __device__ __forceinline__ cx<R> czero() { return
 // Programmatic dependent launch.  The kernels of one reconstruction are launched
 // with programmatic stream serialisation: a kernel may become resident while its
 // predecessor is still running, and waits at pdl_wait() -- before its first
-// global-memory access -- until the predecessor grid has completed and its writes
-// are visible.  pdl_trigger() lets the successor launch as soon as every block of
+// global-memory access other than reads of the constant twiddle tables (made and
+// synchronised once, before any reconstruction) -- until the predecessor grid has
+// completed and its writes are visible.  pdl_trigger() lets the successor launch as soon as every block of
 // this grid has started.  Launched without the attribute, both are no-ops.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }

@@ -44,8 +44,6 @@ template <typename R, int N>
 __global__ void __launch_bounds__(THREADS)
 k_fft2_plane(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, const cx<R>* __restrict__ tw,
              unsigned* __restrict__ clear, int nclear) {
-  pdl_wait();
-  pdl_trigger();
   constexpr int C = plane_cluster<N>(), RB = N / C;
   using IA = LayIdx<Lay::ROW, N, RB, 16>;  // this CTA's rows
   constexpr int E = RB * N;                // elements of the row tile and of the column tile
@@ -55,9 +53,11 @@ k_fft2_plane(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, const cx<R>*
   cx<R>* colt = rows + IA::ELEMS;  // column tile: element i of column b at i RB + b
   cx<R>* tw_s = colt + E;
   const unsigned r = cluster_rank();
+  load_twiddles<R, N>(tw_s, tw);  // a constant table: read while the predecessor drains
+  pdl_wait();
+  pdl_trigger();
   if (clear && blockIdx.x == 0 && blockIdx.y == 0)
     for (int i = threadIdx.x; i < nclear; i += THREADS) clear[i] = 0u;
-  load_twiddles<R, N>(tw_s, tw);
   const long long pb = (long long)blockIdx.y * N * N;
   const cx<R>* src = in + pb + (long long)r * E;
   cx<R> v[PER];

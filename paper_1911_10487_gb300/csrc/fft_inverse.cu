@@ -26,11 +26,14 @@ __global__ void __launch_bounds__(THREADS)
 k_ifft_cols_gather(Problem P, const cx<R>* __restrict__ prof, const int* __restrict__ slot,
                    const int* __restrict__ cols, const int* __restrict__ ncol,
                    cx<R>* __restrict__ t2, const cx<R>* __restrict__ tw) {
-  pdl_wait();
-  pdl_trigger();
   constexpr int TC = tile_cols<R, T>();
   constexpr int E = N * TC;
   constexpr int PER = (E + THREADS - 1) / THREADS;
+  __shared__ cx<R> buf[E];
+  __shared__ cx<R> tw_s[N];
+  load_twiddles<R, N>(tw_s, tw);  // a constant table: read while the predecessor drains
+  pdl_wait();
+  pdl_trigger();
   // grid (M, 2 n_omega, ceil(N / TC)): the column chunk is the slowest index, so that
   // the chunks that hold active columns (the first ceil(ncol / TC)) are dispatched first
   // and the rest, which return at once, last
@@ -39,9 +42,6 @@ k_ifft_cols_gather(Problem P, const cx<R>* __restrict__ prof, const int* __restr
   const int nc = ncol[om];
   const int cb = blockIdx.z * TC;
   if (cb >= nc) return;
-  __shared__ cx<R> buf[E];
-  __shared__ cx<R> tw_s[N];
-  load_twiddles<R, N>(tw_s, tw);
   const long long N2 = (long long)N * N;
   const int M = P.m;
   // element e = t + p THREADS is row i = e / TC of line b = t mod TC (THREADS is a
@@ -110,22 +110,27 @@ template <> __device__ __forceinline__ double inv_sqrt<double>(double x) { retur
 // The recovery pass's tile: for the FP32 large-tile form at N = 2^k, 4096 elements (the
 // V and u rows of 4096 / (2N) rows of X) with radix-16 stages, so that a 128-point row
 // takes two stages (16, 8) with every thread busy in both; otherwise the tile of
-// fs_options.fft_tile
+// fs_options.fft_tile.  MINB: CTAs per SM the register allocation is held to -- three
+// for the default tile at N = 2^k (at most 80 registers a thread, no or a few bytes of
+// spill; measured 1 us faster at 128^2 than two CTAs of 102), one elsewhere (a factor
+// 3, or the small tile in FP64, would spill).
 template <typename R, int N, int T> struct RecTile {
   static constexpr bool BIG = sizeof(R) == 4 && T == 0 && N % 3 != 0;  // radix-3 sizes: too many registers
   static constexpr int ELEMS = BIG ? 4096 : Tile<T>::ELEMS;
   static constexpr int RADIX = BIG ? 16 : Tile<T>::RADIX_RECOVER;
   static constexpr int SKEW = BIG ? 16 : Tile<T>::SKEW_RECOVER;
+  static constexpr int MINB = T == 0 && N % 3 != 0 ? 3 : 1;
 };
 template <typename R, int N, int T> __host__ __device__ constexpr int rec_lines() {
   return RecTile<R, N, T>::ELEMS / N / 2 > 0 ? RecTile<R, N, T>::ELEMS / N / 2 : 1;
 }
 
+// filled: the tile is already zero for the first frequency
 template <typename R, int N, typename A, bool INC, int T>
 __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __restrict__ t2,
                                              const int* __restrict__ cols, const int* __restrict__ ncol,
                                              const cx<R>* __restrict__ u0, cx<R>* buf, const cx<R>* tw_s, A* num,
-                                             A* den) {
+                                             A* den, bool filled) {
   constexpr int LINES = rec_lines<R, N, T>();
   constexpr int E = LINES * N;
   using IX = LayIdx<Lay::ROW, N, 2 * LINES, RecTile<R, N, T>::SKEW>;  // V~ lines, then U~ lines
@@ -138,7 +143,8 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
 #pragma unroll
   for (int p = 0; p < PER; ++p) { num[p] = A(0); den[p] = A(0); }
   for (int om = 0; om < P.n_omega; ++om) {
-    for (int e = threadIdx.x; e < IX::ELEMS; e += THREADS) buf[e] = czero<R>();
+    if (om > 0 || !filled)
+      for (int e = threadIdx.x; e < IX::ELEMS; e += THREADS) buf[e] = czero<R>();
     __syncthreads();
     const int nc = ncol[om];
     const int* cl = cols + om * N;
@@ -226,27 +232,31 @@ __device__ __forceinline__ void recover_epilogue(const Problem& P, const R* num,
 // INC: u0 (the incident field on X) is given and added to u; otherwise the transform
 // already holds the plane wave
 template <typename R, int N, bool INC, int T>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, (RecTile<R, N, T>::MINB))
 k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restrict__ cols,
                     const int* __restrict__ ncol, const cx<R>* __restrict__ u0, R* __restrict__ xi,
                     R* __restrict__ cout, unsigned long long* __restrict__ ctr, const cx<R>* __restrict__ tw) {
-  pdl_wait();
-  pdl_trigger();
   constexpr int LINES = rec_lines<R, N, T>();
   constexpr int E = LINES * N;            // elements of one field
   constexpr int PER = (E + THREADS - 1) / THREADS;
-  __shared__ cx<R> buf[LayIdx<Lay::ROW, N, 2 * LINES, RecTile<R, N, T>::SKEW>::ELEMS];
+  using IX = LayIdx<Lay::ROW, N, 2 * LINES, RecTile<R, N, T>::SKEW>;
+  __shared__ cx<R> buf[IX::ELEMS];
   __shared__ cx<R> tw_s[N];
   __shared__ unsigned red[THREADS / 32];
+  // the constant twiddle table and the cleared tile of the first frequency, while the
+  // predecessor drains
   load_twiddles<R, N>(tw_s, tw);
+  for (int e = threadIdx.x; e < IX::ELEMS; e += THREADS) buf[e] = czero<R>();
+  pdl_wait();
+  pdl_trigger();
   const long long nrows = (long long)P.m * N;
   const long long row0 = (long long)blockIdx.x * LINES;
   R num[PER], den[PER];
-  if (P.sums64 || recover_pass<R, N, R, INC, T>(P, t2, cols, ncol, u0, buf, tw_s, num, den)) {
+  if (P.sums64 || recover_pass<R, N, R, INC, T>(P, t2, cols, ncol, u0, buf, tw_s, num, den, true)) {
     // the sums left the range of R (|u| |V| beyond FP32 for huge evanescent
     // profiles): redo this block with FP64 sums; xi itself is in range
     double nd[PER], dd[PER];
-    recover_pass<R, N, double, INC, T>(P, t2, cols, ncol, u0, buf, tw_s, nd, dd);
+    recover_pass<R, N, double, INC, T>(P, t2, cols, ncol, u0, buf, tw_s, nd, dd, P.sums64 != 0);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const bool g = !(dd[p] >= (double)P.n_omega * P.eps_u * P.eps_u);
@@ -365,8 +375,6 @@ k_ifft2_plane_recover(Problem P, const cx<R>* __restrict__ prof, const int* __re
                       const int* __restrict__ cols, const int* __restrict__ ncol, const cx<R>* __restrict__ u0,
                       R* __restrict__ xi, R* __restrict__ cout, unsigned long long* __restrict__ ctr,
                       const cx<R>* __restrict__ tw) {
-  pdl_wait();
-  pdl_trigger();
   constexpr int C = plane_cluster<N>(), RB = N / C;
   constexpr int E = RB * N;
   constexpr int PER = (E + THREADS - 1) / THREADS;
@@ -378,7 +386,9 @@ k_ifft2_plane_recover(Problem P, const cx<R>* __restrict__ prof, const int* __re
   cx<R>* tw_s = ct + REC_CL * N;
   __shared__ unsigned red[THREADS / 32];
   __shared__ unsigned vote[8];
-  load_twiddles<R, N>(tw_s, tw);
+  load_twiddles<R, N>(tw_s, tw);  // a constant table: read while the predecessor drains
+  pdl_wait();
+  pdl_trigger();
   const unsigned r = cluster_rank();
   const int l = blockIdx.y;
   const long long row0 = (long long)l * N + (long long)r * RB;

@@ -64,13 +64,13 @@ template <typename R, int N, bool INV, typename TI = cx<R>, int T = 0>
 __global__ void __launch_bounds__(THREADS)
 k_fft_rows(const TI* __restrict__ in, cx<R>* __restrict__ out, long long nrows,
            const cx<R>* __restrict__ tw, R scale) {
-  pdl_wait();
-  pdl_trigger();
   constexpr int LINES = row_lines<N, T>();
   using IX = LayIdx<Lay::ROW, N, LINES, Tile<T>::SKEW_ROWS>;
   __shared__ cx<R> buf[IX::ELEMS];
   __shared__ cx<R> tw_s[N];
-  load_twiddles<R, N>(tw_s, tw);
+  load_twiddles<R, N>(tw_s, tw);  // a constant table: read while the predecessor drains
+  pdl_wait();
+  pdl_trigger();
   const long long row0 = (long long)blockIdx.x * LINES;
   const long long base = row0 * N;
   const long long limit = nrows * N;
@@ -97,15 +97,15 @@ k_fft_rows(const TI* __restrict__ in, cx<R>* __restrict__ out, long long nrows,
 template <typename R, int N, bool INV, int T = 0>
 __global__ void __launch_bounds__(THREADS)
 k_fft_cols(cx<R>* __restrict__ data, const cx<R>* __restrict__ tw, unsigned* __restrict__ clear, int nclear) {
-  pdl_wait();
-  pdl_trigger();
-  if (clear && blockIdx.x == 0 && blockIdx.y == 0)
-    for (int i = threadIdx.x; i < nclear; i += THREADS) clear[i] = 0u;
   constexpr int TC = tile_cols<R, T>();
   constexpr int E = N * TC;
   __shared__ cx<R> buf[E];
   __shared__ cx<R> tw_s[N];
-  load_twiddles<R, N>(tw_s, tw);
+  load_twiddles<R, N>(tw_s, tw);  // a constant table: read while the predecessor drains
+  pdl_wait();
+  pdl_trigger();
+  if (clear && blockIdx.x == 0 && blockIdx.y == 0)
+    for (int i = threadIdx.x; i < nclear; i += THREADS) clear[i] = 0u;
   const int c0 = blockIdx.x * TC;
   cx<R>* pl = data + (long long)blockIdx.y * N * N;
   for (int e = threadIdx.x; e < E; e += THREADS) {
