@@ -48,10 +48,15 @@ STAGE_KERNELS = {"fft_x_forward": "k_fft2_plane<float>", "fft_y_forward_norms": 
                  "classify": "k_classify_flags + k_classify_scatter", "ifft_y_gather": "k_ifft_cols_gather<float>",
                  "ifft_x_recover": "k_ifft_rows_recover<float>"}
 HEAD_FORM = 1  # the headline's per-mode solver: the rank-one closed form
-# kernels of one mixed step: 2D FFT (one pass), mode norms, classify (flags, scatter),
-# solve, gather + y-IFFT, x-IFFT + recover; the plain FP64 path transforms in two passes
+# kernels of one mixed step: 2D FFT (one pass at N <= 128, two beyond), mode norms,
+# classify (flags, scatter), solve, gather + y-IFFT, x-IFFT + recover; the plain FP64
+# path transforms in two passes
 KERNELS_PER_STEP_MIXED = 7
 KERNELS_PER_STEP = 8
+
+
+def mixed_kernels(n):
+    return KERNELS_PER_STEP_MIXED + (1 if n > 128 else 0)
 
 
 def peaks():
@@ -538,7 +543,7 @@ def run_batch(args, local, flush, world):
            "voxel_freqs": vox, "steps": K, "cuda_graph": True, "unit": UNIT,
            "l2": "flushed (256 MiB write) before every timed step",
            "mixed": res["mixed"], "fp64": res["fp64"],
-           "gpu_launches_per_step": KERNELS_PER_STEP_MIXED * len(wls)}
+           "gpu_launches_per_step": sum(mixed_kernels(wl.n) for wl in wls)}
     # smallest problem of the batch against the oracle (a parity spot check at full batch)
     j = min(range(len(wls)), key=lambda i: wls[i].voxel_freqs * wls[i].m1)
     out["spot_problem"] = wls[j].name

@@ -125,7 +125,12 @@ template <typename R, int N, int T> __host__ __device__ constexpr int rec_lines(
   return RecTile<R, N, T>::ELEMS / N / 2 > 0 ? RecTile<R, N, T>::ELEMS / N / 2 : 1;
 }
 
-// filled: the tile is already zero for the first frequency
+// filled: the tile is already zero for the first frequency.  In FP64 without a given
+// incident field the sums are taken of the unscaled transforms (N^2 V, N^2 u): xi is
+// their quotient either way, and the guard on sum |u|^2 is scaled instead
+// (Problem::u_guard_raw), which saves four FP64 products per voxel and frequency.
+template <typename R, bool INC> __host__ __device__ constexpr bool raw_sums() { return sizeof(R) == 8 && !INC; }
+
 template <typename R, int N, typename A, bool INC, int T>
 __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __restrict__ t2,
                                              const int* __restrict__ cols, const int* __restrict__ ncol,
@@ -139,7 +144,7 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
   const long long N2 = (long long)N * N;
   const long long nrows = (long long)M * N;
   const long long row0 = (long long)blockIdx.x * LINES;
-  const R scale = R(1.0 / (double)N2);
+  const R scale = raw_sums<R, INC>() ? R(1) : R(1.0 / (double)N2);
 #pragma unroll
   for (int p = 0; p < PER; ++p) { num[p] = A(0); den[p] = A(0); }
   for (int om = 0; om < P.n_omega; ++om) {
@@ -164,8 +169,12 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
     for (int p = 0; p < PER; ++p) {
       const int e = threadIdx.x + p * THREADS;
       if (e < E) {
-        const cx<R> v = scale * buf[IX::at(e / N, e % N)];
-        cx<R> u = scale * buf[IX::at(LINES + e / N, e % N)];
+        cx<R> v = buf[IX::at(e / N, e % N)];
+        cx<R> u = buf[IX::at(LINES + e / N, e % N)];
+        if constexpr (!raw_sums<R, INC>()) {
+          v = scale * v;
+          u = scale * u;
+        }
         if (INC) {  // the given incident field (the transform holds U~ - U~0)
           const long long r = row0 + e / N;
           if (r < nrows) u = u + u0[((long long)om * M + r / N) * N2 + (r % N) * N + (e % N)];
@@ -184,13 +193,13 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
 
 // xi and c of the elements e = threadIdx.x + p THREADS < E of rows row0 + e / N (below
 // nrows) from the least-squares sums, and the counters of guarded, NaN-c and non-finite
-// voxels (almost always zero, so one barrier decides)
+// voxels (almost always zero, so one barrier decides).  guard: the least den of a kept
+// voxel (host-derived: no FP64 division on the device)
 template <typename R, int PER, int N>
-__device__ __forceinline__ void recover_epilogue(const Problem& P, const R* num, const R* den, long long row0,
-                                                 long long nrows, int E, R* __restrict__ xi,
+__device__ __forceinline__ void recover_epilogue(const Problem& P, const R* num, const R* den, R guard,
+                                                 long long row0, long long nrows, int E, R* __restrict__ xi,
                                                  R* __restrict__ cout, unsigned long long* __restrict__ ctr,
                                                  unsigned* red) {
-  const R guard = R(P.u_guard);  // host-derived: no FP64 division on the device
   const R inv_c02 = R(P.inv_c02);
   unsigned n_guard = 0, n_nan = 0, n_bad = 0;
 #pragma unroll
@@ -252,6 +261,8 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
   const long long nrows = (long long)P.m * N;
   const long long row0 = (long long)blockIdx.x * LINES;
   R num[PER], den[PER];
+  const double gd = raw_sums<R, INC>() ? P.u_guard_raw : P.u_guard;
+  R guard = R(gd);
   if (P.sums64 || recover_pass<R, N, R, INC, T>(P, t2, cols, ncol, u0, buf, tw_s, num, den, true)) {
     // the sums left the range of R (|u| |V| beyond FP32 for huge evanescent
     // profiles): redo this block with FP64 sums; xi itself is in range
@@ -259,12 +270,13 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
     recover_pass<R, N, double, INC, T>(P, t2, cols, ncol, u0, buf, tw_s, nd, dd, P.sums64 != 0);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
-      const bool g = !(dd[p] >= (double)P.n_omega * P.eps_u * P.eps_u);
+      const bool g = !(dd[p] >= gd);
       num[p] = g ? R(0) : R(nd[p] / dd[p]);
       den[p] = g ? R(0) : R(1);
     }
+    guard = R(0.5);  // den is now 1 (kept) or 0 (guarded)
   }
-  recover_epilogue<R, PER, N>(P, num, den, row0, nrows, E, xi, cout, ctr, red);
+  recover_epilogue<R, PER, N>(P, num, den, guard, row0, nrows, E, xi, cout, ctr, red);
 }
 
 // ---- single-pass inverse transform and recovery: one X plane per cluster ---------
@@ -433,7 +445,9 @@ k_ifft2_plane_recover(Problem P, const cx<R>* __restrict__ prof, const int* __re
       den[p] = g ? R(0) : R(1);
     }
   }
-  recover_epilogue<R, PER, N>(P, num, den, row0, (long long)P.m * N, E, xi, cout, ctr, red);
+  // after a redo den is 1 (kept) or 0 (guarded)
+  recover_epilogue<R, PER, N>(P, num, den, any ? R(0.5) : R(P.u_guard), row0, (long long)P.m * N, E, xi, cout, ctr,
+                              red);
 }
 
 template <typename R, int N, bool INC>

@@ -51,6 +51,7 @@ struct Problem {
   double k0[MAX_OMEGA], g0[MAX_OMEGA];
   double kn;
   double inv_c02, u_guard;  // c0^-2 and the |u|^2 guard eps_u^2 n_omega of the recovery
+  double u_guard_raw;       // the same guard on the sums of the unscaled transforms: u_guard N^4
   double inv_n2, dscale;    // 1/N^2 and tau max(delta, delta_floor): delta_nu = dscale ||W||
   int sampled;  // 1: the sampled-G kernel of a kernel plan (Work::ktab) replaces the Weyl form
   int incident; // 1: the incident field on X is given (Work::u0) instead of the plane wave
@@ -78,6 +79,7 @@ inline void derive_constants(Problem& P) {
   P.kn = 2.0 * M_PI / P.period;
   P.inv_c02 = 1.0 / (P.c0 * P.c0);
   P.u_guard = P.eps_u * P.eps_u * P.n_omega;
+  P.u_guard_raw = P.u_guard * ((double)P.n * P.n) * ((double)P.n * P.n);
   P.inv_n2 = 1.0 / ((double)P.n * (double)P.n);
   P.dscale = P.tau * fmax(P.delta, P.delta_floor);
   for (int j = 0; j < P.n_omega; ++j) {
