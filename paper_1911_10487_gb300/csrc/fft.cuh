@@ -201,4 +201,63 @@ __device__ __forceinline__ void fft_lines(cx<R>* buf, const cx<R>* tw) {
   FftStages<R, N, INV, LINES, THREADS, L, SKEW, MAXR, 0, 1>::run(buf, tw);
 }
 
+// Out-of-place form of a stage: reads `src`, writes `dst`, one butterfly of a thread
+// at a time (few values live, for tiles with many butterflies per thread, where the
+// in-place form would hold them all in registers); one barrier per stage.
+template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int SKEW, int RAD, int NS>
+__device__ __forceinline__ void fft_stage_pp(const cx<R>* src, cx<R>* dst, const cx<R>* tw) {
+  using C = cx<R>;
+  using IX = LayIdx<L, N, LINES, SKEW>;
+  constexpr int NB = N / RAD;
+  constexpr int TOTAL = LINES * NB;
+  constexpr int STRIDE_TW = N / (NS * RAD);
+#pragma unroll 1
+  for (int t = threadIdx.x; t < TOTAL; t += THREADS) {
+    int b, j;
+    IX::map(t, NB, b, j);
+    const int k = j % NS;
+    C v[RAD];
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) {
+      C x = src[IX::at(b, j + r * NB)];
+      if (r > 0 && NS > 1) {
+        C w = tw[r * k * STRIDE_TW];
+        if (INV) w.y = -w.y;
+        x = x * w;
+      }
+      v[r] = x;
+    }
+    if constexpr (RAD == 2) Dft<R, INV>::d2(v);
+    else if constexpr (RAD == 4) Dft<R, INV>::d4(v);
+    else if constexpr (RAD == 8) Dft<R, INV>::d8(v);
+    else if constexpr (RAD == 16) Dft<R, INV>::d16(v);
+    else Dft<R, INV>::d3(v);
+    const int oi = (j / NS) * NS * RAD + k;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) dst[IX::at(b, oi + r * NS)] = v[r];
+  }
+  __syncthreads();
+}
+
+template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int SKEW, int MAXR, int S, int NS>
+struct FftStagesPP {
+  __device__ __forceinline__ static cx<R>* run(cx<R>* a, cx<R>* b, const cx<R>* tw) {
+    if constexpr (S < FftPlan<N, MAXR>::stages) {
+      constexpr int RAD = FftPlan<N, MAXR>::radix(S);
+      fft_stage_pp<R, N, INV, LINES, THREADS, L, SKEW, RAD, NS>(a, b, tw);
+      return FftStagesPP<R, N, INV, LINES, THREADS, L, SKEW, MAXR, S + 1, NS * RAD>::run(b, a, tw);
+    } else {
+      return a;
+    }
+  }
+};
+
+// Transform the LINES lines of tile `a` through `b` (same layout); returns the one
+// that holds the result (a after an even number of stages, b after an odd one).  The
+// input tile must be complete before the call (a barrier), as for fft_lines.
+template <typename R, int N, bool INV, int LINES, int THREADS, Lay L, int MAXR, int SKEW = 0>
+__device__ __forceinline__ cx<R>* fft_lines_pp(cx<R>* a, cx<R>* b, const cx<R>* tw) {
+  return FftStagesPP<R, N, INV, LINES, THREADS, L, SKEW, MAXR, 0, 1>::run(a, b, tw);
+}
+
 }  // namespace fl

@@ -115,14 +115,23 @@ template <> __device__ __forceinline__ double inv_sqrt<double>(double x) { retur
 // spill; measured 1 us faster at 128^2 than two CTAs of 102), one elsewhere (a factor
 // 3, or the small tile in FP64, would spill).
 template <typename R, int N, int T> struct RecTile {
-  static constexpr bool BIG = sizeof(R) == 4 && T == 0 && N % 3 != 0;  // radix-3 sizes: too many registers
-  static constexpr int ELEMS = BIG ? 4096 : Tile<T>::ELEMS;
-  static constexpr int RADIX = BIG ? 16 : Tile<T>::RADIX_RECOVER;
-  static constexpr int SKEW = BIG ? 16 : Tile<T>::SKEW_RECOVER;
-  static constexpr int MINB = T == 0 && N % 3 != 0 ? 3 : 1;
+  static constexpr bool BIG = sizeof(R) == 4 && T == 0 && N % 3 != 0;
+  // FP32 radix-3 sizes from 96 up: the same 4096-element tile, transformed out of place
+  // (two tiles in shared memory, one butterfly per thread at a time), since the in-place
+  // stages would hold five radix-3 butterflies a thread in registers and spill
+  static constexpr bool PP = sizeof(R) == 4 && T == 0 && N % 3 == 0 && N >= 96;
+  static constexpr int ELEMS = (BIG || PP) ? 4096 : Tile<T>::ELEMS;
+  static constexpr int RADIX = (BIG || PP) ? 16 : Tile<T>::RADIX_RECOVER;
+  static constexpr int SKEW = (BIG || PP) ? 16 : Tile<T>::SKEW_RECOVER;
+  static constexpr int MINB = T == 0 && N % 3 != 0 ? 3 : (PP ? 2 : 1);
 };
 template <typename R, int N, int T> __host__ __device__ constexpr int rec_lines() {
   return RecTile<R, N, T>::ELEMS / N / 2 > 0 ? RecTile<R, N, T>::ELEMS / N / 2 : 1;
+}
+// the recovery pass's dynamic shared memory: its tile (two with PP)
+template <typename R, int N, int T> __host__ __device__ constexpr size_t rec_smem() {
+  return sizeof(cx<R>) * (RecTile<R, N, T>::PP ? 2 : 1) *
+         (size_t)LayIdx<Lay::ROW, N, 2 * rec_lines<R, N, T>(), RecTile<R, N, T>::SKEW>::ELEMS;
 }
 
 // filled: the tile is already zero for the first frequency.  In FP64 without a given
@@ -164,13 +173,18 @@ __device__ __forceinline__ bool recover_pass(const Problem& P, const cx<R>* __re
       }
     }
     __syncthreads();
-    fft_lines<R, N, true, 2 * LINES, THREADS, Lay::ROW, RecTile<R, N, T>::RADIX, RecTile<R, N, T>::SKEW>(buf, tw_s);
+    const cx<R>* res = buf;
+    if constexpr (RecTile<R, N, T>::PP)
+      res = fft_lines_pp<R, N, true, 2 * LINES, THREADS, Lay::ROW, RecTile<R, N, T>::RADIX, RecTile<R, N, T>::SKEW>(
+          buf, buf + IX::ELEMS, tw_s);
+    else
+      fft_lines<R, N, true, 2 * LINES, THREADS, Lay::ROW, RecTile<R, N, T>::RADIX, RecTile<R, N, T>::SKEW>(buf, tw_s);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const int e = threadIdx.x + p * THREADS;
       if (e < E) {
-        cx<R> v = buf[IX::at(e / N, e % N)];
-        cx<R> u = buf[IX::at(LINES + e / N, e % N)];
+        cx<R> v = res[IX::at(e / N, e % N)];
+        cx<R> u = res[IX::at(LINES + e / N, e % N)];
         if constexpr (!raw_sums<R, INC>()) {
           v = scale * v;
           u = scale * u;
@@ -249,7 +263,8 @@ k_ifft_rows_recover(Problem P, const cx<R>* __restrict__ t2, const int* __restri
   constexpr int E = LINES * N;            // elements of one field
   constexpr int PER = (E + THREADS - 1) / THREADS;
   using IX = LayIdx<Lay::ROW, N, 2 * LINES, RecTile<R, N, T>::SKEW>;
-  __shared__ cx<R> buf[IX::ELEMS];
+  extern __shared__ __align__(16) unsigned char rec_smem_raw[];  // rec_smem<R, N, T>() bytes
+  cx<R>* buf = reinterpret_cast<cx<R>*>(rec_smem_raw);
   __shared__ cx<R> tw_s[N];
   __shared__ unsigned red[THREADS / 32];
   // the constant twiddle table and the cleared tile of the first frequency, while the
@@ -473,14 +488,19 @@ cudaError_t rec_tiled(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStrea
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
   constexpr int LINES = rec_lines<R, N, T>();
+  constexpr size_t smem = rec_smem<R, N, T>();
   const long long nrows = (long long)P.m * N;
   const dim3 gr((unsigned)((nrows + LINES - 1) / LINES));
-  if (w.u0)
-    e = launch_pdl(k_ifft_rows_recover<R, N, true, T>, gr, dim3(THREADS), 0, s, P, (const cx<R>*)w.t2,
+  static SmemOptIn attr[2];
+  if (w.u0) {
+    if ((e = opt_in_smem(attr[1], (const void*)k_ifft_rows_recover<R, N, true, T>, smem)) != cudaSuccess) return e;
+    e = launch_pdl(k_ifft_rows_recover<R, N, true, T>, gr, dim3(THREADS), smem, s, P, (const cx<R>*)w.t2,
                    (const int*)w.cols, (const int*)w.ncol, w.u0, xi, c, w.ctr, (const cx<R>*)w.tw);
-  else
-    e = launch_pdl(k_ifft_rows_recover<R, N, false, T>, gr, dim3(THREADS), 0, s, P, (const cx<R>*)w.t2,
+  } else {
+    if ((e = opt_in_smem(attr[0], (const void*)k_ifft_rows_recover<R, N, false, T>, smem)) != cudaSuccess) return e;
+    e = launch_pdl(k_ifft_rows_recover<R, N, false, T>, gr, dim3(THREADS), smem, s, P, (const cx<R>*)w.t2,
                    (const int*)w.cols, (const int*)w.ncol, w.u0, xi, c, w.ctr, (const cx<R>*)w.tw);
+  }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
