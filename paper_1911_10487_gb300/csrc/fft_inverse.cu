@@ -107,22 +107,24 @@ template <typename R> __device__ __forceinline__ R inv_sqrt(R x);
 template <> __device__ __forceinline__ float inv_sqrt<float>(float x) { return rsqrtf(x); }  // <= 2 ulp
 template <> __device__ __forceinline__ double inv_sqrt<double>(double x) { return rsqrt64(x); }
 
-// The recovery pass's tile: for the FP32 large-tile form at N = 2^k, 4096 elements (the
-// V and u rows of 4096 / (2N) rows of X) with radix-16 stages, so that a 128-point row
-// takes two stages (16, 8) with every thread busy in both; otherwise the tile of
-// fs_options.fft_tile.  MINB: CTAs per SM the register allocation is held to -- three
-// for the default tile at N = 2^k (at most 80 registers a thread, no or a few bytes of
-// spill; measured 1 us faster at 128^2 than two CTAs of 102), one elsewhere (a factor
-// 3, or the small tile in FP64, would spill).
+// The recovery pass's tile.  FP32, default tile (fs_options.fft_tile = 0): from N = 96
+// up, 4096 elements (the V and u rows of 4096 / (2N) rows of X) with radix-16 stages
+// (a 128-point row in two stages, 16 and 8, every thread busy in both), transformed out
+// of place (PP: two tiles in shared memory, one butterfly per thread at a time, one
+// barrier per stage; in place, the radix-3 stages of N = 96 and 192 would hold five
+// butterflies a thread in registers and spill); below 96 at N = 2^k, 1024 elements in
+// place (small problems need the CTAs: 64^2 x 16 recovers in 18 us instead of 33 with
+// 4096); otherwise the tile of fs_options.fft_tile.  MINB: CTAs per SM the register
+// allocation is held to -- three at N = 2^k (at most 80 registers a thread; 1 us faster
+// at 128^2 than two CTAs of 102), two with PP at radix-3 sizes (128 registers, no
+// spill), one elsewhere.
 template <typename R, int N, int T> struct RecTile {
-  static constexpr bool BIG = sizeof(R) == 4 && T == 0 && N % 3 != 0;
-  // FP32 radix-3 sizes from 96 up: the same 4096-element tile, transformed out of place
-  // (two tiles in shared memory, one butterfly per thread at a time), since the in-place
-  // stages would hold five radix-3 butterflies a thread in registers and spill
-  static constexpr bool PP = sizeof(R) == 4 && T == 0 && N % 3 == 0 && N >= 96;
-  static constexpr int ELEMS = (BIG || PP) ? 4096 : Tile<T>::ELEMS;
-  static constexpr int RADIX = (BIG || PP) ? 16 : Tile<T>::RADIX_RECOVER;
-  static constexpr int SKEW = (BIG || PP) ? 16 : Tile<T>::SKEW_RECOVER;
+  static constexpr bool F32 = sizeof(R) == 4 && T == 0;
+  static constexpr bool PP = F32 && N >= 96;
+  static constexpr bool BIG = F32 && (PP || N % 3 != 0);
+  static constexpr int ELEMS = BIG ? (N >= 96 ? 4096 : 1024) : Tile<T>::ELEMS;
+  static constexpr int RADIX = BIG ? 16 : Tile<T>::RADIX_RECOVER;
+  static constexpr int SKEW = BIG ? 16 : Tile<T>::SKEW_RECOVER;
   static constexpr int MINB = T == 0 && N % 3 != 0 ? 3 : (PP ? 2 : 1);
 };
 template <typename R, int N, int T> __host__ __device__ constexpr int rec_lines() {
