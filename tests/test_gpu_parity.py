@@ -101,7 +101,9 @@ def test_given_alpha_fp64(rc):
     assert rep["n_active"] == int(ref.active.sum())
 
 
-@pytest.mark.parametrize("name", ["c1", "r48", "r192"])
+# every recovery tile form of the mixed path: in place at 8 and 32 (1024 elements), at
+# 12, 24 and 48 (the small tiles with radix 3), out of place at 96, 192 (radix 3) and 256
+@pytest.mark.parametrize("name", ["c1", "r8", "r12", "r24", "r48", "r96", "r192", "r256"])
 def test_mixed_precision(rc, name):
     g, om, W, _ = case(name, 0.01)
     ref = oracle_result(name, 0.01)
