@@ -354,7 +354,9 @@ def run_ours(args, rank, world, local):
                        for p in ("mixed", "fp64")},
         "stage_ms": stage_ms["mixed"],
         "e2e": {"value": world * vox / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": int(W_h.numel() * 8), "d2h_bytes_per_step": int(xi_h.numel() * 4)},
+                "h2d_bytes_per_step": int(W_h.numel() * 8), "d2h_bytes_per_step": int(xi_h.numel() * 4),
+                "transfer": "page-locked host buffers read (W) and written (xi) by the kernels themselves "
+                            "over the host link, inside the timed call; wall clock around fs_reconstruct_host"},
         "clocks": ck,
     }
     # per-stage rooflines, both precisions: algorithmic bytes against the measured copy

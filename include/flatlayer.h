@@ -251,14 +251,20 @@ fs_status fs_workspace_size(const fs_geometry* geom, int n_omega, fs_precision p
      alpha_out device, [n_omega][N][N] float64, or NULL: chosen alpha of each active
                mode (other entries are left untouched).
    The workspace grows (synchronously) when a larger problem arrives; otherwise the
-   call only enqueues work.  Counters of the call are read with fs_get_report. */
+   call only enqueues work.  Counters of the call are read with fs_get_report.
+   Every buffer must be aligned to its element (W and the incident field to the complex
+   element, xi and c to the real one, alpha_out to 8 bytes): FS_EINVAL otherwise. */
 fs_status fs_reconstruct(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* W,
                          const double* omega, int n_omega, double delta, double c0,
                          const fs_options* opts, void* xi, void* c, double* alpha_out);
 
-/* Same as fs_reconstruct with HOST buffers W, xi, c (c may be NULL): copies W to
-   the device, runs, copies xi (and c) back and synchronises the stream before
-   returning.  Page-locked host buffers give the fastest copies. */
+/* Same as fs_reconstruct with HOST buffers W, xi, c (c may be NULL), synchronising
+   the stream before returning.  Page-locked buffers mapped into the device's address
+   space at the same address (cudaHostAlloc / torch pin_memory under unified
+   addressing), aligned to their elements: the kernels read W and write xi and c there
+   directly over the host link (on a Grace-Blackwell node the coherent NVLink-C2C), no
+   staging copy; a repeated call replays a graph captured after the first.  Other host
+   buffers: W is copied to a device staging buffer, xi (and c) copied back. */
 fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* geom, fs_precision prec, const void* W_host,
                               const double* omega, int n_omega, double delta, double c0,
                               const fs_options* opts, void* xi_host, void* c_host);

@@ -86,6 +86,17 @@ bool pinned(const void* p) {
   return a.type == cudaMemoryTypeHost;
 }
 
+// page-locked host memory that the current device reaches at the same address (mapped
+// under unified addressing): kernels may read and write it directly
+bool mapped_here(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
 template <typename T> void key_put(std::vector<unsigned char>& k, const T& v) {
   const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
   k.insert(k.end(), b, b + sizeof(T));
@@ -547,6 +558,8 @@ fs_status fs_reconstruct(fs_ctx* ctx, const fs_geometry* g, fs_precision prec, c
   fs_options o;
   fs_default_options(&o);
   if (opts) o = *opts;
+  if (!elems_aligned(prec == FS_FP64, W, xi, c, o.incident) || ((uintptr_t)alpha_out % 8) != 0)
+    return fail(ctx, FS_EINVAL, "W, xi, c, alpha_out and the incident field must be aligned to their elements");
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
   const bool fp64 = prec == FS_FP64;
@@ -573,7 +586,15 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
   const size_t N2 = (size_t)g->n * g->n;
   const size_t wbytes = cxs * (size_t)n_omega * g->m1 * N2;
   const size_t obytes = rs * (size_t)g->m * N2;
-  const size_t need = align_up(wbytes) + 2 * align_up(obytes);
+  fs_options o;
+  fs_default_options(&o);
+  if (opts) o = *opts;
+  const bool graphable = o.stage_timing == 0 && pinned(W_host) && pinned(xi_host) && (!c_host || pinned(c_host));
+  // mapped, aligned page-locked buffers: the kernels read W and write xi and c in host
+  // memory themselves (no staging buffers, no copies)
+  const bool direct = graphable && mapped_here(W_host) && mapped_here(xi_host) && (!c_host || mapped_here(c_host)) &&
+                      elems_aligned(prec == FS_FP64, W_host, xi_host, c_host);
+  const size_t need = direct ? 0 : align_up(wbytes) + 2 * align_up(obytes);
   if (need > ctx->stage_bytes) {
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "sync");
     if (ctx->stage) cudaFree(ctx->stage);
@@ -589,10 +610,6 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
   // device buffers) replays the graph captured after its first run: one launch
   // instead of the copies and eight kernel launches.  Only with page-locked host
   // buffers (copies from pageable memory cannot be captured) and without stage timing.
-  fs_options o;
-  fs_default_options(&o);
-  if (opts) o = *opts;
-  const bool graphable = o.stage_timing == 0 && pinned(W_host) && pinned(xi_host) && (!c_host || pinned(c_host));
   std::vector<unsigned char> key;
   if (graphable) {
     // values only (no struct padding, no pointers to argument arrays)
@@ -616,6 +633,7 @@ fs_status fs_reconstruct_host(fs_ctx* ctx, const fs_geometry* g, fs_precision pr
     }
   }
   auto enqueue = [&]() -> fs_status {
+    if (direct) return fs_reconstruct(ctx, g, prec, W_host, omega, n_omega, delta, c0, opts, xi_host, c_host, nullptr);
     cudaError_t e2;
     if ((e2 = cudaMemcpyAsync(dW, W_host, wbytes, cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess)
       return cuda_fail(ctx, e2, "H2D W");
@@ -679,6 +697,8 @@ fs_status fs_reconstruct_batch(fs_ctx* ctx, const fs_problem* probs, int n_probs
       return fail(ctx, st, "problem %d: %s", i, m);
     }
     if (!q.W || !q.xi) return fail(ctx, FS_EINVAL, "problem %d: W and xi must be device pointers", i);
+    if (!elems_aligned(prec == FS_FP64, q.W, q.xi, q.c))
+      return fail(ctx, FS_EINVAL, "problem %d: W, xi and c must be aligned to their elements", i);
     total += align_up(layout(q.geom.n, q.geom.m, q.geom.m1, q.n_omega, fp64).total);
   }
   cudaError_t e = cudaSetDevice(ctx->device);

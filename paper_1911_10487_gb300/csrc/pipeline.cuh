@@ -75,6 +75,15 @@ inline float2 two_float(double x) {
   return make_float2(hi, (float)(x - (double)hi));
 }
 
+// Element alignment of the caller's buffers (the kernels load and store whole complex
+// and real elements): W (and a given incident field) to its complex element, xi and c
+// to the real one.  NULL passes.
+inline bool elems_aligned(bool fp64, const void* W, const void* xi, const void* c, const void* u0 = nullptr) {
+  const uintptr_t cx = fp64 ? 16 : 8, re = cx / 2;
+  return ((uintptr_t)W % cx) == 0 && ((uintptr_t)u0 % cx) == 0 && ((uintptr_t)xi % re) == 0 &&
+         ((uintptr_t)c % re) == 0;
+}
+
 inline void derive_constants(Problem& P) {
   P.kn = 2.0 * M_PI / P.period;
   P.inv_c02 = 1.0 / (P.c0 * P.c0);

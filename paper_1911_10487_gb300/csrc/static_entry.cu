@@ -87,6 +87,7 @@ extern "C" fs_status fs_reconstruct_static(const fs_geometry* g, fs_precision pr
   if (st != FS_OK) return st;
   if (opts && opts->kernel_plan) return FS_EUNSUPPORTED;  // the sampled kernel needs its plan's memory
   if (!W || !xi) return FS_EINVAL;
+  if (!elems_aligned(prec == FS_FP64, W, xi, c, opts ? opts->incident : nullptr)) return FS_EINVAL;
   const bool fp64 = prec == FS_FP64;
   const Layout L = layout(g->n, g->m, g->m1, n_omega, fp64);
   size_t ctr_off, tw_off, tw64_off;

@@ -179,6 +179,26 @@ def test_invalid_arguments_rejected(rc):
         rc.reconstruct(W2, [1.0], Geometry(16, 65, 0.2, 1.0, (1.2, 1.3)), 0.01)
 
 
+def test_misaligned_buffers_refused(rc):
+    """A buffer off its element boundary is refused (FS_EINVAL) before any device work:
+    the kernels load and store whole complex and real elements."""
+    import torch
+    from paper_1911_10487_gb300 import FS_FP64, FS_MIXED, FlatLayerError, Geometry
+    from paper_1911_10487_gb300._abi import FS_EINVAL, fs_reconstruct
+    g = Geometry(16, 4, 0.2, 1.0, (1.2, 1.3))
+    for prec, cdt, rdt, off in ((FS_FP64, torch.complex128, torch.float64, 8), (FS_MIXED, torch.complex64,
+                                                                              torch.float32, 4)):
+        W = torch.zeros((1 * 2 * 16 * 16 + 1,), dtype=cdt, device=rc.device)
+        xi = torch.zeros((4 * 16 * 16 + 1,), dtype=rdt, device=rc.device)
+        for wp, xp in ((W.data_ptr() + off, xi.data_ptr()), (W.data_ptr(), xi.data_ptr() + off // 2)):
+            with pytest.raises(FlatLayerError) as ei:
+                fs_reconstruct(rc.ctx, g.c_struct(), prec, wp, [1.0], 0.01, 1.0, None, xp)
+            assert ei.value.status == FS_EINVAL
+        fs_reconstruct(rc.ctx, g.c_struct(), prec, W.data_ptr(), [1.0], 0.01, 1.0, None, xi.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.all(xi[: 4 * 16 * 16] == 0)
+
+
 @pytest.mark.parametrize("name", ["c1", "r12", "r48", "r192"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_forward_born_matches_oracle(rc, name, precision):
