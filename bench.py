@@ -489,7 +489,11 @@ def run_batch(args, local, flush, world):
     res = {}
     cfgs = {}
     for prec in ("fp64", "mixed"):  # FP64 first: it sizes the workspace for both
-        cfgs[prec] = tuner.best(rc, items[prec], prec, repeats=2, outs=outs[prec], options={"solve_form": HEAD_FORM})
+        if args.batch_config:  # a fixed launch configuration (profiling runs): no tuning
+            cfgs[prec] = tuple(int(x) for x in args.batch_config.split(","))
+        else:
+            cfgs[prec] = tuner.best(rc, items[prec], prec, repeats=2, outs=outs[prec],
+                                    options={"solve_form": HEAD_FORM})
     graphs = {}
     for prec in ("fp64", "mixed"):
         s_, b_, t_, c_ = cfgs[prec]
@@ -813,6 +817,9 @@ def main():
     ap.add_argument("--no-forward", action="store_true", help="skip the full-scattering forward measurement")
     ap.add_argument("--no-sampled", action="store_true", help="skip the sampled-G kernel measurement")
     ap.add_argument("--no-paper", action="store_true", help="skip the paper-geometry workload")
+    ap.add_argument("--batch-config", default="",
+                    help="n_streams,solve_blocks_per_sm,fft_tile,classify_single_pass for both batch precisions "
+                         "instead of the autotuner's choice (for profiling runs)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":  # host cores only: no device is touched
