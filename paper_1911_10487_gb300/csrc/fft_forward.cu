@@ -121,7 +121,7 @@ cudaError_t fwd_plane(const cx<R>* W, const Problem& P, const Work<R>& w, cudaSt
 // of the mixed truncated-SVD route, in FP64
 template <int N>
 cudaError_t fwd_wide_impl(const float2* W, const Problem& P, const Work<float>& w, cudaStream_t s, cudaEvent_t mid) {
-  constexpr int LINES = row_lines<N, 0>();
+  constexpr int LINES = row_lines<double, N, 0>();
   const long long nrows = (long long)P.n_omega * P.m1 * N;
   const long long nblk = (nrows + LINES - 1) / LINES;
   cudaError_t e = launch_pdl(k_fft_rows<double, N, false, float2>, dim3((unsigned)nblk), dim3(THREADS), 0, s, W,
@@ -141,7 +141,7 @@ cudaError_t fwd_wide_impl(const float2* W, const Problem& P, const Work<float>& 
 template <typename R, int N, int T>
 cudaError_t fwd_tiled(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStream_t s, cudaEvent_t mid,
                       bool norms) {
-  constexpr int LINES = row_lines<N, T>();
+  constexpr int LINES = row_lines<R, N, T>();
   const long long nrows = (long long)P.n_omega * P.m1 * N;
   const long long nblk = (nrows + LINES - 1) / LINES;
   cudaError_t e = launch_pdl(k_fft_rows<R, N, false, cx<R>, T>, dim3((unsigned)nblk), dim3(THREADS), 0, s, W, w.wt,
@@ -174,7 +174,7 @@ cudaError_t fwd_impl(const cx<R>* W, const Problem& P, const Work<R>& w, cudaStr
 
 template <typename R, int N>
 cudaError_t dense_impl(cx<R>* in, cx<R>* out, long long planes, bool inverse, const cx<R>* tw, cudaStream_t s) {
-  constexpr int LINES = row_lines<N, 0>();
+  constexpr int LINES = row_lines<R, N, 0>();
   constexpr long long MAX_Y = 32768;  // planes per column launch (grid y <= 65535)
   const long long nrows = planes * N;
   const unsigned nblk = (unsigned)((nrows + LINES - 1) / LINES);
