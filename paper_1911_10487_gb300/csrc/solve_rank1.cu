@@ -439,7 +439,10 @@ cudaError_t launch_solve_rank1(const Problem& P, const Work<R>& w, cudaStream_t 
   const int sms = sm_count();
   const long long modes = (long long)P.n_omega * P.n * P.n;
   const long long want = (modes + RW - 1) / RW;
-  const long long cap = 8LL * sms;
+  // two blocks of RW warps per SM, all resident at once (the grid-stride loop takes any
+  // count): the successor's launch waits for every block to start, and a grid of idle
+  // blocks only delays it (64-problem batch 6.24 -> 6.16 ms against 8 blocks per SM)
+  const long long cap = 2LL * sms;
   const unsigned grid = (unsigned)(want < cap ? want : cap);
   if constexpr (sizeof(R) == 4) {
     if (P.m <= 64 && P.m1 <= 32)
