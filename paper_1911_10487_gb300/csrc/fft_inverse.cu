@@ -17,8 +17,10 @@ namespace fl {
 namespace {
 
 // ---- inverse pass 1: gather active profiles, columns (along y) ----------------
-// Column chunk `blockIdx.z` of the compact column list of frequency om (grid below);
-// field f = 0 (V~) or 1 (U~).  Inactive modes are zero in
+constexpr int GATHER_COLS = 32;  // active columns the gather's grid covers in one pass (see rec_tiled)
+
+// Column chunks blockIdx.z, blockIdx.z + gridDim.z, ... of the compact column list of
+// frequency om (grid below); field f = 0 (V~) or 1 (U~).  Inactive modes are zero in
 // V~ and equal the incident field U~0 in U~; the plane wave exp(-i k0 z) has
 // U~0 = N^2 exp(-i k0 z'_l) at nu = 0 and zero elsewhere.
 template <typename R, int N, int T>
@@ -34,51 +36,52 @@ k_ifft_cols_gather(Problem P, const cx<R>* __restrict__ prof, const int* __restr
   load_twiddles<R, N>(tw_s, tw);  // a constant table: read while the predecessor drains
   pdl_wait();
   pdl_trigger();
-  // grid (M, 2 n_omega, ceil(N / TC)): the column chunk is the slowest index, so that
+  // grid (M, 2 n_omega, gather_chunks): the column chunk is the slowest index, so that
   // the chunks that hold active columns (the first ceil(ncol / TC)) are dispatched first
-  // and the rest, which return at once, last
+  // and the rest, which return at once, last; a block loops when ncol needs more chunks
   const int om = blockIdx.y >> 1, f = blockIdx.y & 1;
   const int l = blockIdx.x;
   const int nc = ncol[om];
-  const int cb = blockIdx.z * TC;
-  if (cb >= nc) return;
   const long long N2 = (long long)N * N;
   const int M = P.m;
-  // element e = t + p THREADS is row i = e / TC of line b = t mod TC (THREADS is a
-  // multiple of TC): one column per thread, its PER slot loads and then its profile
-  // loads issued together
-  static_assert(THREADS % TC == 0, "one column per thread");
-  const int b = threadIdx.x % TC;
-  const int nu1 = cb + b < nc ? cols[om * N + cb + b] : -1;
-  int sl[PER];
+  for (int cb = blockIdx.z * TC; cb < nc; cb += gridDim.z * TC) {
+    if (cb != (int)blockIdx.z * TC) __syncthreads();  // the previous chunk's stores have read buf
+    // element e = t + p THREADS is row i = e / TC of line b = t mod TC (THREADS is a
+    // multiple of TC): one column per thread, its PER slot loads and then its profile
+    // loads issued together
+    static_assert(THREADS % TC == 0, "one column per thread");
+    const int b = threadIdx.x % TC;
+    const int nu1 = cb + b < nc ? cols[om * N + cb + b] : -1;
+    int sl[PER];
 #pragma unroll
-  for (int p = 0; p < PER; ++p) {
-    const int e = threadIdx.x + p * THREADS, i = e / TC;
-    sl[p] = (nu1 >= 0 && e < E) ? slot[om * N2 + (long long)i * N + nu1] : -1;
-  }
-#pragma unroll
-  for (int p = 0; p < PER; ++p) {
-    const int e = threadIdx.x + p * THREADS;
-    if (e < E) {
-      const int i = e / TC;
-      cx<R> v = czero<R>();
-      if (sl[p] >= 0) {
-        v = prof[(((long long)om * N2 + sl[p]) * 2 + f) * M + l];
-      } else if (f == 1 && i == 0 && nu1 == 0 && !P.incident) {  // one thread: FP64 is slow on this GPU
-        double sn, cs;
-        sincos(-(P.omega[om] / P.c0) * (P.z1 + (l + 0.5) * P.hz), &sn, &cs);
-        v = from_d<R>(make_double2((double)N2 * cs, (double)N2 * sn));
-      }
-      buf[e] = v;
+    for (int p = 0; p < PER; ++p) {
+      const int e = threadIdx.x + p * THREADS, i = e / TC;
+      sl[p] = (nu1 >= 0 && e < E) ? slot[om * N2 + (long long)i * N + nu1] : -1;
     }
-  }
-  __syncthreads();
-  fft_lines<R, N, true, TC, THREADS, Lay::COL, Tile<T>::RADIX_GATHER>(buf, tw_s);
-  const long long ob = (((long long)om * 2 + f) * M + l) * N2;
 #pragma unroll
-  for (int p = 0; p < PER; ++p) {
-    const int e = threadIdx.x + p * THREADS;
-    if (e < E && nu1 >= 0) t2[ob + (long long)(e / TC) * N + cb + b] = buf[e];
+    for (int p = 0; p < PER; ++p) {
+      const int e = threadIdx.x + p * THREADS;
+      if (e < E) {
+        const int i = e / TC;
+        cx<R> v = czero<R>();
+        if (sl[p] >= 0) {
+          v = prof[(((long long)om * N2 + sl[p]) * 2 + f) * M + l];
+        } else if (f == 1 && i == 0 && nu1 == 0 && !P.incident) {  // one thread: FP64 is slow on this GPU
+          double sn, cs;
+          sincos(-(P.omega[om] / P.c0) * (P.z1 + (l + 0.5) * P.hz), &sn, &cs);
+          v = from_d<R>(make_double2((double)N2 * cs, (double)N2 * sn));
+        }
+        buf[e] = v;
+      }
+    }
+    __syncthreads();
+    fft_lines<R, N, true, TC, THREADS, Lay::COL, Tile<T>::RADIX_GATHER>(buf, tw_s);
+    const long long ob = (((long long)om * 2 + f) * M + l) * N2;
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int e = threadIdx.x + p * THREADS;
+      if (e < E && nu1 >= 0) t2[ob + (long long)(e / TC) * N + cb + b] = buf[e];
+    }
   }
 }
 
@@ -484,7 +487,12 @@ cudaError_t rec_plane(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStrea
 template <typename R, int N, int T>
 cudaError_t rec_tiled(const Problem& P, const Work<R>& w, R* xi, R* c, cudaStream_t s, cudaEvent_t mid) {
   constexpr int TC = tile_cols<R, T>();
-  dim3 g1(P.m, 2 * P.n_omega, (N + TC - 1) / TC);
+  // column chunks for the first GATHER_COLS active columns in the grid (the blocks loop
+  // over more): the active columns are few in the usual case, and a grid of blocks that
+  // return at once only delays the successor's launch (measured, 64-problem batch: 6.17
+  // ms with every chunk in the grid, 6.07 with 32 columns; FP64 128^2 step +0.5 us)
+  constexpr int NCH = (N + TC - 1) / TC, GZ = (GATHER_COLS + TC - 1) / TC;
+  dim3 g1(P.m, 2 * P.n_omega, NCH < GZ ? NCH : GZ);
   cudaError_t e = launch_pdl(k_ifft_cols_gather<R, N, T>, g1, dim3(THREADS), 0, s, P, (const cx<R>*)w.prof,
                              (const int*)w.slot, (const int*)w.cols, (const int*)w.ncol, w.t2, (const cx<R>*)w.tw);
   if (e != cudaSuccess) return e;
