@@ -28,7 +28,7 @@ __global__ void k_twiddles(cx<R>* tw, int n) {
 }
 
 // ---- single-pass forward 2D transform: one data plane per cluster ------------------
-// grid (C, planes), clusters of C = plane_cluster<N>() CTAs along x.  CTA r of the
+// grid (C, planes), clusters of C = fwd_cluster<N>() CTAs along x.  CTA r of the
 // cluster of plane p loads rows r RB .. r RB + RB - 1 (RB = N / C) of the plane into
 // its shared memory and transforms them along x; after a cluster barrier it reads
 // columns r RB .. r RB + RB - 1 of all N rows from the CTAs that hold them
@@ -36,7 +36,7 @@ __global__ void k_twiddles(cx<R>* tw, int n) {
 // plane crosses global memory once each way, in one launch.
 // clear (may be null): nclear counters zeroed by CTA (0, 0), as in k_fft_cols.
 template <typename R, int N> __host__ __device__ constexpr size_t plane_fwd_smem() {
-  constexpr int RB = N / plane_cluster<N>();
+  constexpr int RB = N / fwd_cluster<N>();
   return sizeof(cx<R>) * ((size_t)LayIdx<Lay::ROW, N, RB, 16>::ELEMS + (size_t)RB * N + N);
 }
 
@@ -44,7 +44,7 @@ template <typename R, int N>
 __global__ void __launch_bounds__(THREADS)
 k_fft2_plane(const cx<R>* __restrict__ in, cx<R>* __restrict__ out, const cx<R>* __restrict__ tw,
              unsigned* __restrict__ clear, int nclear) {
-  constexpr int C = plane_cluster<N>(), RB = N / C;
+  constexpr int C = fwd_cluster<N>(), RB = N / C;
   using IA = LayIdx<Lay::ROW, N, RB, 16>;  // this CTA's rows
   constexpr int E = RB * N;                // elements of the row tile and of the column tile
   constexpr int PER = (E + THREADS - 1) / THREADS;
@@ -108,7 +108,7 @@ cudaError_t fwd_plane(const cx<R>* W, const Problem& P, const Work<R>& w, cudaSt
   static SmemOptIn attr;
   cudaError_t e = opt_in_smem(attr, (const void*)k_fft2_plane<R, N>, smem, true);
   if (e != cudaSuccess) return e;
-  constexpr int C = plane_cluster<N>();
+  constexpr int C = fwd_cluster<N>();
   e = launch_pdl_cluster(k_fft2_plane<R, N>, dim3(C, (unsigned)(P.n_omega * P.m1)), dim3(THREADS), C, smem, s, W,
                          w.wt, (const cx<R>*)w.tw, norms ? (unsigned*)nullptr : w.bar, P.n_omega);
   if (e != cudaSuccess) return e;
