@@ -106,6 +106,21 @@ def test_mixed_noise_limit_is_checked_before_any_device_work(abi):
                                    None) == abi.FS_EINVAL
 
 
+def test_misaligned_buffers_refused_before_any_device_work(abi):
+    """A buffer off its element boundary (W: the complex element, xi and c: the real one)
+    is refused with FS_EINVAL by the argument checks; the allocation-free entry runs them
+    before touching the device, and the pointers are never dereferenced on the host."""
+    g = abi.make_geometry(32, 16, 0.2, 1.0, [1.2 + 0.05 * k for k in range(8)])
+    om = (C.c_double * 1)(1.0)
+    L = abi.lib()
+    base = 1 << 20  # fake addresses: only their alignment is looked at
+    for prec, cx, re_ in ((abi.FS_FP64, 16, 8), (abi.FS_MIXED, 8, 4)):
+        for W, xi, c in ((base + cx // 2, base, None), (base, base + re_ // 2, None), (base, base, base + 2)):
+            st = L.fs_reconstruct_static(C.byref(g), prec, C.c_void_p(W), om, 1, 0.01, 1.0, None,
+                                         C.c_void_p(xi), C.c_void_p(c), None)
+            assert st == abi.FS_EINVAL, (prec, W - base, xi - base, c)
+
+
 def test_reserve_and_generation_without_a_context(abi):
     g = abi.make_geometry(32, 16, 0.2, 1.0, [1.3])
     assert abi.lib().fs_reserve(None, C.byref(g), 1, abi.FS_MIXED) == abi.FS_EINVAL
